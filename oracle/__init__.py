@@ -1,0 +1,174 @@
+"""CPU oracle for the 3-D segmentation stage -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports it, and the two share no code.
+
+The arithmetic lives in ``seg_oracle.c`` (plain single-threaded C, built by
+``oracle/build.py``); this module only marshals numpy arrays through ctypes.
+Every function follows the paper's Segmentation section (Otsu thresholding,
+connected components, minimum volume) and Background Noise Removal section
+(Eq. 1, Gaussian low-pass read as binomial smoothing); see the C file for the
+exact readings.
+
+Parity status: every function is pinned by tests/test_oracle_pins.py against
+brute force, closed forms, exact-rational Otsu and library routines.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CELL_DTYPE = np.dtype([
+    ("count", "<u8"),
+    ("sum", "<i8", (3,)),
+    ("bbox_min", "<u4", (3,)),
+    ("bbox_max", "<u4", (3,)),
+    ("pad", "<u4", (2,)),
+])
+assert CELL_DTYPE.itemsize == 64
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        u16p = ctypes.POINTER(ctypes.c_uint16)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        vp = ctypes.c_void_p
+        lib.oracle_smooth.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u16p]
+        lib.oracle_smooth.restype = ctypes.c_int
+        lib.oracle_histogram.argtypes = [u16p, ctypes.c_uint64, u64p]
+        lib.oracle_histogram.restype = ctypes.c_int
+        lib.oracle_otsu.argtypes = [u64p]
+        lib.oracle_otsu.restype = ctypes.c_uint16
+        lib.oracle_label26.argtypes = [u8p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u32p]
+        lib.oracle_label26.restype = ctypes.c_int64
+        lib.oracle_filter_features.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                               ctypes.c_uint32, ctypes.c_uint32, u32p, vp,
+                                               ctypes.c_uint64, u64p]
+        lib.oracle_filter_features.restype = ctypes.c_int
+        lib.oracle_segment.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_uint32, u32p, vp, ctypes.c_uint64, u64p, u16p,
+                                       u64p, u16p]
+        lib.oracle_segment.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _dims(vol):
+    if vol.ndim != 3:
+        raise ValueError("volume must be [Z][Y][X]")
+    Z, Y, X = vol.shape
+    return int(X), int(Y), int(Z)
+
+
+def smooth(vol: np.ndarray) -> np.ndarray:
+    """Binomial smoothing, uint16 [Z,Y,X] -> uint16 [Z,Y,X] (Eq. 1 low-pass)."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint16)
+    X, Y, Z = _dims(vol)
+    out = np.empty_like(vol)
+    rc = _load().oracle_smooth(_ptr(vol, ctypes.c_uint16), X, Y, Z, _ptr(out, ctypes.c_uint16))
+    if rc:
+        raise RuntimeError("oracle_smooth failed: %d" % rc)
+    return out
+
+
+def histogram(s: np.ndarray) -> np.ndarray:
+    """65536-bin uint64 histogram of a uint16 array."""
+    s = np.ascontiguousarray(s, dtype=np.uint16)
+    h = np.zeros(65536, dtype=np.uint64)
+    rc = _load().oracle_histogram(_ptr(s, ctypes.c_uint16), s.size, _ptr(h, ctypes.c_uint64))
+    if rc:
+        raise RuntimeError("oracle_histogram failed: %d" % rc)
+    return h
+
+
+def otsu(h: np.ndarray) -> int:
+    """Otsu level t* of a 65536-bin histogram (foreground is s > t*)."""
+    h = np.ascontiguousarray(h, dtype=np.uint64)
+    if h.shape != (65536,):
+        raise ValueError("histogram must have 65536 bins")
+    return int(_load().oracle_otsu(_ptr(h, ctypes.c_uint64)))
+
+
+def label26(mask: np.ndarray):
+    """26-connected labelling; returns (uint32 labels [Z,Y,X], n_components)."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    X, Y, Z = _dims(m)
+    lab = np.empty(m.shape, dtype=np.uint32)
+    n = _load().oracle_label26(_ptr(m, ctypes.c_uint8), X, Y, Z, _ptr(lab, ctypes.c_uint32))
+    if n < 0:
+        raise RuntimeError("oracle_label26 failed: %d" % n)
+    return lab, int(n)
+
+
+def filter_features(prov: np.ndarray, ncomp: int, min_volume: int):
+    """Minimum-volume filter + canonical numbering + features.
+
+    Returns (labels uint32 [Z,Y,X], cells structured array of CELL_DTYPE)."""
+    prov = np.ascontiguousarray(prov, dtype=np.uint32)
+    X, Y, Z = _dims(prov)
+    lab = np.empty_like(prov)
+    cap = max(int(ncomp), 1)
+    cells = np.zeros(cap, dtype=CELL_DTYPE)
+    k = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_filter_features(_ptr(prov, ctypes.c_uint32), ncomp, X, Y, Z, min_volume,
+                                        _ptr(lab, ctypes.c_uint32), cells.ctypes.data, cap,
+                                        _ptr(k, ctypes.c_uint64))
+    if rc:
+        raise RuntimeError("oracle_filter_features failed: %d" % rc)
+    return lab, cells[: int(k[0])].copy()
+
+
+class OracleResult:
+    __slots__ = ("labels", "cells", "threshold", "hist", "smoothed")
+
+    def __init__(self, labels, cells, threshold, hist, smoothed):
+        self.labels = labels
+        self.cells = cells
+        self.threshold = threshold
+        self.hist = hist
+        self.smoothed = smoothed
+
+    @property
+    def n_cells(self):
+        return len(self.cells)
+
+
+def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
+            keep_smoothed: bool = False) -> OracleResult:
+    """The whole stage for one frame and channel (uint16 [Z,Y,X])."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint16)
+    X, Y, Z = _dims(vol)
+    n = vol.size
+    labels = np.empty(vol.shape, dtype=np.uint32)
+    # K can not exceed the number of components; each keeps >= 1 voxel and,
+    # being 26-separated, components are at most ceil(X/2)ceil(Y/2)ceil(Z/2).
+    cap = ((X + 1) // 2) * ((Y + 1) // 2) * ((Z + 1) // 2)
+    if min_volume > 1:
+        cap = min(cap, n // min_volume + 1)
+    cells = np.zeros(max(cap, 1), dtype=CELL_DTYPE)
+    k = np.zeros(1, dtype=np.uint64)
+    t = np.zeros(1, dtype=np.uint16)
+    hist = np.zeros(65536, dtype=np.uint64) if keep_hist else None
+    sm = np.empty_like(vol) if keep_smoothed else None
+    rc = _load().oracle_segment(
+        _ptr(vol, ctypes.c_uint16), X, Y, Z, int(min_volume), _ptr(labels, ctypes.c_uint32),
+        cells.ctypes.data, len(cells), _ptr(k, ctypes.c_uint64), _ptr(t, ctypes.c_uint16),
+        _ptr(hist, ctypes.c_uint64) if hist is not None else None,
+        _ptr(sm, ctypes.c_uint16) if sm is not None else None)
+    if rc:
+        raise RuntimeError("oracle_segment failed: %d" % rc)
+    return OracleResult(labels, cells[: int(k[0])].copy(), int(t[0]), hist, sm)

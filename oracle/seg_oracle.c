@@ -1,0 +1,280 @@
+/*
+ * seg_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU statement of the per-frame, per-channel
+ * 3-D segmentation stage (smooth -> histogram -> Otsu -> threshold ->
+ * 26-connected labelling -> minimum-volume filter -> canonical numbering ->
+ * per-cell features).  It exists so that the CUDA path can be checked against
+ * something written independently of it.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load this file; the
+ * product path never calls it and shares no code, header or table with it.
+ *
+ * Sources (Wait et al., "Visualization and Correction of Automated
+ * Segmentation, Tracking and Lineaging from 5-D Stem Cell Image Sequences"):
+ *   - Background Noise Removal, Eq. 1: the stem-cell channel is low-pass
+ *     (Gaussian) filtered.  Read here as integer separable binomial smoothing
+ *     [1 4 6 4 1] per axis (the binomial kernel is the integer form of a
+ *     Gaussian with sigma = 1 voxel), uint32 accumulation, one final rounding
+ *     (S + 2048) >> 12, replicate-edge borders.
+ *   - Segmentation: adaptive Otsu thresholding of every channel (Otsu 1979,
+ *     the paper's ref. [11]) giving a binary foreground image; a connected
+ *     component filter; components below 19 um^3 discarded (user settable).
+ *     Read here as a global Otsu over the frame's 65536-level integer
+ *     histogram (FP64 between-class variance, ties to the lowest level,
+ *     foreground strictly above the level), 26-connectivity, components
+ *     numbered 1..K in increasing order of their lowest linear voxel index
+ *     after dropping those with fewer than m voxels (m = 30 voxels is
+ *     19 um^3 at the 0.8 x 0.8 x 1.0 um spacing of the Methods section).
+ *   - Per-cell features (voxel count, inclusive bounding box, int64 coordinate
+ *     sums) stand in for the per-cell voxel sets used by tracking (Eq. 6 uses
+ *     the voxel count).
+ *
+ * Linear index i = x + X*(y + Y*z), x fastest.
+ *
+ * Build with -O2 -ffp-contract=off and without -ffast-math: the Otsu
+ * variance must be evaluated in IEEE binary64 exactly in the order written.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL (-1)
+#define ORACLE_ENOMEM (-2)
+#define ORACLE_ESMALL (-3)
+
+/* Per-cell record, 64 bytes, defined here independently of the CUDA path. */
+typedef struct {
+    uint64_t count;
+    int64_t sum[3];      /* sum of x, y, z over the cell's voxels */
+    uint32_t bbox_min[3];/* inclusive */
+    uint32_t bbox_max[3];/* inclusive */
+    uint32_t pad[2];
+} oracle_cell;
+
+static const uint32_t BINOM5[5] = {1u, 4u, 6u, 4u, 1u};
+
+static int64_t clamp_i64(int64_t k, int64_t n) {
+    if (k < 0) return 0;
+    if (k >= n) return n - 1;
+    return k;
+}
+
+/* Background Noise Removal (Eq. 1, Gaussian low-pass) as binomial smoothing:
+ *   S(x,y,z) = sum_{a,b,c in -2..2} B[a] B[b] B[c] v(cl(x+a), cl(y+b), cl(z+c))
+ *   s = (S + 2048) >> 12
+ * computed as three 1-D passes (x, then y, then z) in uint32 with the single
+ * rounding at the end, which equals the 125-term sum exactly. */
+int oracle_smooth(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint16_t *s) {
+    if (!v || !s || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    uint64_t n = (uint64_t)X * Y * Z;
+    uint32_t *a = (uint32_t *)malloc(n * sizeof(uint32_t));
+    uint32_t *b = (uint32_t *)malloc(n * sizeof(uint32_t));
+    if (!a || !b) { free(a); free(b); return ORACLE_ENOMEM; }
+    /* pass along x */
+    for (uint64_t z = 0; z < Z; ++z)
+        for (uint64_t y = 0; y < Y; ++y)
+            for (uint64_t x = 0; x < X; ++x) {
+                uint32_t acc = 0;
+                for (int k = 0; k < 5; ++k) {
+                    int64_t xx = clamp_i64((int64_t)x + k - 2, X);
+                    acc += BINOM5[k] * (uint32_t)v[xx + X * (y + Y * z)];
+                }
+                a[x + X * (y + Y * z)] = acc;
+            }
+    /* pass along y */
+    for (uint64_t z = 0; z < Z; ++z)
+        for (uint64_t y = 0; y < Y; ++y)
+            for (uint64_t x = 0; x < X; ++x) {
+                uint32_t acc = 0;
+                for (int k = 0; k < 5; ++k) {
+                    int64_t yy = clamp_i64((int64_t)y + k - 2, Y);
+                    acc += BINOM5[k] * a[x + X * (yy + Y * z)];
+                }
+                b[x + X * (y + Y * z)] = acc;
+            }
+    /* pass along z, then the one rounding */
+    for (uint64_t z = 0; z < Z; ++z)
+        for (uint64_t y = 0; y < Y; ++y)
+            for (uint64_t x = 0; x < X; ++x) {
+                uint32_t acc = 0;
+                for (int k = 0; k < 5; ++k) {
+                    int64_t zz = clamp_i64((int64_t)z + k - 2, Z);
+                    acc += BINOM5[k] * b[x + X * (y + Y * zz)];
+                }
+                s[x + X * (y + Y * z)] = (uint16_t)((acc + 2048u) >> 12);
+            }
+    free(a);
+    free(b);
+    return ORACLE_OK;
+}
+
+/* Histogram of the smoothed frame: h[u] = number of voxels with value u. */
+int oracle_histogram(const uint16_t *s, uint64_t n, uint64_t *h) {
+    if (!s || !h) return ORACLE_EINVAL;
+    memset(h, 0, 65536 * sizeof(uint64_t));
+    for (uint64_t i = 0; i < n; ++i) h[s[i]] += 1;
+    return ORACLE_OK;
+}
+
+/* Otsu's threshold (Segmentation section, ref. [11]).
+ * For every level t = 0..65534 with C0 = {u <= t}, C1 = {u > t}:
+ *   n0 = sum_{u<=t} h[u], s0 = sum_{u<=t} u h[u], n1 = N - n0, s1 = S - s0,
+ *   skip t when n0 == 0 or n1 == 0, else
+ *   var(t) = ((n0 * n1) * (s1/n1 - s0/n0)) * (s1/n1 - s0/n0)   in binary64,
+ * which is N^2 times Otsu's between-class variance (the same argmax).
+ * t* = the lowest t attaining the maximum.  A frame with one distinct value has
+ * no admissible t; then t* is that value, so nothing lies strictly above it. */
+uint16_t oracle_otsu(const uint64_t *h) {
+    uint64_t N = 0, S = 0;
+    for (uint32_t u = 0; u < 65536u; ++u) {
+        N += h[u];
+        S += (uint64_t)u * h[u];
+    }
+    uint64_t n0 = 0, s0 = 0;
+    double best = -1.0;
+    int found = 0;
+    uint32_t best_t = 0;
+    for (uint32_t t = 0; t < 65535u; ++t) {
+        n0 += h[t];
+        s0 += (uint64_t)t * h[t];
+        uint64_t n1 = N - n0;
+        uint64_t s1 = S - s0;
+        if (n0 == 0 || n1 == 0) continue;
+        double m0 = (double)s0 / (double)n0;
+        double m1 = (double)s1 / (double)n1;
+        double d = m1 - m0;
+        double var = (((double)n0 * (double)n1) * d) * d;
+        if (!found || var > best) {
+            best = var;
+            best_t = t;
+            found = 1;
+        }
+    }
+    if (!found) {
+        for (uint32_t u = 0; u < 65536u; ++u)
+            if (h[u]) return (uint16_t)u;
+        return 0;
+    }
+    return (uint16_t)best_t;
+}
+
+/* 26-connected component labelling of a binary volume (Segmentation section,
+ * "connected component image filter").  Voxels are scanned in increasing
+ * linear index; each unlabelled foreground voxel starts a breadth-first flood
+ * over its 26 neighbours (in bounds, no wrap).  Provisional ids are 1, 2, ...
+ * in discovery order, i.e. in increasing order of each component's lowest
+ * linear index.  Returns the number of components, or a negative error. */
+int64_t oracle_label26(const uint8_t *mask, uint32_t X, uint32_t Y, uint32_t Z, uint32_t *lab) {
+    if (!mask || !lab || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    uint64_t n = (uint64_t)X * Y * Z;
+    uint64_t *queue = (uint64_t *)malloc(n * sizeof(uint64_t));
+    if (!queue) return ORACLE_ENOMEM;
+    memset(lab, 0, n * sizeof(uint32_t));
+    uint32_t next = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (!mask[i] || lab[i]) continue;
+        next += 1;
+        uint64_t head = 0, tail = 0;
+        lab[i] = next;
+        queue[tail++] = i;
+        while (head < tail) {
+            uint64_t p = queue[head++];
+            int64_t px = (int64_t)(p % X);
+            int64_t py = (int64_t)((p / X) % Y);
+            int64_t pz = (int64_t)(p / ((uint64_t)X * Y));
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (!dx && !dy && !dz) continue;
+                        int64_t qx = px + dx, qy = py + dy, qz = pz + dz;
+                        if (qx < 0 || qy < 0 || qz < 0) continue;
+                        if (qx >= X || qy >= Y || qz >= Z) continue;
+                        uint64_t q = (uint64_t)qx + X * ((uint64_t)qy + (uint64_t)Y * qz);
+                        if (mask[q] && !lab[q]) {
+                            lab[q] = next;
+                            queue[tail++] = q;
+                        }
+                    }
+        }
+    }
+    free(queue);
+    return (int64_t)next;
+}
+
+/* Minimum-volume filter, canonical numbering and per-cell features
+ * (Segmentation section: components under the user-set volume are discarded).
+ * A provisional component survives iff its voxel count >= min_volume; the
+ * survivors are numbered 1..K keeping the provisional (lowest-index) order.
+ * labels_out may alias prov.  Features are gathered by visiting every voxel. */
+int oracle_filter_features(const uint32_t *prov, uint64_t ncomp, uint32_t X, uint32_t Y, uint32_t Z,
+                           uint32_t min_volume, uint32_t *labels_out, oracle_cell *cells,
+                           uint64_t cap, uint64_t *k_out) {
+    if (!prov || !labels_out || !k_out || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    uint64_t n = (uint64_t)X * Y * Z;
+    uint64_t *count = (uint64_t *)calloc(ncomp + 1, sizeof(uint64_t));
+    uint32_t *remap = (uint32_t *)calloc(ncomp + 1, sizeof(uint32_t));
+    if (!count || !remap) { free(count); free(remap); return ORACLE_ENOMEM; }
+    for (uint64_t i = 0; i < n; ++i) count[prov[i]] += 1;
+    uint64_t K = 0;
+    for (uint64_t c = 1; c <= ncomp; ++c)
+        if (count[c] >= min_volume) remap[c] = (uint32_t)(++K);
+    *k_out = K;
+    int rc = ORACLE_OK;
+    if (cells && cap < K) rc = ORACLE_ESMALL;
+    if (cells && rc == ORACLE_OK) {
+        for (uint64_t k = 0; k < K; ++k) {
+            memset(&cells[k], 0, sizeof(oracle_cell));
+            for (int a = 0; a < 3; ++a) cells[k].bbox_min[a] = 0xFFFFFFFFu;
+        }
+    }
+    for (uint64_t z = 0; z < Z; ++z)
+        for (uint64_t y = 0; y < Y; ++y)
+            for (uint64_t x = 0; x < X; ++x) {
+                uint64_t i = x + X * (y + Y * z);
+                uint32_t l = remap[prov[i]];
+                labels_out[i] = l;
+                if (!l || !cells || rc != ORACLE_OK) continue;
+                oracle_cell *c = &cells[l - 1];
+                uint64_t p[3] = {x, y, z};
+                c->count += 1;
+                for (int a = 0; a < 3; ++a) {
+                    c->sum[a] += (int64_t)p[a];
+                    if (p[a] < c->bbox_min[a]) c->bbox_min[a] = (uint32_t)p[a];
+                    if (p[a] > c->bbox_max[a]) c->bbox_max[a] = (uint32_t)p[a];
+                }
+            }
+    free(count);
+    free(remap);
+    return rc;
+}
+
+/* The whole stage for one frame and channel: smooth, histogram, Otsu,
+ * threshold (foreground iff s > t*), label, filter, features.
+ * hist (65536 entries) and smoothed (n entries) are optional outputs. */
+int oracle_segment(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32_t min_volume,
+                   uint32_t *labels, oracle_cell *cells, uint64_t cap, uint64_t *k_out,
+                   uint16_t *t_out, uint64_t *hist, uint16_t *smoothed) {
+    if (!v || !labels || !k_out || !t_out || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    uint64_t n = (uint64_t)X * Y * Z;
+    uint16_t *s = smoothed ? smoothed : (uint16_t *)malloc(n * sizeof(uint16_t));
+    uint64_t *h = hist ? hist : (uint64_t *)malloc(65536 * sizeof(uint64_t));
+    uint8_t *m = (uint8_t *)malloc(n);
+    int rc = ORACLE_OK;
+    if (!s || !h || !m) { rc = ORACLE_ENOMEM; goto done; }
+    rc = oracle_smooth(v, X, Y, Z, s);
+    if (rc) goto done;
+    rc = oracle_histogram(s, n, h);
+    if (rc) goto done;
+    uint16_t t = oracle_otsu(h);
+    *t_out = t;
+    for (uint64_t i = 0; i < n; ++i) m[i] = (uint8_t)(s[i] > t);
+    int64_t nc = oracle_label26(m, X, Y, Z, labels);
+    if (nc < 0) { rc = (int)nc; goto done; }
+    rc = oracle_filter_features(labels, (uint64_t)nc, X, Y, Z, min_volume, labels, cells, cap, k_out);
+done:
+    if (!smoothed) free(s);
+    if (!hist) free(h);
+    free(m);
+    return rc;
+}

@@ -1,0 +1,413 @@
+"""Pins for the CPU oracle, independent of the oracle's own code.
+
+Each test checks the oracle against something the paper or mathematics fixes:
+brute-force definitions (the 125-term smoothing sum, iterative min-label
+propagation, per-label enumeration), closed forms (impulse response, exact
+rational Otsu, symmetric sums), invariants and library special cases
+(numpy.bincount, scipy.ndimage.label with the full 3x3x3 structure).
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+B5 = np.array([1, 4, 6, 4, 1], dtype=np.int64)
+
+
+# ----------------------------------------------------------------------------
+# smoothing (Background Noise Removal, Eq. 1: Gaussian low-pass -> binomial)
+# ----------------------------------------------------------------------------
+
+def smooth_bruteforce(v):
+    """The 125-term definition with per-axis edge clamping, int64, one rounding."""
+    Z, Y, X = v.shape
+    v = v.astype(np.int64)
+    S = np.zeros_like(v)
+    xs, ys, zs = np.arange(X), np.arange(Y), np.arange(Z)
+    for c in range(5):
+        zi = np.clip(zs + c - 2, 0, Z - 1)
+        for b in range(5):
+            yi = np.clip(ys + b - 2, 0, Y - 1)
+            for a in range(5):
+                xi = np.clip(xs + a - 2, 0, X - 1)
+                S += B5[a] * B5[b] * B5[c] * v[np.ix_(zi, yi, xi)]
+    assert S.max() < 2 ** 32
+    return ((S + 2048) >> 12).astype(np.uint16)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 3, 4), (5, 5, 5), (7, 3, 9), (13, 11, 6),
+                                  (1, 17, 2), (33, 4, 3)])
+def test_smooth_equals_125_term_sum(dims):
+    X, Y, Z = dims
+    rng = np.random.default_rng(hash(dims) & 0xFFFF)
+    for kind in range(3):
+        if kind == 0:
+            v = rng.integers(0, 65536, size=(Z, Y, X), dtype=np.uint16)
+        elif kind == 1:
+            v = rng.choice(np.array([0, 65535], dtype=np.uint16), size=(Z, Y, X))
+        else:
+            v = rng.integers(150, 260, size=(Z, Y, X), dtype=np.uint16)
+        np.testing.assert_array_equal(oracle.smooth(v), smooth_bruteforce(v))
+
+
+def test_smooth_impulse_response():
+    # an interior impulse of height 4096 returns exactly B[a]B[b]B[c]
+    v = np.zeros((9, 9, 9), dtype=np.uint16)
+    v[4, 4, 4] = 4096
+    s = oracle.smooth(v).astype(np.int64)
+    expect = np.zeros((9, 9, 9), dtype=np.int64)
+    expect[2:7, 2:7, 2:7] = B5[:, None, None] * B5[None, :, None] * B5[None, None, :]
+    np.testing.assert_array_equal(s, expect)
+
+
+def test_smooth_constant_and_bounds():
+    for c in (0, 1, 200, 4095, 65535):
+        v = np.full((6, 7, 8), c, dtype=np.uint16)
+        np.testing.assert_array_equal(oracle.smooth(v), v)
+    rng = np.random.default_rng(7)
+    v = rng.integers(1000, 3000, size=(10, 12, 14), dtype=np.uint16)
+    s = oracle.smooth(v)
+    assert s.min() >= v.min() and s.max() <= v.max()
+
+
+def test_smooth_half_rounds_up():
+    # S = 2048 exactly (half of 4096) must round up to 1: an impulse of height
+    # 2048/(B[a]B[b]B[c]) with B=6*6*6=216 is not integral, so build S=2048 by
+    # a single corner-adjacent value: impulse 8 at distance 2 in x and y and z
+    # contributes 8*1*1*1*...; use height 2048 at a voxel seen with weight 1.
+    v = np.zeros((5, 5, 5), dtype=np.uint16)
+    v[0, 0, 0] = 2048
+    s = smooth_bruteforce(v)
+    # voxel (2,2,2) sees (0,0,0) with weight 1*1*1 -> S = 2048 -> s = 1
+    assert s[2, 2, 2] == 1
+    assert oracle.smooth(v)[2, 2, 2] == 1
+
+
+# ----------------------------------------------------------------------------
+# histogram
+# ----------------------------------------------------------------------------
+
+def test_histogram_matches_bincount():
+    rng = np.random.default_rng(3)
+    s = rng.integers(0, 65536, size=100000, dtype=np.uint16)
+    h = oracle.histogram(s)
+    np.testing.assert_array_equal(h, np.bincount(s, minlength=65536).astype(np.uint64))
+    assert int(h.sum()) == s.size
+
+
+# ----------------------------------------------------------------------------
+# Otsu (Segmentation section, ref. [11])
+# ----------------------------------------------------------------------------
+
+def load_otsu_golden():
+    cases = []
+    with open(os.path.join(GOLDEN, "otsu_hand.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            lhs, rhs = line.split("->")
+            h = np.zeros(65536, dtype=np.uint64)
+            for tok in lhs.split():
+                lvl, cnt = tok.split(":")
+                h[int(lvl)] += int(cnt)
+            cases.append((h, int(rhs)))
+    return cases
+
+
+def test_otsu_hand_worked():
+    cases = load_otsu_golden()
+    assert len(cases) >= 8
+    for h, t in cases:
+        assert oracle.otsu(h) == t
+
+
+def otsu_exact(h):
+    """Exact-rational Otsu: argmax of (S n0 - N s0)^2 / (n0 n1), ties -> lowest t.
+
+    Returns (t*, best value, runner-up value among distinct classes)."""
+    nz = np.nonzero(h)[0]
+    N = int(h.sum())
+    S = int(sum(int(u) * int(h[u]) for u in nz))
+    best = None
+    best_t = None
+    values = []
+    n0 = s0 = 0
+    for u in nz:
+        n0 += int(h[u])
+        s0 += int(u) * int(h[u])
+        n1 = N - n0
+        if n1 == 0:
+            break
+        val = Fraction((S * n0 - N * s0) ** 2, n0 * n1)
+        values.append(val)
+        if best is None or val > best:
+            best, best_t = val, int(u)
+    if best_t is None:
+        return int(nz[0]), None, None
+    vs = sorted(set(values), reverse=True)
+    return best_t, best, (vs[1] if len(vs) > 1 else None)
+
+
+def test_otsu_vs_exact_rational():
+    rng = np.random.default_rng(11)
+    near_ties = 0
+    for trial in range(400):
+        h = np.zeros(65536, dtype=np.uint64)
+        k = int(rng.integers(1, 12))
+        span = int(rng.choice([8, 64, 4096, 65536]))
+        lo = int(rng.integers(0, 65536 - span + 1))
+        k = min(k, span)
+        levels = rng.choice(np.arange(lo, lo + span), size=k, replace=False)
+        h[levels] = rng.integers(1, 10 ** int(rng.integers(1, 7)), size=k).astype(np.uint64)
+        t_exact, best, second = otsu_exact(h)
+        t = oracle.otsu(h)
+        if t != t_exact:
+            # only admissible when binary64 cannot separate the top two values
+            assert second is not None and abs(best - second) <= Fraction(1, 10 ** 12) * best
+            near_ties += 1
+    assert near_ties == 0
+
+
+def test_otsu_two_spikes_and_scale():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        a, b = sorted(rng.choice(65536, size=2, replace=False))
+        h = np.zeros(65536, dtype=np.uint64)
+        h[a] = rng.integers(1, 10 ** 6)
+        h[b] = rng.integers(1, 10 ** 6)
+        assert oracle.otsu(h) == a
+        # power-of-two scaling of all counts scales var exactly by 4^j
+        h2 = h * np.uint64(1 << int(rng.integers(1, 8)))
+        assert oracle.otsu(h2) == a
+
+
+def test_otsu_empty_runs_pick_lowest():
+    # levels between occupied bins repeat the same (n0, s0) -> same value;
+    # the answer must be an occupied level
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        h = np.zeros(65536, dtype=np.uint64)
+        lv = rng.choice(65536, size=6, replace=False)
+        h[lv] = rng.integers(1, 1000, size=6).astype(np.uint64)
+        assert h[oracle.otsu(h)] > 0
+
+
+# ----------------------------------------------------------------------------
+# 26-connected labelling (Segmentation section, connected component filter)
+# ----------------------------------------------------------------------------
+
+def minlabel_propagation(mask):
+    """Brute force: every foreground voxel repeatedly takes the minimum linear
+    index over itself and its 26 neighbours until nothing changes; components
+    are then numbered by that minimum."""
+    Z, Y, X = mask.shape
+    big = np.iinfo(np.int64).max
+    idx = np.arange(mask.size, dtype=np.int64).reshape(mask.shape)
+    cur = np.where(mask, idx, big)
+    while True:
+        pad = np.pad(cur, 1, constant_values=big)
+        nxt = cur.copy()
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    sh = pad[1 + dz:1 + dz + Z, 1 + dy:1 + dy + Y, 1 + dx:1 + dx + X]
+                    nxt = np.minimum(nxt, sh)
+        nxt = np.where(mask, nxt, big)
+        if np.array_equal(nxt, cur):
+            break
+        cur = nxt
+    roots = np.unique(cur[mask])
+    rank = {int(r): i + 1 for i, r in enumerate(roots)}
+    out = np.zeros(mask.shape, dtype=np.uint32)
+    out[mask] = [rank[int(r)] for r in cur[mask]]
+    return out, len(roots)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (3, 3, 3), (12, 5, 1), (6, 7, 8), (12, 12, 12),
+                                  (1, 9, 11), (10, 1, 10)])
+def test_label26_vs_minlabel_propagation(dims):
+    X, Y, Z = dims
+    rng = np.random.default_rng(sum(dims))
+    for p in (0.05, 0.1, 0.3, 0.5, 0.7, 0.95):
+        mask = rng.uniform(size=(Z, Y, X)) < p
+        lab, n = oracle.label26(mask)
+        ref, nref = minlabel_propagation(mask)
+        assert n == nref
+        np.testing.assert_array_equal(lab, ref)
+
+
+def test_label26_vs_scipy():
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(21)
+    for trial in range(10):
+        dims = rng.integers(5, 40, size=3)
+        mask = rng.uniform(size=tuple(dims)) < rng.uniform(0.05, 0.6)
+        lab, n = oracle.label26(mask)
+        ref, nref = ndimage.label(mask, structure=np.ones((3, 3, 3), dtype=bool))
+        assert n == nref
+        np.testing.assert_array_equal(lab, ref.astype(np.uint32))
+
+
+def load_label_golden():
+    cases = []
+    with open(os.path.join(GOLDEN, "label_tiny.txt")) as f:
+        lines = [l.rstrip("\n") for l in f if l.strip() and not l.startswith("#")]
+    i = 0
+    while i < len(lines):
+        _, X, Y, Z = lines[i].split()
+        X, Y, Z = int(X), int(Y), int(Z)
+        i += 1
+        rows = lines[i:i + Y * Z]
+        i += Y * Z
+        assert lines[i] == "labels"
+        i += 1
+        lrows = lines[i:i + Y * Z]
+        i += Y * Z
+        assert lines[i] == "end"
+        i += 1
+        mask = np.array([[c == "o" for c in r] for r in rows]).reshape(Z, Y, X)
+        lab = np.array([[0 if c == "." else int(c) for c in r] for r in lrows],
+                       dtype=np.uint32).reshape(Z, Y, X)
+        cases.append((mask, lab))
+    return cases
+
+
+def test_label26_hand_worked():
+    cases = load_label_golden()
+    assert len(cases) == 4
+    for mask, expect in cases:
+        lab, n = oracle.label26(mask)
+        np.testing.assert_array_equal(lab, expect)
+        assert n == expect.max()
+
+
+def test_label26_connectivity_kinds():
+    # face, edge and corner contacts all join under 26-connectivity
+    for off in [(0, 0, 1), (0, 1, 1), (1, 1, 1), (1, -1, 1)]:
+        m = np.zeros((3, 3, 3), dtype=bool)
+        m[1, 1, 1] = True
+        m[1 + off[0], 1 + off[1], 1 + off[2]] = True
+        _, n = oracle.label26(m)
+        assert n == 1
+    # distance 2 never joins
+    m = np.zeros((1, 1, 5), dtype=bool)
+    m[0, 0, 0] = m[0, 0, 2] = m[0, 0, 4] = True
+    lab, n = oracle.label26(m)
+    assert n == 3 and list(lab[0, 0]) == [1, 0, 2, 0, 3]
+
+
+# ----------------------------------------------------------------------------
+# minimum volume, canonical numbering, features
+# ----------------------------------------------------------------------------
+
+def features_enumerated(labels, K):
+    out = []
+    for l in range(1, K + 1):
+        z, y, x = np.nonzero(labels == l)
+        out.append((len(x), (int(x.sum()), int(y.sum()), int(z.sum())),
+                    (int(x.min()), int(y.min()), int(z.min())),
+                    (int(x.max()), int(y.max()), int(z.max()))))
+    return out
+
+
+def check_cells(cells, labels):
+    K = len(cells)
+    assert labels.max() == K
+    for c, (cnt, sums, mn, mx) in zip(cells, features_enumerated(labels, K)):
+        assert int(c["count"]) == cnt
+        assert tuple(int(v) for v in c["sum"]) == sums
+        assert tuple(int(v) for v in c["bbox_min"]) == mn
+        assert tuple(int(v) for v in c["bbox_max"]) == mx
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 5, 30])
+def test_filter_and_features(m):
+    rng = np.random.default_rng(100 + m)
+    mask = rng.uniform(size=(9, 14, 17)) < 0.25
+    prov, n = oracle.label26(mask)
+    lab, cells = oracle.filter_features(prov, n, m)
+    counts = np.bincount(prov.ravel(), minlength=n + 1)
+    keep = [c for c in range(1, n + 1) if counts[c] >= m]
+    assert len(cells) == len(keep)
+    # survivors keep their relative (lowest-index) order and become 1..K
+    for new, old in enumerate(keep, start=1):
+        np.testing.assert_array_equal(lab == new, prov == old)
+    assert np.all(lab[np.isin(prov, [c for c in range(1, n + 1) if counts[c] < m])] == 0)
+    check_cells(cells, lab)
+
+
+def test_symmetric_shapes_closed_form():
+    # digitised sphere centred on a voxel: sums are count * centre exactly
+    Z, Y, X = 21, 23, 25
+    zz, yy, xx = np.mgrid[0:Z, 0:Y, 0:X]
+    c = (12, 11, 10)
+    ball = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2 <= 36
+    box = (xx >= 1) & (xx <= 4) & (yy >= 2) & (yy <= 20) & (zz >= 18) & (zz <= 19)
+    prov, n = oracle.label26(ball | box)
+    lab, cells = oracle.filter_features(prov, n, 1)
+    assert len(cells) == 2
+    bi = 0 if cells[0]["bbox_min"][2] < 10 else 1
+    b, q = cells[bi], cells[1 - bi]
+    k = int(b["count"])
+    assert k == int(ball.sum())
+    assert tuple(int(v) for v in b["sum"]) == (k * c[0], k * c[1], k * c[2])
+    assert tuple(int(v) for v in b["bbox_min"]) == (6, 5, 4)
+    assert tuple(int(v) for v in b["bbox_max"]) == (18, 17, 16)
+    # box 4 x 19 x 2: sum of x = 19*2*(1+2+3+4), y = 4*2*sum(2..20), z = 4*19*(18+19)
+    assert int(q["count"]) == 4 * 19 * 2
+    assert tuple(int(v) for v in q["sum"]) == (19 * 2 * 10, 4 * 2 * sum(range(2, 21)),
+                                              4 * 19 * 37)
+
+
+# ----------------------------------------------------------------------------
+# whole pipeline
+# ----------------------------------------------------------------------------
+
+def test_segment_composes_the_steps():
+    rng = np.random.default_rng(4)
+    v = rng.integers(100, 400, size=(10, 20, 30), dtype=np.uint16)
+    v[3:7, 5:12, 8:20] += 2000
+    r = oracle.segment(v, min_volume=3, keep_hist=True, keep_smoothed=True)
+    s = smooth_bruteforce(v)
+    np.testing.assert_array_equal(r.smoothed, s)
+    np.testing.assert_array_equal(r.hist, np.bincount(s.ravel(), minlength=65536))
+    t_exact, _, _ = otsu_exact(r.hist)
+    assert r.threshold == t_exact
+    ref, _ = minlabel_propagation(s > r.threshold)
+    counts = np.bincount(ref.ravel())
+    keep = [c for c in range(1, len(counts)) if counts[c] >= 3]
+    assert r.n_cells == len(keep)
+    check_cells(r.cells, r.labels)
+
+
+def test_blank_volume_has_no_cells():
+    for c in (0, 200, 65535):
+        v = np.full((8, 9, 10), c, dtype=np.uint16)
+        r = oracle.segment(v)
+        assert r.threshold == c and r.n_cells == 0 and not r.labels.any()
+
+
+def test_well_separated_nuclei_counted_exactly():
+    for seed in (1, 2, 3):
+        vol, nuc = synth.well_separated((96, 96, 40), seed, 25)
+        assert len(nuc) >= 15
+        r = oracle.segment(vol, min_volume=30)
+        assert r.n_cells == len(nuc)
+        # each planted centre lies in the bbox of exactly one cell
+        for c in nuc[:, :3]:
+            inside = [(cell["bbox_min"] <= c).all() and (c <= cell["bbox_max"]).all()
+                      for cell in r.cells]
+            assert sum(inside) == 1
+
+
+def test_single_frame_workload_counts():
+    vol = synth.single_frame()
+    r = oracle.segment(vol, min_volume=30)
+    assert 30 <= r.n_cells <= 40
+    assert 300 < r.threshold < 1500
