@@ -1,0 +1,185 @@
+/*
+ * seg.h -- C ABI of libseg, a GB300 (sm_103a) library for the per-frame,
+ * per-channel 3-D segmentation stage of LEVER 3-D (Wait et al.): smooth ->
+ * histogram -> Otsu -> threshold -> 26-connected labelling -> minimum-volume
+ * filter -> canonical numbering -> per-cell features.
+ *
+ * Paper passages the operations come from:
+ *   - Background Noise Removal, Eq. 1: the stem-cell channel is low-pass
+ *     (Gaussian) filtered.  Here: integer separable binomial smoothing
+ *     [1 4 6 4 1] per axis, uint32 sums, one rounding (S + 2048) >> 12,
+ *     replicate-edge borders.
+ *   - Segmentation: adaptive Otsu thresholding of all channels (ref. [11])
+ *     giving a binary foreground image; a connected component filter; cells
+ *     below 19 um^3 discarded, the limit settable by the user before the run.
+ *     Here: global Otsu over the frame's 65536-level histogram (binary64
+ *     between-class variance, ties to the lowest level, foreground strictly
+ *     above it), 26-connectivity, survivors numbered 1..K by their lowest
+ *     linear voxel index.  The default limit, 30 voxels, is 19 um^3 at the
+ *     0.8 x 0.8 x 1.0 um spacing of the Methods section.
+ *   - Tracking, Eq. 6 uses each cell's voxel count; the per-cell record
+ *     (count, inclusive bounding box, int64 coordinate sums) is what the
+ *     later stages consume.
+ *
+ * Layout: a volume is uint16 [C][Z][Y][X] (channels planar, x fastest);
+ * linear index i = x + X*(y + Y*z).  Labels are uint32 [Z][Y][X] per channel,
+ * 0 = background, 1..K = cells.  Limits: X*Y*Z < 2^32, X <= 65536.
+ *
+ * Threading: one thread may submit while another polls and reads; calls on
+ * one context are otherwise serialised by the caller.  No call throws; every
+ * call returns SEG_OK (0) or a negative SEG_E* code.  Device pointers are
+ * CUDA device addresses on the context's device.
+ */
+#ifndef SEG_H
+#define SEG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define SEG_OK 0
+#define SEG_EINVAL (-1)    /* null pointer, zero dimension, channels == 0, bad field */
+#define SEG_ETOOBIG (-2)   /* X*Y*Z >= 2^32, X > 65536, or footprint > HBM budget  */
+#define SEG_EAGAIN (-3)    /* host queue full: retry after polling / releasing      */
+#define SEG_ENOTREADY (-4) /* read of a request that is not DONE                    */
+#define SEG_ETIMEOUT (-5)  /* seg_poll timed out, or a bounded device wait gave up  */
+#define SEG_ECUDA (-6)     /* a CUDA call failed; the request is FAILED             */
+#define SEG_ESMALL (-7)    /* destination too small (n_cells is still reported)     */
+#define SEG_ENOENT (-8)    /* unknown or released request handle                    */
+#define SEG_EFAILED (-9)   /* the request FAILED (device error flag or CUDA error)  */
+
+/* ---- request states (seg_poll) ------------------------------------------ */
+#define SEG_PENDING 0
+#define SEG_DONE 1
+#define SEG_FAILED 2
+
+/* ---- seg_config.flags ---------------------------------------------------- */
+#define SEG_FORCE_TILE 0x1u /* use tile_y / tile_z as given, skip the autotuner   */
+#define SEG_PLAIN 0x2u      /* plain per-frame form: one request per launch
+                               sequence, one stream, no batching, no graphs      */
+#define SEG_NO_GRAPH 0x4u   /* batched form without CUDA-graph capture           */
+#define SEG_PROFILE 0x8u    /* record CUDA events around every kernel launch     */
+
+typedef struct seg_ctx seg_ctx; /* opaque; owns streams, graphs, device state   */
+typedef uint64_t seg_req;       /* request handle, never 0                       */
+
+typedef struct {
+    uint32_t x, y, z;
+} seg_dims;
+
+/* One cell, 64 bytes; cells are stored in label order 1..K. */
+typedef struct {
+    uint64_t count;       /* voxels in the cell                                 */
+    int64_t sum[3];       /* sum of x, y, z over its voxels (0-based coords)   */
+    uint32_t bbox_min[3]; /* inclusive                                          */
+    uint32_t bbox_max[3]; /* inclusive                                          */
+    uint32_t pad[2];
+} seg_cell_features;
+
+typedef struct {
+    int device;                /* CUDA ordinal                                   */
+    uint32_t max_inflight;     /* batches in flight (streams); 0 -> 2            */
+    uint64_t hbm_budget_bytes; /* admission limit for all device state; 0 -> 80 %
+                                  of the device's free memory at seg_create      */
+    uint32_t flags;            /* SEG_FORCE_TILE | SEG_PLAIN | ...               */
+    uint32_t tile_y;           /* smoothing tile rows: 8, 16 or 32 (FORCE_TILE) */
+    uint32_t tile_z;           /* smoothing z-chunk, >= 1 (FORCE_TILE)           */
+    uint32_t max_batch_volumes;/* volume-channels per launch; 0 -> 512           */
+    uint32_t batch_window_us;  /* wait this long for more requests before a
+                                  launch when nothing is in flight; 0 -> launch
+                                  at once                                        */
+    uint32_t host_queue;       /* requests held on the host awaiting admission;
+                                  0 -> 4096                                      */
+    void *order_stream;        /* optional cudaStream_t: device inputs are read
+                                  only after the work queued on it at submit    */
+} seg_config;
+
+typedef struct {
+    uint32_t min_volume_voxels; /* keep cells with >= this many voxels (30)      */
+} seg_channel_params;
+
+/* Creates a context on cfg->device.  Allocates streams and descriptor buffers;
+ * runs the tile autotuner unless SEG_FORCE_TILE or SEG_PLAIN is set.
+ * *out is set on success.  Errors: SEG_EINVAL, SEG_ECUDA. */
+int seg_create(const seg_config *cfg, seg_ctx **out);
+
+/* Waits for all in-flight work, frees every request and the context. */
+int seg_destroy(seg_ctx *ctx);
+
+/* Submits one volume of `channels` planar channels, each [Z][Y][X] uint16.
+ *   voxels     host pointer (on_device = 0) or device pointer (on_device = 1).
+ *              A host input is copied before the call returns (the caller may
+ *              free or reuse it).  A device input must stay valid and
+ *              unchanged until seg_poll reports DONE or FAILED.
+ *   per_channel  array of `channels` params, or NULL for the default (30).
+ * On success *out is a new handle.  Results stay on the device until
+ * seg_release.  Errors: SEG_EINVAL, SEG_ETOOBIG (can never be admitted),
+ * SEG_EAGAIN (host queue full), SEG_ECUDA. */
+int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_dims dims,
+                      uint32_t channels, const seg_channel_params *per_channel, seg_req *out);
+
+/* Launches everything submitted so far without waiting for the batch window. */
+int seg_flush(seg_ctx *ctx);
+
+/* Waits up to timeout_ms for the request to leave PENDING; *state is set to
+ * SEG_PENDING, SEG_DONE or SEG_FAILED.  Returns SEG_ETIMEOUT if still
+ * pending, SEG_ENOENT for an unknown handle. */
+int seg_poll(seg_ctx *ctx, seg_req req, uint32_t timeout_ms, int *state);
+
+/* Makes `stream` (a cudaStream_t on the context's device) wait until the
+ * request's results are complete, without blocking the host.  The request
+ * must have been launched or be pending; ordering holds for either. */
+int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream);
+
+/* Copies channel `channel`'s label image (X*Y*Z uint32) to dst (host, or
+ * device when dst_on_device = 1).  Blocks until the copy is complete.
+ * Errors: SEG_ENOTREADY, SEG_EFAILED, SEG_ESMALL (dst_elems < X*Y*Z),
+ * SEG_EINVAL, SEG_ENOENT, SEG_ECUDA. */
+int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
+                    uint64_t dst_elems, int dst_on_device);
+
+/* Copies channel `channel`'s cells (label order) to host memory dst (cap
+ * entries) and reports n_cells and the Otsu level t* (foreground = s > t*).
+ * dst may be NULL with cap 0 to query n_cells.  SEG_ESMALL if cap < n_cells
+ * (n_cells and the threshold are still set). */
+int seg_read_features(seg_ctx *ctx, seg_req req, uint32_t channel, seg_cell_features *dst,
+                      uint64_t cap, uint64_t *n_cells, uint16_t *otsu_threshold);
+
+/* Frees the request's device state and returns its bytes to the budget. */
+int seg_release(seg_ctx *ctx, seg_req req);
+
+/* Host timestamps of a request in milliseconds since seg_create: submitted,
+ * admitted (device memory reserved), launched, completed (device work done,
+ * observed by the runtime).  Values not reached yet are negative. */
+int seg_request_times(seg_ctx *ctx, seg_req req, double *submit_ms, double *admit_ms,
+                      double *launch_ms, double *done_ms);
+
+#define SEG_MAX_KERNELS 16
+typedef struct {
+    uint64_t batches;                 /* launch sequences completed            */
+    uint64_t volumes;                 /* volume-channels segmented             */
+    uint64_t voxels;                  /* voxels segmented (all channels)       */
+    uint32_t tile_y, tile_z;          /* tile shape in use                     */
+    uint32_t n_kernels;
+    char names[SEG_MAX_KERNELS][32];  /* kernel names, launch order            */
+    uint64_t launches[SEG_MAX_KERNELS];
+    double total_ms[SEG_MAX_KERNELS]; /* CUDA-event time (SEG_PROFILE only)    */
+    uint64_t bytes_in_use;            /* budget accounting                     */
+    uint64_t budget_bytes;
+} seg_stats;
+
+/* Counters since seg_create or the last seg_reset_stats. */
+int seg_get_stats(seg_ctx *ctx, seg_stats *out);
+int seg_reset_stats(seg_ctx *ctx);
+
+/* Human-readable text for a return code (static storage). */
+const char *seg_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEG_H */

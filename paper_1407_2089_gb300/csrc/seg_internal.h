@@ -1,0 +1,101 @@
+// seg_internal.h -- device-side batch descriptors shared by the runtime and
+// the kernels of libseg (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "seg.h"
+
+namespace seg {
+
+// Per-volume status words (VolDev::stat).
+enum StatWord : uint32_t {
+    ST_THRESH = 0,     // Otsu level t* (foreground = s > t*)
+    ST_RUNS = 1,       // number of foreground runs R
+    ST_CELLS = 2,      // number of surviving cells K
+    ST_TILES_DONE = 3, // smoothing tiles whose histogram share is merged
+    ST_ERROR = 4,      // error bits (ERR_*)
+    ST_WORDS = 16,
+};
+
+enum ErrBits : uint32_t {
+    ERR_UNION = 1u << 0,   // union retry limit reached
+    ERR_KCAP = 1u << 1,    // more cells than the feature buffer holds
+    ERR_RCAP = 1u << 2,    // more runs than the run buffer holds
+    ERR_OTSU = 1u << 3,    // histogram total differs from the voxel count
+};
+
+constexpr int TILE_X = 64;        // smoothing tile width (outputs along x)
+constexpr int ROW_TILE = 256;     // rows per row tile (run kernels)
+constexpr int HIST_BINS = 65536;
+
+// One volume-channel inside a batch.  All pointers are device addresses.
+struct VolDev {
+    const uint16_t *raw;      // [Z][Y][X]
+    uint32_t *labels;         // [Z][Y][X] output
+    seg_cell_features *feat;  // k_cap cells output
+    uint32_t *stat;           // ST_WORDS words
+    uint32_t *hist;           // 65536 uint32 bins
+    uint32_t *mask;           // rows x W words, bit b of word w is x = 32w + b
+    uint32_t *rowoff;         // rows + 1: run count per row, then run offsets
+    uint32_t *rowk;           // rows: kept-root count per row, then label base
+    uint32_t *tsum;           // row tiles: run totals, then offsets
+    uint32_t *tkeep;          // row tiles: kept-root totals, then offsets
+    uint32_t *run_x;          // r_cap: x0 | x1 << 16 (inclusive run ends)
+    uint32_t *run_par;        // r_cap: union-find parent (run index)
+    uint32_t *run_aux;        // r_cap: voxel count at roots, then label
+    uint64_t k_cap;
+    uint64_t r_cap;
+    uint32_t X, Y, Z, W;      // W = words per mask row
+    uint32_t rows;            // Y * Z
+    uint32_t min_volume;
+    uint32_t ntx, nty, ntz;   // smoothing tiles per axis
+    uint32_t nrt;             // row tiles
+    uint32_t tile_base;       // first flat smoothing-tile index
+    uint32_t rt_base;         // first flat row-tile index
+};
+
+// Batch header, followed in memory by VolDev[nvol].
+struct BatchHdr {
+    uint32_t nvol;
+    uint32_t ntiles;     // smoothing tiles over the batch
+    uint32_t nrowtiles;  // row tiles over the batch
+    uint32_t tile_z;     // z-chunk of a smoothing tile
+    uint32_t tile_y;     // rows of a smoothing tile
+    uint32_t pad[3];
+    VolDev vol[1];       // nvol entries
+};
+
+inline size_t batch_bytes(uint32_t nvol) {
+    return offsetof(BatchHdr, vol) + sizeof(VolDev) * (nvol ? nvol : 1);
+}
+
+// Host-side description of the kernels launched for one batch.
+constexpr int NUM_KERNELS = 13;
+extern const char *const kKernelNames[NUM_KERNELS];
+
+struct LaunchPlan {
+    int sms;             // multiprocessors on the device
+    int tile_y;          // 8, 16 or 32
+    int grid_hist;       // persistent grid of the histogram kernel
+    int grid_mask;
+    int grid_rows;       // row-tile kernels
+    int grid_vols;       // per-volume kernels
+};
+
+// Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)
+// on `stream`.  ev, when non-null, holds NUM_KERNELS + 1 events recorded
+// around the launches (external records, so they survive graph capture).
+// stat_out receives nvol * ST_WORDS status words (volume-major).
+cudaError_t launch_pipeline(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream,
+                            cudaEvent_t *ev, uint32_t *stat_out);
+
+// Histogram-kernel shared memory per block for a tile height.
+size_t hist_smem_bytes(int tile_y);
+size_t mask_smem_bytes(int tile_y);
+cudaError_t configure_kernels(int device);
+
+}  // namespace seg

@@ -1,0 +1,781 @@
+// seg_runtime.cu -- host runtime behind the C ABI in include/seg.h.
+//
+// A context owns `max_inflight` launch slots (a CUDA stream each, a pinned +
+// device batch descriptor, optional captured CUDA graphs, profiling events)
+// and one scheduler thread.  Requests are admitted against an HBM budget
+// (their own results plus the scratch of the batch that carries them),
+// grouped into batches of up to max_batch_volumes volume-channels and
+// launched on a free slot; every kernel walks the batch descriptor, so one
+// launch sequence segments any mix of volume sizes.  Requests arriving while
+// batches run are admitted into the next batch as slots and memory free up
+// (continuous batching).  Completion is observed through a host function
+// enqueued behind each batch.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "seg.h"
+#include "seg_internal.h"
+
+namespace seg {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr size_t ALIGN = 256;
+inline size_t al(size_t b) { return (b + ALIGN - 1) / ALIGN * ALIGN; }
+inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+struct Batch;
+
+// Geometry and footprint of one channel of a request.
+struct VolGeom {
+    uint32_t X, Y, Z, W, rows, nrt;
+    uint64_t n, r_cap, k_cap;
+    size_t scratch;  // bytes of per-batch scratch for this volume-channel
+};
+
+VolGeom geom(seg_dims d, uint32_t min_volume) {
+    VolGeom g;
+    g.X = d.x; g.Y = d.y; g.Z = d.z;
+    g.W = (uint32_t)cdiv(d.x, 32);
+    g.rows = d.y * d.z;
+    g.nrt = (uint32_t)cdiv(g.rows, ROW_TILE);
+    g.n = (uint64_t)d.x * d.y * d.z;
+    g.r_cap = (uint64_t)g.rows * cdiv(d.x, 2);
+    // 26-separated components: at most one per 2x2x2 block; each surviving
+    // cell also holds >= min_volume voxels.
+    uint64_t kc = cdiv(d.x, 2) * cdiv(d.y, 2) * cdiv(d.z, 2);
+    if (min_volume > 1) kc = std::min<uint64_t>(kc, g.n / min_volume + 1);
+    g.k_cap = std::max<uint64_t>(kc, 1);
+    g.scratch = al(4ull * HIST_BINS) + al(4ull * g.rows * g.W) + al(4ull * (g.rows + 1)) +
+                al(4ull * g.rows) + 2 * al(4ull * g.nrt) + 3 * al(4ull * g.r_cap);
+    return g;
+}
+
+struct Request {
+    seg_req id = 0;
+    seg_dims dims{};
+    uint32_t C = 0;
+    std::vector<uint32_t> minvol;
+    std::vector<VolGeom> g;
+    const uint16_t *user_dev = nullptr;  // device input owned by the caller
+    std::vector<uint16_t> host_copy;     // host input waiting for admission
+    char *block = nullptr;               // labels | feat | stat | [input]
+    size_t block_bytes = 0;
+    size_t off_labels = 0, off_feat = 0, off_stat = 0, off_input = 0;
+    size_t per_labels = 0, per_feat = 0;  // bytes per channel
+    bool owns_input = false;
+    bool admitted = false;
+    bool launched = false;
+    bool issued = false;  // launch sequence (and done_ev record) enqueued
+    int state = SEG_PENDING;
+    int err = SEG_OK;
+    size_t persist = 0, scratch = 0;
+    std::vector<uint32_t> thresh, ncells, errbits;
+    cudaEvent_t ready_ev = nullptr;  // order-stream point for device inputs
+    cudaEvent_t done_ev = nullptr;
+    double t_submit = -1, t_admit = -1, t_launch = -1, t_done = -1;
+
+    const uint16_t *input(uint32_t c) const {
+        const uint16_t *base = user_dev ? user_dev : reinterpret_cast<const uint16_t *>(block + off_input);
+        return base + (size_t)c * g[0].n;
+    }
+    uint32_t *labels(uint32_t c) const {
+        return reinterpret_cast<uint32_t *>(block + off_labels + c * per_labels);
+    }
+    seg_cell_features *feat(uint32_t c) const {
+        return reinterpret_cast<seg_cell_features *>(block + off_feat + c * per_feat);
+    }
+    uint32_t *stat(uint32_t c) const {
+        return reinterpret_cast<uint32_t *>(block + off_stat) + (size_t)c * ST_WORDS;
+    }
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    BatchHdr *h_hdr = nullptr;  // pinned
+    BatchHdr *d_hdr = nullptr;
+    uint32_t *h_stat = nullptr;  // pinned
+    uint32_t *d_stat = nullptr;
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // tile_y 8/16/32
+    cudaEvent_t ev[NUM_KERNELS + 1] = {};
+    Batch *busy = nullptr;
+};
+
+struct Batch {
+    Slot *slot = nullptr;
+    std::vector<Request *> reqs;
+    char *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    uint32_t nvol = 0;
+    uint64_t voxels = 0;
+    std::atomic<bool> done{false};
+    int launch_err = SEG_OK;
+    struct seg_ctx *ctx = nullptr;
+};
+
+}  // namespace
+}  // namespace seg
+
+using namespace seg;
+
+struct seg_ctx {
+    seg_config cfg{};
+    int device = 0;
+    int sms = 0;
+    LaunchPlan plan{};
+    uint32_t tile_z = 64;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    uint32_t cap_vols = 512;
+    bool plain = false, graphs = true, profile = false;
+    cudaStream_t copy_stream = nullptr;
+    cudaStream_t read_stream = nullptr;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request *> pending;
+    std::unordered_map<seg_req, std::unique_ptr<Request>> reqs;
+    seg_req next_id = 1;
+    bool stop = false;
+    bool flush = false;
+    Clock::time_point t0;
+    Clock::time_point first_pending;
+    std::thread worker;
+    // stats
+    uint64_t st_batches = 0, st_volumes = 0, st_voxels = 0;
+    uint64_t st_launches[NUM_KERNELS] = {};
+    double st_ms[NUM_KERNELS] = {};
+
+    double now() const {
+        return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SEG_OK;
+    if (std::getenv("SEG_DEBUG")) std::fprintf(stderr, "libseg: %s: %s\n", what, cudaGetErrorString(e));
+    return SEG_ECUDA;
+}
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t e__ = (call);                        \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+    } while (0)
+
+void CUDART_CB on_batch_done(void *p) {
+    Batch *b = static_cast<Batch *>(p);
+    seg_ctx *ctx = b->ctx;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        b->done.store(true);
+    }
+    ctx->cv.notify_all();
+}
+
+// Lays out a request's device block: labels, features, status, [input].
+void layout_request(Request &r) {
+    const VolGeom &g = r.g[0];
+    r.per_labels = al(4ull * g.n);
+    r.per_feat = al(sizeof(seg_cell_features) * g.k_cap);
+    for (uint32_t c = 1; c < r.C; ++c) r.per_feat = std::max(r.per_feat, al(sizeof(seg_cell_features) * r.g[c].k_cap));
+    size_t off = 0;
+    r.off_labels = off;
+    off += r.per_labels * r.C;
+    r.off_feat = off;
+    off += r.per_feat * r.C;
+    r.off_stat = off;
+    off += al(4ull * ST_WORDS * r.C);
+    r.off_input = off;
+    if (r.owns_input) off += al(2ull * g.n * r.C);
+    r.block_bytes = off;
+    r.persist = off;
+    r.scratch = 0;
+    for (uint32_t c = 0; c < r.C; ++c) r.scratch += r.g[c].scratch;
+}
+
+// Builds the batch descriptor on the slot's pinned header.
+void build_header(seg_ctx *ctx, Batch &b) {
+    BatchHdr *h = b.slot->h_hdr;
+    const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = ctx->tile_z;
+    uint32_t v = 0, tiles = 0, rts = 0;
+    char *sp = b.scratch;
+    for (Request *r : b.reqs) {
+        for (uint32_t c = 0; c < r->C; ++c) {
+            const VolGeom &g = r->g[c];
+            VolDev &V = h->vol[v++];
+            V.raw = r->input(c);
+            V.labels = r->labels(c);
+            V.feat = r->feat(c);
+            V.stat = r->stat(c);
+            V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
+            V.mask = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows * g.W);
+            V.rowoff = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * (g.rows + 1));
+            V.rowk = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows);
+            V.tsum = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.nrt);
+            V.tkeep = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.nrt);
+            V.run_x = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.r_cap);
+            V.run_par = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.r_cap);
+            V.run_aux = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.r_cap);
+            V.k_cap = g.k_cap;
+            V.r_cap = g.r_cap;
+            V.X = g.X; V.Y = g.Y; V.Z = g.Z; V.W = g.W;
+            V.rows = g.rows;
+            V.min_volume = r->minvol[c];
+            V.ntx = (uint32_t)cdiv(g.X, TILE_X);
+            V.nty = (uint32_t)cdiv(g.Y, ty);
+            V.ntz = (uint32_t)cdiv(g.Z, tz);
+            V.nrt = g.nrt;
+            V.tile_base = tiles;
+            V.rt_base = rts;
+            tiles += V.ntx * V.nty * V.ntz;
+            rts += g.nrt;
+        }
+    }
+    h->nvol = v;
+    h->ntiles = tiles;
+    h->nrowtiles = rts;
+    h->tile_z = tz;
+    h->tile_y = ty;
+    b.nvol = v;
+}
+
+int graph_index(int ty) { return ty == 8 ? 0 : (ty == 16 ? 1 : 2); }
+
+// Enqueues descriptor upload, the pipeline and the status read-back.
+int enqueue_body(seg_ctx *ctx, Slot &s, uint32_t nvol) {
+    const size_t hb = ctx->graphs ? batch_bytes(ctx->cap_vols) : batch_bytes(nvol);
+    const size_t sb = 4ull * ST_WORDS * (ctx->graphs ? ctx->cap_vols : nvol);
+    CK(cudaMemcpyAsync(s.d_hdr, s.h_hdr, hb, cudaMemcpyHostToDevice, s.stream));
+    CK(launch_pipeline(s.d_hdr, ctx->plan, s.stream, ctx->profile ? s.ev : nullptr, s.d_stat));
+    CK(cudaMemcpyAsync(s.h_stat, s.d_stat, sb, cudaMemcpyDeviceToHost, s.stream));
+    return SEG_OK;
+}
+
+int launch_batch(seg_ctx *ctx, Batch &b) {
+    Slot &s = *b.slot;
+    // Inputs that waited on the host are copied now (pageable source: the
+    // call returns once the data is staged).
+    for (Request *r : b.reqs) {
+        if (!r->block) {
+            CK(cudaMallocAsync(reinterpret_cast<void **>(&r->block), r->block_bytes, s.stream));
+        }
+        if (!r->host_copy.empty()) {
+            CK(cudaMemcpyAsync(r->block + r->off_input, r->host_copy.data(), r->host_copy.size() * 2,
+                               cudaMemcpyHostToDevice, s.stream));
+        }
+        if (r->ready_ev) CK(cudaStreamWaitEvent(s.stream, r->ready_ev, 0));
+    }
+    for (Request *r : b.reqs) std::vector<uint16_t>().swap(r->host_copy);
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&b.scratch), b.scratch_bytes, s.stream));
+    build_header(ctx, b);
+    if (ctx->graphs) {
+        cudaGraphExec_t &ge = s.graph[graph_index(ctx->plan.tile_y)];
+        if (!ge) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_body(ctx, s, b.nvol);
+            cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+            if (rc != SEG_OK) return rc;
+            CK(e);
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+        }
+        CK(cudaGraphLaunch(ge, s.stream));
+    } else {
+        int rc = enqueue_body(ctx, s, b.nvol);
+        if (rc != SEG_OK) return rc;
+    }
+    for (Request *r : b.reqs) CK(cudaEventRecord(r->done_ev, s.stream));
+    CK(cudaFreeAsync(b.scratch, s.stream));
+    b.scratch = nullptr;
+    CK(cudaLaunchHostFunc(s.stream, on_batch_done, &b));
+    return SEG_OK;
+}
+
+// Called with ctx->mu held, after the batch's host function ran.
+void finalize_batch(seg_ctx *ctx, Slot &s) {
+    Batch *b = s.busy;
+    const double t = ctx->now();
+    uint32_t v = 0;
+    for (Request *r : b->reqs) {
+        bool bad = b->launch_err != SEG_OK;
+        for (uint32_t c = 0; c < r->C; ++c, ++v) {
+            const uint32_t *w = s.h_stat + (size_t)v * ST_WORDS;
+            r->thresh[c] = w[ST_THRESH];
+            r->ncells[c] = w[ST_CELLS];
+            r->errbits[c] = w[ST_ERROR];
+            if (w[ST_ERROR]) bad = true;
+        }
+        r->state = bad ? SEG_FAILED : SEG_DONE;
+        r->err = bad ? (b->launch_err != SEG_OK ? b->launch_err : SEG_EFAILED) : SEG_OK;
+        r->t_done = t;
+    }
+    if (ctx->profile && b->launch_err == SEG_OK) {
+        for (int k = 0; k < NUM_KERNELS; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, s.ev[k], s.ev[k + 1]) == cudaSuccess) ctx->st_ms[k] += ms;
+        }
+    }
+    for (int k = 0; k < NUM_KERNELS; ++k) ctx->st_launches[k] += 1;
+    ctx->st_batches += 1;
+    ctx->st_volumes += b->nvol;
+    ctx->st_voxels += b->voxels;
+    ctx->used -= b->scratch_bytes;
+    s.busy = nullptr;
+    delete b;
+}
+
+void worker_main(seg_ctx *ctx) {
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    for (;;) {
+        bool progressed = false;
+        for (Slot &s : ctx->slots) {
+            if (s.busy && s.busy->done.load()) {
+                finalize_batch(ctx, s);
+                progressed = true;
+            }
+        }
+        if (progressed) ctx->cv.notify_all();
+        bool inflight = false;
+        for (Slot &s : ctx->slots) inflight |= (s.busy != nullptr);
+        if (ctx->stop && !inflight && ctx->pending.empty()) break;
+        Slot *free_slot = nullptr;
+        for (Slot &s : ctx->slots)
+            if (!s.busy) { free_slot = &s; break; }
+        if (free_slot && !ctx->pending.empty()) {
+            bool go = ctx->flush || ctx->stop || inflight || ctx->cfg.batch_window_us == 0;
+            if (!go) {
+                double waited = std::chrono::duration<double, std::micro>(Clock::now() - ctx->first_pending).count();
+                go = waited >= ctx->cfg.batch_window_us;
+            }
+            if (go) {
+                Batch *b = new Batch();
+                b->slot = free_slot;
+                b->ctx = ctx;
+                uint32_t nv = 0;
+                const uint32_t max_req = ctx->plain ? 1u : 0xFFFFFFFFu;
+                while (!ctx->pending.empty() && b->reqs.size() < max_req) {
+                    Request *r = ctx->pending.front();
+                    if (nv + r->C > ctx->cap_vols) break;
+                    size_t need = r->scratch + (r->admitted ? 0 : r->persist);
+                    if (ctx->used + need > ctx->budget) break;
+                    ctx->used += need;
+                    b->scratch_bytes += r->scratch;
+                    if (!r->admitted) { r->admitted = true; r->t_admit = ctx->now(); }
+                    r->launched = true;
+                    r->t_launch = ctx->now();
+                    nv += r->C;
+                    b->voxels += r->g[0].n * r->C;
+                    b->reqs.push_back(r);
+                    ctx->pending.pop_front();
+                }
+                if (ctx->pending.empty()) ctx->flush = false;
+                else ctx->first_pending = Clock::now();
+                if (b->reqs.empty()) {
+                    delete b;  // budget exhausted: wait for completions
+                } else {
+                    free_slot->busy = b;
+                    lk.unlock();
+                    int rc = launch_batch(ctx, *b);
+                    lk.lock();
+                    for (Request *r : b->reqs) r->issued = true;
+                    if (rc != SEG_OK) {
+                        b->launch_err = rc;
+                        // the batch may be partly enqueued: wait for the stream
+                        lk.unlock();
+                        cudaStreamSynchronize(free_slot->stream);
+                        cudaGetLastError();
+                        lk.lock();
+                        b->done.store(true);
+                    }
+                    ctx->cv.notify_all();
+                    continue;
+                }
+            }
+        }
+        if (free_slot && !ctx->pending.empty() && !ctx->flush && ctx->cfg.batch_window_us) {
+            ctx->cv.wait_for(lk, std::chrono::microseconds(std::max<uint32_t>(ctx->cfg.batch_window_us / 4, 20)));
+        } else {
+            ctx->cv.wait_for(lk, std::chrono::milliseconds(50));
+        }
+    }
+}
+
+Request *find_req(seg_ctx *ctx, seg_req id) {
+    auto it = ctx->reqs.find(id);
+    return it == ctx->reqs.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *seg_strerror(int code) {
+    switch (code) {
+        case SEG_OK: return "ok";
+        case SEG_EINVAL: return "invalid argument";
+        case SEG_ETOOBIG: return "volume too large for the limits or the HBM budget";
+        case SEG_EAGAIN: return "host queue full, retry later";
+        case SEG_ENOTREADY: return "request not finished";
+        case SEG_ETIMEOUT: return "timed out";
+        case SEG_ECUDA: return "CUDA error";
+        case SEG_ESMALL: return "destination too small";
+        case SEG_ENOENT: return "unknown request";
+        case SEG_EFAILED: return "request failed";
+        default: return "unknown error code";
+    }
+}
+
+int seg_create(const seg_config *cfg, seg_ctx **out) {
+    if (!cfg || !out) return SEG_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return SEG_EINVAL;
+    }
+    if (cfg->flags & SEG_FORCE_TILE) {
+        if (cfg->tile_y != 8 && cfg->tile_y != 16 && cfg->tile_y != 32) return SEG_EINVAL;
+        if (cfg->tile_z == 0) return SEG_EINVAL;
+    }
+    std::unique_ptr<seg_ctx> ctx(new seg_ctx());
+    ctx->cfg = *cfg;
+    ctx->device = cfg->device;
+    ctx->t0 = Clock::now();
+    CK(cudaSetDevice(cfg->device));
+    CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, cfg->device));
+    CK(configure_kernels(cfg->device));
+    ctx->plain = (cfg->flags & SEG_PLAIN) != 0;
+    ctx->graphs = !ctx->plain && !(cfg->flags & SEG_NO_GRAPH);
+    ctx->profile = (cfg->flags & SEG_PROFILE) != 0;
+    ctx->cap_vols = cfg->max_batch_volumes ? cfg->max_batch_volumes : 512;
+    const uint32_t nslots = ctx->plain ? 1 : (cfg->max_inflight ? cfg->max_inflight : 2);
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    ctx->budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (uint64_t)(0.8 * (double)fr);
+    int ty = 32;
+    uint32_t tz = 64;
+    if (cfg->flags & SEG_FORCE_TILE) { ty = (int)cfg->tile_y; tz = cfg->tile_z; }
+    ctx->tile_z = tz;
+    ctx->plan.sms = ctx->sms;
+    ctx->plan.tile_y = ty;
+    ctx->plan.grid_hist = ctx->sms;  // one resident block per SM (128 KiB histogram)
+    ctx->plan.grid_mask = ctx->sms * 4;
+    ctx->plan.grid_rows = ctx->sms * 8;
+    ctx->plan.grid_vols = ctx->sms;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->read_stream, cudaStreamNonBlocking));
+    ctx->slots.resize(nslots);
+    for (Slot &s : ctx->slots) {
+        CK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+        CK(cudaMallocHost(reinterpret_cast<void **>(&s.h_hdr), batch_bytes(ctx->cap_vols)));
+        CK(cudaMalloc(reinterpret_cast<void **>(&s.d_hdr), batch_bytes(ctx->cap_vols)));
+        CK(cudaMallocHost(reinterpret_cast<void **>(&s.h_stat), 4ull * ST_WORDS * ctx->cap_vols));
+        CK(cudaMalloc(reinterpret_cast<void **>(&s.d_stat), 4ull * ST_WORDS * ctx->cap_vols));
+        std::memset(s.h_hdr, 0, batch_bytes(ctx->cap_vols));
+        for (auto &e : s.ev) CK(cudaEventCreate(&e));
+    }
+    ctx->worker = std::thread(worker_main, ctx.get());
+    *out = ctx.release();
+    return SEG_OK;
+}
+
+int seg_destroy(seg_ctx *ctx) {
+    if (!ctx) return SEG_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv.notify_all();
+    if (ctx->worker.joinable()) ctx->worker.join();
+    cudaSetDevice(ctx->device);
+    for (auto &kv : ctx->reqs) {
+        Request &r = *kv.second;
+        if (r.block) cudaFree(r.block);
+        if (r.ready_ev) cudaEventDestroy(r.ready_ev);
+        if (r.done_ev) cudaEventDestroy(r.done_ev);
+    }
+    for (Slot &s : ctx->slots) {
+        for (auto &g : s.graph)
+            if (g) cudaGraphExecDestroy(g);
+        for (auto &e : s.ev)
+            if (e) cudaEventDestroy(e);
+        if (s.h_hdr) cudaFreeHost(s.h_hdr);
+        if (s.d_hdr) cudaFree(s.d_hdr);
+        if (s.h_stat) cudaFreeHost(s.h_stat);
+        if (s.d_stat) cudaFree(s.d_stat);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->read_stream) cudaStreamDestroy(ctx->read_stream);
+    delete ctx;
+    return SEG_OK;
+}
+
+int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_dims dims,
+                      uint32_t channels, const seg_channel_params *per_channel, seg_req *out) {
+    if (!ctx || !voxels || !out || channels == 0 || dims.x == 0 || dims.y == 0 || dims.z == 0)
+        return SEG_EINVAL;
+    const uint64_t n = (uint64_t)dims.x * dims.y * dims.z;
+    if (n >= (1ull << 32) || dims.x > 65536u) return SEG_ETOOBIG;
+    if (channels > ctx->cap_vols) return SEG_ETOOBIG;
+    std::unique_ptr<Request> r(new Request());
+    r->dims = dims;
+    r->C = channels;
+    r->minvol.resize(channels);
+    for (uint32_t c = 0; c < channels; ++c) {
+        uint32_t m = per_channel ? per_channel[c].min_volume_voxels : 30u;
+        r->minvol[c] = m ? m : 1u;  // a cell has at least one voxel
+        r->g.push_back(geom(dims, r->minvol[c]));
+    }
+    r->thresh.assign(channels, 0);
+    r->ncells.assign(channels, 0);
+    r->errbits.assign(channels, 0);
+    r->owns_input = !on_device;
+    if (on_device) r->user_dev = voxels;
+    layout_request(*r);
+    if (r->persist + r->scratch > ctx->budget) return SEG_ETOOBIG;
+    cudaSetDevice(ctx->device);
+    if (cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return SEG_ECUDA;
+    }
+    if (on_device && ctx->cfg.order_stream) {
+        if (cudaEventCreateWithFlags(&r->ready_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(r->ready_ev, static_cast<cudaStream_t>(ctx->cfg.order_stream)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventDestroy(r->done_ev);
+            return SEG_ECUDA;
+        }
+    }
+    bool copy_now = false;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r->t_submit = ctx->now();
+        uint32_t hq = ctx->cfg.host_queue ? ctx->cfg.host_queue : 4096u;
+        if (ctx->pending.size() >= hq) {
+            cudaEventDestroy(r->done_ev);
+            if (r->ready_ev) cudaEventDestroy(r->ready_ev);
+            return SEG_EAGAIN;
+        }
+        if (!on_device && ctx->used + r->persist <= ctx->budget) {
+            // reserve the request's own device memory now and copy straight
+            // from the caller's buffer
+            ctx->used += r->persist;
+            r->admitted = true;
+            r->t_admit = ctx->now();
+            copy_now = true;
+        }
+    }
+    if (!on_device) {
+        const size_t bytes = 2ull * n * channels;
+        int rc = SEG_OK;
+        if (copy_now) {
+            cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&r->block), r->block_bytes, ctx->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(r->block + r->off_input, voxels, bytes, cudaMemcpyHostToDevice, ctx->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copy_stream);
+            if (e != cudaSuccess) rc = cuda_fail(e, "submit copy");
+        } else {
+            r->host_copy.assign(voxels, voxels + n * channels);
+        }
+        if (rc != SEG_OK) {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            if (r->admitted) ctx->used -= r->persist;
+            if (r->block) cudaFreeAsync(r->block, ctx->copy_stream);
+            cudaEventDestroy(r->done_ev);
+            return rc;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r->id = ctx->next_id++;
+        *out = r->id;
+        if (ctx->pending.empty()) ctx->first_pending = Clock::now();
+        ctx->pending.push_back(r.get());
+        ctx->reqs.emplace(r->id, std::move(r));
+    }
+    ctx->cv.notify_all();
+    return SEG_OK;
+}
+
+int seg_flush(seg_ctx *ctx) {
+    if (!ctx) return SEG_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (!ctx->pending.empty()) ctx->flush = true;
+    }
+    ctx->cv.notify_all();
+    return SEG_OK;
+}
+
+int seg_poll(seg_ctx *ctx, seg_req req, uint32_t timeout_ms, int *state) {
+    if (!ctx || !state) return SEG_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    Request *r = find_req(ctx, req);
+    if (!r) return SEG_ENOENT;
+    if (r->state == SEG_PENDING && timeout_ms) {
+        ctx->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->state != SEG_PENDING; });
+    }
+    *state = r->state;
+    return r->state == SEG_PENDING ? SEG_ETIMEOUT : SEG_OK;
+}
+
+int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream) {
+    if (!ctx || !stream) return SEG_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    Request *r = find_req(ctx, req);
+    if (!r) return SEG_ENOENT;
+    if (!r->issued && r->state == SEG_PENDING) {
+        ctx->flush = true;
+        ctx->cv.notify_all();
+        ctx->cv.wait(lk, [&] { return r->issued || r->state != SEG_PENDING; });
+    }
+    cudaEvent_t ev = r->done_ev;
+    lk.unlock();
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), ev, 0);
+    return cuda_fail(e, "seg_enqueue_wait");
+}
+
+int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst, uint64_t dst_elems,
+                    int dst_on_device) {
+    if (!ctx || !dst) return SEG_EINVAL;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (r->state == SEG_PENDING) return SEG_ENOTREADY;
+        if (r->state == SEG_FAILED) return SEG_EFAILED;
+    }
+    if (channel >= r->C) return SEG_EINVAL;
+    const uint64_t n = r->g[channel].n;
+    if (dst_elems < n) return SEG_ESMALL;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpyAsync(dst, r->labels(channel), 4ull * n,
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    ctx->read_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
+    return cuda_fail(e, "seg_read_labels");
+}
+
+int seg_read_features(seg_ctx *ctx, seg_req req, uint32_t channel, seg_cell_features *dst, uint64_t cap,
+                      uint64_t *n_cells, uint16_t *otsu_threshold) {
+    if (!ctx) return SEG_EINVAL;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (r->state == SEG_PENDING) return SEG_ENOTREADY;
+        if (r->state == SEG_FAILED) return SEG_EFAILED;
+    }
+    if (channel >= r->C) return SEG_EINVAL;
+    const uint64_t k = r->ncells[channel];
+    if (n_cells) *n_cells = k;
+    if (otsu_threshold) *otsu_threshold = (uint16_t)r->thresh[channel];
+    if (!dst) return cap == 0 ? SEG_OK : SEG_EINVAL;
+    const uint64_t m = std::min<uint64_t>(k, cap);
+    if (m) {
+        cudaSetDevice(ctx->device);
+        cudaError_t e = cudaMemcpyAsync(dst, r->feat(channel), m * sizeof(seg_cell_features),
+                                        cudaMemcpyDeviceToHost, ctx->read_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "seg_read_features");
+    }
+    return cap < k ? SEG_ESMALL : SEG_OK;
+}
+
+int seg_release(seg_ctx *ctx, seg_req req) {
+    if (!ctx) return SEG_EINVAL;
+    std::unique_ptr<Request> owned;
+    {
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        Request *r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (!r->launched) {
+            auto it = std::find(ctx->pending.begin(), ctx->pending.end(), r);
+            if (it != ctx->pending.end()) ctx->pending.erase(it);
+        } else {
+            ctx->cv.wait(lk, [&] { return r->state != SEG_PENDING; });
+        }
+        if (r->admitted) ctx->used -= r->persist;
+        auto it = ctx->reqs.find(req);
+        owned = std::move(it->second);
+        ctx->reqs.erase(it);
+    }
+    cudaSetDevice(ctx->device);
+    if (owned->block) cudaFreeAsync(owned->block, ctx->copy_stream);
+    if (owned->ready_ev) cudaEventDestroy(owned->ready_ev);
+    if (owned->done_ev) cudaEventDestroy(owned->done_ev);
+    cudaGetLastError();
+    ctx->cv.notify_all();
+    return SEG_OK;
+}
+
+int seg_request_times(seg_ctx *ctx, seg_req req, double *submit_ms, double *admit_ms, double *launch_ms,
+                      double *done_ms) {
+    if (!ctx) return SEG_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Request *r = find_req(ctx, req);
+    if (!r) return SEG_ENOENT;
+    if (submit_ms) *submit_ms = r->t_submit;
+    if (admit_ms) *admit_ms = r->t_admit;
+    if (launch_ms) *launch_ms = r->t_launch;
+    if (done_ms) *done_ms = r->t_done;
+    return SEG_OK;
+}
+
+int seg_get_stats(seg_ctx *ctx, seg_stats *out) {
+    if (!ctx || !out) return SEG_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->batches = ctx->st_batches;
+    out->volumes = ctx->st_volumes;
+    out->voxels = ctx->st_voxels;
+    out->tile_y = (uint32_t)ctx->plan.tile_y;
+    out->tile_z = ctx->tile_z;
+    out->n_kernels = NUM_KERNELS;
+    for (int k = 0; k < NUM_KERNELS; ++k) {
+        std::snprintf(out->names[k], sizeof(out->names[k]), "%s", kKernelNames[k]);
+        out->launches[k] = ctx->st_launches[k];
+        out->total_ms[k] = ctx->st_ms[k];
+    }
+    out->bytes_in_use = ctx->used;
+    out->budget_bytes = ctx->budget;
+    return SEG_OK;
+}
+
+int seg_reset_stats(seg_ctx *ctx) {
+    if (!ctx) return SEG_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->st_batches = ctx->st_volumes = ctx->st_voxels = 0;
+    for (int k = 0; k < NUM_KERNELS; ++k) { ctx->st_launches[k] = 0; ctx->st_ms[k] = 0; }
+    return SEG_OK;
+}
+
+}  // extern "C"

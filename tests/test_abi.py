@@ -1,0 +1,62 @@
+"""Host-side checks of the C-ABI library: it loads without a GPU and exports
+every entry point declared in include/seg.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "seg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(seg_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "segbuild", os.path.join(ROOT, "paper_1407_2089_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    path = mod.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["seg_create", "seg_destroy", "seg_submit_volume", "seg_poll", "seg_read_labels",
+              "seg_read_features", "seg_release", "seg_strerror"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    import paper_1407_2089_gb300 as seg
+    for n in declared_functions():
+        assert hasattr(seg, n), n
+    assert set(seg.EXPORTS) == set(declared_functions())
+
+
+def test_strerror_and_null_arguments(lib):
+    lib.seg_strerror.restype = ctypes.c_char_p
+    assert lib.seg_strerror(0) == b"ok"
+    assert b"invalid" in lib.seg_strerror(-1)
+    # null arguments are rejected before any CUDA call
+    assert lib.seg_create(None, None) == -1
+    assert lib.seg_destroy(None) == -1
+    assert lib.seg_flush(None) == -1
+
+
+def test_struct_layouts():
+    import paper_1407_2089_gb300 as seg
+    assert ctypes.sizeof(seg.seg_cell_features) == 64
+    assert ctypes.sizeof(seg.seg_dims) == 12
+    assert ctypes.sizeof(seg.seg_config) == 48
