@@ -129,9 +129,11 @@ int seg_flush(seg_ctx *ctx);
  * pending, SEG_ENOENT for an unknown handle. */
 int seg_poll(seg_ctx *ctx, seg_req req, uint32_t timeout_ms, int *state);
 
-/* Makes `stream` (a cudaStream_t on the context's device) wait until the
- * request's results are complete, without blocking the host.  The request
- * must have been launched or be pending; ordering holds for either. */
+/* Makes `stream` (a cudaStream_t on the context's device; NULL is the legacy
+ * default stream) wait until the request's results are complete.  If the
+ * request has not been launched yet this flushes the queue and blocks the
+ * host until its launch sequence is enqueued; the device wait itself never
+ * blocks the host. */
 int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream);
 
 /* Copies channel `channel`'s label image (X*Y*Z uint32) to dst (host, or

@@ -112,7 +112,7 @@ def _bind(lib):
 def load_library(path: str = LIB_PATH):
     if not os.path.exists(path):
         raise ImportError("libseg.so not built (run __graft_entry__.build() or "
-                          "python -m paper_1407_2089_gb300.build): %s" % path)
+                          "python paper_1407_2089_gb300/build.py): %s" % path)
     return _bind(ctypes.CDLL(path))
 
 
@@ -209,7 +209,7 @@ def seg_wait(ctx, req, timeout_ms=600000):
 
 
 def seg_enqueue_wait(ctx, req, stream_ptr):
-    _check(_lib.seg_enqueue_wait(ctx, req, ctypes.c_void_p(stream_ptr)), "seg_enqueue_wait")
+    _check(_lib.seg_enqueue_wait(ctx, req, ctypes.c_void_p(stream_ptr or None)), "seg_enqueue_wait")
 
 
 def seg_read_labels(ctx, req, channel, out):

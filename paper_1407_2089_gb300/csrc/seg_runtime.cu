@@ -360,7 +360,7 @@ void worker_main(seg_ctx *ctx) {
         for (Slot &s : ctx->slots)
             if (!s.busy) { free_slot = &s; break; }
         if (free_slot && !ctx->pending.empty()) {
-            bool go = ctx->flush || ctx->stop || inflight || ctx->cfg.batch_window_us == 0;
+            bool go = ctx->flush || ctx->stop || ctx->cfg.batch_window_us == 0;
             if (!go) {
                 double waited = std::chrono::duration<double, std::micro>(Clock::now() - ctx->first_pending).count();
                 go = waited >= ctx->cfg.batch_window_us;
@@ -645,7 +645,7 @@ int seg_poll(seg_ctx *ctx, seg_req req, uint32_t timeout_ms, int *state) {
 }
 
 int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream) {
-    if (!ctx || !stream) return SEG_EINVAL;
+    if (!ctx) return SEG_EINVAL;
     std::unique_lock<std::mutex> lk(ctx->mu);
     Request *r = find_req(ctx, req);
     if (!r) return SEG_ENOENT;
