@@ -177,6 +177,34 @@ typedef struct {
 int seg_get_stats(seg_ctx *ctx, seg_stats *out);
 int seg_reset_stats(seg_ctx *ctx);
 
+/* Allocation-free Otsu level of one device-resident volume.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- their HBM is wholly reserved by another allocator (for
+ * example a framework's caching allocator), or they run latency-critical
+ * loops where cudaMalloc/cudaFree and their implicit synchronisation are not
+ * acceptable.  It needs no seg_ctx and calls no allocating routine.
+ *
+ *   d_voxels  device pointer, uint16 [Z][Y][X] of the current device.
+ *   d_result  device pointer to 2 uint32: [0] = Otsu level t* of the
+ *             smoothed volume (the value seg_read_features reports for the
+ *             same input), [1] = error bits (0 = ok).
+ *   stream    cudaStream_t on the current device (NULL = legacy default).
+ * Work is enqueued on `stream`; the call does not wait for it.
+ *
+ * Scratch: one fixed 262,208-byte device array per GPU (65536 histogram bins
+ * and 16 status words), held by every GPU that loads the library until the
+ * process exits.  Every call on a device shares it and it keeps the last
+ * call's contents; the call clears it on `stream` first.  Calls whose work
+ * overlaps on the GPU (different streams, or several host threads) race on it
+ * and must be serialised by the caller.  The first call on a device (with
+ * that device current) resolves the array's device address and sets kernel
+ * attributes; make that first call before any stream capture.
+ * Limits: X*Y*Z <= SEG_NOALLOC_MAX_VOXELS (the bins count in uint32) and
+ * X <= 65536, else SEG_ETOOBIG.  Other errors: SEG_EINVAL, SEG_ECUDA. */
+#define SEG_NOALLOC_MAX_VOXELS 4294967295ull
+int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dims, uint32_t *d_result,
+                               void *stream);
+
 /* Human-readable text for a return code (static storage). */
 const char *seg_strerror(int code);
 

@@ -79,7 +79,8 @@ class seg_stats(ctypes.Structure):
 
 EXPORTS = ["seg_create", "seg_destroy", "seg_submit_volume", "seg_flush", "seg_poll",
            "seg_enqueue_wait", "seg_read_labels", "seg_read_features", "seg_release",
-           "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror"]
+           "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror",
+           "seg_otsu_threshold_noalloc"]
 
 
 def _bind(lib):
@@ -99,6 +100,7 @@ def _bind(lib):
                               P(ctypes.c_double), P(ctypes.c_double)],
         "seg_get_stats": [vp, P(seg_stats)],
         "seg_reset_stats": [vp],
+        "seg_otsu_threshold_noalloc": [vp, seg_dims, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -262,6 +264,17 @@ def seg_get_stats(ctx):
 
 def seg_reset_stats(ctx):
     _check(_lib.seg_reset_stats(ctx), "seg_reset_stats")
+
+
+def seg_otsu_threshold_noalloc(voxels_ptr, dims, result_ptr, stream_ptr=None):
+    """Allocation-free Otsu level of one device volume (see include/seg.h).
+
+    voxels_ptr / result_ptr are device addresses (uint16 volume, 2 x uint32
+    result); dims = (X, Y, Z).  Enqueues on stream_ptr and returns."""
+    _check(_lib.seg_otsu_threshold_noalloc(ctypes.c_void_p(voxels_ptr), seg_dims(*dims),
+                                           ctypes.c_void_p(result_ptr),
+                                           ctypes.c_void_p(stream_ptr or None)),
+           "seg_otsu_threshold_noalloc")
 
 
 def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000):

@@ -28,6 +28,8 @@
 //                   count / bbox / coordinate sums
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
 
 #include "seg_internal.h"
 
@@ -845,3 +847,136 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
 }
 
 }  // namespace seg
+
+// ----------------------------------------------------------------------------
+// Allocation-free Otsu level (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory: their HBM is fully reserved by
+// another allocator (for example a framework's caching allocator), or they
+// run latency-critical loops in which cudaMalloc / cudaFree, with their
+// implicit synchronisation, are not acceptable.  seg_otsu_threshold_noalloc
+// serves them: it runs the histogram + Otsu kernel on one device-resident
+// volume with its scratch (the 65536-bin histogram and the status words) in
+// the fixed array below, so it allocates nothing.
+// ----------------------------------------------------------------------------
+
+namespace seg {
+namespace {
+
+constexpr int NOALLOC_WORDS = HIST_BINS + ST_WORDS;  // 262,208 bytes per device
+
+// Scratch of seg_otsu_threshold_noalloc: histogram bins, then status words.
+// Every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
+
+constexpr int NOALLOC_TY = 32;
+constexpr int NOALLOC_TZ = 64;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+// Device address of g_noalloc_scratch per device (host code must not use the
+// symbol itself: in host code it names a host-side stand-in).
+uint32_t *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mu;
+
+// The histogram kernel with its one-volume descriptor passed by value.
+template <int TY>
+__global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist_noalloc(const __grid_constant__ BatchHdr hdr) {
+    using T = Tile<TY>;
+    const BatchHdr *h = &hdr;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *sh = smem;
+    uint32_t *sraw = sh + HIST_WORDS;
+    uint32_t *spx = sraw + T::RAW_WORDS;
+    for (int i = threadIdx.x; i < HIST_WORDS / 4; i += T::NT)
+        reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const uint32_t nt = h->ntiles, G = gridDim.x;
+    const uint32_t tb = (uint32_t)(((uint64_t)nt * blockIdx.x) / G);
+    const uint32_t te = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / G);
+    if (tb >= te) return;
+    const VolDev &V = h->vol[0];
+    const int tz = (int)h->tile_z;
+    uint32_t ndone = 0;
+    for (uint32_t t = tb; t < te; ++t) {
+        const uint32_t ix = t % V.ntx, rest = t / V.ntx;
+        const uint32_t iy = rest % V.nty, iz = rest / V.nty;
+        const int z0 = (int)iz * tz;
+        const int z1 = min(z0 + tz, (int)V.Z);
+        HistEmit e{sh, V.hist, V.X, V.Y};
+        smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, sraw, spx, e);
+        ++ndone;
+    }
+    flush_hist<T::NT>(h, 0, ndone, sh);
+}
+
+// Once per device, with that device current: resolve the scratch address and
+// raise the kernel's dynamic shared-memory limit.
+int noalloc_setup(int dev, uint32_t **ptr, int *sms) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SEG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
+        e = cudaFuncSetAttribute(k_smooth_hist_noalloc<NOALLOC_TY>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)hist_smem_bytes(NOALLOC_TY));
+        if (e != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
+        g_noalloc_sms[dev] = n;
+        g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
+    return SEG_OK;
+}
+
+}  // namespace
+
+}  // namespace seg
+
+extern "C" int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dims, uint32_t *d_result,
+                                          void *stream) {
+    using namespace seg;
+    if (!d_voxels || !d_result || dims.x == 0 || dims.y == 0 || dims.z == 0) return SEG_EINVAL;
+    const uint64_t n = (uint64_t)dims.x * dims.y * dims.z;
+    if (n > SEG_NOALLOC_MAX_VOXELS || dims.x > 65536u) return SEG_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
+    uint32_t *scratch = nullptr;
+    int sms = 0;
+    int rc = noalloc_setup(dev, &scratch, &sms);
+    if (rc != SEG_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchHdr hdr;
+    std::memset(&hdr, 0, sizeof(hdr));
+    VolDev &V = hdr.vol[0];
+    V.raw = d_voxels;
+    V.hist = scratch;
+    V.stat = scratch + HIST_BINS;
+    V.X = dims.x; V.Y = dims.y; V.Z = dims.z;
+    V.ntx = (dims.x + TILE_X - 1) / TILE_X;
+    V.nty = (dims.y + NOALLOC_TY - 1) / NOALLOC_TY;
+    V.ntz = (dims.z + NOALLOC_TZ - 1) / NOALLOC_TZ;
+    hdr.nvol = 1;
+    hdr.ntiles = V.ntx * V.nty * V.ntz;
+    hdr.tile_z = NOALLOC_TZ;
+    hdr.tile_y = NOALLOC_TY;
+    // the array keeps the previous call's contents: clear bins and counters
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * NOALLOC_WORDS, s);
+    if (e == cudaSuccess) {
+        k_smooth_hist_noalloc<NOALLOC_TY><<<sms, 16 * NOALLOC_TY, hist_smem_bytes(NOALLOC_TY), s>>>(hdr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_result, scratch + HIST_BINS + ST_THRESH, sizeof(uint32_t),
+                            cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_result + 1, scratch + HIST_BINS + ST_ERROR, sizeof(uint32_t),
+                            cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
+    return SEG_OK;
+}
