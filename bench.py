@@ -233,7 +233,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(dev)  # ordering stream (a non-null handle)
     flags = seg.SEG_PROFILE
     ctx = seg.seg_create(device=local, flags=flags, batch_window_us=2_000_000, order_stream=stream.cuda_stream,
-                         max_inflight=2)
+                         max_inflight=args.inflight)
 
     def step(ctx, in_ptr_fn):
         reqs = []
@@ -383,6 +383,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--inflight", type=int, default=1,
+                    help="batches in flight; 1 keeps per-kernel CUDA-event times free of overlap")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -26,6 +26,7 @@ enum ErrBits : uint32_t {
     ERR_KCAP = 1u << 1,    // more cells than the feature buffer holds
     ERR_RCAP = 1u << 2,    // more runs than the run buffer holds
     ERR_OTSU = 1u << 3,    // histogram total differs from the voxel count
+    ERR_TIMEOUT = 1u << 4, // a bounded wait on an asynchronous copy gave up
 };
 
 constexpr int TILE_X = 64;        // smoothing tile width (outputs along x)
@@ -39,6 +40,7 @@ struct VolDev {
     seg_cell_features *feat;  // k_cap cells output
     uint32_t *stat;           // ST_WORDS words
     uint32_t *hist;           // 65536 uint32 bins
+    uint16_t *smooth;         // [Z][Y][X] smoothed voxels (pass 1 -> threshold pass)
     uint32_t *mask;           // rows x W words, bit b of word w is x = 32w + b
     uint32_t *rowoff;         // rows + 1: run count per row, then run offsets
     uint32_t *rowk;           // rows: kept-root count per row, then label base
@@ -74,14 +76,13 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 13;
+constexpr int NUM_KERNELS = 12;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {
     int sms;             // multiprocessors on the device
     int tile_y;          // 8, 16 or 32
     int grid_hist;       // persistent grid of the histogram kernel
-    int grid_mask;
     int grid_rows;       // row-tile kernels
     int grid_vols;       // per-volume kernels
 };
@@ -95,7 +96,6 @@ cudaError_t launch_pipeline(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaS
 
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);
-size_t mask_smem_bytes(int tile_y);
 cudaError_t configure_kernels(int device);
 
 }  // namespace seg

@@ -8,13 +8,14 @@
 // Pipeline for one batch of volume-channels (all kernels walk the batch
 // descriptor, so one launch sequence serves any mix of volume sizes):
 //   init            zero histograms and status words
-//   smooth_hist     pass 1 over the raw voxels: binomial smoothing in
-//                   registers/shared memory, 65536-bin shared histogram
-//                   (two 16-bit counters per word), merge into the volume's
-//                   histogram; the last block of a volume runs Otsu
-//   smooth_mask     pass 2: smoothing again, foreground = s > t*, written as
-//                   a bit mask (32 voxels per word along x)
-//   row_count       foreground runs per x-row
+//   smooth_hist     the one pass over the raw voxels: binomial smoothing in
+//                   shared memory and registers, the smoothed volume written
+//                   as uint16, a 65536-bin shared histogram (two 16-bit
+//                   counters per word) merged into the volume's histogram;
+//                   the last block of a volume runs Otsu
+//   threshold_runs  streaming pass over the smoothed volume: foreground =
+//                   s > t*, written as a bit mask (32 voxels per word along
+//                   x), foreground runs counted per x-row
 //   scan_runs       per-volume scan of run counts over row tiles
 //   row_runs        run table (x0, x1) per row; union-find parent = self
 //   union           26-adjacency between runs of neighbouring rows, union by
@@ -36,13 +37,16 @@
 namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
-    "init",     "smooth_hist_otsu", "smooth_mask", "row_count", "scan_runs",      "row_runs", "union",
-    "flatten",  "keep_count",       "scan_keep",   "rank",      "label_features", "gather_stat"};
+    "init",    "smooth_hist_otsu", "threshold_runs", "scan_runs", "row_runs",       "union",
+    "flatten", "keep_count",       "scan_keep",      "rank",      "label_features", "gather_stat"};
 
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int HIST_WORDS = HIST_BINS / 2;  // two 16-bit counters per word
+// Shared histogram: levels below HIST_LOW have a 32-bit counter each; the
+// rest share words as two 16-bit counters.
+constexpr int HIST_LOW = 16384;
+constexpr int HIST_WORDS = HIST_LOW + (HIST_BINS - HIST_LOW) / 2;
 constexpr uint32_t UNION_LIMIT = 1u << 24;
 
 // ----------------------------------------------------------------------------
@@ -128,10 +132,19 @@ __device__ __forceinline__ uint32_t find_bit(const uint32_t *__restrict__ row, u
 // union-find over runs (parent index <= own index at all times)
 // ----------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t uf_find(const uint32_t *P, uint32_t x) {
+// Root of x with path halving: every visited node is re-pointed at its
+// grandparent.  The store can only replace a parent by one of its ancestors
+// (all parents point to lower indices), so it never breaks a path; if it
+// overwrites a concurrent atomicMin, that union sees old != root and retries
+// from the old parent, so no link is lost.  Reads go through L2 (ld.cg):
+// parents change under other SMs and a stale L1 copy could stall a retry.
+__device__ __forceinline__ uint32_t uf_find(uint32_t *P, uint32_t x) {
     uint32_t p = __ldcg(P + x);
     while (p != x) {
-        x = p;
+        const uint32_t g = __ldcg(P + p);
+        if (g == p) return p;
+        __stcg(P + x, g);
+        x = g;
         p = __ldcg(P + x);
     }
     return x;
@@ -159,82 +172,153 @@ __device__ __forceinline__ void uf_union(uint32_t *P, uint32_t a, uint32_t b, ui
 }
 
 // ----------------------------------------------------------------------------
+// 16-byte asynchronous global -> shared copies (cp.async, LDGSTS)
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// src and dst 16-byte aligned; cached in L2 only.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until at most N of this thread's committed groups are outstanding.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ----------------------------------------------------------------------------
 // separable binomial smoothing of one tile (shared by both passes)
 // ----------------------------------------------------------------------------
 //
 // A block of 16*TY threads owns a TILE_X x TY column of outputs and marches
-// along z from z0 - 2 to z1 + 1.  For each input plane it stages the
-// (TY+4) x (TILE_X+4) clamped halo in shared memory as uint32, runs the x
-// pass (each thread 4 adjacent outputs from 8 staged values), then the y pass
-// (5 rows), and feeds the z pass in scatter form: with accumulators a0..a3
-// holding the partial sums of outputs zi-2..zi+1,
+// along z from z0 - 2 to z1 + 1.  Input planes stream through a ring of S
+// shared-memory stages, S - 1 planes ahead of use.  For each of the plane's
+// TY+4 halo rows the 16-byte-aligned 160-byte window holding the row's 68
+// needed voxels is copied as ten 16-byte cp.async chunks (one chunk per
+// thread); the row's offset inside its window (0..7 voxels) is kept per row,
+// so any X and any base alignment work.  Rows whose window would leave the
+// volume's buffer (first and last rows of a volume) are read with plain loads
+// instead.  Each plane is re-laid out as uint32 with the per-axis edge
+// clamping, then the x pass (each thread 4 adjacent outputs from 8 values),
+// the y pass (5 rows) and the z pass run; the z pass is in scatter form: with
+// accumulators a0..a3 holding the partial sums of outputs zi-2..zi+1,
 //     out(zi-2) = a0 + P, a0 <- a1 + 4P, a1 <- a2 + 6P, a2 <- a3 + 4P, a3 <- P.
 // All sums are exact in uint32 (at most 4096 * 65535); the one rounding
 // (S + 2048) >> 12 is applied to the completed sum, which equals the 125-term
-// definition.  Clamped coordinates replicate edge voxels per axis.
+// definition.
 
 template <int TY>
 struct Tile {
     static constexpr int NT = 16 * TY;
     static constexpr int RH = TY + 4;
-    static constexpr int RW = TILE_X + 8;  // staged row stride in words
-    static constexpr int CW = TILE_X + 4;  // staged columns
-    static constexpr int NLOAD = RH * CW;
-    static constexpr int LPT = (NLOAD + NT - 1) / NT;
-    static constexpr int RAW_WORDS = RH * RW;
+    static constexpr int PX_WORDS = RH * TILE_X;
+    static constexpr int XITEMS = RH * (TILE_X / 4);  // x-pass quads per plane
+    static constexpr int S = 4;              // ring stages
+    static constexpr int ROWB = 160;         // bytes staged per halo row
+    static constexpr int ROWE = ROWB / 2;    // voxels per staged row
+    static constexpr int CHUNKS = ROWB / 16; // 16-byte copies per row
+    static constexpr int STAGE_BYTES = RH * ROWB;
+    static constexpr int RING_BYTES = S * STAGE_BYTES;
+    static constexpr int SHIFT_BYTES = (S * RH + 15) / 16 * 16;
+    // dynamic shared memory without / with the 160 KiB histogram
+    static constexpr size_t MASK_SMEM = RING_BYTES + 4 * PX_WORDS + SHIFT_BYTES;
+    static constexpr size_t HIST_SMEM = MASK_SMEM + 4 * (size_t)HIST_WORDS;
+    static_assert(RH * CHUNKS <= NT, "one chunk per thread per plane");
 };
+
+struct Ring {
+    unsigned char *stage;  // S stages of RH rows x ROWB bytes
+    int8_t *shift;         // per stage and row: voxel offset in the window, -1 = plain loads
+    uint32_t pc;           // planes consumed by this block so far
+};
+
+// x pass of one quad: 4 adjacent outputs from 8 consecutive inputs.
+__device__ __forceinline__ uint4 xpass(const uint32_t *v) {
+    uint4 o;
+    o.x = v[0] + 4u * v[1] + 6u * v[2] + 4u * v[3] + v[4];
+    o.y = v[1] + 4u * v[2] + 6u * v[3] + 4u * v[4] + v[5];
+    o.z = v[2] + 4u * v[3] + 6u * v[4] + 4u * v[5] + v[6];
+    o.w = v[3] + 4u * v[4] + 6u * v[5] + 4u * v[6] + v[7];
+    return o;
+}
 
 template <int TY, class Emit>
 __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, uint32_t X, uint32_t Y,
                                             uint32_t Z, int x0, int y0, int z0, int z1,
-                                            uint32_t *__restrict__ sraw, uint32_t *__restrict__ spx,
-                                            Emit &emit) {
+                                            uint32_t *__restrict__ spx, Ring &R, Emit &emit) {
     using T = Tile<TY>;
     const int tid = threadIdx.x;
     const int q = tid & 15, ty = tid >> 4;
-    uint32_t goff[T::LPT];
-    int soff[T::LPT];
-#pragma unroll
-    for (int k = 0; k < T::LPT; ++k) {
-        const int e = tid + k * T::NT;
-        if (e < T::NLOAD) {
-            const int r = e / T::CW, c = e - r * T::CW;
-            const int gx = min(max(x0 - 2 + c, 0), (int)X - 1);
-            const int gy = min(max(y0 - 2 + r, 0), (int)Y - 1);
-            goff[k] = (uint32_t)gy * X + (uint32_t)gx;
-            soff[k] = r * T::RW + c;
-        } else {
-            goff[k] = 0;
-            soff[k] = -1;
-        }
-    }
-    const size_t plane = (size_t)X * Y;
-    uint32_t pre[T::LPT];
-    auto fetch = [&](int zi) {
-        const uint16_t *p = raw + (size_t)min(max(zi, 0), (int)Z - 1) * plane;
-#pragma unroll
-        for (int k = 0; k < T::LPT; ++k)
-            if (soff[k] >= 0) pre[k] = __ldg(p + goff[k]);
+    const int n = z1 - z0 + 4;
+    const uint64_t plane = (uint64_t)X * Y;
+    const uintptr_t lo = (uintptr_t)raw, hi = lo + 2 * plane * Z;
+    const bool interior = x0 >= 2 && x0 + TILE_X + 2 <= (int)X;
+    // this thread's copy chunk: halo row cr, 16-byte piece cc; byte offset of
+    // the row's first needed voxel inside a plane
+    const int cr = tid / T::CHUNKS, cc = tid - cr * T::CHUNKS;
+    const bool copier = tid < T::RH * T::CHUNKS;
+    const int64_t crow = 2 * ((int64_t)min(max(y0 - 2 + cr, 0), (int)Y - 1) * X + (x0 - 2));
+    auto issue = [&](int zi, uint32_t st) {
+        if (!copier) return;
+        const uintptr_t addr = lo + 2 * (uint64_t)min(max(zi, 0), (int)Z - 1) * plane + (uintptr_t)crow;
+        const uintptr_t a16 = addr & ~(uintptr_t)15;
+        const bool inside = a16 >= lo && a16 + T::ROWB <= hi;
+        if (cc == 0) R.shift[st * T::RH + cr] = inside ? (int8_t)((addr - a16) >> 1) : (int8_t)-1;
+        if (inside)
+            cp_async16(R.stage + st * T::STAGE_BYTES + cr * T::ROWB + cc * 16,
+                       reinterpret_cast<const void *>(a16 + 16 * cc));
     };
-    uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0}, a3[4] = {0, 0, 0, 0};
-    fetch(z0 - 2);
-    for (int zi = z0 - 2; zi < z1 + 2; ++zi) {
-        __syncthreads();
+    emit.bind(x0 + 4 * q, y0 + ty);
+    __syncthreads();  // the previous tile is done with the ring and spx
 #pragma unroll
-        for (int k = 0; k < T::LPT; ++k)
-            if (soff[k] >= 0) sraw[soff[k]] = pre[k];
-        __syncthreads();
-        if (zi + 1 < z1 + 2) fetch(zi + 1);
-        for (int r = ty; r < T::RH; r += TY) {
-            const uint4 u = *reinterpret_cast<const uint4 *>(sraw + r * T::RW + 4 * q);
-            const uint4 w = *reinterpret_cast<const uint4 *>(sraw + r * T::RW + 4 * q + 4);
-            uint4 o;
-            o.x = u.x + 4u * u.y + 6u * u.z + 4u * u.w + w.x;
-            o.y = u.y + 4u * u.z + 6u * u.w + 4u * w.x + w.y;
-            o.z = u.z + 4u * u.w + 6u * w.x + 4u * w.y + w.z;
-            o.w = u.w + 4u * w.x + 6u * w.y + 4u * w.z + w.w;
-            *reinterpret_cast<uint4 *>(spx + r * TILE_X + 4 * q) = o;
+    for (int j = 0; j < T::S - 1; ++j) {
+        if (j < n) issue(z0 - 2 + j, (R.pc + j) % T::S);
+        cp_async_commit();
+    }
+    uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0}, a3[4] = {0, 0, 0, 0};
+    for (int k = 0; k < n; ++k) {
+        const int zi = z0 - 2 + k;
+        const uint32_t st = (R.pc + k) % T::S;
+        cp_async_wait<T::S - 2>();  // this thread's chunks of plane k have landed
+        __syncthreads();            // everyone's have; the y pass of k-1 is done with spx
+        const unsigned char *stage = R.stage + st * T::STAGE_BYTES;
+        const int8_t *sh = R.shift + st * T::RH;
+        for (int it = tid; it < T::XITEMS; it += T::NT) {
+            const int r = it >> 4, qq = it & 15;
+            const int s = sh[r];
+            uint32_t v[8];
+            if (interior && s >= 0) {
+                // 8 voxels from a 2-byte-aligned offset: 5 words, byte_perm by parity
+                const int o = r * T::ROWE + s + 4 * qq;
+                const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (o >> 1);
+                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+                const uint32_t sel = (o & 1) ? 0x5432u : 0x3210u;
+                const uint32_t p0 = __byte_perm(w0, w1, sel), p1 = __byte_perm(w1, w2, sel);
+                const uint32_t p2 = __byte_perm(w2, w3, sel), p3 = __byte_perm(w3, w4, sel);
+                v[0] = p0 & 0xFFFFu; v[1] = p0 >> 16; v[2] = p1 & 0xFFFFu; v[3] = p1 >> 16;
+                v[4] = p2 & 0xFFFFu; v[5] = p2 >> 16; v[6] = p3 & 0xFFFFu; v[7] = p3 >> 16;
+            } else {
+                // edge tile or a row read with plain loads: clamp every x
+                const uint16_t *st16 = reinterpret_cast<const uint16_t *>(stage) + r * T::ROWE;
+                const uint64_t rowg = ((uint64_t)min(max(zi, 0), (int)Z - 1) * Y +
+                                       (uint64_t)min(max(y0 - 2 + r, 0), (int)Y - 1)) * X;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int x = min(max(x0 - 2 + 4 * qq + j, 0), (int)X - 1);
+                    v[j] = s >= 0 ? (uint32_t)st16[x - (x0 - 2) + s] : (uint32_t)__ldg(raw + rowg + x);
+                }
+            }
+            *reinterpret_cast<uint4 *>(spx + r * TILE_X + 4 * qq) = xpass(v);
         }
+        // the stage of plane k-1 was last read before the barrier above
+        if (k + T::S - 1 < n) issue(zi + T::S - 1, (R.pc + k + T::S - 1) % T::S);
+        cp_async_commit();
         __syncthreads();
         const uint4 r0 = *reinterpret_cast<const uint4 *>(spx + (ty + 0) * TILE_X + 4 * q);
         const uint4 r1 = *reinterpret_cast<const uint4 *>(spx + (ty + 1) * TILE_X + 4 * q);
@@ -256,52 +340,67 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
             a3[j] = p[j];
             s[j] = (out + 2048u) >> 12;
         }
-        if (zi >= z0 + 2) emit(x0 + 4 * q, y0 + ty, zi - 2, s);
+        emit(zi - 2, zi >= z0 + 2, s);
     }
+    cp_async_wait<0>();  // only empty groups remain; keeps the count at zero between tiles
+    R.pc += (uint32_t)n;
 }
 
-// Histogram emit: two 16-bit counters per shared word.  The thread whose
-// increment takes a counter to 0x8000 moves 0x8000 to the global bin, so a
-// counter never exceeds 0x8000 + (increments in flight) < 0x10000 and never
-// carries into its neighbour.
+// Histogram emit.  Levels below HIST_LOW (where microscope data live) count
+// in 32-bit shared words; higher levels share words as two 16-bit counters,
+// and the thread whose increment takes such a counter to 0x8000 moves 0x8000
+// to the global bin, so a counter never exceeds 0x8000 + (increments in
+// flight) < 0x10000 and never carries into its neighbour.  With STORE the smoothed voxels are also
+// written (8-byte stores when rows are 8-byte aligned).  bind() fixes, per
+// tile, which of the thread's 4 voxels lie inside the volume.
+template <bool STORE>
 struct HistEmit {
     uint32_t *sh;
     uint32_t *gh;
+    uint16_t *sm;       // smoothed volume (STORE only)
     uint32_t X, Y;
-    __device__ __forceinline__ void operator()(int xb, int y, int z, const uint32_t *s) {
-        if ((uint32_t)y >= Y) return;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if ((uint32_t)(xb + j) < X) {
-                const uint32_t v = s[j];
-                const uint32_t sft = (v & 1u) << 4;
-                const uint32_t old = atomicAdd(sh + (v >> 1), 1u << sft);
-                if (((old >> sft) & 0xFFFFu) == 0x7FFFu) {
-                    atomicSub(sh + (v >> 1), 0x8000u << sft);
-                    atomicAdd(gh + v, 0x8000u);
-                }
-            }
+    uint32_t valid;     // bit j: voxel j of the quad is inside the volume
+    uint16_t *row;      // &sm[y * X + xb] at z = 0
+    size_t zstride;     // voxels per z-plane
+    bool vec;           // all 4 inside and 8-byte aligned
+    __device__ __forceinline__ void bind(int xb, int y) {
+        valid = 0;
+        if ((uint32_t)y < Y)
+            for (int j = 0; j < 4; ++j) valid |= ((uint32_t)(xb + j) < X ? 1u : 0u) << j;
+        if (STORE) {
+            zstride = (size_t)X * Y;
+            row = sm + ((size_t)(valid ? (uint32_t)y : 0u) * X + (uint32_t)xb);
+            vec = valid == 0xFu && (X & 3u) == 0u;
         }
     }
-};
-
-// Mask emit: 4 bits per thread, 8 lanes form one 32-bit word.
-struct MaskEmit {
-    uint32_t *mask;
-    uint32_t X, Y, W, t;
-    __device__ __forceinline__ void operator()(int xb, int y, int z, const uint32_t *s) {
-        uint32_t nib = 0;
+    __device__ __forceinline__ void operator()(int z, bool live, const uint32_t *s) {
+        if (!live) return;
+        if (STORE) {
+            uint16_t *p = row + (size_t)(uint32_t)z * zstride;
+            if (vec) {
+                *reinterpret_cast<uint2 *>(p) = make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
+            } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if ((uint32_t)(xb + j) < X && s[j] > t) nib |= 1u << j;
-        const int lane = threadIdx.x & 31;
-        uint32_t word = nib << (4 * (lane & 7));
-        word |= __shfl_xor_sync(FULL, word, 1);
-        word |= __shfl_xor_sync(FULL, word, 2);
-        word |= __shfl_xor_sync(FULL, word, 4);
-        if ((lane & 7) == 0 && (uint32_t)y < Y) {
-            const uint32_t wi = (uint32_t)xb >> 5;
-            if (wi < W) mask[((size_t)z * Y + (uint32_t)y) * W + wi] = word;
+                for (int j = 0; j < 4; ++j)
+                    if (valid & (1u << j)) p[j] = (uint16_t)s[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (valid & (1u << j)) {
+                const uint32_t v = s[j];
+                if (v < (uint32_t)HIST_LOW) {
+                    atomicAdd(sh + v, 1u);
+                } else {
+                    const uint32_t w = HIST_LOW + ((v - HIST_LOW) >> 1);
+                    const uint32_t sft = (v & 1u) << 4;
+                    const uint32_t old = atomicAdd(sh + w, 1u << sft);
+                    if (((old >> sft) & 0xFFFFu) == 0x7FFFu) {
+                        atomicSub(sh + w, 0x8000u << sft);
+                        atomicAdd(gh + v, 0x8000u);
+                    }
+                }
+            }
         }
     }
 };
@@ -422,12 +521,19 @@ __device__ void flush_hist(const BatchHdr *__restrict__ h, uint32_t v, uint32_t 
         uint4 w = reinterpret_cast<uint4 *>(sh)[i];
         if (w.x | w.y | w.z | w.w) {
             reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
-            const uint32_t b = 8u * (uint32_t)i;
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+            const uint32_t wi = 4u * (uint32_t)i;
+            if (wi < (uint32_t)HIST_LOW) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (ws[j] & 0xFFFFu) atomicAdd(V.hist + b + 2 * j, ws[j] & 0xFFFFu);
-                if (ws[j] >> 16) atomicAdd(V.hist + b + 2 * j + 1, ws[j] >> 16);
+                for (int j = 0; j < 4; ++j)
+                    if (ws[j]) atomicAdd(V.hist + wi + j, ws[j]);
+            } else {
+                const uint32_t b = HIST_LOW + 2u * (wi - HIST_LOW);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (ws[j] & 0xFFFFu) atomicAdd(V.hist + b + 2 * j, ws[j] & 0xFFFFu);
+                    if (ws[j] >> 16) atomicAdd(V.hist + b + 2 * j + 1, ws[j] >> 16);
+                }
             }
         }
     }
@@ -467,10 +573,12 @@ __global__ void k_init(const BatchHdr *__restrict__ h) {
 template <int TY>
 __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist(const BatchHdr *__restrict__ h) {
     using T = Tile<TY>;
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *sh = smem;
-    uint32_t *sraw = sh + HIST_WORDS;
-    uint32_t *spx = sraw + T::RAW_WORDS;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char *ring = dsm;
+    uint32_t *sh = reinterpret_cast<uint32_t *>(dsm + T::RING_BYTES);
+    uint32_t *spx = sh + HIST_WORDS;
+    int8_t *shift = reinterpret_cast<int8_t *>(spx + T::PX_WORDS);
+    Ring R{ring, shift, 0};
     for (int i = threadIdx.x; i < HIST_WORDS / 4; i += T::NT)
         reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
@@ -493,52 +601,98 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist(const BatchHdr *__re
         const uint32_t iy = rest % V.nty, iz = rest / V.nty;
         const int z0 = (int)iz * tz;
         const int z1 = min(z0 + tz, (int)V.Z);
-        HistEmit e{sh, V.hist, V.X, V.Y};
-        smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, sraw, spx, e);
+        HistEmit<true> e{sh, V.hist, V.smooth, V.X, V.Y, 0u, nullptr, 0, false};
+        smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
         ++ndone;
     }
     flush_hist<T::NT>(h, v, ndone, sh);
 }
 
-template <int TY>
-__global__ void __launch_bounds__(16 * TY) k_smooth_mask(const BatchHdr *__restrict__ h) {
-    using T = Tile<TY>;
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *sraw = smem;
-    uint32_t *spx = sraw + T::RAW_WORDS;
-    const int tz = (int)h->tile_z;
-    for (uint32_t t = blockIdx.x; t < h->ntiles; t += gridDim.x) {
-        const uint32_t v = find_vol_tile(h, t);
-        const VolDev &V = h->vol[v];
-        const uint32_t tl = t - V.tile_base;
-        const uint32_t ix = tl % V.ntx, rest = tl / V.ntx;
-        const uint32_t iy = rest % V.nty, iz = rest / V.nty;
-        const int z0 = (int)iz * tz;
-        const int z1 = min(z0 + tz, (int)V.Z);
-        MaskEmit e{V.mask, V.X, V.Y, V.W, V.stat[ST_THRESH]};
-        smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, sraw, spx, e);
-    }
-}
-
-__global__ void __launch_bounds__(ROW_TILE) k_row_count(const BatchHdr *__restrict__ h) {
-    __shared__ uint32_t sbuf[33];
+// Threshold + run count, streaming over the smoothed volume.  One block per
+// row tile, one warp per row at a time: foreground bits s > t* are gathered
+// into mask words (ballot, or 8 voxels per lane with 16-byte loads when rows
+// are 16-byte aligned), and run starts (a set bit whose left neighbour is
+// clear, across word boundaries) are counted per row.  The row counts and the
+// row tile's total feed the run scan.
+__global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__restrict__ h) {
+    constexpr int WARPS = ROW_TILE / 32;
+    __shared__ uint32_t wsum[WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[find_vol_rt(h, rt)];
         const uint32_t lt = rt - V.rt_base;
-        const uint32_t row = lt * ROW_TILE + threadIdx.x;
-        uint32_t cnt = 0;
-        if (row < V.rows) {
-            const uint32_t *m = V.mask + (size_t)row * V.W;
-            uint32_t carry = 0;
-            for (uint32_t w = 0; w < V.W; ++w) {
-                const uint32_t x = m[w];
-                cnt += __popc(x & ~((x << 1) | carry));
-                carry = x >> 31;
+        const uint32_t row0 = lt * ROW_TILE;
+        const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
+        const uint32_t X = V.X, W = V.W, t = V.stat[ST_THRESH];
+        const bool vec = (X & 7u) == 0u;
+        uint32_t wtot = 0;
+        for (uint32_t rr = warp; rr < nrows; rr += WARPS) {
+            const uint32_t row = row0 + rr;
+            const uint16_t *src = V.smooth + (size_t)row * X;
+            uint32_t *dst = V.mask + (size_t)row * W;
+            uint32_t carry = 0, cnt = 0;
+            if (vec) {
+                // up to 4 x 256 voxels per lane batch: all loads first
+                for (uint32_t xb0 = 0; xb0 < X; xb0 += 1024) {
+                    uint4 q4[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t x = xb0 + 256u * c + 8u * (uint32_t)lane;
+                        q4[c] = x < X ? __ldcs(reinterpret_cast<const uint4 *>(src + x)) : make_uint4(0, 0, 0, 0);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t xb = xb0 + 256u * c;
+                        if (xb >= X) break;
+                        const uint32_t x = xb + 8u * (uint32_t)lane;
+                        uint32_t bits = 0;
+                        if (x < X) {
+                            const uint32_t w4[4] = {q4[c].x, q4[c].y, q4[c].z, q4[c].w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                bits |= ((w4[j] & 0xFFFFu) > t ? 1u : 0u) << (2 * j);
+                                bits |= ((w4[j] >> 16) > t ? 1u : 0u) << (2 * j + 1);
+                            }
+                        }
+                        // lanes 4g..4g+3 hold the 32 bits of word g of this chunk
+                        uint32_t word = bits << (8 * (lane & 3));
+                        word |= __shfl_xor_sync(FULL, word, 1);
+                        word |= __shfl_xor_sync(FULL, word, 2);
+                        const uint32_t prev = __shfl_up_sync(FULL, word, 4);
+                        const uint32_t left = lane < 4 ? carry : (prev >> 31);
+                        const uint32_t wi = (xb >> 5) + ((uint32_t)lane >> 2);
+                        if ((lane & 3) == 0 && wi < W) {
+                            dst[wi] = word;
+                            cnt += __popc(word & ~((word << 1) | left));
+                        }
+                        carry = __shfl_sync(FULL, word, 28) >> 31;
+                    }
+                }
+            } else {
+                for (uint32_t xb = 0; xb < X; xb += 32) {
+                    const uint32_t x = xb + (uint32_t)lane;
+                    const bool on = x < X && __ldcs(src + x) > t;
+                    const uint32_t word = __ballot_sync(FULL, on);
+                    if (lane == 0) {
+                        dst[xb >> 5] = word;
+                        cnt += __popc(word & ~((word << 1) | carry));
+                    }
+                    carry = word >> 31;
+                }
             }
-            V.rowoff[row] = cnt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+            if (lane == 0) V.rowoff[row] = cnt;
+            wtot += cnt;
         }
-        const uint32_t tot = block_sum<ROW_TILE>(cnt, sbuf);
-        if (threadIdx.x == 0) V.tsum[lt] = tot;
+        if (lane == 0) wsum[warp] = wtot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < WARPS; ++w) tot += wsum[w];
+            V.tsum[lt] = tot;
+        }
+        __syncthreads();
     }
 }
 
@@ -708,48 +862,138 @@ __global__ void __launch_bounds__(ROW_TILE) k_rank(const BatchHdr *__restrict__ 
     }
 }
 
+// Per-block aggregation of cell features: an open-addressed table keyed by
+// label in shared memory; a run whose label finds no slot within FEAT_PROBES
+// probes goes straight to global atomics.
+constexpr int FEAT_SLOTS = 256;
+constexpr int FEAT_PROBES = 8;
+
+struct FeatTable {
+    uint32_t key[FEAT_SLOTS];
+    unsigned long long cnt[FEAT_SLOTS], sx[FEAT_SLOTS], sy[FEAT_SLOTS], sz[FEAT_SLOTS];
+    uint32_t mn[3][FEAT_SLOTS], mx[3][FEAT_SLOTS];
+};
+
+__device__ __forceinline__ void feat_global(seg_cell_features *f, unsigned long long cnt, unsigned long long sx,
+                                            unsigned long long sy, unsigned long long sz, const uint32_t *mn,
+                                            const uint32_t *mx) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(&f->count), cnt);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&f->sum[0]), sx);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&f->sum[1]), sy);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&f->sum[2]), sz);
+    for (int a = 0; a < 3; ++a) {
+        atomicMin(&f->bbox_min[a], mn[a]);
+        atomicMax(&f->bbox_max[a], mx[a]);
+    }
+}
+
+// One block per row tile (256 consecutive rows; their labels are one
+// contiguous range).  Phase 1, one thread per run: label of the run's root,
+// stored back on the run, and the run's contribution to its cell (count,
+// coordinate sums, bounding box) folded into the shared table.  Phase 2:
+// table -> global cells.  Phase 3, one warp per row: the row's labels, with
+// 16-byte streaming stores when rows are 16-byte aligned (X % 4 == 0).
 __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__restrict__ h) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int WARPS = ROW_TILE / 32;
+    __shared__ uint32_t soff[ROW_TILE + 1];
+    __shared__ FeatTable T;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[find_vol_rt(h, rt)];
         const uint32_t lt = rt - V.rt_base;
-        for (uint32_t rr = warp; rr < ROW_TILE; rr += WARPS) {
-            const uint32_t row = lt * ROW_TILE + rr;
-            if (row >= V.rows) break;
-            const uint32_t X = V.X;
-            uint32_t *out = V.labels + (size_t)row * X;
-            const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
-            if (ib == ie) {
-                for (uint32_t x = lane; x < X; x += 32) out[x] = 0u;
-                continue;
+        const uint32_t row0 = lt * ROW_TILE;
+        const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
+        __syncthreads();  // previous tile done with soff and T
+        for (uint32_t i = tid; i <= nrows; i += ROW_TILE) soff[i] = V.rowoff[row0 + i];
+        T.key[tid] = 0u;
+        T.cnt[tid] = T.sx[tid] = T.sy[tid] = T.sz[tid] = 0ull;
+        for (int a = 0; a < 3; ++a) {
+            T.mn[a][tid] = 0xFFFFFFFFu;
+            T.mx[a][tid] = 0u;
+        }
+        __syncthreads();
+        const uint32_t rb = soff[0], re = soff[nrows];
+        for (uint32_t j = rb + tid; j < re; j += ROW_TILE) {
+            // row of run j: the last i with soff[i] <= j
+            uint32_t lo = 0, hi = nrows;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (soff[mid] <= j) lo = mid; else hi = mid;
             }
+            const uint32_t lab = V.run_aux[V.run_par[j]];
+            V.run_aux[j] = lab;
+            if (!lab || lab > V.k_cap) continue;
+            const uint32_t row = row0 + lo;
             const uint32_t y = row % V.Y, z = row / V.Y;
-            for (uint32_t r = ib + lane; r < ie; r += 32) {
-                const uint32_t lab = V.run_aux[V.run_par[r]];
-                if (!lab || lab > V.k_cap) continue;
-                const uint32_t rx = V.run_x[r];
-                const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
-                const unsigned long long len = x1 - x0 + 1u;
-                seg_cell_features *f = V.feat + (lab - 1);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&f->count), len);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&f->sum[0]),
-                          ((unsigned long long)(x0 + x1) * len) >> 1);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&f->sum[1]), len * y);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&f->sum[2]), len * z);
-                atomicMin(&f->bbox_min[0], x0);
-                atomicMax(&f->bbox_max[0], x1);
-                atomicMin(&f->bbox_min[1], y);
-                atomicMax(&f->bbox_max[1], y);
-                atomicMin(&f->bbox_min[2], z);
-                atomicMax(&f->bbox_max[2], z);
+            const uint32_t rx = V.run_x[j];
+            const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
+            const unsigned long long len = x1 - x0 + 1u;
+            const unsigned long long sx = ((unsigned long long)(x0 + x1) * len) >> 1;
+            const unsigned long long sy = len * y, sz = len * z;
+            uint32_t slot = (lab * 2654435761u) >> 24;
+            bool done = false;
+            for (int p = 0; p < FEAT_PROBES && !done; ++p, slot = (slot + 1) & (FEAT_SLOTS - 1)) {
+                const uint32_t k = atomicCAS(&T.key[slot], 0u, lab);
+                if (k == 0u || k == lab) {
+                    atomicAdd(&T.cnt[slot], len);
+                    atomicAdd(&T.sx[slot], sx);
+                    atomicAdd(&T.sy[slot], sy);
+                    atomicAdd(&T.sz[slot], sz);
+                    atomicMin(&T.mn[0][slot], x0);
+                    atomicMax(&T.mx[0][slot], x1);
+                    atomicMin(&T.mn[1][slot], y);
+                    atomicMax(&T.mx[1][slot], y);
+                    atomicMin(&T.mn[2][slot], z);
+                    atomicMax(&T.mx[2][slot], z);
+                    done = true;
+                }
             }
-            uint32_t j = ib;
-            for (uint32_t x = lane; x < X; x += 32) {
-                while (j < ie && (V.run_x[j] >> 16) < x) ++j;
-                uint32_t lab = 0;
-                if (j < ie && (V.run_x[j] & 0xFFFFu) <= x) lab = V.run_aux[V.run_par[j]];
-                out[x] = lab;
+            if (!done) {
+                const uint32_t mn[3] = {x0, y, z}, mx[3] = {x1, y, z};
+                feat_global(V.feat + (lab - 1), len, sx, sy, sz, mn, mx);
+            }
+        }
+        __syncthreads();
+        {
+            const uint32_t lab = T.key[tid];
+            if (lab) {
+                const uint32_t mn[3] = {T.mn[0][tid], T.mn[1][tid], T.mn[2][tid]};
+                const uint32_t mx[3] = {T.mx[0][tid], T.mx[1][tid], T.mx[2][tid]};
+                feat_global(V.feat + (lab - 1), T.cnt[tid], T.sx[tid], T.sy[tid], T.sz[tid], mn, mx);
+            }
+        }
+        const uint32_t X = V.X;
+        const bool vec = (X & 3u) == 0u;
+        for (uint32_t rr = warp; rr < nrows; rr += WARPS) {
+            uint32_t *out = V.labels + (size_t)(row0 + rr) * X;
+            const uint32_t ib = soff[rr], ie = soff[rr + 1];
+            if (vec) {
+                uint4 *o4 = reinterpret_cast<uint4 *>(out);
+                if (ib == ie) {
+                    for (uint32_t x = lane; x < X / 4; x += 32) __stcs(o4 + x, make_uint4(0, 0, 0, 0));
+                    continue;
+                }
+                uint32_t j = ib;
+                for (uint32_t xb = 4 * lane; xb < X; xb += 128) {
+                    uint32_t l4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t x = xb + q;
+                        while (j < ie && (V.run_x[j] >> 16) < x) ++j;
+                        l4[q] = (j < ie && (V.run_x[j] & 0xFFFFu) <= x) ? V.run_aux[j] : 0u;
+                    }
+                    __stcs(o4 + xb / 4, make_uint4(l4[0], l4[1], l4[2], l4[3]));
+                }
+            } else {
+                if (ib == ie) {
+                    for (uint32_t x = lane; x < X; x += 32) __stcs(out + x, 0u);
+                    continue;
+                }
+                uint32_t j = ib;
+                for (uint32_t x = lane; x < X; x += 32) {
+                    while (j < ie && (V.run_x[j] >> 16) < x) ++j;
+                    __stcs(out + x, (j < ie && (V.run_x[j] & 0xFFFFu) <= x) ? V.run_aux[j] : 0u);
+                }
             }
         }
     }
@@ -772,21 +1016,13 @@ cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStre
     };
     rec();
     k_smooth_hist<TY><<<p.grid_hist, 16 * TY, hist_smem_bytes(TY), s>>>(d);
-    rec();
-    k_smooth_mask<TY><<<p.grid_mask, 16 * TY, mask_smem_bytes(TY), s>>>(d);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t hist_smem_bytes(int tile_y) {
-    const int rh = tile_y + 4;
-    return (size_t)4 * (HIST_WORDS + rh * (TILE_X + 8) + rh * TILE_X);
-}
-
-size_t mask_smem_bytes(int tile_y) {
-    const int rh = tile_y + 4;
-    return (size_t)4 * (rh * (TILE_X + 8) + rh * TILE_X);
+    return tile_y == 8 ? Tile<8>::HIST_SMEM : (tile_y == 16 ? Tile<16>::HIST_SMEM : Tile<32>::HIST_SMEM);
 }
 
 cudaError_t configure_kernels(int device) {
@@ -796,9 +1032,7 @@ cudaError_t configure_kernels(int device) {
     e = cudaFuncSetAttribute(k_smooth_hist<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)hist_smem_bytes(TY));                                    \
     if (e != cudaSuccess) return e;                                                        \
-    e = cudaFuncSetAttribute(k_smooth_mask<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)mask_smem_bytes(TY));                                    \
-    if (e != cudaSuccess) return e;
+
     SEG_CFG(8)
     SEG_CFG(16)
     SEG_CFG(32)
@@ -823,7 +1057,7 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     }
     if (e != cudaSuccess) return e;
     rec();
-    k_row_count<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
+    k_threshold_runs<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
     k_tile_scan<0><<<p.grid_vols, 1024, 0, s>>>(d);
     rec();
@@ -884,10 +1118,13 @@ template <int TY>
 __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist_noalloc(const __grid_constant__ BatchHdr hdr) {
     using T = Tile<TY>;
     const BatchHdr *h = &hdr;
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *sh = smem;
-    uint32_t *sraw = sh + HIST_WORDS;
-    uint32_t *spx = sraw + T::RAW_WORDS;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char *ring = dsm;
+    uint32_t *sh = reinterpret_cast<uint32_t *>(dsm + T::RING_BYTES);
+    uint32_t *spx = sh + HIST_WORDS;
+    int8_t *shift = reinterpret_cast<int8_t *>(spx + T::PX_WORDS);
+    const VolDev &V = h->vol[0];
+    Ring R{ring, shift, 0};
     for (int i = threadIdx.x; i < HIST_WORDS / 4; i += T::NT)
         reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
@@ -895,7 +1132,6 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist_noalloc(const __grid
     const uint32_t tb = (uint32_t)(((uint64_t)nt * blockIdx.x) / G);
     const uint32_t te = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / G);
     if (tb >= te) return;
-    const VolDev &V = h->vol[0];
     const int tz = (int)h->tile_z;
     uint32_t ndone = 0;
     for (uint32_t t = tb; t < te; ++t) {
@@ -903,8 +1139,8 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist_noalloc(const __grid
         const uint32_t iy = rest % V.nty, iz = rest / V.nty;
         const int z0 = (int)iz * tz;
         const int z1 = min(z0 + tz, (int)V.Z);
-        HistEmit e{sh, V.hist, V.X, V.Y};
-        smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, sraw, spx, e);
+        HistEmit<false> e{sh, V.hist, nullptr, V.X, V.Y, 0u, nullptr, 0, false};
+        smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
         ++ndone;
     }
     flush_hist<T::NT>(h, 0, ndone, sh);

@@ -58,7 +58,7 @@ VolGeom geom(seg_dims d, uint32_t min_volume) {
     uint64_t kc = cdiv(d.x, 2) * cdiv(d.y, 2) * cdiv(d.z, 2);
     if (min_volume > 1) kc = std::min<uint64_t>(kc, g.n / min_volume + 1);
     g.k_cap = std::max<uint64_t>(kc, 1);
-    g.scratch = al(4ull * HIST_BINS) + al(4ull * g.rows * g.W) + al(4ull * (g.rows + 1)) +
+    g.scratch = al(4ull * HIST_BINS) + al(2ull * g.n) + al(4ull * g.rows * g.W) + al(4ull * (g.rows + 1)) +
                 al(4ull * g.rows) + 2 * al(4ull * g.nrt) + 3 * al(4ull * g.r_cap);
     return g;
 }
@@ -223,6 +223,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.feat = r->feat(c);
             V.stat = r->stat(c);
             V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
+            V.smooth = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
             V.mask = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows * g.W);
             V.rowoff = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * (g.rows + 1));
             V.rowk = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows);
@@ -477,7 +478,6 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->plan.sms = ctx->sms;
     ctx->plan.tile_y = ty;
     ctx->plan.grid_hist = ctx->sms;  // one resident block per SM (128 KiB histogram)
-    ctx->plan.grid_mask = ctx->sms * 4;
     ctx->plan.grid_rows = ctx->sms * 8;
     ctx->plan.grid_vols = ctx->sms;
     cudaMemPool_t pool;
