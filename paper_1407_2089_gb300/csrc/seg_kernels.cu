@@ -43,10 +43,14 @@ const char *const kKernelNames[NUM_KERNELS] = {
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-// Shared histogram: levels below HIST_LOW have a 32-bit counter each; the
-// rest share words as two 16-bit counters.
-constexpr int HIST_LOW = 16384;
-constexpr int HIST_WORDS = HIST_LOW + (HIST_BINS - HIST_LOW) / 2;
+// Shared histogram: levels below HIST_LOW have a 32-bit counter in each of
+// two copies (one per half-warp, the second offset by 16 words so that equal
+// levels in the two copies sit in different banks); the rest share words as
+// two 16-bit counters.
+constexpr int HIST_LOW = 8192;
+constexpr int HIST_COPY1 = HIST_LOW + 16;         // word offset of the second copy
+constexpr int HIST_PAIRS = 2 * HIST_LOW + 16;     // word offset of the 16-bit pairs
+constexpr int HIST_WORDS = HIST_PAIRS + (HIST_BINS - HIST_LOW) / 2;
 constexpr uint32_t UNION_LIMIT = 1u << 24;
 
 // ----------------------------------------------------------------------------
@@ -226,7 +230,7 @@ struct Tile {
     static constexpr int STAGE_BYTES = RH * ROWB;
     static constexpr int RING_BYTES = S * STAGE_BYTES;
     static constexpr int SHIFT_BYTES = (S * RH + 15) / 16 * 16;
-    // dynamic shared memory without / with the 160 KiB histogram
+    // dynamic shared memory without / with the shared histogram
     static constexpr size_t MASK_SMEM = RING_BYTES + 4 * PX_WORDS + SHIFT_BYTES;
     static constexpr size_t HIST_SMEM = MASK_SMEM + 4 * (size_t)HIST_WORDS;
     static_assert(RH * CHUNKS <= NT, "one chunk per thread per plane");
@@ -289,7 +293,7 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
         __syncthreads();            // everyone's have; the y pass of k-1 is done with spx
         const unsigned char *stage = R.stage + st * T::STAGE_BYTES;
         const int8_t *sh = R.shift + st * T::RH;
-        for (int it = tid; it < T::XITEMS; it += T::NT) {
+        auto xitem = [&](const int it) {
             const int r = it >> 4, qq = it & 15;
             const int s = sh[r];
             uint32_t v[8];
@@ -315,7 +319,10 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
                 }
             }
             *reinterpret_cast<uint4 *>(spx + r * TILE_X + 4 * qq) = xpass(v);
-        }
+        };
+        // quads beyond one per thread go to the top threads, which issue no copies
+        xitem(tid);
+        if (T::XITEMS > T::NT && tid >= 2 * T::NT - T::XITEMS) xitem(tid + T::XITEMS - T::NT);
         // the stage of plane k-1 was last read before the barrier above
         if (k + T::S - 1 < n) issue(zi + T::S - 1, (R.pc + k + T::S - 1) % T::S);
         cp_async_commit();
@@ -360,6 +367,7 @@ struct HistEmit {
     uint16_t *sm;       // smoothed volume (STORE only)
     uint32_t X, Y;
     uint32_t valid;     // bit j: voxel j of the quad is inside the volume
+    uint32_t copy;      // word offset of this half-warp's copy of the low levels
     uint16_t *row;      // &sm[y * X + xb] at z = 0
     size_t zstride;     // voxels per z-plane
     bool vec;           // all 4 inside and 8-byte aligned
@@ -367,6 +375,7 @@ struct HistEmit {
         valid = 0;
         if ((uint32_t)y < Y)
             for (int j = 0; j < 4; ++j) valid |= ((uint32_t)(xb + j) < X ? 1u : 0u) << j;
+        copy = (threadIdx.x & 16u) ? (uint32_t)HIST_COPY1 : 0u;
         if (STORE) {
             zstride = (size_t)X * Y;
             row = sm + ((size_t)(valid ? (uint32_t)y : 0u) * X + (uint32_t)xb);
@@ -375,6 +384,20 @@ struct HistEmit {
     }
     __device__ __forceinline__ void operator()(int z, bool live, const uint32_t *s) {
         if (!live) return;
+        const uint32_t vmax = max(max(s[0], s[1]), max(s[2], s[3]));
+        // warp-uniform fast path: 4 voxels inside, aligned row, low levels only
+        const bool fast = __all_sync(FULL, valid == 0xFu && (!STORE || vec) && vmax < (uint32_t)HIST_LOW);
+        if (fast) {
+            if (STORE)
+                *reinterpret_cast<uint2 *>(row + (size_t)(uint32_t)z * zstride) =
+                    make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
+            uint32_t *hc = sh + copy;
+            atomicAdd(hc + s[0], 1u);
+            atomicAdd(hc + s[1], 1u);
+            atomicAdd(hc + s[2], 1u);
+            atomicAdd(hc + s[3], 1u);
+            return;
+        }
         if (STORE) {
             uint16_t *p = row + (size_t)(uint32_t)z * zstride;
             if (vec) {
@@ -390,9 +413,9 @@ struct HistEmit {
             if (valid & (1u << j)) {
                 const uint32_t v = s[j];
                 if (v < (uint32_t)HIST_LOW) {
-                    atomicAdd(sh + v, 1u);
+                    atomicAdd(sh + copy + v, 1u);
                 } else {
-                    const uint32_t w = HIST_LOW + ((v - HIST_LOW) >> 1);
+                    const uint32_t w = HIST_PAIRS + ((v - HIST_LOW) >> 1);
                     const uint32_t sft = (v & 1u) << 4;
                     const uint32_t old = atomicAdd(sh + w, 1u << sft);
                     if (((old >> sft) & 0xFFFFu) == 0x7FFFu) {
@@ -517,23 +540,29 @@ __device__ void flush_hist(const BatchHdr *__restrict__ h, uint32_t v, uint32_t 
     __shared__ uint32_t s_last;
     const VolDev &V = h->vol[v];
     __syncthreads();
-    for (int i = threadIdx.x; i < HIST_WORDS / 4; i += NT) {
-        uint4 w = reinterpret_cast<uint4 *>(sh)[i];
-        if (w.x | w.y | w.z | w.w) {
+    for (int i = threadIdx.x; i < HIST_LOW / 4; i += NT) {
+        uint4 a = reinterpret_cast<uint4 *>(sh)[i];
+        uint4 b = reinterpret_cast<uint4 *>(sh + HIST_COPY1)[i];
+        a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+        if (a.x | a.y | a.z | a.w) {
             reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
+            reinterpret_cast<uint4 *>(sh + HIST_COPY1)[i] = make_uint4(0, 0, 0, 0);
+            const uint32_t ws[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ws[j]) atomicAdd(V.hist + 4u * i + j, ws[j]);
+        }
+    }
+    for (int i = threadIdx.x; i < (HIST_WORDS - HIST_PAIRS) / 4; i += NT) {
+        uint4 w = reinterpret_cast<uint4 *>(sh + HIST_PAIRS)[i];
+        if (w.x | w.y | w.z | w.w) {
+            reinterpret_cast<uint4 *>(sh + HIST_PAIRS)[i] = make_uint4(0, 0, 0, 0);
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-            const uint32_t wi = 4u * (uint32_t)i;
-            if (wi < (uint32_t)HIST_LOW) {
+            const uint32_t b = HIST_LOW + 8u * (uint32_t)i;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (ws[j]) atomicAdd(V.hist + wi + j, ws[j]);
-            } else {
-                const uint32_t b = HIST_LOW + 2u * (wi - HIST_LOW);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (ws[j] & 0xFFFFu) atomicAdd(V.hist + b + 2 * j, ws[j] & 0xFFFFu);
-                    if (ws[j] >> 16) atomicAdd(V.hist + b + 2 * j + 1, ws[j] >> 16);
-                }
+            for (int j = 0; j < 4; ++j) {
+                if (ws[j] & 0xFFFFu) atomicAdd(V.hist + b + 2 * j, ws[j] & 0xFFFFu);
+                if (ws[j] >> 16) atomicAdd(V.hist + b + 2 * j + 1, ws[j] >> 16);
             }
         }
     }
@@ -601,7 +630,7 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist(const BatchHdr *__re
         const uint32_t iy = rest % V.nty, iz = rest / V.nty;
         const int z0 = (int)iz * tz;
         const int z1 = min(z0 + tz, (int)V.Z);
-        HistEmit<true> e{sh, V.hist, V.smooth, V.X, V.Y, 0u, nullptr, 0, false};
+        HistEmit<true> e{sh, V.hist, V.smooth, V.X, V.Y, 0u, 0u, nullptr, 0, false};
         smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
         ++ndone;
     }
@@ -1139,7 +1168,7 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist_noalloc(const __grid
         const uint32_t iy = rest % V.nty, iz = rest / V.nty;
         const int z0 = (int)iz * tz;
         const int z1 = min(z0 + tz, (int)V.Z);
-        HistEmit<false> e{sh, V.hist, nullptr, V.X, V.Y, 0u, nullptr, 0, false};
+        HistEmit<false> e{sh, V.hist, nullptr, V.X, V.Y, 0u, 0u, nullptr, 0, false};
         smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
         ++ndone;
     }
