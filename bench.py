@@ -43,7 +43,8 @@ ALGO_BYTES_PER_VOXEL = 8.0  # 2 B raw read + 2 B re-read after Otsu + 4 B label 
 # are all voxels of the batch).
 KERNEL_BYTES_PER_VOXEL = {
     "smooth_hist_otsu": 2.0,       # raw uint16 read once
-    "smooth_mask": 2.0 + 1 / 8.0,  # raw read again + 1-bit mask write
+    "threshold_runs": 1 / 8.0,     # 1-bit mask write (the smoothed re-read is the 2 B
+                                   # counted in the 8 B/voxel path total)
     "label_features": 4.0,         # uint32 label write (run tables are O(runs))
     "row_count": 1 / 8.0,
     "row_runs": 1 / 8.0,

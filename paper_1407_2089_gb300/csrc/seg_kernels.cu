@@ -136,12 +136,24 @@ __device__ __forceinline__ uint32_t find_bit(const uint32_t *__restrict__ row, u
 // union-find over runs (parent index <= own index at all times)
 // ----------------------------------------------------------------------------
 
-// Root of x with path halving: every visited node is re-pointed at its
-// grandparent.  The store can only replace a parent by one of its ancestors
-// (all parents point to lower indices), so it never breaks a path; if it
-// overwrites a concurrent atomicMin, that union sees old != root and retries
-// from the old parent, so no link is lost.  Reads go through L2 (ld.cg):
-// parents change under other SMs and a stale L1 copy could stall a retry.
+// Root of x without writing.  k_flatten must use this: a compressing store
+// racing with another thread's final "parent = root" store could replace the
+// root by an intermediate ancestor.  Reads go through L2 (ld.cg) because
+// parents change under other SMs.
+__device__ __forceinline__ uint32_t uf_root(const uint32_t *P, uint32_t x) {
+    uint32_t p = __ldcg(P + x);
+    while (p != x) {
+        x = p;
+        p = __ldcg(P + x);
+    }
+    return x;
+}
+
+// Root of x with path halving, for the union phase only: every visited node
+// is re-pointed at its grandparent.  The store can only replace a parent by
+// one of its ancestors (all parents point to lower indices), so it never
+// breaks a path; if it overwrites a concurrent atomicMin, that union sees
+// old != root and retries from the old parent, so no link is lost.
 __device__ __forceinline__ uint32_t uf_find(uint32_t *P, uint32_t x) {
     uint32_t p = __ldcg(P + x);
     while (p != x) {
@@ -163,11 +175,11 @@ __device__ __forceinline__ void uf_union(uint32_t *P, uint32_t a, uint32_t b, ui
         b = uf_find(P, b);
         if (a == b) return;
         if (a < b) {
-            uint32_t old = atomicMin(P + b, a);
+            const uint32_t old = atomicMin(P + b, a);
             if (old == b) return;
             b = old;
         } else {
-            uint32_t old = atomicMin(P + a, b);
+            const uint32_t old = atomicMin(P + a, b);
             if (old == a) return;
             a = old;
         }
@@ -655,6 +667,60 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
         const uint32_t X = V.X, W = V.W, t = V.stat[ST_THRESH];
         const bool vec = (X & 7u) == 0u;
         uint32_t wtot = 0;
+        if (vec && X <= 512u) {
+            // 4 rows per warp at once, all 16-byte loads issued first
+            for (uint32_t rb = warp; rb < nrows; rb += 4 * WARPS) {
+                uint4 q4[4][2];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t rr = rb + k * WARPS;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t x = 256u * c + 8u * (uint32_t)lane;
+                        q4[k][c] = (rr < nrows && x < X)
+                                       ? __ldcs(reinterpret_cast<const uint4 *>(V.smooth + (size_t)(row0 + rr) * X + x))
+                                       : make_uint4(0, 0, 0, 0);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t rr = rb + k * WARPS;
+                    if (rr >= nrows) break;
+                    uint32_t *dst = V.mask + (size_t)(row0 + rr) * W;
+                    uint32_t carry = 0, cnt = 0;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t xb = 256u * c;
+                        if (xb >= X) break;
+                        const uint32_t x = xb + 8u * (uint32_t)lane;
+                        uint32_t bits = 0;
+                        if (x < X) {
+                            const uint32_t w4[4] = {q4[k][c].x, q4[k][c].y, q4[k][c].z, q4[k][c].w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                bits |= ((w4[j] & 0xFFFFu) > t ? 1u : 0u) << (2 * j);
+                                bits |= ((w4[j] >> 16) > t ? 1u : 0u) << (2 * j + 1);
+                            }
+                        }
+                        uint32_t word = bits << (8 * (lane & 3));
+                        word |= __shfl_xor_sync(FULL, word, 1);
+                        word |= __shfl_xor_sync(FULL, word, 2);
+                        const uint32_t prev = __shfl_up_sync(FULL, word, 4);
+                        const uint32_t left = lane < 4 ? carry : (prev >> 31);
+                        const uint32_t wi = (xb >> 5) + ((uint32_t)lane >> 2);
+                        if ((lane & 3) == 0 && wi < W) {
+                            dst[wi] = word;
+                            cnt += __popc(word & ~((word << 1) | left));
+                        }
+                        carry = __shfl_sync(FULL, word, 28) >> 31;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+                    if (lane == 0) V.rowoff[row0 + rr] = cnt;
+                    wtot += cnt;
+                }
+            }
+        } else
         for (uint32_t rr = warp; rr < nrows; rr += WARPS) {
             const uint32_t row = row0 + rr;
             const uint16_t *src = V.smooth + (size_t)row * X;
@@ -800,27 +866,36 @@ __device__ __forceinline__ void unite_rows(uint32_t *P, const uint32_t *__restri
     }
 }
 
-__global__ void __launch_bounds__(ROW_TILE) k_union(const BatchHdr *__restrict__ h) {
+// One thread per (row, backward neighbour row): (y-1,z), (y-1,z-1), (y,z-1),
+// (y+1,z-1).  Every pair of 26-adjacent rows is visited once, and the four
+// sweeps of a row run in parallel (the union-find is latency-bound).
+__global__ void __launch_bounds__(4 * ROW_TILE) k_union(const BatchHdr *__restrict__ h) {
+    const uint32_t nb = threadIdx.x / ROW_TILE;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[find_vol_rt(h, rt)];
-        const uint32_t row = (rt - V.rt_base) * ROW_TILE + threadIdx.x;
+        const uint32_t row = (rt - V.rt_base) * ROW_TILE + (threadIdx.x % ROW_TILE);
         if (row >= V.rows) continue;
         const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
         if (ib == ie) continue;
         const uint32_t y = row % V.Y, z = row / V.Y;
-        uint32_t *err = V.stat + ST_ERROR;
-        // backward neighbour rows: (y-1,z), (y-1,z-1), (y,z-1), (y+1,z-1)
-        if (y > 0) {
-            const uint32_t r = row - 1;
-            unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[r], V.rowoff[r + 1], err);
-        }
-        if (z > 0) {
+        uint32_t r;
+        if (nb == 0) {
+            if (y == 0) continue;
+            r = row - 1;
+        } else {
+            if (z == 0) continue;
             const uint32_t rz = row - V.Y;
-            if (y > 0) unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[rz - 1], V.rowoff[rz], err);
-            unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[rz], V.rowoff[rz + 1], err);
-            if (y + 1 < V.Y)
-                unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[rz + 1], V.rowoff[rz + 2], err);
+            if (nb == 1) {
+                if (y == 0) continue;
+                r = rz - 1;
+            } else if (nb == 2) {
+                r = rz;
+            } else {
+                if (y + 1 >= V.Y) continue;
+                r = rz + 1;
+            }
         }
+        unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[r], V.rowoff[r + 1], V.stat + ST_ERROR);
     }
 }
 
@@ -831,7 +906,7 @@ __global__ void __launch_bounds__(ROW_TILE) k_flatten(const BatchHdr *__restrict
         if (row >= V.rows) continue;
         const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
         for (uint32_t r = ib; r < ie; ++r) {
-            const uint32_t root = uf_find(V.run_par, r);
+            const uint32_t root = uf_root(V.run_par, r);
             V.run_par[r] = root;
             const uint32_t x = V.run_x[r];
             atomicAdd(V.run_aux + root, (x >> 16) - (x & 0xFFFFu) + 1u);
@@ -917,11 +992,12 @@ __device__ __forceinline__ void feat_global(seg_cell_features *f, unsigned long 
 }
 
 // One block per row tile (256 consecutive rows; their labels are one
-// contiguous range).  Phase 1, one thread per run: label of the run's root,
-// stored back on the run, and the run's contribution to its cell (count,
-// coordinate sums, bounding box) folded into the shared table.  Phase 2:
-// table -> global cells.  Phase 3, one warp per row: the row's labels, with
-// 16-byte streaming stores when rows are 16-byte aligned (X % 4 == 0).
+// contiguous range).  Labels first, one warp per row: a run's label is its
+// root's (set by k_rank), written with 16-byte streaming stores when rows are
+// 16-byte aligned (X % 4 == 0), zeros elsewhere.  Then, with no barrier in
+// between, one thread per run folds the run's contribution to its cell
+// (count, coordinate sums, bounding box) into a shared table; after a barrier
+// the table goes to the global cells with one set of atomics per (tile, cell).
 __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__restrict__ h) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int WARPS = ROW_TILE / 32;
@@ -941,20 +1017,67 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
             T.mx[a][tid] = 0u;
         }
         __syncthreads();
+        // labels
+        const uint32_t X = V.X;
+        const uint32_t *__restrict__ RX = V.run_x;
+        const uint32_t *__restrict__ RP = V.run_par;
+        const uint32_t *__restrict__ RA = V.run_aux;
+        const bool vec = (X & 3u) == 0u;
+        for (uint32_t rr = warp; rr < nrows; rr += WARPS) {
+            uint32_t *out = V.labels + (size_t)(row0 + rr) * X;
+            const uint32_t ib = soff[rr], ie = soff[rr + 1];
+            if (vec) {
+                uint4 *o4 = reinterpret_cast<uint4 *>(out);
+                if (ib == ie) {
+                    for (uint32_t x = lane; x < X / 4; x += 32) __stcs(o4 + x, make_uint4(0, 0, 0, 0));
+                    continue;
+                }
+                uint32_t j = ib, jx = RX[ib], jl = RA[RP[ib]];
+                for (uint32_t xb = 4 * lane; xb < X; xb += 128) {
+                    uint32_t l4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t x = xb + q;
+                        while (j < ie && (jx >> 16) < x) {
+                            if (++j < ie) {
+                                jx = RX[j];
+                                jl = RA[RP[j]];
+                            }
+                        }
+                        l4[q] = (j < ie && (jx & 0xFFFFu) <= x) ? jl : 0u;
+                    }
+                    __stcs(o4 + xb / 4, make_uint4(l4[0], l4[1], l4[2], l4[3]));
+                }
+            } else {
+                if (ib == ie) {
+                    for (uint32_t x = lane; x < X; x += 32) __stcs(out + x, 0u);
+                    continue;
+                }
+                uint32_t j = ib, jx = RX[ib], jl = RA[RP[ib]];
+                for (uint32_t x = lane; x < X; x += 32) {
+                    while (j < ie && (jx >> 16) < x) {
+                        if (++j < ie) {
+                            jx = RX[j];
+                            jl = RA[RP[j]];
+                        }
+                    }
+                    __stcs(out + x, (j < ie && (jx & 0xFFFFu) <= x) ? jl : 0u);
+                }
+            }
+        }
         const uint32_t rb = soff[0], re = soff[nrows];
         for (uint32_t j = rb + tid; j < re; j += ROW_TILE) {
+            const uint32_t lab = RA[RP[j]];
+            if (!lab || lab > V.k_cap) continue;
             // row of run j: the last i with soff[i] <= j
             uint32_t lo = 0, hi = nrows;
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (soff[mid] <= j) lo = mid; else hi = mid;
             }
-            const uint32_t lab = V.run_aux[V.run_par[j]];
-            V.run_aux[j] = lab;
-            if (!lab || lab > V.k_cap) continue;
             const uint32_t row = row0 + lo;
             const uint32_t y = row % V.Y, z = row / V.Y;
-            const uint32_t rx = V.run_x[j];
+            const uint32_t rx = RX[j];
             const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
             const unsigned long long len = x1 - x0 + 1u;
             const unsigned long long sx = ((unsigned long long)(x0 + x1) * len) >> 1;
@@ -989,40 +1112,6 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                 const uint32_t mn[3] = {T.mn[0][tid], T.mn[1][tid], T.mn[2][tid]};
                 const uint32_t mx[3] = {T.mx[0][tid], T.mx[1][tid], T.mx[2][tid]};
                 feat_global(V.feat + (lab - 1), T.cnt[tid], T.sx[tid], T.sy[tid], T.sz[tid], mn, mx);
-            }
-        }
-        const uint32_t X = V.X;
-        const bool vec = (X & 3u) == 0u;
-        for (uint32_t rr = warp; rr < nrows; rr += WARPS) {
-            uint32_t *out = V.labels + (size_t)(row0 + rr) * X;
-            const uint32_t ib = soff[rr], ie = soff[rr + 1];
-            if (vec) {
-                uint4 *o4 = reinterpret_cast<uint4 *>(out);
-                if (ib == ie) {
-                    for (uint32_t x = lane; x < X / 4; x += 32) __stcs(o4 + x, make_uint4(0, 0, 0, 0));
-                    continue;
-                }
-                uint32_t j = ib;
-                for (uint32_t xb = 4 * lane; xb < X; xb += 128) {
-                    uint32_t l4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t x = xb + q;
-                        while (j < ie && (V.run_x[j] >> 16) < x) ++j;
-                        l4[q] = (j < ie && (V.run_x[j] & 0xFFFFu) <= x) ? V.run_aux[j] : 0u;
-                    }
-                    __stcs(o4 + xb / 4, make_uint4(l4[0], l4[1], l4[2], l4[3]));
-                }
-            } else {
-                if (ib == ie) {
-                    for (uint32_t x = lane; x < X; x += 32) __stcs(out + x, 0u);
-                    continue;
-                }
-                uint32_t j = ib;
-                for (uint32_t x = lane; x < X; x += 32) {
-                    while (j < ie && (V.run_x[j] >> 16) < x) ++j;
-                    __stcs(out + x, (j < ie && (V.run_x[j] & 0xFFFFu) <= x) ? V.run_aux[j] : 0u);
-                }
             }
         }
     }
@@ -1092,7 +1181,7 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     rec();
     k_row_runs<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
-    k_union<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
+    k_union<<<p.grid_rows, 4 * ROW_TILE, 0, s>>>(d);
     rec();
     k_flatten<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();

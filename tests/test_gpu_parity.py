@@ -142,3 +142,16 @@ def test_device_resident_input(seg, ctx):
     lab = out.cpu().numpy().view(np.uint32).reshape(vol.shape)
     assert_matches_oracle(vol, lab, cells, thr, what="device input")
     seg.seg_release(ctx, req)
+
+
+def test_union_find_stress(seg, ctx):
+    # dense random masks in many shapes: every missed or wrong union changes
+    # the labels (m = 1 keeps every fragment), so races show up here
+    rng = np.random.default_rng(77)
+    for trial in range(40):
+        dims = tuple(int(v) for v in rng.integers(3, 90, size=3))
+        X, Y, Z = dims
+        p = float(rng.uniform(0.2, 0.6))
+        vol = np.where(rng.uniform(size=(Z, Y, X)) < p, 3000, 100).astype(np.uint16)
+        lab, cells, thr = run(seg, ctx, vol, 1)
+        assert_matches_oracle(vol, lab, cells, thr, min_volume=1, what="stress %d %s p=%.2f" % (trial, dims, p))
