@@ -62,6 +62,10 @@ extern "C" {
                                sequence, one stream, no batching, no graphs      */
 #define SEG_NO_GRAPH 0x4u   /* batched form without CUDA-graph capture           */
 #define SEG_PROFILE 0x8u    /* record CUDA events around every kernel launch     */
+#define SEG_TEST_UNION_FAIL 0x10u /* test hook: every union-find union gives up at
+                                     once and raises its error bit, so requests
+                                     with adjacent runs end FAILED (error path
+                                     without any device fault)                  */
 
 typedef struct seg_ctx seg_ctx; /* opaque; owns streams, graphs, device state   */
 typedef uint64_t seg_req;       /* request handle, never 0                       */

@@ -35,6 +35,7 @@ SEG_FORCE_TILE = 0x1
 SEG_PLAIN = 0x2
 SEG_NO_GRAPH = 0x4
 SEG_PROFILE = 0x8
+SEG_TEST_UNION_FAIL = 0x10
 
 SEG_MAX_KERNELS = 16
 

@@ -30,6 +30,7 @@ enum ErrBits : uint32_t {
 };
 
 constexpr int TILE_X = 64;        // smoothing tile width (outputs along x)
+constexpr uint32_t UNION_LIMIT = 1u << 24;  // union-find retries before ERR_UNION
 constexpr int ROW_TILE = 256;     // rows per row tile (run kernels)
 constexpr int HIST_BINS = 65536;
 
@@ -54,6 +55,7 @@ struct VolDev {
     uint32_t X, Y, Z, W;      // W = words per mask row
     uint32_t rows;            // Y * Z
     uint32_t min_volume;
+    uint32_t union_limit;     // retries before a union gives up (ERR_UNION)
     uint32_t ntx, nty, ntz;   // smoothing tiles per axis
     uint32_t nrt;             // row tiles
     uint32_t tile_base;       // first flat smoothing-tile index
@@ -93,6 +95,9 @@ struct LaunchPlan {
 // stat_out receives nvol * ST_WORDS status words (volume-major).
 cudaError_t launch_pipeline(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream,
                             cudaEvent_t *ev, uint32_t *stat_out);
+
+// Only the tile-dependent part (init + smoothing/histogram), for tile tuning.
+cudaError_t launch_tile_probe(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);
 
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);

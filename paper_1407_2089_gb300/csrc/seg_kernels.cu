@@ -51,7 +51,7 @@ constexpr int HIST_LOW = 8192;
 constexpr int HIST_COPY1 = HIST_LOW + 16;         // word offset of the second copy
 constexpr int HIST_PAIRS = 2 * HIST_LOW + 16;     // word offset of the 16-bit pairs
 constexpr int HIST_WORDS = HIST_PAIRS + (HIST_BINS - HIST_LOW) / 2;
-constexpr uint32_t UNION_LIMIT = 1u << 24;
+
 
 // ----------------------------------------------------------------------------
 // small helpers
@@ -169,8 +169,9 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t *P, uint32_t x) {
 // Union with the lower index as the surviving root.  atomicMin only ever
 // lowers a parent, so each component ends rooted at its minimum run index
 // whatever the interleaving.  Bounded retries; exhaustion raises ERR_UNION.
-__device__ __forceinline__ void uf_union(uint32_t *P, uint32_t a, uint32_t b, uint32_t *err) {
-    for (uint32_t it = 0; it < UNION_LIMIT; ++it) {
+__device__ __forceinline__ void uf_union(uint32_t *P, uint32_t a, uint32_t b, uint32_t *err,
+                                         uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         a = uf_find(P, a);
         b = uf_find(P, b);
         if (a == b) return;
@@ -855,13 +856,14 @@ __global__ void __launch_bounds__(ROW_TILE) k_row_runs(const BatchHdr *__restric
 // Sweep two x-sorted run lists and unite every pair at x-distance <= 1
 // (26-adjacency between runs of rows that differ by one in y and/or z).
 __device__ __forceinline__ void unite_rows(uint32_t *P, const uint32_t *__restrict__ RX, uint32_t i,
-                                           uint32_t ie, uint32_t j, uint32_t je, uint32_t *err) {
+                                           uint32_t ie, uint32_t j, uint32_t je, uint32_t *err,
+                                           uint32_t limit) {
     while (i < ie && j < je) {
         const uint32_t a = RX[i], b = RX[j];
         const uint32_t a0 = a & 0xFFFFu, a1 = a >> 16, b0 = b & 0xFFFFu, b1 = b >> 16;
         if (b1 + 1 < a0) { ++j; continue; }
         if (a1 + 1 < b0) { ++i; continue; }
-        uf_union(P, i, j, err);
+        uf_union(P, i, j, err, limit);
         if (a1 < b1) ++i; else ++j;
     }
 }
@@ -895,7 +897,7 @@ __global__ void __launch_bounds__(4 * ROW_TILE) k_union(const BatchHdr *__restri
                 r = rz + 1;
             }
         }
-        unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[r], V.rowoff[r + 1], V.stat + ST_ERROR);
+        unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[r], V.rowoff[r + 1], V.stat + ST_ERROR, V.union_limit);
     }
 }
 
@@ -1156,6 +1158,16 @@ cudaError_t configure_kernels(int device) {
     SEG_CFG(32)
 #undef SEG_CFG
     return cudaSuccess;
+}
+
+cudaError_t launch_tile_probe(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
+    k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
+    switch (p.tile_y) {
+        case 8: k_smooth_hist<8><<<p.grid_hist, 16 * 8, hist_smem_bytes(8), s>>>(d); break;
+        case 16: k_smooth_hist<16><<<p.grid_hist, 16 * 16, hist_smem_bytes(16), s>>>(d); break;
+        default: k_smooth_hist<32><<<p.grid_hist, 16 * 32, hist_smem_bytes(32), s>>>(d); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s, cudaEvent_t *ev,

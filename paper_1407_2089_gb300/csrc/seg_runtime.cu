@@ -140,6 +140,7 @@ struct seg_ctx {
     uint64_t used = 0;
     uint32_t cap_vols = 512;
     bool plain = false, graphs = true, profile = false;
+    bool tuned = false;  // tile shape fixed (forced, or tuned on the first batch)
     cudaStream_t copy_stream = nullptr;
     cudaStream_t read_stream = nullptr;
     std::vector<Slot> slots;
@@ -237,6 +238,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.X = g.X; V.Y = g.Y; V.Z = g.Z; V.W = g.W;
             V.rows = g.rows;
             V.min_volume = r->minvol[c];
+            V.union_limit = (ctx->cfg.flags & SEG_TEST_UNION_FAIL) ? 0u : UNION_LIMIT;
             V.ntx = (uint32_t)cdiv(g.X, TILE_X);
             V.nty = (uint32_t)cdiv(g.Y, ty);
             V.ntz = (uint32_t)cdiv(g.Z, tz);
@@ -267,6 +269,48 @@ int enqueue_body(seg_ctx *ctx, Slot &s, uint32_t nvol) {
     return SEG_OK;
 }
 
+// Tile tuning on the first batch: time init + smoothing/histogram for each
+// candidate tile shape on the batch's own data and keep the fastest.  The
+// pipeline's results do not depend on the tile shape.
+int tune_tiles(seg_ctx *ctx, Batch &b) {
+    static const int kTy[] = {16, 32};
+    static const uint32_t kTz[] = {16, 32, 64};
+    Slot &s = *b.slot;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_ty = ctx->plan.tile_y;
+    uint32_t best_tz = ctx->tile_z;
+    for (int ty : kTy) {
+        for (uint32_t tz : kTz) {
+            ctx->plan.tile_y = ty;
+            ctx->tile_z = tz;
+            build_header(ctx, b);
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {  // first run warms caches and clocks
+                CK(cudaMemcpyAsync(s.d_hdr, s.h_hdr, batch_bytes(b.nvol), cudaMemcpyHostToDevice, s.stream));
+                CK(cudaEventRecord(e0, s.stream));
+                CK(launch_tile_probe(s.d_hdr, ctx->plan, s.stream));
+                CK(cudaEventRecord(e1, s.stream));
+                CK(cudaEventSynchronize(e1));
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (ms < best) {
+                best = ms;
+                best_ty = ty;
+                best_tz = tz;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->plan.tile_y = best_ty;
+    ctx->tile_z = best_tz;
+    ctx->tuned = true;
+    return SEG_OK;
+}
+
 int launch_batch(seg_ctx *ctx, Batch &b) {
     Slot &s = *b.slot;
     // Inputs that waited on the host are copied now (pageable source: the
@@ -283,6 +327,10 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
     }
     for (Request *r : b.reqs) std::vector<uint16_t>().swap(r->host_copy);
     CK(cudaMallocAsync(reinterpret_cast<void **>(&b.scratch), b.scratch_bytes, s.stream));
+    if (!ctx->tuned) {
+        const int rc = tune_tiles(ctx, b);
+        if (rc != SEG_OK) return rc;
+    }
     build_header(ctx, b);
     if (ctx->graphs) {
         cudaGraphExec_t &ge = s.graph[graph_index(ctx->plan.tile_y)];
@@ -375,11 +423,15 @@ void worker_main(seg_ctx *ctx) {
                 while (!ctx->pending.empty() && b->reqs.size() < max_req) {
                     Request *r = ctx->pending.front();
                     if (nv + r->C > ctx->cap_vols) break;
-                    size_t need = r->scratch + (r->admitted ? 0 : r->persist);
-                    if (ctx->used + need > ctx->budget) break;
-                    ctx->used += need;
+                    // an admitted request already holds its results and its
+                    // scratch, so it can always launch (no head-of-line deadlock)
+                    if (!r->admitted) {
+                        if (ctx->used + r->persist + r->scratch > ctx->budget) break;
+                        ctx->used += r->persist + r->scratch;
+                        r->admitted = true;
+                        r->t_admit = ctx->now();
+                    }
                     b->scratch_bytes += r->scratch;
-                    if (!r->admitted) { r->admitted = true; r->t_admit = ctx->now(); }
                     r->launched = true;
                     r->t_launch = ctx->now();
                     nv += r->C;
@@ -474,6 +526,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     int ty = 32;
     uint32_t tz = 64;
     if (cfg->flags & SEG_FORCE_TILE) { ty = (int)cfg->tile_y; tz = cfg->tile_z; }
+    ctx->tuned = (cfg->flags & SEG_FORCE_TILE) != 0;
     ctx->tile_z = tz;
     ctx->plan.sms = ctx->sms;
     ctx->plan.tile_y = ty;
@@ -581,10 +634,10 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
             if (r->ready_ev) cudaEventDestroy(r->ready_ev);
             return SEG_EAGAIN;
         }
-        if (!on_device && ctx->used + r->persist <= ctx->budget) {
-            // reserve the request's own device memory now and copy straight
-            // from the caller's buffer
-            ctx->used += r->persist;
+        if (!on_device && ctx->pending.empty() && ctx->used + r->persist + r->scratch <= ctx->budget) {
+            // admit now (its results and its batch scratch reserved) and copy
+            // straight from the caller's buffer
+            ctx->used += r->persist + r->scratch;
             r->admitted = true;
             r->t_admit = ctx->now();
             copy_now = true;
@@ -604,7 +657,7 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
         }
         if (rc != SEG_OK) {
             std::lock_guard<std::mutex> lk(ctx->mu);
-            if (r->admitted) ctx->used -= r->persist;
+            if (r->admitted) ctx->used -= r->persist + r->scratch;
             if (r->block) cudaFreeAsync(r->block, ctx->copy_stream);
             cudaEventDestroy(r->done_ev);
             return rc;
@@ -723,7 +776,7 @@ int seg_release(seg_ctx *ctx, seg_req req) {
         } else {
             ctx->cv.wait(lk, [&] { return r->state != SEG_PENDING; });
         }
-        if (r->admitted) ctx->used -= r->persist;
+        if (r->admitted) ctx->used -= r->launched ? r->persist : r->persist + r->scratch;
         auto it = ctx->reqs.find(req);
         owned = std::move(it->second);
         ctx->reqs.erase(it);
