@@ -298,8 +298,16 @@ def run_gpu(args):
     total_kernel_ms = sum(k["ms"] for k in kern.values())
     shares = {n: round(k["ms"] / total_kernel_ms, 4) for n, k in kern.items()} if total_kernel_ms else {}
     seg.seg_destroy(ctx)
+    forms = None
+    if not args.no_forms:
+        forms = {"batched": value / ws, "plain": plain_form(seg, torch, d_in, (X, Y, Z), local,
+                                                            max(1, min(args.steps, 3)))}
     del d_in
     torch.cuda.empty_cache()
+    serve = None
+    if args.serving_requests and rank == 0:
+        serve = {"batched": serving(seg, torch, local, args.serving_requests, 200.0, 0, 2),
+                 "plain": serving(seg, torch, local, args.serving_requests, 200.0, seg.SEG_PLAIN, 1)}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -368,6 +376,8 @@ def run_gpu(args):
             "kernel_share": shares,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "forms_gvox_s_per_gpu": forms,
+            "serving": serve,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }
@@ -375,6 +385,115 @@ def run_gpu(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def plain_form(seg, torch, d_in, dims, local, steps):
+    """Same workload through the plain per-frame form: one request (both
+    channels of a frame) per launch sequence, one stream, no graphs."""
+    T, C = d_in.shape[0], d_in.shape[1]
+    X, Y, Z = dims
+    stream = torch.cuda.Stream()
+    ctx = seg.seg_create(device=local, flags=seg.SEG_PLAIN, order_stream=stream.cuda_stream)
+    vox = 0
+
+    def one_pass():
+        reqs = [seg.seg_submit_volume(ctx, d_in[t], dims=(X, Y, Z), channels=C) for t in range(T)]
+        for r in reqs:
+            seg.seg_enqueue_wait(ctx, r, stream.cuda_stream)
+        return reqs
+
+    def finish(reqs):
+        for r in reqs:
+            if seg.seg_wait(ctx, r) != seg.SEG_DONE:
+                raise RuntimeError("request failed")
+            seg.seg_release(ctx, r)
+
+    finish(one_pass())
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pend = []
+    for _ in range(steps):
+        pend.append(one_pass())
+        vox += d_in.numel()
+        if len(pend) > 1:
+            finish(pend.pop(0))
+    e1.record(stream)
+    for p in pend:
+        finish(p)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    seg.seg_destroy(ctx)
+    return vox / (ms / 1e3) / 1e9
+
+
+def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
+    """Open-loop Poisson request stream (2-channel volumes, sizes log-uniform
+    from 128^3 to 2048x2048x64) through the C ABI from pinned host memory.
+    Latency = completion observed by the runtime - arrival time."""
+    import synth
+    reqs = synth.serving_requests(seed=5, n=n_requests, rate=rate)
+    maxn = max(d[0] * d[1] * d[2] for _, d in reqs)
+    # one pinned pool [channel 0 | channel 1] of the largest size; a request
+    # of n voxels per channel uses its first 2n voxels as [2][Z][Y][X]
+    base = np.empty(2 * maxn, dtype=np.uint16)
+    base[:maxn] = synth.density_volume((2048, 2048, 64), synth.mix_seed(5, 1)).reshape(-1)[:maxn]
+    base[maxn:] = synth.density_volume((2048, 2048, 64), synth.mix_seed(5, 2)).reshape(-1)[:maxn]
+    pool = torch.from_numpy(base.view(np.int16)).pin_memory()
+    ctx = seg.seg_create(device=local, flags=flags, hbm_budget_bytes=120 * 10 ** 9, max_inflight=max_inflight)
+    lat = []
+    vox = 0
+    done_at = []
+    lock = threading.Lock()
+    pending = []
+    finished = threading.Event()
+
+    def waiter():
+        while True:
+            with lock:
+                item = pending.pop(0) if pending else None
+            if item is None:
+                if finished.is_set():
+                    return
+                time.sleep(0.0002)
+                continue
+            rid, arrival, submit_wall, nvox = item
+            st = seg.seg_wait(ctx, rid)
+            sub_ms, _, _, done_ms = seg.seg_request_times(ctx, rid)
+            if st != seg.SEG_DONE:
+                raise RuntimeError("request failed")
+            lat.append((done_ms - sub_ms) + (submit_wall - arrival) * 1e3)
+            done_at.append(submit_wall + (done_ms - sub_ms) / 1e3)
+            seg.seg_release(ctx, rid)
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for arrival, (X, Y, Z) in reqs:
+        n = X * Y * Z
+        host = pool[:2 * n]
+        while True:
+            left = arrival - (time.perf_counter() - t0)
+            if left <= 0:
+                break
+            if left > 0.001:
+                time.sleep(left - 0.0005)
+        a_wall = t0 + arrival
+        rid = seg.seg_submit_volume(ctx, host, dims=(X, Y, Z), channels=2)
+        s_wall = time.perf_counter()
+        vox += 2 * n
+        with lock:
+            pending.append((rid, a_wall, s_wall, 2 * n))
+    finished.set()
+    th.join()
+    seg.seg_destroy(ctx)
+    span = max(done_at) - t0
+    lat = np.sort(np.array(lat))
+    return {"requests": len(reqs), "rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "achieved_gvox_s": vox / span / 1e9,
+            "offered_gvox_s": vox / reqs[-1][0] / 1e9}
 
 
 def main():
@@ -388,6 +507,9 @@ def main():
                     help="batches in flight; 1 keeps per-kernel CUDA-event times free of overlap")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the plain per-frame comparison")
+    ap.add_argument("--serving-requests", type=int, default=400,
+                    help="Poisson requests (200/s) for the served latency; 0 skips serving")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

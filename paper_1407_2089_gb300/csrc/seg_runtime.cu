@@ -420,13 +420,23 @@ void worker_main(seg_ctx *ctx) {
                 b->ctx = ctx;
                 uint32_t nv = 0;
                 const uint32_t max_req = ctx->plain ? 1u : 0xFFFFFFFFu;
+                // FIFO, except that a request still waiting for memory does not
+                // hold back admitted ones queued behind it
+                std::deque<Request *> rest;
                 while (!ctx->pending.empty() && b->reqs.size() < max_req) {
                     Request *r = ctx->pending.front();
-                    if (nv + r->C > ctx->cap_vols) break;
+                    ctx->pending.pop_front();
+                    if (nv + r->C > ctx->cap_vols) {
+                        rest.push_back(r);
+                        break;
+                    }
                     // an admitted request already holds its results and its
-                    // scratch, so it can always launch (no head-of-line deadlock)
+                    // scratch, so it can always launch
                     if (!r->admitted) {
-                        if (ctx->used + r->persist + r->scratch > ctx->budget) break;
+                        if (ctx->used + r->persist + r->scratch > ctx->budget) {
+                            rest.push_back(r);
+                            continue;
+                        }
                         ctx->used += r->persist + r->scratch;
                         r->admitted = true;
                         r->t_admit = ctx->now();
@@ -437,8 +447,12 @@ void worker_main(seg_ctx *ctx) {
                     nv += r->C;
                     b->voxels += r->g[0].n * r->C;
                     b->reqs.push_back(r);
+                }
+                while (!ctx->pending.empty()) {
+                    rest.push_back(ctx->pending.front());
                     ctx->pending.pop_front();
                 }
+                ctx->pending.swap(rest);
                 if (ctx->pending.empty()) ctx->flush = false;
                 else ctx->first_pending = Clock::now();
                 if (b->reqs.empty()) {
@@ -634,7 +648,7 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
             if (r->ready_ev) cudaEventDestroy(r->ready_ev);
             return SEG_EAGAIN;
         }
-        if (!on_device && ctx->pending.empty() && ctx->used + r->persist + r->scratch <= ctx->budget) {
+        if (!on_device && ctx->used + r->persist + r->scratch <= ctx->budget) {
             // admit now (its results and its batch scratch reserved) and copy
             // straight from the caller's buffer
             ctx->used += r->persist + r->scratch;
