@@ -326,7 +326,7 @@ def serving_volume(dims, seed, index, channel):
     rng = np.random.Generator(np.random.PCG64(mix_seed(5, seed, index, 1)))
     X, Y, Z = dims
     vol = background(dims, mix_seed(5, seed, index, 2), 200.0, 25.0)
-    nv = max(1, int(round(8 * X * Y / (512 * 512))))
+    nv = max(1, int(round(X * Y / (1024 * 1024))))
     add_field(vol, tube_field(dims, spline_vessels(rng, dims, nv), 1.0))
     return vol
 
@@ -340,6 +340,7 @@ def montage(seed=4, dims=(5530, 5530, 80), n_nuclei=20000, channel=0):
     rng = np.random.Generator(np.random.PCG64(mix_seed(4, seed, 1)))
     X, Y, Z = dims
     vol = background(dims, mix_seed(4, seed, 2), 200.0, 25.0)
-    nv = max(1, int(round(8 * X * Y / (512 * 512))))
+    # about one long vessel per 1024 x 1024 of stage area
+    nv = max(1, int(round(X * Y / (1024 * 1024))))
     add_field(vol, tube_field(dims, spline_vessels(rng, dims, nv), 1.0))
     return vol

@@ -1,0 +1,168 @@
+"""Parity on the full-size workloads (seeded synthetic stand-ins for the
+paper's data, generated by synth/):
+
+* batched uneven: all 48 volumes (64^3 .. 1024x1024x96) in one launch,
+  compared with the oracle on a sample that includes the smallest and the
+  largest volume, and bit-identical to the plain per-frame form for every
+  volume;
+* serving: requests of mixed sizes submitted concurrently (continuous
+  batching) give the same labels, cells and levels as each request alone;
+* montage: the full oracle at a reduced montage size, and at the full
+  5530x5530x80 size the Otsu level against an independently computed
+  histogram plus exact properties on samples (no oracle run at that size).
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from fullsize_util import (check_adjacency_samples, check_cells_by_planes, check_sampled_cells,
+                           check_threshold_samples, smooth_histogram_slabs)
+from gpu_util import assert_cells_equal, assert_matches_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def seg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1407_2089_gb300 as seg
+    return seg
+
+
+def read_all(seg, ctx, req, shape, channels=1):
+    out = []
+    for c in range(channels):
+        lab = np.empty(shape, dtype=np.uint32)
+        seg.seg_read_labels(ctx, req, c, lab)
+        cells, thr = seg.seg_read_features(ctx, req, c)
+        out.append((lab, cells, thr))
+    return out
+
+
+def test_batched_uneven_workload(seg):
+    dims = synth.batched_uneven_dims()
+    vols = [synth.density_volume(d, synth.mix_seed(3, 3, i)) for i, d in enumerate(dims)]
+    batched = seg.seg_create(device=0, batch_window_us=30_000_000)
+    plain = seg.seg_create(device=0, flags=seg.SEG_PLAIN)
+    try:
+        reqs = [seg.seg_submit_volume(batched, v) for v in vols]
+        seg.seg_flush(batched)
+        res_b = []
+        for v, r in zip(vols, reqs):
+            assert seg.seg_wait(batched, r) == seg.SEG_DONE
+            res_b.append(read_all(seg, batched, r, v.shape)[0])
+            seg.seg_release(batched, r)
+        assert seg.seg_get_stats(batched)["batches"] == 1
+        for i, v in enumerate(vols):
+            (lab, cells, thr), = seg.segment(plain, v)
+            lb, cb, tb = res_b[i]
+            assert tb == thr and np.array_equal(lb, lab), "batched != plain, volume %d" % i
+            assert_cells_equal(cb, cells, "batched vs plain %d" % i)
+        rng = np.random.default_rng(3)
+        sample = sorted({0, len(vols) - 1, *rng.choice(len(vols), size=4, replace=False).tolist()})
+        for i in sample:
+            lab, cells, thr = res_b[i]
+            assert_matches_oracle(vols[i], lab, cells, thr, what="uneven %d %s" % (i, dims[i]))
+    finally:
+        seg.seg_destroy(batched)
+        seg.seg_destroy(plain)
+
+
+def test_serving_mix_equals_alone(seg):
+    stream = synth.serving_requests(seed=5, n=400)
+    rng = np.random.default_rng(55)
+    picks = sorted(rng.choice(len(stream), size=10, replace=False).tolist())
+    # include the largest request of the stream
+    picks.append(int(np.argmax([d[0] * d[1] * d[2] for _, d in stream])))
+    items = []
+    for i in picks:
+        d = stream[i][1]
+        vol = np.stack([synth.serving_volume(d, 5, i, 0), synth.serving_volume(d, 5, i, 1)])
+        items.append(vol)
+    mix = seg.seg_create(device=0, max_inflight=2, hbm_budget_bytes=120 * 10 ** 9)
+    handles = [None] * len(items)
+
+    def submitter(idx):
+        for j in idx:
+            time.sleep(float(rng.uniform(0, 0.003)))
+            handles[j] = seg.seg_submit_volume(mix, items[j])
+
+    try:
+        order = np.arange(len(items))
+        threads = [threading.Thread(target=submitter, args=(order[k::3],)) for k in range(3)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        seg.seg_flush(mix)
+        mixed = []
+        for j, vol in enumerate(items):
+            assert seg.seg_wait(mix, handles[j]) == seg.SEG_DONE
+            mixed.append(read_all(seg, mix, handles[j], vol.shape[1:], 2))
+            seg.seg_release(mix, handles[j])
+        batches = seg.seg_get_stats(mix)["batches"]
+    finally:
+        seg.seg_destroy(mix)
+    alone = seg.seg_create(device=0)
+    try:
+        for j, vol in enumerate(items):
+            res = seg.segment(alone, vol)
+            for c in range(2):
+                lab, cells, thr = res[c]
+                ml, mc, mt = mixed[j][c]
+                assert mt == thr and np.array_equal(ml, lab), "mix != alone, request %d ch %d" % (j, c)
+                assert_cells_equal(mc, cells, "mix vs alone %d/%d" % (j, c))
+    finally:
+        seg.seg_destroy(alone)
+    assert batches < len(items)  # some requests shared a launch
+    # the oracle on the smallest request of the sample, both channels
+    j = int(np.argmin([v[0].size for v in items]))
+    for c in range(2):
+        lab, cells, thr = mixed[j][c]
+        assert_matches_oracle(items[j][c], lab, cells, thr, what="serving %d ch%d" % (j, c))
+
+
+def test_montage_reduced_size_full_oracle(seg):
+    dims = (1800, 1800, 40)
+    n = int(round(20000 * (1800 * 1800 * 40) / (5530 * 5530 * 80)))
+    vol = np.stack([synth.montage(dims=dims, n_nuclei=n, channel=0),
+                    synth.montage(dims=dims, channel=1)])
+    ctx = seg.seg_create(device=0)
+    try:
+        res = seg.segment(ctx, vol)
+    finally:
+        seg.seg_destroy(ctx)
+    for c in range(2):
+        lab, cells, thr = res[c]
+        assert_matches_oracle(vol[c], lab, cells, thr, what="montage 1800^2x40 ch%d" % c)
+
+
+@pytest.mark.slow
+def test_montage_full_size_properties(seg):
+    vol = np.stack([synth.montage(channel=0), synth.montage(channel=1)])
+    ctx = seg.seg_create(device=0)
+    try:
+        req = seg.seg_submit_volume(ctx, vol)
+        seg.seg_flush(ctx)
+        assert seg.seg_wait(ctx, req) == seg.SEG_DONE
+        res = read_all(seg, ctx, req, vol.shape[1:], 2)
+        seg.seg_release(ctx, req)
+    finally:
+        seg.seg_destroy(ctx)
+    rng = np.random.default_rng(4)
+    for c in range(2):
+        lab, cells, thr = res[c]
+        assert len(cells) > 0
+        if c == 0:
+            # Otsu level from an independently computed histogram
+            assert thr == oracle.otsu(smooth_histogram_slabs(vol[c]))
+        fg = check_threshold_samples(vol[c], lab, thr, rng)
+        assert fg > 0
+        check_adjacency_samples(lab, rng)
+        check_cells_by_planes(lab, cells, 30)
+        check_sampled_cells(lab, cells, rng)
