@@ -122,12 +122,34 @@ def dist_env():
     return ws, rank, local
 
 
-def make_workload(rank):
+def rank_seed(rank):
+    """Each rank segments its own time-lapse (weak scaling, independent
+    volumes, no data exchanged between ranks)."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(ms, device, ws):
+    """Largest per-rank time: the whole job ends when the slowest rank does."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gvox_per_s(voxels_per_rank, ms, ws):
+    """Whole-job throughput: voxels of all ranks over the slowest rank's time."""
+    return voxels_per_rank * ws / (ms / 1e3) / 1e9
+
+
+def make_workload(rank, frames=FRAMES):
     import synth
-    tl = synth.TimeLapse(seed=2 + 1000 * rank, frames=FRAMES)
+    tl = synth.TimeLapse(seed=rank_seed(rank), frames=frames)
     X, Y, Z = DIMS
-    host = np.empty((FRAMES, CHANNELS, Z, Y, X), dtype=np.uint16)
-    for t in range(FRAMES):
+    host = np.empty((frames, CHANNELS, Z, Y, X), dtype=np.uint16)
+    for t in range(frames):
         for c in range(CHANNELS):
             host[t, c] = tl.frame(t, c)
     return host
@@ -277,14 +299,11 @@ def run_gpu(args):
         for p in pend:
             finish(p)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev, ws)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     stats = seg.seg_get_stats(ctx)
-    value = vox_step * args.steps * ws / (ms / 1e3) / 1e9
+    value = job_gvox_per_s(vox_step * args.steps, ms, ws)
     launches = sum(k["launches"] for k in stats["kernels"].values())
 
     # dominant kernel and its roofline
@@ -347,13 +366,9 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        ems = max(e0.elapsed_time(e1), wall * 1e3)
-        if ws > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), dev, ws)
         seg.seg_destroy(ctx2)
-        e2e = {"value": vox_step * n2 * ws / (ems / 1e3) / 1e9, "unit": "Gvoxels/s",
+        e2e = {"value": job_gvox_per_s(vox_step * n2, ems, ws), "unit": "Gvoxels/s",
                "h2d_bytes_per_step": int(host.nbytes),
                "d2h_bytes_per_step": int(h_lab.numel() * 4 + cells_bytes),
                "steps": n2}
