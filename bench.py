@@ -50,6 +50,13 @@ KERNEL_BYTES_PER_VOXEL = {
     "row_runs": 1 / 8.0,
     "init": 0.0,
 }
+# DRAM bytes (read + write) per voxel measured by ncu on the same kernel build
+# (8 volume-channels of the 512x512x64 time-lapse, 134 M voxels, inputs larger
+# than L2); the per-launch figure scales with the voxels a launch processes
+# since every 512x512x64 volume is tiled the same way.
+KERNEL_TRAFFIC_BYTES_PER_VOXEL = {
+    "smooth_hist_otsu": 7.59,      # 5.75 read (halo lines re-read) + 1.85 smoothed write
+}
 
 
 def peaks():
@@ -246,7 +253,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    host = make_workload(rank)
+    host = make_workload(rank, args.frames)
     T, C, Z, Y, X = host.shape
     vox_step = host.size
     cpu = cpu_baseline(host) if (rank == 0 and not args.no_cpu) else None
@@ -255,8 +262,13 @@ def run_gpu(args):
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(dev)  # ordering stream (a non-null handle)
     flags = seg.SEG_PROFILE
+    tile = {}
+    if args.tile:
+        ty, tz = (int(v) for v in args.tile.split(","))
+        flags |= seg.SEG_FORCE_TILE
+        tile = {"tile_y": ty, "tile_z": tz}
     ctx = seg.seg_create(device=local, flags=flags, batch_window_us=2_000_000, order_stream=stream.cuda_stream,
-                         max_inflight=args.inflight)
+                         max_inflight=args.inflight, **tile)
 
     def step(ctx, in_ptr_fn):
         reqs = []
@@ -379,13 +391,15 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16/u32 (Otsu f64)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "voxels_per_step": vox_step, "min_volume": 30,
+            "config": {"workload": WORKLOAD.replace("x 60 frames", "x %d frames" % T), "voxels_per_step": vox_step, "min_volume": 30,
                        "tile": [int(stats["tile_y"]), int(stats["tile_z"])],
-                       "l2": "inputs 4.0 GB per step > 129 MB L2; no flush",
+                       "l2": "inputs %.2f GB per step > 129 MB L2; no flush" % (vox_step * 2 / 1e9),
                        "form": "batched (one graph-captured launch sequence per step)"},
             "hbm_fraction": value * ALGO_BYTES_PER_VOXEL / peak,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": (KERNEL_TRAFFIC_BYTES_PER_VOXEL[dom] * vox_launch
+                                     if dom in KERNEL_TRAFFIC_BYTES_PER_VOXEL else None),
                          "peak_source": peak_kind,
                          "algo_bytes_per_voxel": KERNEL_BYTES_PER_VOXEL[dom]},
             "kernel_share": shares,
@@ -520,6 +534,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--inflight", type=int, default=1,
                     help="batches in flight; 1 keeps per-kernel CUDA-event times free of overlap")
+    ap.add_argument("--frames", type=int, default=FRAMES,
+                    help="time-lapse frames per step (fewer frames: a small case for profiling)")
+    ap.add_argument("--tile", default="", help="force the tile height and z-chunk, e.g. 32,64")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain per-frame comparison")
