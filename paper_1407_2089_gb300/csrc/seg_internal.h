@@ -33,6 +33,11 @@ constexpr int TILE_X = 64;        // smoothing tile width (outputs along x)
 constexpr uint32_t UNION_LIMIT = 1u << 24;  // union-find retries before ERR_UNION
 constexpr int ROW_TILE = 256;     // rows per row tile (run kernels)
 constexpr int HIST_BINS = 65536;
+// Union-find bricks: BRICK_Y x BRICK_Z rows (one thread each) whose runs are
+// united in shared memory when there are at most BRICK_CAP of them.
+constexpr int BRICK_Y = 32;
+constexpr int BRICK_Z = 8;
+constexpr int BRICK_CAP = 4096;
 
 // One volume-channel inside a batch.  All pointers are device addresses.
 struct VolDev {
@@ -60,6 +65,11 @@ struct VolDev {
     uint32_t nrt;             // row tiles
     uint32_t tile_base;       // first flat smoothing-tile index
     uint32_t rt_base;         // first flat row-tile index
+    uint32_t nby;             // union-find bricks along y
+    uint32_t nbk;             // union-find bricks
+    uint32_t bk_base;         // first flat brick index
+    uint32_t nbt;             // row pairs that cross a brick face (k_union tasks)
+    uint32_t bt_base;         // first flat k_union task index
 };
 
 // Batch header, followed in memory by VolDev[nvol].
@@ -69,7 +79,9 @@ struct BatchHdr {
     uint32_t nrowtiles;  // row tiles over the batch
     uint32_t tile_z;     // z-chunk of a smoothing tile
     uint32_t tile_y;     // rows of a smoothing tile
-    uint32_t pad[3];
+    uint32_t nbricks;    // union-find bricks over the batch
+    uint32_t nbtasks;    // k_union tasks over the batch
+    uint32_t pad;
     VolDev vol[1];       // nvol entries
 };
 
@@ -78,7 +90,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 12;
+constexpr int NUM_KERNELS = 13;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {

@@ -37,8 +37,9 @@
 namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
-    "init",    "smooth_hist_otsu", "threshold_runs", "scan_runs", "row_runs",       "union",
-    "flatten", "keep_count",       "scan_keep",      "rank",      "label_features", "gather_stat"};
+    "init",        "smooth_hist_otsu", "threshold_runs", "scan_runs", "row_runs",
+    "union_local", "union",            "flatten",        "keep_count", "scan_keep",
+    "rank",        "label_features",   "gather_stat"};
 
 namespace {
 
@@ -71,6 +72,15 @@ __device__ __forceinline__ uint32_t find_vol_rt(const BatchHdr *__restrict__ h, 
     while (hi - lo > 1) {
         uint32_t mid = (lo + hi) >> 1;
         if (h->vol[mid].rt_base <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t find_vol_brick(const BatchHdr *__restrict__ h, uint32_t t) {
+    uint32_t lo = 0, hi = h->nvol;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (h->vol[mid].bk_base <= t) lo = mid; else hi = mid;
     }
     return lo;
 }
@@ -868,50 +878,256 @@ __device__ __forceinline__ void unite_rows(uint32_t *P, const uint32_t *__restri
     }
 }
 
-// One thread per (row, backward neighbour row): (y-1,z), (y-1,z-1), (y,z-1),
-// (y+1,z-1).  Every pair of 26-adjacent rows is visited once, and the four
-// sweeps of a row run in parallel (the union-find is latency-bound).
-__global__ void __launch_bounds__(4 * ROW_TILE) k_union(const BatchHdr *__restrict__ h) {
-    const uint32_t nb = threadIdx.x / ROW_TILE;
-    for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_rt(h, rt)];
-        const uint32_t row = (rt - V.rt_base) * ROW_TILE + (threadIdx.x % ROW_TILE);
-        if (row >= V.rows) continue;
-        const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
-        if (ib == ie) continue;
-        const uint32_t y = row % V.Y, z = row / V.Y;
-        uint32_t r;
-        if (nb == 0) {
-            if (y == 0) continue;
-            r = row - 1;
+// ---- brick-local union-find in shared memory ------------------------------
+//
+// Same rules as the global structure (parent index <= own index, union by
+// atomicMin towards the lower index, halving only while uniting), on local
+// run indices.  Local indices follow the global run order (brick rows are
+// taken z-major, y-minor, like the rows themselves), so the lowest local
+// index of a component is also its lowest global index within the brick.
+
+__device__ __forceinline__ uint32_t sm_find(volatile uint32_t *P, uint32_t x) {
+    uint32_t p = P[x];
+    while (p != x) {
+        const uint32_t g = P[p];
+        if (g == p) return p;
+        P[x] = g;
+        x = g;
+        p = P[x];
+    }
+    return x;
+}
+
+// Returns false when the retry limit is reached.
+__device__ __forceinline__ bool sm_union(volatile uint32_t *P, uint32_t a, uint32_t b, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        a = sm_find(P, a);
+        b = sm_find(P, b);
+        if (a == b) return true;
+        if (a < b) {
+            const uint32_t old = atomicMin(const_cast<uint32_t *>(P) + b, a);
+            if (old == b) return true;
+            b = old;
         } else {
-            if (z == 0) continue;
-            const uint32_t rz = row - V.Y;
-            if (nb == 1) {
-                if (y == 0) continue;
-                r = rz - 1;
-            } else if (nb == 2) {
-                r = rz;
+            const uint32_t old = atomicMin(const_cast<uint32_t *>(P) + a, b);
+            if (old == a) return true;
+            a = old;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool sm_unite_rows(volatile uint32_t *P, const uint32_t *RX, uint32_t i,
+                                              uint32_t ie, uint32_t j, uint32_t je, uint32_t limit) {
+    bool ok = true;
+    while (i < ie && j < je) {
+        const uint32_t a = RX[i], b = RX[j];
+        const uint32_t a0 = a & 0xFFFFu, a1 = a >> 16, b0 = b & 0xFFFFu, b1 = b >> 16;
+        if (b1 + 1 < a0) { ++j; continue; }
+        if (a1 + 1 < b0) { ++i; continue; }
+        ok &= sm_union(P, i, j, limit);
+        if (a1 < b1) ++i; else ++j;
+    }
+    return ok;
+}
+
+// Every run's parent becomes its root.  Called between barriers, with no
+// union in progress: a concurrent reader sees the old parent or the root,
+// both ancestors of the node.
+__device__ __forceinline__ void sm_compress(volatile uint32_t *P, uint32_t n, uint32_t t, uint32_t nt) {
+    for (uint32_t l = t; l < n; l += nt) {
+        uint32_t r = P[l];
+        if (r == l) continue;
+        uint32_t p = P[r];
+        while (p != r) {
+            r = p;
+            p = P[r];
+        }
+        P[l] = r;
+    }
+}
+
+// Global run index of local run l: the brick's runs of z-plane lz are one
+// contiguous global range starting at gb[lz] (local start soff[lz * BRICK_Y]).
+__device__ __forceinline__ uint32_t brick_global(uint32_t l, const uint32_t *soff, const uint32_t *gb) {
+    uint32_t lz = 0;
+#pragma unroll
+    for (int k = 1; k < BRICK_Z; ++k) lz = soff[k * BRICK_Y] <= l ? (uint32_t)k : lz;
+    return gb[lz] + (l - soff[lz * BRICK_Y]);
+}
+
+// One block per brick of BRICK_Y x BRICK_Z rows, one thread per row.  The
+// brick's runs are copied to shared memory, every 26-adjacent pair of runs
+// whose rows both lie in the brick is united there, and each run's global
+// parent is set to its local root (a valid union-find state: the parent is
+// a lower run of the same component).  A brick with more than BRICK_CAP runs
+// unites the same pairs through the global structure instead; that touches
+// only the brick's own runs, so it cannot interfere with other bricks.
+// k_union then unites the pairs of rows that lie in different bricks.
+__global__ void __launch_bounds__(BRICK_Y * BRICK_Z) k_union_local(const BatchHdr *__restrict__ h) {
+    constexpr int NT = BRICK_Y * BRICK_Z;
+    __shared__ uint32_t sx[BRICK_CAP];       // run x0 | x1 << 16
+    __shared__ uint32_t sp[BRICK_CAP];       // local parent
+    __shared__ uint32_t soff[NT + 1];        // local run offset of each brick row
+    __shared__ uint32_t gb[BRICK_Z];         // global index of each plane's first run
+    __shared__ uint32_t sbuf[33];
+    const uint32_t t = threadIdx.x, ly = t % BRICK_Y, lz = t / BRICK_Y;
+    for (uint32_t bk = blockIdx.x; bk < h->nbricks; bk += gridDim.x) {
+        const VolDev &V = h->vol[find_vol_brick(h, bk)];
+        const uint32_t lb = bk - V.bk_base;
+        const uint32_t y = (lb % V.nby) * BRICK_Y + ly, z = (lb / V.nby) * BRICK_Z + lz;
+        const bool valid = y < V.Y && z < V.Z;
+        const uint32_t row = z * V.Y + y;
+        uint32_t ib = 0, cnt = 0;
+        if (valid) {
+            ib = V.rowoff[row];
+            cnt = V.rowoff[row + 1] - ib;
+        }
+        uint32_t n;
+        // the scan's barriers also order this iteration's shared writes after
+        // the previous iteration's reads
+        const uint32_t loc = block_exscan<NT>(cnt, &n, sbuf);
+        if (n == 0) continue;  // n is the same in every thread
+        if (n > (uint32_t)BRICK_CAP) {
+            if (cnt) {
+                const uint32_t ie = ib + cnt, lim = V.union_limit;
+                uint32_t *err = V.stat + ST_ERROR;
+                if (ly > 0) unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[row - 1], ib, err, lim);
+                if (lz > 0) {
+                    const uint32_t rz = row - V.Y;
+                    if (ly > 0)
+                        unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[rz - 1], V.rowoff[rz], err, lim);
+                    unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[rz], V.rowoff[rz + 1], err, lim);
+                    if (ly + 1 < (uint32_t)BRICK_Y && y + 1 < V.Y)
+                        unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[rz + 1], V.rowoff[rz + 2], err, lim);
+                }
+            }
+            continue;
+        }
+        soff[t] = loc;
+        if (t == NT - 1) soff[NT] = n;
+        if (ly == 0) gb[lz] = ib;
+        __syncthreads();
+        for (uint32_t l = t; l < n; l += NT) {
+            sx[l] = V.run_x[brick_global(l, soff, gb)];
+            sp[l] = l;
+        }
+        __syncthreads();
+        // Three phases, each followed by a full compression (every run points
+        // at its root) so that no phase walks long paths: rows of one plane,
+        // then the same row of the plane below, then the two diagonals.
+        const uint32_t i1 = loc + cnt, lim = V.union_limit, u = t - BRICK_Y;
+        bool ok = true;
+        if (cnt && ly > 0) ok &= sm_unite_rows(sp, sx, loc, i1, soff[t - 1], soff[t], lim);  // (y-1, z)
+        __syncthreads();
+        sm_compress(sp, n, t, NT);
+        __syncthreads();
+        if (cnt && lz > 0) ok &= sm_unite_rows(sp, sx, loc, i1, soff[u], soff[u + 1], lim);  // (y, z-1)
+        __syncthreads();
+        sm_compress(sp, n, t, NT);
+        __syncthreads();
+        if (cnt && lz > 0) {
+            if (ly > 0) ok &= sm_unite_rows(sp, sx, loc, i1, soff[u - 1], soff[u], lim);     // (y-1, z-1)
+            if (ly + 1 < (uint32_t)BRICK_Y)
+                ok &= sm_unite_rows(sp, sx, loc, i1, soff[u + 1], soff[u + 2], lim);         // (y+1, z-1)
+        }
+        if (!ok) atomicOr(V.stat + ST_ERROR, ERR_UNION);
+        __syncthreads();
+        for (uint32_t l = t; l < n; l += NT) {
+            uint32_t r = l, p = sp[r];
+            while (p != r) {  // no writers any more; parents only decrease
+                r = p;
+                p = sp[r];
+            }
+            V.run_par[brick_global(l, soff, gb)] = brick_global(r, soff, gb);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t find_vol_btask(const BatchHdr *__restrict__ h, uint32_t t) {
+    uint32_t lo = 0, hi = h->nvol;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (h->vol[mid].bt_base <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One thread per pair of 26-adjacent rows that lie in different bricks, in
+// four groups (row y, plane z; neighbour rows (y-1,z), (y-1,z-1), (y,z-1),
+// (y+1,z-1)):
+//   planes z = 8k > 0: every row with each of its three neighbours in z-1;
+//   rows y = 32k > 0, every plane: (y-1, z);
+//   rows y = 32k > 0, the other planes z > 0: (y-1, z-1);
+//   rows y = 32k - 1 (y+1 < Y), the other planes z > 0: (y+1, z-1).
+// Consecutive threads take consecutive rows of a plane where they can.
+__global__ void __launch_bounds__(ROW_TILE) k_union(const BatchHdr *__restrict__ h) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x; gt < h->nbtasks; gt += stride) {
+        const VolDev &V = h->vol[find_vol_btask(h, gt)];
+        uint32_t t = gt - V.bt_base;
+        const uint32_t Y = V.Y, Z = V.Z;
+        const uint32_t nzb = (Z - 1) / BRICK_Z, nyb = (Y - 1) / BRICK_Y, nzi = Z - 1 - nzb;
+        uint32_t y, z, nb;
+        if (t < nzb * Y * 3) {
+            const uint32_t pz = t / (3 * Y), rem = t - pz * 3 * Y;
+            z = BRICK_Z * (pz + 1);
+            nb = 1 + rem / Y;
+            y = rem % Y;
+        } else {
+            t -= nzb * Y * 3;
+            if (t < nyb * Z) {
+                z = t / nyb;
+                y = BRICK_Y * (t % nyb + 1);
+                nb = 0;
             } else {
-                if (y + 1 >= V.Y) continue;
-                r = rz + 1;
+                t -= nyb * Z;
+                const uint32_t grp = t / (nyb * nzi);  // 0: (y-1, z-1) at y = 32k; 1: (y+1, z-1) at 32k - 1
+                t -= grp * nyb * nzi;
+                const uint32_t iz = t / nyb;
+                z = iz + 1 + iz / (BRICK_Z - 1);  // the iz-th plane with z % 8 != 0, z > 0
+                y = BRICK_Y * (t % nyb + 1) - grp;
+                nb = grp ? 3u : 1u;
             }
         }
+        if (nb == 1 && y == 0) continue;
+        if (nb == 3 && y + 1 >= Y) continue;
+        const uint32_t row = z * Y + y;
+        const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
+        if (ib == ie) continue;
+        const uint32_t r = nb == 0 ? row - 1 : row - Y + nb - 2;
         unite_rows(V.run_par, V.run_x, ib, ie, V.rowoff[r], V.rowoff[r + 1], V.stat + ST_ERROR, V.union_limit);
     }
 }
 
+// One thread per run (all volumes of the batch in turn): parent = root, and
+// the run's voxels are added to the root's size, one atomic per warp when all
+// its lanes share a root.
 __global__ void __launch_bounds__(ROW_TILE) k_flatten(const BatchHdr *__restrict__ h) {
-    for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_rt(h, rt)];
-        const uint32_t row = (rt - V.rt_base) * ROW_TILE + threadIdx.x;
-        if (row >= V.rows) continue;
-        const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
-        for (uint32_t r = ib; r < ie; ++r) {
-            const uint32_t root = uf_root(V.run_par, r);
-            V.run_par[r] = root;
-            const uint32_t x = V.run_x[r];
-            atomicAdd(V.run_aux + root, (x >> 16) - (x & 0xFFFFu) + 1u);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t v = 0; v < h->nvol; ++v) {
+        const VolDev &V = h->vol[v];
+        const uint32_t R = V.rowoff[V.rows];
+        // whole warps stay in the loop so that the shuffles see every lane
+        for (uint32_t j0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); j0 < R; j0 += stride) {
+            const uint32_t j = j0 + lane;
+            uint32_t root = 0xFFFFFFFFu, len = 0;
+            if (j < R) {
+                root = uf_root(V.run_par, j);
+                V.run_par[j] = root;
+                const uint32_t x = V.run_x[j];
+                len = (x >> 16) - (x & 0xFFFFu) + 1u;
+            }
+            const uint32_t r0 = __shfl_sync(FULL, root, 0);
+            if (__all_sync(FULL, root == r0 || j >= R)) {
+                uint32_t sum = len;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+                if (lane == 0) atomicAdd(V.run_aux + r0, sum);
+            } else if (j < R) {
+                atomicAdd(V.run_aux + root, len);
+            }
         }
     }
 }
@@ -994,23 +1210,29 @@ __device__ __forceinline__ void feat_global(seg_cell_features *f, unsigned long 
 }
 
 // One block per row tile (256 consecutive rows; their labels are one
-// contiguous range).  Labels first, one warp per row: a run's label is its
-// root's (set by k_rank), written with 16-byte streaming stores when rows are
-// 16-byte aligned (X % 4 == 0), zeros elsewhere.  Then, with no barrier in
-// between, one thread per run folds the run's contribution to its cell
-// (count, coordinate sums, bounding box) into a shared table; after a barrier
-// the table goes to the global cells with one set of atomics per (tile, cell).
+// contiguous range).  The tile's runs (x extent and final label, the label
+// being its root's, set by k_rank) are first loaded into shared memory by all
+// threads at once, so that no row waits on its own chain of global loads;
+// a tile with more than LABEL_RUNS runs reads them from global memory
+// instead.  Labels: one warp per row, 16-byte streaming stores when rows are
+// 16-byte aligned (X % 4 == 0), zeros between runs.  Then one thread per run
+// folds the run's contribution to its cell (count, coordinate sums, bounding
+// box) into a shared table; after a barrier the table goes to the global
+// cells with one set of atomics per (tile, cell).
+constexpr int LABEL_RUNS = 2048;
+
 __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__restrict__ h) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int WARPS = ROW_TILE / 32;
     __shared__ uint32_t soff[ROW_TILE + 1];
+    __shared__ uint32_t srx[LABEL_RUNS], slab[LABEL_RUNS];
     __shared__ FeatTable T;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[find_vol_rt(h, rt)];
         const uint32_t lt = rt - V.rt_base;
         const uint32_t row0 = lt * ROW_TILE;
         const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
-        __syncthreads();  // previous tile done with soff and T
+        __syncthreads();  // previous tile done with soff, srx, slab and T
         for (uint32_t i = tid; i <= nrows; i += ROW_TILE) soff[i] = V.rowoff[row0 + i];
         T.key[tid] = 0u;
         T.cnt[tid] = T.sx[tid] = T.sy[tid] = T.sz[tid] = 0ull;
@@ -1019,11 +1241,22 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
             T.mx[a][tid] = 0u;
         }
         __syncthreads();
-        // labels
-        const uint32_t X = V.X;
         const uint32_t *__restrict__ RX = V.run_x;
         const uint32_t *__restrict__ RP = V.run_par;
         const uint32_t *__restrict__ RA = V.run_aux;
+        const uint32_t rb = soff[0], re = soff[nrows];
+        const bool staged = re - rb <= (uint32_t)LABEL_RUNS;  // the same in every thread
+        if (staged) {
+            for (uint32_t j = rb + tid; j < re; j += ROW_TILE) {
+                srx[j - rb] = RX[j];
+                slab[j - rb] = RA[RP[j]];
+            }
+            __syncthreads();
+        }
+        auto run_x = [&](uint32_t j) { return staged ? srx[j - rb] : RX[j]; };
+        auto run_label = [&](uint32_t j) { return staged ? slab[j - rb] : RA[RP[j]]; };
+        // labels
+        const uint32_t X = V.X;
         const bool vec = (X & 3u) == 0u;
         for (uint32_t rr = warp; rr < nrows; rr += WARPS) {
             uint32_t *out = V.labels + (size_t)(row0 + rr) * X;
@@ -1034,7 +1267,7 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                     for (uint32_t x = lane; x < X / 4; x += 32) __stcs(o4 + x, make_uint4(0, 0, 0, 0));
                     continue;
                 }
-                uint32_t j = ib, jx = RX[ib], jl = RA[RP[ib]];
+                uint32_t j = ib, jx = run_x(ib), jl = run_label(ib);
                 for (uint32_t xb = 4 * lane; xb < X; xb += 128) {
                     uint32_t l4[4];
 #pragma unroll
@@ -1042,8 +1275,8 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                         const uint32_t x = xb + q;
                         while (j < ie && (jx >> 16) < x) {
                             if (++j < ie) {
-                                jx = RX[j];
-                                jl = RA[RP[j]];
+                                jx = run_x(j);
+                                jl = run_label(j);
                             }
                         }
                         l4[q] = (j < ie && (jx & 0xFFFFu) <= x) ? jl : 0u;
@@ -1055,21 +1288,20 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                     for (uint32_t x = lane; x < X; x += 32) __stcs(out + x, 0u);
                     continue;
                 }
-                uint32_t j = ib, jx = RX[ib], jl = RA[RP[ib]];
+                uint32_t j = ib, jx = run_x(ib), jl = run_label(ib);
                 for (uint32_t x = lane; x < X; x += 32) {
                     while (j < ie && (jx >> 16) < x) {
                         if (++j < ie) {
-                            jx = RX[j];
-                            jl = RA[RP[j]];
+                            jx = run_x(j);
+                            jl = run_label(j);
                         }
                     }
                     __stcs(out + x, (j < ie && (jx & 0xFFFFu) <= x) ? jl : 0u);
                 }
             }
         }
-        const uint32_t rb = soff[0], re = soff[nrows];
         for (uint32_t j = rb + tid; j < re; j += ROW_TILE) {
-            const uint32_t lab = RA[RP[j]];
+            const uint32_t lab = run_label(j);
             if (!lab || lab > V.k_cap) continue;
             // row of run j: the last i with soff[i] <= j
             uint32_t lo = 0, hi = nrows;
@@ -1079,7 +1311,7 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
             }
             const uint32_t row = row0 + lo;
             const uint32_t y = row % V.Y, z = row / V.Y;
-            const uint32_t rx = RX[j];
+            const uint32_t rx = run_x(j);
             const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
             const unsigned long long len = x1 - x0 + 1u;
             const unsigned long long sx = ((unsigned long long)(x0 + x1) * len) >> 1;
@@ -1193,7 +1425,9 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     rec();
     k_row_runs<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
-    k_union<<<p.grid_rows, 4 * ROW_TILE, 0, s>>>(d);
+    k_union_local<<<p.sms * 6, BRICK_Y * BRICK_Z, 0, s>>>(d);
+    rec();
+    k_union<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
     k_flatten<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();

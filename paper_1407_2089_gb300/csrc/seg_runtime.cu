@@ -213,7 +213,7 @@ void layout_request(Request &r) {
 void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = ctx->tile_z;
-    uint32_t v = 0, tiles = 0, rts = 0;
+    uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0;
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
         for (uint32_t c = 0; c < r->C; ++c) {
@@ -245,13 +245,30 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.nrt = g.nrt;
             V.tile_base = tiles;
             V.rt_base = rts;
+            V.nby = (uint32_t)cdiv(g.Y, BRICK_Y);
+            V.nbk = V.nby * (uint32_t)cdiv(g.Z, BRICK_Z);
+            V.bk_base = bks;
+            {
+                // row pairs across brick faces: every pair of a plane z = 8k
+                // with the plane below; pairs (y, y-1) with y = 32k in every
+                // plane; the two diagonals through y = 32k and y = 32k - 1 in
+                // the other planes
+                const uint32_t nzb = (g.Z - 1) / BRICK_Z, nyb = (g.Y - 1) / BRICK_Y;
+                const uint32_t nzi = g.Z - 1 - nzb;
+                V.nbt = nzb * g.Y * 3 + nyb * g.Z + 2 * nyb * nzi;
+            }
+            V.bt_base = bts;
             tiles += V.ntx * V.nty * V.ntz;
             rts += g.nrt;
+            bks += V.nbk;
+            bts += V.nbt;
         }
     }
     h->nvol = v;
     h->ntiles = tiles;
     h->nrowtiles = rts;
+    h->nbricks = bks;
+    h->nbtasks = bts;
     h->tile_z = tz;
     h->tile_y = ty;
     b.nvol = v;

@@ -155,3 +155,36 @@ def test_union_find_stress(seg, ctx):
         vol = np.where(rng.uniform(size=(Z, Y, X)) < p, 3000, 100).astype(np.uint16)
         lab, cells, thr = run(seg, ctx, vol, 1)
         assert_matches_oracle(vol, lab, cells, thr, min_volume=1, what="stress %d %s p=%.2f" % (trial, dims, p))
+
+
+def brick_run_counts(mask, by=32, bz=8):
+    """x-runs per brick of by x bz rows of a [Z][Y][X] boolean mask."""
+    starts = mask & ~np.concatenate([np.zeros_like(mask[..., :1]), mask[..., :-1]], axis=-1)
+    per_row = starts.sum(axis=-1)  # [Z][Y]
+    Z, Y = per_row.shape
+    out = []
+    for z0 in range(0, Z, bz):
+        for y0 in range(0, Y, by):
+            out.append(int(per_row[z0:z0 + bz, y0:y0 + by].sum()))
+    return out
+
+
+def test_union_bricks_shared_and_overflow(seg, ctx):
+    # Bricks of 32 x 8 rows unite their runs in shared memory when they hold
+    # at most 4096 runs; denser bricks go through the global union-find.  Here
+    # stripes (period 8 along x) fill the bricks at y < 32, z < 8 with more
+    # runs than that, blobs elsewhere cross brick faces, and the stripes'
+    # components reach into neighbouring bricks.
+    X, Y, Z = 300, 70, 20
+    rng = np.random.default_rng(21)
+    vol = rng.normal(100, 10, size=(Z, Y, X)).clip(0, 65535).astype(np.uint16)
+    xs = np.arange(X)
+    vol[:8, :32, :] = np.where((xs % 8) < 4, 3000, 100).astype(np.uint16)
+    for c in [(8, 32, 50), (7, 31, 200), (15, 60, 280), (3, 45, 10), (12, 20, 150)]:
+        z, y, x = c
+        vol[max(0, z - 3):z + 4, max(0, y - 4):y + 5, max(0, x - 5):x + 6] = 2500
+    ref = oracle.segment(vol, min_volume=1, keep_smoothed=True)
+    counts = brick_run_counts(ref.smoothed > ref.threshold)
+    assert max(counts) > 4096 and 0 < min(c for c in counts if c) <= 4096, counts
+    lab, cells, thr = run(seg, ctx, vol, 1)
+    assert_matches_oracle(vol, lab, cells, thr, min_volume=1, ref=ref, what="bricks")
