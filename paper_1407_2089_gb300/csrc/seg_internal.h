@@ -97,8 +97,15 @@ struct LaunchPlan {
     int sms;             // multiprocessors on the device
     int tile_y;          // 8, 16 or 32
     int grid_hist;       // persistent grid of the histogram kernel
-    int grid_rows;       // row-tile kernels
     int grid_vols;       // per-volume kernels
+    // persistent grids of the row-tile, brick and run kernels: the blocks
+    // that are resident at once (occupancy x SMs), so no block waits for a
+    // slot while others already loop over their second item
+    int grid_thr;        // k_threshold_runs
+    int grid_rows;       // k_row_runs, k_keep_count, k_rank
+    int grid_ul;         // k_union_local
+    int grid_task;       // k_union, k_flatten
+    int grid_lab;        // k_label_features
 };
 
 // Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)
@@ -113,6 +120,8 @@ cudaError_t launch_tile_probe(const BatchHdr *d_hdr, const LaunchPlan &plan, cud
 
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);
-cudaError_t configure_kernels(int device);
+// Sets kernel attributes on `device` and fills the persistent grid sizes of
+// `plan` (plan.sms must be set).
+cudaError_t configure_kernels(int device, LaunchPlan &plan);
 
 }  // namespace seg

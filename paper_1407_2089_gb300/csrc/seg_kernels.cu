@@ -32,6 +32,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <algorithm>
+
 #include "seg_internal.h"
 
 namespace seg {
@@ -231,9 +233,9 @@ __device__ __forceinline__ void cp_async_wait() {
 // thread); the row's offset inside its window (0..7 voxels) is kept per row,
 // so any X and any base alignment work.  Rows whose window would leave the
 // volume's buffer (first and last rows of a volume) are read with plain loads
-// instead.  Each plane is re-laid out as uint32 with the per-axis edge
-// clamping, then the x pass (each thread 4 adjacent outputs from 8 values),
-// the y pass (5 rows) and the z pass run; the z pass is in scatter form: with
+// instead.  The x pass (each thread 4 adjacent outputs from 8 values, edges
+// clamped per axis) writes one of two shared buffers while the y pass (5
+// rows) of the previous plane reads the other; the z pass is in scatter form: with
 // accumulators a0..a3 holding the partial sums of outputs zi-2..zi+1,
 //     out(zi-2) = a0 + P, a0 <- a1 + 4P, a1 <- a2 + 6P, a2 <- a3 + 4P, a3 <- P.
 // All sums are exact in uint32 (at most 4096 * 65535); the one rounding
@@ -254,7 +256,7 @@ struct Tile {
     static constexpr int RING_BYTES = S * STAGE_BYTES;
     static constexpr int SHIFT_BYTES = (S * RH + 15) / 16 * 16;
     // dynamic shared memory without / with the shared histogram
-    static constexpr size_t MASK_SMEM = RING_BYTES + 4 * PX_WORDS + SHIFT_BYTES;
+    static constexpr size_t MASK_SMEM = RING_BYTES + 8 * PX_WORDS + SHIFT_BYTES;  // two x-pass buffers
     static constexpr size_t HIST_SMEM = MASK_SMEM + 4 * (size_t)HIST_WORDS;
     static_assert(RH * CHUNKS <= NT, "one chunk per thread per plane");
 };
@@ -309,68 +311,77 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
         cp_async_commit();
     }
     uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0}, a3[4] = {0, 0, 0, 0};
-    for (int k = 0; k < n; ++k) {
-        const int zi = z0 - 2 + k;
-        const uint32_t st = (R.pc + k) % T::S;
-        cp_async_wait<T::S - 2>();  // this thread's chunks of plane k have landed
-        __syncthreads();            // everyone's have; the y pass of k-1 is done with spx
-        const unsigned char *stage = R.stage + st * T::STAGE_BYTES;
-        const int8_t *sh = R.shift + st * T::RH;
-        auto xitem = [&](const int it) {
-            const int r = it >> 4, qq = it & 15;
-            const int s = sh[r];
-            uint32_t v[8];
-            if (interior && s >= 0) {
-                // 8 voxels from a 2-byte-aligned offset: 5 words, byte_perm by parity
-                const int o = r * T::ROWE + s + 4 * qq;
-                const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (o >> 1);
-                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
-                const uint32_t sel = (o & 1) ? 0x5432u : 0x3210u;
-                const uint32_t p0 = __byte_perm(w0, w1, sel), p1 = __byte_perm(w1, w2, sel);
-                const uint32_t p2 = __byte_perm(w2, w3, sel), p3 = __byte_perm(w3, w4, sel);
-                v[0] = p0 & 0xFFFFu; v[1] = p0 >> 16; v[2] = p1 & 0xFFFFu; v[3] = p1 >> 16;
-                v[4] = p2 & 0xFFFFu; v[5] = p2 >> 16; v[6] = p3 & 0xFFFFu; v[7] = p3 >> 16;
-            } else {
-                // edge tile or a row read with plain loads: clamp every x
-                const uint16_t *st16 = reinterpret_cast<const uint16_t *>(stage) + r * T::ROWE;
-                const uint64_t rowg = ((uint64_t)min(max(zi, 0), (int)Z - 1) * Y +
-                                       (uint64_t)min(max(y0 - 2 + r, 0), (int)Y - 1)) * X;
+    // Iteration k runs the x pass of plane k into buffer k & 1 and the y and
+    // z passes of plane k - 1 from the other buffer, so one barrier per plane
+    // separates the two uses of each buffer and of each ring stage.
+    for (int k = 0; k <= n; ++k) {
+        if (k < n) cp_async_wait<T::S - 2>();  // this thread's chunks of plane k have landed
+        __syncthreads();  // everyone's have; x pass k-1 is written; y pass k-2 is done
+        if (k < n) {
+            const int zi = z0 - 2 + k;
+            const uint32_t st = (R.pc + k) % T::S;
+            const unsigned char *stage = R.stage + st * T::STAGE_BYTES;
+            const int8_t *sh = R.shift + st * T::RH;
+            uint32_t *px = spx + (k & 1) * T::PX_WORDS;
+            auto xitem = [&](const int it) {
+                const int r = it >> 4, qq = it & 15;
+                const int s = sh[r];
+                uint32_t v[8];
+                if (interior && s >= 0) {
+                    // 8 voxels from a 2-byte-aligned offset: 5 words, byte_perm by parity
+                    const int o = r * T::ROWE + s + 4 * qq;
+                    const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (o >> 1);
+                    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+                    const uint32_t sel = (o & 1) ? 0x5432u : 0x3210u;
+                    const uint32_t p0 = __byte_perm(w0, w1, sel), p1 = __byte_perm(w1, w2, sel);
+                    const uint32_t p2 = __byte_perm(w2, w3, sel), p3 = __byte_perm(w3, w4, sel);
+                    v[0] = p0 & 0xFFFFu; v[1] = p0 >> 16; v[2] = p1 & 0xFFFFu; v[3] = p1 >> 16;
+                    v[4] = p2 & 0xFFFFu; v[5] = p2 >> 16; v[6] = p3 & 0xFFFFu; v[7] = p3 >> 16;
+                } else {
+                    // edge tile or a row read with plain loads: clamp every x
+                    const uint16_t *st16 = reinterpret_cast<const uint16_t *>(stage) + r * T::ROWE;
+                    const uint64_t rowg = ((uint64_t)min(max(zi, 0), (int)Z - 1) * Y +
+                                           (uint64_t)min(max(y0 - 2 + r, 0), (int)Y - 1)) * X;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int x = min(max(x0 - 2 + 4 * qq + j, 0), (int)X - 1);
-                    v[j] = s >= 0 ? (uint32_t)st16[x - (x0 - 2) + s] : (uint32_t)__ldg(raw + rowg + x);
+                    for (int j = 0; j < 8; ++j) {
+                        const int x = min(max(x0 - 2 + 4 * qq + j, 0), (int)X - 1);
+                        v[j] = s >= 0 ? (uint32_t)st16[x - (x0 - 2) + s] : (uint32_t)__ldg(raw + rowg + x);
+                    }
                 }
-            }
-            *reinterpret_cast<uint4 *>(spx + r * TILE_X + 4 * qq) = xpass(v);
-        };
-        // quads beyond one per thread go to the top threads, which issue no copies
-        xitem(tid);
-        if (T::XITEMS > T::NT && tid >= 2 * T::NT - T::XITEMS) xitem(tid + T::XITEMS - T::NT);
-        // the stage of plane k-1 was last read before the barrier above
-        if (k + T::S - 1 < n) issue(zi + T::S - 1, (R.pc + k + T::S - 1) % T::S);
-        cp_async_commit();
-        __syncthreads();
-        const uint4 r0 = *reinterpret_cast<const uint4 *>(spx + (ty + 0) * TILE_X + 4 * q);
-        const uint4 r1 = *reinterpret_cast<const uint4 *>(spx + (ty + 1) * TILE_X + 4 * q);
-        const uint4 r2 = *reinterpret_cast<const uint4 *>(spx + (ty + 2) * TILE_X + 4 * q);
-        const uint4 r3 = *reinterpret_cast<const uint4 *>(spx + (ty + 3) * TILE_X + 4 * q);
-        const uint4 r4 = *reinterpret_cast<const uint4 *>(spx + (ty + 4) * TILE_X + 4 * q);
-        uint32_t p[4];
-        p[0] = r0.x + 4u * r1.x + 6u * r2.x + 4u * r3.x + r4.x;
-        p[1] = r0.y + 4u * r1.y + 6u * r2.y + 4u * r3.y + r4.y;
-        p[2] = r0.z + 4u * r1.z + 6u * r2.z + 4u * r3.z + r4.z;
-        p[3] = r0.w + 4u * r1.w + 6u * r2.w + 4u * r3.w + r4.w;
-        uint32_t s[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t out = a0[j] + p[j];
-            a0[j] = a1[j] + 4u * p[j];
-            a1[j] = a2[j] + 6u * p[j];
-            a2[j] = a3[j] + 4u * p[j];
-            a3[j] = p[j];
-            s[j] = (out + 2048u) >> 12;
+                *reinterpret_cast<uint4 *>(px + r * TILE_X + 4 * qq) = xpass(v);
+            };
+            // quads beyond one per thread go to the top threads, which issue no copies
+            xitem(tid);
+            if (T::XITEMS > T::NT && tid >= 2 * T::NT - T::XITEMS) xitem(tid + T::XITEMS - T::NT);
+            // the stage of plane k-1 was last read before the barrier above
+            if (k + T::S - 1 < n) issue(zi + T::S - 1, (R.pc + k + T::S - 1) % T::S);
+            cp_async_commit();
         }
-        emit(zi - 2, zi >= z0 + 2, s);
+        if (k > 0) {
+            const uint32_t *px = spx + ((k - 1) & 1) * T::PX_WORDS;
+            const int zi = z0 - 3 + k;  // plane k - 1
+            const uint4 r0 = *reinterpret_cast<const uint4 *>(px + (ty + 0) * TILE_X + 4 * q);
+            const uint4 r1 = *reinterpret_cast<const uint4 *>(px + (ty + 1) * TILE_X + 4 * q);
+            const uint4 r2 = *reinterpret_cast<const uint4 *>(px + (ty + 2) * TILE_X + 4 * q);
+            const uint4 r3 = *reinterpret_cast<const uint4 *>(px + (ty + 3) * TILE_X + 4 * q);
+            const uint4 r4 = *reinterpret_cast<const uint4 *>(px + (ty + 4) * TILE_X + 4 * q);
+            uint32_t p[4];
+            p[0] = r0.x + 4u * r1.x + 6u * r2.x + 4u * r3.x + r4.x;
+            p[1] = r0.y + 4u * r1.y + 6u * r2.y + 4u * r3.y + r4.y;
+            p[2] = r0.z + 4u * r1.z + 6u * r2.z + 4u * r3.z + r4.z;
+            p[3] = r0.w + 4u * r1.w + 6u * r2.w + 4u * r3.w + r4.w;
+            uint32_t s[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t out = a0[j] + p[j];
+                a0[j] = a1[j] + 4u * p[j];
+                a1[j] = a2[j] + 6u * p[j];
+                a2[j] = a3[j] + 4u * p[j];
+                a3[j] = p[j];
+                s[j] = (out + 2048u) >> 12;
+            }
+            emit(zi - 2, zi >= z0 + 2, s);
+        }
     }
     cp_async_wait<0>();  // only empty groups remain; keeps the count at zero between tiles
     R.pc += (uint32_t)n;
@@ -629,7 +640,7 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist(const BatchHdr *__re
     unsigned char *ring = dsm;
     uint32_t *sh = reinterpret_cast<uint32_t *>(dsm + T::RING_BYTES);
     uint32_t *spx = sh + HIST_WORDS;
-    int8_t *shift = reinterpret_cast<int8_t *>(spx + T::PX_WORDS);
+    int8_t *shift = reinterpret_cast<int8_t *>(spx + 2 * T::PX_WORDS);
     Ring R{ring, shift, 0};
     for (int i = threadIdx.x; i < HIST_WORDS / 4; i += T::NT)
         reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
@@ -1269,19 +1280,34 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                 }
                 uint32_t j = ib, jx = run_x(ib), jl = run_label(ib);
                 for (uint32_t xb = 4 * lane; xb < X; xb += 128) {
-                    uint32_t l4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t x = xb + q;
-                        while (j < ie && (jx >> 16) < x) {
-                            if (++j < ie) {
-                                jx = run_x(j);
-                                jl = run_label(j);
-                            }
+                    // j: the first run that does not end before xb
+                    while (j < ie && (jx >> 16) < xb) {
+                        if (++j < ie) {
+                            jx = run_x(j);
+                            jl = run_label(j);
                         }
-                        l4[q] = (j < ie && (jx & 0xFFFFu) <= x) ? jl : 0u;
                     }
-                    __stcs(o4 + xb / 4, make_uint4(l4[0], l4[1], l4[2], l4[3]));
+                    uint4 o;
+                    if (j >= ie || (jx & 0xFFFFu) > xb + 3u) {
+                        o = make_uint4(0, 0, 0, 0);            // the 4 voxels lie before run j
+                    } else if ((jx & 0xFFFFu) <= xb && (jx >> 16) >= xb + 3u) {
+                        o = make_uint4(jl, jl, jl, jl);        // all 4 inside run j
+                    } else {
+                        uint32_t l4[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t x = xb + q;
+                            while (j < ie && (jx >> 16) < x) {
+                                if (++j < ie) {
+                                    jx = run_x(j);
+                                    jl = run_label(j);
+                                }
+                            }
+                            l4[q] = (j < ie && (jx & 0xFFFFu) <= x) ? jl : 0u;
+                        }
+                        o = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+                    }
+                    __stcs(o4 + xb / 4, o);
                 }
             } else {
                 if (ib == ie) {
@@ -1377,7 +1403,7 @@ size_t hist_smem_bytes(int tile_y) {
     return tile_y == 8 ? Tile<8>::HIST_SMEM : (tile_y == 16 ? Tile<16>::HIST_SMEM : Tile<32>::HIST_SMEM);
 }
 
-cudaError_t configure_kernels(int device) {
+cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return e;
 #define SEG_CFG(TY)                                                                        \
@@ -1389,6 +1415,24 @@ cudaError_t configure_kernels(int device) {
     SEG_CFG(16)
     SEG_CFG(32)
 #undef SEG_CFG
+    auto resident = [&](const void *fn, int threads, int *grid) -> cudaError_t {
+        int per_sm = 0;
+        const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+        if (r != cudaSuccess) return r;
+        *grid = plan.sms * (per_sm > 0 ? per_sm : 1);
+        return cudaSuccess;
+    };
+    int g1 = 0, g2 = 0, g3 = 0;
+    if ((e = resident((const void *)k_threshold_runs, ROW_TILE, &plan.grid_thr)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_row_runs, ROW_TILE, &g1)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_keep_count, ROW_TILE, &g2)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_rank, ROW_TILE, &g3)) != cudaSuccess) return e;
+    plan.grid_rows = std::min(g1, std::min(g2, g3));
+    if ((e = resident((const void *)k_union_local, BRICK_Y * BRICK_Z, &plan.grid_ul)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_union, ROW_TILE, &g1)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_flatten, ROW_TILE, &g2)) != cudaSuccess) return e;
+    plan.grid_task = std::min(g1, g2);
+    if ((e = resident((const void *)k_label_features, ROW_TILE, &plan.grid_lab)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1419,17 +1463,17 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     }
     if (e != cudaSuccess) return e;
     rec();
-    k_threshold_runs<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
+    k_threshold_runs<<<p.grid_thr, ROW_TILE, 0, s>>>(d);
     rec();
     k_tile_scan<0><<<p.grid_vols, 1024, 0, s>>>(d);
     rec();
     k_row_runs<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
-    k_union_local<<<p.sms * 6, BRICK_Y * BRICK_Z, 0, s>>>(d);
+    k_union_local<<<p.grid_ul, BRICK_Y * BRICK_Z, 0, s>>>(d);
     rec();
-    k_union<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
+    k_union<<<p.grid_task, ROW_TILE, 0, s>>>(d);
     rec();
-    k_flatten<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
+    k_flatten<<<p.grid_task, ROW_TILE, 0, s>>>(d);
     rec();
     k_keep_count<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
@@ -1437,7 +1481,7 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     rec();
     k_rank<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
-    k_label_features<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
+    k_label_features<<<p.grid_lab, ROW_TILE, 0, s>>>(d);
     rec();
     k_gather_stat<<<p.grid_vols, 256, 0, s>>>(d, stat_out);
     if (ev) cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal);
@@ -1486,7 +1530,7 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist_noalloc(const __grid
     unsigned char *ring = dsm;
     uint32_t *sh = reinterpret_cast<uint32_t *>(dsm + T::RING_BYTES);
     uint32_t *spx = sh + HIST_WORDS;
-    int8_t *shift = reinterpret_cast<int8_t *>(spx + T::PX_WORDS);
+    int8_t *shift = reinterpret_cast<int8_t *>(spx + 2 * T::PX_WORDS);
     const VolDev &V = h->vol[0];
     Ring R{ring, shift, 0};
     for (int i = threadIdx.x; i < HIST_WORDS / 4; i += T::NT)

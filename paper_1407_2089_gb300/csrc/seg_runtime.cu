@@ -545,7 +545,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->t0 = Clock::now();
     CK(cudaSetDevice(cfg->device));
     CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, cfg->device));
-    CK(configure_kernels(cfg->device));
+
     ctx->plain = (cfg->flags & SEG_PLAIN) != 0;
     ctx->graphs = !ctx->plain && !(cfg->flags & SEG_NO_GRAPH);
     ctx->profile = (cfg->flags & SEG_PROFILE) != 0;
@@ -561,9 +561,9 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->tile_z = tz;
     ctx->plan.sms = ctx->sms;
     ctx->plan.tile_y = ty;
-    ctx->plan.grid_hist = ctx->sms;  // one resident block per SM (128 KiB histogram)
-    ctx->plan.grid_rows = ctx->sms * 8;
+    ctx->plan.grid_hist = ctx->sms;  // one resident block per SM (176 KiB histogram)
     ctx->plan.grid_vols = ctx->sms;
+    CK(configure_kernels(cfg->device, ctx->plan));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
