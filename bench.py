@@ -393,6 +393,7 @@ def run_gpu(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("x 60 frames", "x %d frames" % T), "voxels_per_step": vox_step, "min_volume": 30,
                        "tile": [int(stats["tile_y"]), int(stats["tile_z"])],
+                       "batches_per_step": stats["batches"] / args.steps,
                        "l2": "inputs %.2f GB per step > 129 MB L2; no flush" % (vox_step * 2 / 1e9),
                        "form": "batched (one graph-captured launch sequence per step)"},
             "hbm_fraction": value * ALGO_BYTES_PER_VOXEL / peak,

@@ -69,23 +69,38 @@ __device__ __forceinline__ uint32_t find_vol_tile(const BatchHdr *__restrict__ h
     return lo;
 }
 
-__device__ __forceinline__ uint32_t find_vol_rt(const BatchHdr *__restrict__ h, uint32_t t) {
-    uint32_t lo = 0, hi = h->nvol;
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (h->vol[mid].rt_base <= t) lo = mid; else hi = mid;
-    }
-    return lo;
-}
+// Volume lookup for the persistent loops: the blocks copy the volumes' first
+// flat indices of one kind (row tiles, bricks, ...) into shared memory once,
+// so each item's binary search runs on shared memory rather than on one
+// header cache line per step.  Batches of more than SMEM_VOLS volumes search
+// the header itself.
+constexpr uint32_t SMEM_VOLS = 512;
 
-__device__ __forceinline__ uint32_t find_vol_brick(const BatchHdr *__restrict__ h, uint32_t t) {
-    uint32_t lo = 0, hi = h->nvol;
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (h->vol[mid].bk_base <= t) lo = mid; else hi = mid;
+template <uint32_t VolDev::*BASE>
+struct VolIndex {
+    uint32_t base[SMEM_VOLS];
+    __device__ __forceinline__ void load(const BatchHdr *__restrict__ h) {
+        if (h->nvol <= SMEM_VOLS)
+            for (uint32_t i = threadIdx.x; i < h->nvol; i += blockDim.x) base[i] = h->vol[i].*BASE;
+        __syncthreads();
     }
-    return lo;
-}
+    __device__ __forceinline__ uint32_t find(const BatchHdr *__restrict__ h, uint32_t t) const {
+        const uint32_t nv = h->nvol;
+        uint32_t lo = 0, hi = nv;
+        if (nv <= SMEM_VOLS) {
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (base[mid] <= t) lo = mid; else hi = mid;
+            }
+        } else {
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (h->vol[mid].*BASE <= t) lo = mid; else hi = mid;
+            }
+        }
+        return lo;
+    }
+};
 
 // Exclusive block scan of one uint32 per thread; *total gets the block sum.
 // sbuf: 33 words of shared memory.  Contains the barriers needed so that
@@ -678,11 +693,13 @@ __global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist(const BatchHdr *__re
 // clear, across word boundaries) are counted per row.  The row counts and the
 // row tile's total feed the run scan.
 __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::rt_base> VI;
+    VI.load(h);
     constexpr int WARPS = ROW_TILE / 32;
     __shared__ uint32_t wsum[WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_rt(h, rt)];
+        const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
         const uint32_t row0 = lt * ROW_TILE;
         const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
@@ -843,9 +860,11 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const BatchHdr *__restrict__
 }
 
 __global__ void __launch_bounds__(ROW_TILE) k_row_runs(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::rt_base> VI;
+    VI.load(h);
     __shared__ uint32_t sbuf[33];
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_rt(h, rt)];
+        const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
         const uint32_t row = lt * ROW_TILE + threadIdx.x;
         const uint32_t cnt = row < V.rows ? V.rowoff[row] : 0u;
@@ -976,6 +995,8 @@ __device__ __forceinline__ uint32_t brick_global(uint32_t l, const uint32_t *sof
 // only the brick's own runs, so it cannot interfere with other bricks.
 // k_union then unites the pairs of rows that lie in different bricks.
 __global__ void __launch_bounds__(BRICK_Y * BRICK_Z) k_union_local(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::bk_base> VI;
+    VI.load(h);
     constexpr int NT = BRICK_Y * BRICK_Z;
     __shared__ uint32_t sx[BRICK_CAP];       // run x0 | x1 << 16
     __shared__ uint32_t sp[BRICK_CAP];       // local parent
@@ -984,7 +1005,7 @@ __global__ void __launch_bounds__(BRICK_Y * BRICK_Z) k_union_local(const BatchHd
     __shared__ uint32_t sbuf[33];
     const uint32_t t = threadIdx.x, ly = t % BRICK_Y, lz = t / BRICK_Y;
     for (uint32_t bk = blockIdx.x; bk < h->nbricks; bk += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_brick(h, bk)];
+        const VolDev &V = h->vol[VI.find(h, bk)];
         const uint32_t lb = bk - V.bk_base;
         const uint32_t y = (lb % V.nby) * BRICK_Y + ly, z = (lb / V.nby) * BRICK_Z + lz;
         const bool valid = y < V.Y && z < V.Z;
@@ -1055,15 +1076,6 @@ __global__ void __launch_bounds__(BRICK_Y * BRICK_Z) k_union_local(const BatchHd
     }
 }
 
-__device__ __forceinline__ uint32_t find_vol_btask(const BatchHdr *__restrict__ h, uint32_t t) {
-    uint32_t lo = 0, hi = h->nvol;
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (h->vol[mid].bt_base <= t) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 // One thread per pair of 26-adjacent rows that lie in different bricks, in
 // four groups (row y, plane z; neighbour rows (y-1,z), (y-1,z-1), (y,z-1),
 // (y+1,z-1)):
@@ -1073,9 +1085,11 @@ __device__ __forceinline__ uint32_t find_vol_btask(const BatchHdr *__restrict__ 
 //   rows y = 32k - 1 (y+1 < Y), the other planes z > 0: (y+1, z-1).
 // Consecutive threads take consecutive rows of a plane where they can.
 __global__ void __launch_bounds__(ROW_TILE) k_union(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::bt_base> VI;
+    VI.load(h);
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x; gt < h->nbtasks; gt += stride) {
-        const VolDev &V = h->vol[find_vol_btask(h, gt)];
+        const VolDev &V = h->vol[VI.find(h, gt)];
         uint32_t t = gt - V.bt_base;
         const uint32_t Y = V.Y, Z = V.Z;
         const uint32_t nzb = (Z - 1) / BRICK_Z, nyb = (Y - 1) / BRICK_Y, nzi = Z - 1 - nzb;
@@ -1144,9 +1158,11 @@ __global__ void __launch_bounds__(ROW_TILE) k_flatten(const BatchHdr *__restrict
 }
 
 __global__ void __launch_bounds__(ROW_TILE) k_keep_count(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::rt_base> VI;
+    VI.load(h);
     __shared__ uint32_t sbuf[33];
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_rt(h, rt)];
+        const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
         const uint32_t row = lt * ROW_TILE + threadIdx.x;
         uint32_t cnt = 0;
@@ -1162,9 +1178,11 @@ __global__ void __launch_bounds__(ROW_TILE) k_keep_count(const BatchHdr *__restr
 }
 
 __global__ void __launch_bounds__(ROW_TILE) k_rank(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::rt_base> VI;
+    VI.load(h);
     __shared__ uint32_t sbuf[33];
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_rt(h, rt)];
+        const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
         const uint32_t row = lt * ROW_TILE + threadIdx.x;
         const uint32_t cnt = row < V.rows ? V.rowk[row] : 0u;
@@ -1201,11 +1219,26 @@ __global__ void __launch_bounds__(ROW_TILE) k_rank(const BatchHdr *__restrict__ 
 constexpr int FEAT_SLOTS = 256;
 constexpr int FEAT_PROBES = 8;
 
+// cx packs a cell's voxel count in a row tile (at most 256 * 65536 = 2^24,
+// 25 bits) under its x-coordinate sum (at most 256 * (0 + ... + 65535) < 2^39),
+// so one 64-bit add carries both exactly.
+constexpr int CX_SHIFT = 25;
+
 struct FeatTable {
     uint32_t key[FEAT_SLOTS];
-    unsigned long long cnt[FEAT_SLOTS], sx[FEAT_SLOTS], sy[FEAT_SLOTS], sz[FEAT_SLOTS];
+    unsigned long long cx[FEAT_SLOTS], sy[FEAT_SLOTS], sz[FEAT_SLOTS];
     uint32_t mn[3][FEAT_SLOTS], mx[3][FEAT_SLOTS];
 };
+
+// Shared min / max that skip the atomic when the value cannot change the
+// result: a stale read is never below the current minimum (above the
+// current maximum), so a value it rules out is ruled out for good.
+__device__ __forceinline__ void smin(uint32_t *a, uint32_t v) {
+    if (v < *reinterpret_cast<volatile uint32_t *>(a)) atomicMin(a, v);
+}
+__device__ __forceinline__ void smax(uint32_t *a, uint32_t v) {
+    if (v > *reinterpret_cast<volatile uint32_t *>(a)) atomicMax(a, v);
+}
 
 __device__ __forceinline__ void feat_global(seg_cell_features *f, unsigned long long cnt, unsigned long long sx,
                                             unsigned long long sy, unsigned long long sz, const uint32_t *mn,
@@ -1233,20 +1266,23 @@ __device__ __forceinline__ void feat_global(seg_cell_features *f, unsigned long 
 constexpr int LABEL_RUNS = 2048;
 
 __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::rt_base> VI;
+    VI.load(h);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int WARPS = ROW_TILE / 32;
     __shared__ uint32_t soff[ROW_TILE + 1];
     __shared__ uint32_t srx[LABEL_RUNS], slab[LABEL_RUNS];
+    __shared__ uint8_t srow[LABEL_RUNS];  // row of each staged run in the tile
     __shared__ FeatTable T;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
-        const VolDev &V = h->vol[find_vol_rt(h, rt)];
+        const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
         const uint32_t row0 = lt * ROW_TILE;
         const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
         __syncthreads();  // previous tile done with soff, srx, slab and T
         for (uint32_t i = tid; i <= nrows; i += ROW_TILE) soff[i] = V.rowoff[row0 + i];
         T.key[tid] = 0u;
-        T.cnt[tid] = T.sx[tid] = T.sy[tid] = T.sz[tid] = 0ull;
+        T.cx[tid] = T.sy[tid] = T.sz[tid] = 0ull;
         for (int a = 0; a < 3; ++a) {
             T.mn[a][tid] = 0xFFFFFFFFu;
             T.mx[a][tid] = 0u;
@@ -1262,6 +1298,8 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                 srx[j - rb] = RX[j];
                 slab[j - rb] = RA[RP[j]];
             }
+            if ((uint32_t)tid < nrows)
+                for (uint32_t j = soff[tid]; j < soff[tid + 1]; ++j) srow[j - rb] = (uint8_t)tid;
             __syncthreads();
         }
         auto run_x = [&](uint32_t j) { return staged ? srx[j - rb] : RX[j]; };
@@ -1276,6 +1314,40 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                 uint4 *o4 = reinterpret_cast<uint4 *>(out);
                 if (ib == ie) {
                     for (uint32_t x = lane; x < X / 4; x += 32) __stcs(o4 + x, make_uint4(0, 0, 0, 0));
+                    continue;
+                }
+                if (staged && ie - ib <= 16u) {
+                    // few runs: every lane goes through the row's runs in
+                    // step (broadcast reads, no divergent walk) and fills its
+                    // 4 chunks of each 512-voxel segment
+                    uint32_t j = ib;
+                    for (uint32_t seg = 0; seg < X; seg += 512) {
+                        uint32_t v[4][4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) v[c][q] = 0u;
+                        while (j < ie && (srx[j - rb] >> 16) < seg) ++j;
+                        for (uint32_t k = j; k < ie; ++k) {
+                            const uint32_t rx = srx[k - rb];
+                            const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
+                            if (x0 >= seg + 512u) break;
+                            const uint32_t L = slab[k - rb];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const uint32_t xb = seg + 128u * c + 4u * lane;
+                                if (x1 < xb || x0 > xb + 3u) continue;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    if (xb + q - x0 <= x1 - x0) v[c][q] = L;
+                            }
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const uint32_t xb = seg + 128u * c + 4u * lane;
+                            if (xb < X) __stcs(o4 + xb / 4, make_uint4(v[c][0], v[c][1], v[c][2], v[c][3]));
+                        }
+                    }
                     continue;
                 }
                 uint32_t j = ib, jx = run_x(ib), jl = run_label(ib);
@@ -1329,11 +1401,17 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
         for (uint32_t j = rb + tid; j < re; j += ROW_TILE) {
             const uint32_t lab = run_label(j);
             if (!lab || lab > V.k_cap) continue;
-            // row of run j: the last i with soff[i] <= j
-            uint32_t lo = 0, hi = nrows;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (soff[mid] <= j) lo = mid; else hi = mid;
+            uint32_t lo;
+            if (staged) {
+                lo = srow[j - rb];
+            } else {
+                // row of run j: the last i with soff[i] <= j
+                uint32_t hi = nrows;
+                lo = 0;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (soff[mid] <= j) lo = mid; else hi = mid;
+                }
             }
             const uint32_t row = row0 + lo;
             const uint32_t y = row % V.Y, z = row / V.Y;
@@ -1341,28 +1419,27 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
             const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
             const unsigned long long len = x1 - x0 + 1u;
             const unsigned long long sx = ((unsigned long long)(x0 + x1) * len) >> 1;
-            const unsigned long long sy = len * y, sz = len * z;
             uint32_t slot = (lab * 2654435761u) >> 24;
             bool done = false;
             for (int p = 0; p < FEAT_PROBES && !done; ++p, slot = (slot + 1) & (FEAT_SLOTS - 1)) {
-                const uint32_t k = atomicCAS(&T.key[slot], 0u, lab);
+                uint32_t k = *reinterpret_cast<volatile uint32_t *>(&T.key[slot]);
+                if (k == 0u) k = atomicCAS(&T.key[slot], 0u, lab);
                 if (k == 0u || k == lab) {
-                    atomicAdd(&T.cnt[slot], len);
-                    atomicAdd(&T.sx[slot], sx);
-                    atomicAdd(&T.sy[slot], sy);
-                    atomicAdd(&T.sz[slot], sz);
-                    atomicMin(&T.mn[0][slot], x0);
-                    atomicMax(&T.mx[0][slot], x1);
-                    atomicMin(&T.mn[1][slot], y);
-                    atomicMax(&T.mx[1][slot], y);
-                    atomicMin(&T.mn[2][slot], z);
-                    atomicMax(&T.mx[2][slot], z);
+                    atomicAdd(&T.cx[slot], (sx << CX_SHIFT) | len);
+                    atomicAdd(&T.sy[slot], len * y);
+                    atomicAdd(&T.sz[slot], len * z);
+                    smin(&T.mn[0][slot], x0);
+                    smax(&T.mx[0][slot], x1);
+                    smin(&T.mn[1][slot], y);
+                    smax(&T.mx[1][slot], y);
+                    smin(&T.mn[2][slot], z);
+                    smax(&T.mx[2][slot], z);
                     done = true;
                 }
             }
             if (!done) {
                 const uint32_t mn[3] = {x0, y, z}, mx[3] = {x1, y, z};
-                feat_global(V.feat + (lab - 1), len, sx, sy, sz, mn, mx);
+                feat_global(V.feat + (lab - 1), len, sx, len * y, len * z, mn, mx);
             }
         }
         __syncthreads();
@@ -1371,7 +1448,9 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
             if (lab) {
                 const uint32_t mn[3] = {T.mn[0][tid], T.mn[1][tid], T.mn[2][tid]};
                 const uint32_t mx[3] = {T.mx[0][tid], T.mx[1][tid], T.mx[2][tid]};
-                feat_global(V.feat + (lab - 1), T.cnt[tid], T.sx[tid], T.sy[tid], T.sz[tid], mn, mx);
+                const unsigned long long cx = T.cx[tid];
+                feat_global(V.feat + (lab - 1), cx & ((1ull << CX_SHIFT) - 1), cx >> CX_SHIFT, T.sy[tid],
+                            T.sz[tid], mn, mx);
             }
         }
     }

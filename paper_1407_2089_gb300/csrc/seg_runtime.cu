@@ -151,6 +151,7 @@ struct seg_ctx {
     seg_req next_id = 1;
     bool stop = false;
     bool flush = false;
+    uint64_t flush_upto = 0;  // requests with a lower id are flushed
     Clock::time_point t0;
     Clock::time_point first_pending;
     std::thread worker;
@@ -426,11 +427,15 @@ void worker_main(seg_ctx *ctx) {
         for (Slot &s : ctx->slots)
             if (!s.busy) { free_slot = &s; break; }
         if (free_slot && !ctx->pending.empty()) {
-            bool go = ctx->flush || ctx->stop || ctx->cfg.batch_window_us == 0;
+            bool go = ctx->stop || ctx->cfg.batch_window_us == 0;
             if (!go) {
                 double waited = std::chrono::duration<double, std::micro>(Clock::now() - ctx->first_pending).count();
                 go = waited >= ctx->cfg.batch_window_us;
             }
+            // a flush launches what was submitted before it, not requests
+            // that arrive while the batch is being formed
+            const bool flush_only = !go && ctx->flush;
+            go = go || ctx->flush;
             if (go) {
                 Batch *b = new Batch();
                 b->slot = free_slot;
@@ -443,6 +448,10 @@ void worker_main(seg_ctx *ctx) {
                 while (!ctx->pending.empty() && b->reqs.size() < max_req) {
                     Request *r = ctx->pending.front();
                     ctx->pending.pop_front();
+                    if (flush_only && r->id >= ctx->flush_upto) {
+                        rest.push_back(r);
+                        break;
+                    }
                     if (nv + r->C > ctx->cap_vols) {
                         rest.push_back(r);
                         break;
@@ -470,8 +479,8 @@ void worker_main(seg_ctx *ctx) {
                     ctx->pending.pop_front();
                 }
                 ctx->pending.swap(rest);
-                if (ctx->pending.empty()) ctx->flush = false;
-                else ctx->first_pending = Clock::now();
+                ctx->flush = !ctx->pending.empty() && ctx->pending.front()->id < ctx->flush_upto;
+                if (!ctx->pending.empty()) ctx->first_pending = Clock::now();
                 if (b->reqs.empty()) {
                     delete b;  // budget exhausted: wait for completions
                 } else {
@@ -710,7 +719,10 @@ int seg_flush(seg_ctx *ctx) {
     if (!ctx) return SEG_EINVAL;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
-        if (!ctx->pending.empty()) ctx->flush = true;
+        if (!ctx->pending.empty()) {
+            ctx->flush = true;
+            ctx->flush_upto = ctx->next_id;
+        }
     }
     ctx->cv.notify_all();
     return SEG_OK;
@@ -735,6 +747,7 @@ int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream) {
     if (!r) return SEG_ENOENT;
     if (!r->issued && r->state == SEG_PENDING) {
         ctx->flush = true;
+        ctx->flush_upto = std::max<uint64_t>(ctx->flush_upto, r->id + 1);
         ctx->cv.notify_all();
         ctx->cv.wait(lk, [&] { return r->issued || r->state != SEG_PENDING; });
     }
