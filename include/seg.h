@@ -89,7 +89,7 @@ typedef struct {
     uint64_t hbm_budget_bytes; /* admission limit for all device state; 0 -> 80 %
                                   of the device's free memory at seg_create      */
     uint32_t flags;            /* SEG_FORCE_TILE | SEG_PLAIN | ...               */
-    uint32_t tile_y;           /* smoothing tile rows: 8, 16 or 32 (FORCE_TILE) */
+    uint32_t tile_y;           /* smoothing tile rows: 16, 32 or 64 (FORCE_TILE) */
     uint32_t tile_z;           /* smoothing z-chunk, >= 1 (FORCE_TILE)           */
     uint32_t max_batch_volumes;/* volume-channels per launch; 0 -> 512           */
     uint32_t batch_window_us;  /* wait this long for more requests before a

@@ -50,7 +50,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 // two copies (one per half-warp, the second offset by 16 words so that equal
 // levels in the two copies sit in different banks); the rest share words as
 // two 16-bit counters.
-constexpr int HIST_LOW = 8192;
+constexpr int HIST_LOW = 4096;
 constexpr int HIST_COPY1 = HIST_LOW + 16;         // word offset of the second copy
 constexpr int HIST_PAIRS = 2 * HIST_LOW + 16;     // word offset of the 16-bit pairs
 constexpr int HIST_WORDS = HIST_PAIRS + (HIST_BINS - HIST_LOW) / 2;
@@ -223,9 +223,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// src and dst 16-byte aligned; cached in L2 only.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+// dst (a shared-memory address) and src 16-byte aligned; cached in L2 only.
+__device__ __forceinline__ void cp_async16(uint32_t dst, uintptr_t src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -237,43 +237,49 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ----------------------------------------------------------------------------
-// separable binomial smoothing of one tile (shared by both passes)
+// separable binomial smoothing of one tile
 // ----------------------------------------------------------------------------
 //
-// A block of 16*TY threads owns a TILE_X x TY column of outputs and marches
-// along z from z0 - 2 to z1 + 1.  Input planes stream through a ring of S
-// shared-memory stages, S - 1 planes ahead of use.  For each of the plane's
-// TY+4 halo rows the 16-byte-aligned 160-byte window holding the row's 68
-// needed voxels is copied as ten 16-byte cp.async chunks (one chunk per
-// thread); the row's offset inside its window (0..7 voxels) is kept per row,
-// so any X and any base alignment work.  Rows whose window would leave the
-// volume's buffer (first and last rows of a volume) are read with plain loads
-// instead.  The x pass (each thread 4 adjacent outputs from 8 values, edges
+// A block of 8*TY threads owns a TILE_X x TY column of outputs (each thread 8
+// adjacent outputs of one row) and marches along z from z0 - 2 to z1 + 1.
+// Input planes stream through a ring of S shared-memory stages, S - 1 planes
+// ahead of use.  For each of the plane's TY+4 halo rows the 16-byte-aligned
+// 160-byte window holding the row's 68 needed voxels is copied as ten 16-byte
+// cp.async chunks; the row's offset inside its window (0..7 voxels) is kept
+// per row, so any X and any base alignment work.  Rows whose window would
+// leave the volume's buffer (first and last rows of a volume) are read with
+// plain loads instead.  The x pass (8 adjacent outputs from 12 inputs, edges
 // clamped per axis) writes one of two shared buffers while the y pass (5
-// rows) of the previous plane reads the other; the z pass is in scatter form: with
-// accumulators a0..a3 holding the partial sums of outputs zi-2..zi+1,
+// rows) of the previous plane reads the other; the z pass is in scatter form:
+// with accumulators a0..a3 holding the partial sums of outputs zi-2..zi+1,
 //     out(zi-2) = a0 + P, a0 <- a1 + 4P, a1 <- a2 + 6P, a2 <- a3 + 4P, a3 <- P.
 // All sums are exact in uint32 (at most 4096 * 65535); the one rounding
 // (S + 2048) >> 12 is applied to the completed sum, which equals the 125-term
 // definition.
+//
+// x-pass buffer layout: the 8 outputs of octet o of a row sit at words 4o..4o+3
+// (the first four) and 32+4o..32+4o+3 (the last four), so that the eight
+// threads of one row read or write 8 distinct groups of 4 banks.
 
 template <int TY>
 struct Tile {
-    static constexpr int NT = 16 * TY;
+    static constexpr int NT = 8 * TY;
     static constexpr int RH = TY + 4;
     static constexpr int PX_WORDS = RH * TILE_X;
-    static constexpr int XITEMS = RH * (TILE_X / 4);  // x-pass quads per plane
-    static constexpr int S = 4;              // ring stages
+    static constexpr int XITEMS = RH * (TILE_X / 8);  // x-pass octets per plane
+    static constexpr int S = 3;              // ring stages
     static constexpr int ROWB = 160;         // bytes staged per halo row
     static constexpr int ROWE = ROWB / 2;    // voxels per staged row
     static constexpr int CHUNKS = ROWB / 16; // 16-byte copies per row
+    static constexpr int NCHUNK = RH * CHUNKS;
     static constexpr int STAGE_BYTES = RH * ROWB;
     static constexpr int RING_BYTES = S * STAGE_BYTES;
     static constexpr int SHIFT_BYTES = (S * RH + 15) / 16 * 16;
     // dynamic shared memory without / with the shared histogram
     static constexpr size_t MASK_SMEM = RING_BYTES + 8 * PX_WORDS + SHIFT_BYTES;  // two x-pass buffers
     static constexpr size_t HIST_SMEM = MASK_SMEM + 4 * (size_t)HIST_WORDS;
-    static_assert(RH * CHUNKS <= NT, "one chunk per thread per plane");
+    static_assert(NCHUNK <= 2 * NT, "at most two copy chunks per thread per plane");
+    static_assert(XITEMS <= 2 * NT, "at most two x-pass octets per thread per plane");
 };
 
 struct Ring {
@@ -282,14 +288,25 @@ struct Ring {
     uint32_t pc;           // planes consumed by this block so far
 };
 
-// x pass of one quad: 4 adjacent outputs from 8 consecutive inputs.
-__device__ __forceinline__ uint4 xpass(const uint32_t *v) {
-    uint4 o;
-    o.x = v[0] + 4u * v[1] + 6u * v[2] + 4u * v[3] + v[4];
-    o.y = v[1] + 4u * v[2] + 6u * v[3] + 4u * v[4] + v[5];
-    o.z = v[2] + 4u * v[3] + 6u * v[4] + 4u * v[5] + v[6];
-    o.w = v[3] + 4u * v[4] + 6u * v[5] + 4u * v[6] + v[7];
-    return o;
+// x pass of 8 adjacent outputs from the 12 inputs v[0..11].
+__device__ __forceinline__ void xpass8(const uint32_t *v, uint32_t *o) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = v[j] + 4u * v[j + 1] + 6u * v[j + 2] + 4u * v[j + 3] + v[j + 4];
+}
+
+// The 12 inputs of an octet from the 7 staged words that hold them, the
+// first input at voxel offset `odd` (0 or 1) of the first word.
+__device__ __forceinline__ void unpack12(const uint32_t *w, bool odd, uint32_t *v) {
+    const uint32_t sel = odd ? 0x5432u : 0x3210u;
+    uint32_t wd[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) wd[k] = w[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const uint32_t p = __byte_perm(wd[k], wd[k + 1], sel);
+        v[2 * k] = p & 0xFFFFu;
+        v[2 * k + 1] = p >> 16;
+    }
 }
 
 template <int TY, class Emit>
@@ -298,34 +315,81 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
                                             uint32_t *__restrict__ spx, Ring &R, Emit &emit) {
     using T = Tile<TY>;
     const int tid = threadIdx.x;
-    const int q = tid & 15, ty = tid >> 4;
+    const int q = tid & 7, ty = tid >> 3;
     const int n = z1 - z0 + 4;
     const uint64_t plane = (uint64_t)X * Y;
     const uintptr_t lo = (uintptr_t)raw, hi = lo + 2 * plane * Z;
-    const bool interior = x0 >= 2 && x0 + TILE_X + 2 <= (int)X;
-    // this thread's copy chunk: halo row cr, 16-byte piece cc; byte offset of
-    // the row's first needed voxel inside a plane
-    const int cr = tid / T::CHUNKS, cc = tid - cr * T::CHUNKS;
-    const bool copier = tid < T::RH * T::CHUNKS;
-    const int64_t crow = 2 * ((int64_t)min(max(y0 - 2 + cr, 0), (int)Y - 1) * X + (x0 - 2));
+    // Planes strictly between the first and the last cannot take a window
+    // outside the buffer when a plane holds more than two windows.
+    const bool mid_inside = plane >= (uint64_t)T::ROWB;
+    // this thread's copy chunks (at most two): halo row cr, 16-byte piece cc;
+    // address of the row's first needed voxel in plane 0 (may lie before the
+    // buffer)
+    int cr[2], cc[2];
+    uintptr_t crow[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int c = tid + u * T::NT;
+        cr[u] = c / T::CHUNKS;
+        cc[u] = c - cr[u] * T::CHUNKS;
+        crow[u] = lo + (uintptr_t)(2 * ((int64_t)min(max(y0 - 2 + cr[u], 0), (int)Y - 1) * X + (x0 - 2)));
+    }
+    const uint32_t ring0 = smem_addr(R.stage);
     auto issue = [&](int zi, uint32_t st) {
-        if (!copier) return;
-        const uintptr_t addr = lo + 2 * (uint64_t)min(max(zi, 0), (int)Z - 1) * plane + (uintptr_t)crow;
-        const uintptr_t a16 = addr & ~(uintptr_t)15;
-        const bool inside = a16 >= lo && a16 + T::ROWB <= hi;
-        if (cc == 0) R.shift[st * T::RH + cr] = inside ? (int8_t)((addr - a16) >> 1) : (int8_t)-1;
-        if (inside)
-            cp_async16(R.stage + st * T::STAGE_BYTES + cr * T::ROWB + cc * 16,
-                       reinterpret_cast<const void *>(a16 + 16 * cc));
+        const int zc = min(max(zi, 0), (int)Z - 1);
+        const bool mid = mid_inside && zc > 0 && zc + 1 < (int)Z;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (tid + u * T::NT >= T::NCHUNK) break;
+            const uintptr_t addr = crow[u] + 2 * plane * (uint64_t)zc;
+            const uintptr_t a16 = addr & ~(uintptr_t)15;
+            const bool inside = mid || (a16 >= lo && a16 + T::ROWB <= hi);
+            if (cc[u] == 0) R.shift[st * T::RH + cr[u]] = inside ? (int8_t)((addr & 15) >> 1) : (int8_t)-1;
+            if (inside)
+                cp_async16(ring0 + st * T::STAGE_BYTES + cr[u] * T::ROWB + cc[u] * 16, a16 + 16 * cc[u]);
+        }
     };
-    emit.bind(x0 + 4 * q, y0 + ty);
+    // this thread's x-pass octets (row r, octet o of the 8 in a row); the
+    // second one only for the first XITEMS - NT threads
+    constexpr int EXTRA = T::XITEMS - T::NT;
+    const bool two = EXTRA > 0 && tid < EXTRA;
+    const int rA = tid >> 3, oA = tid & 7, rB = (tid + T::NT) >> 3, oB = tid & 7;
+    // an octet reads inputs x0 + 8 o - 2 .. x0 + 8 o + 9; inside the row it
+    // takes the staged words, at a volume edge it clamps every x
+    const bool fA = x0 + 8 * oA - 2 >= 0 && x0 + 8 * oA + 10 <= (int)X;
+    auto xitem = [&](const unsigned char *stage, const int8_t *sh, uint32_t *px, int r, int o, bool f, int zi) {
+        const int s = sh[r];
+        uint32_t v[12];
+        if (f && s >= 0) {
+            const int off = r * T::ROWE + s + 8 * o;
+            unpack12(reinterpret_cast<const uint32_t *>(stage) + (off >> 1), off & 1, v);
+        } else {
+            const uint16_t *st16 = reinterpret_cast<const uint16_t *>(stage) + r * T::ROWE;
+            const uint64_t rowg = ((uint64_t)min(max(zi, 0), (int)Z - 1) * Y +
+                                   (uint64_t)min(max(y0 - 2 + r, 0), (int)Y - 1)) * X;
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                const int x = min(max(x0 - 2 + 8 * o + j, 0), (int)X - 1);
+                v[j] = s >= 0 ? (uint32_t)st16[x - (x0 - 2) + s] : (uint32_t)__ldg(raw + rowg + x);
+            }
+        }
+        uint32_t out[8];
+        xpass8(v, out);
+        uint32_t *d = px + r * TILE_X + 4 * o;
+        *reinterpret_cast<uint4 *>(d) = make_uint4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<uint4 *>(d + 32) = make_uint4(out[4], out[5], out[6], out[7]);
+    };
+    const uint32_t *py = spx + ty * TILE_X + 4 * q;  // this thread's y-pass column
+    emit.bind(x0 + 8 * q, y0 + ty);
     __syncthreads();  // the previous tile is done with the ring and spx
 #pragma unroll
     for (int j = 0; j < T::S - 1; ++j) {
         if (j < n) issue(z0 - 2 + j, (R.pc + j) % T::S);
         cp_async_commit();
     }
-    uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0}, a3[4] = {0, 0, 0, 0};
+    uint32_t a0[8], a1[8], a2[8], a3[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a0[j] = a1[j] = a2[j] = a3[j] = 0u;
     // Iteration k runs the x pass of plane k into buffer k & 1 and the y and
     // z passes of plane k - 1 from the other buffer, so one barrier per plane
     // separates the two uses of each buffer and of each ring stage.
@@ -338,56 +402,31 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
             const unsigned char *stage = R.stage + st * T::STAGE_BYTES;
             const int8_t *sh = R.shift + st * T::RH;
             uint32_t *px = spx + (k & 1) * T::PX_WORDS;
-            auto xitem = [&](const int it) {
-                const int r = it >> 4, qq = it & 15;
-                const int s = sh[r];
-                uint32_t v[8];
-                if (interior && s >= 0) {
-                    // 8 voxels from a 2-byte-aligned offset: 5 words, byte_perm by parity
-                    const int o = r * T::ROWE + s + 4 * qq;
-                    const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (o >> 1);
-                    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
-                    const uint32_t sel = (o & 1) ? 0x5432u : 0x3210u;
-                    const uint32_t p0 = __byte_perm(w0, w1, sel), p1 = __byte_perm(w1, w2, sel);
-                    const uint32_t p2 = __byte_perm(w2, w3, sel), p3 = __byte_perm(w3, w4, sel);
-                    v[0] = p0 & 0xFFFFu; v[1] = p0 >> 16; v[2] = p1 & 0xFFFFu; v[3] = p1 >> 16;
-                    v[4] = p2 & 0xFFFFu; v[5] = p2 >> 16; v[6] = p3 & 0xFFFFu; v[7] = p3 >> 16;
-                } else {
-                    // edge tile or a row read with plain loads: clamp every x
-                    const uint16_t *st16 = reinterpret_cast<const uint16_t *>(stage) + r * T::ROWE;
-                    const uint64_t rowg = ((uint64_t)min(max(zi, 0), (int)Z - 1) * Y +
-                                           (uint64_t)min(max(y0 - 2 + r, 0), (int)Y - 1)) * X;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int x = min(max(x0 - 2 + 4 * qq + j, 0), (int)X - 1);
-                        v[j] = s >= 0 ? (uint32_t)st16[x - (x0 - 2) + s] : (uint32_t)__ldg(raw + rowg + x);
-                    }
-                }
-                *reinterpret_cast<uint4 *>(px + r * TILE_X + 4 * qq) = xpass(v);
-            };
-            // quads beyond one per thread go to the top threads, which issue no copies
-            xitem(tid);
-            if (T::XITEMS > T::NT && tid >= 2 * T::NT - T::XITEMS) xitem(tid + T::XITEMS - T::NT);
+            xitem(stage, sh, px, rA, oA, fA, zi);
+            if (two) xitem(stage, sh, px, rB, oB, fA, zi);
             // the stage of plane k-1 was last read before the barrier above
             if (k + T::S - 1 < n) issue(zi + T::S - 1, (R.pc + k + T::S - 1) % T::S);
             cp_async_commit();
         }
         if (k > 0) {
-            const uint32_t *px = spx + ((k - 1) & 1) * T::PX_WORDS;
+            const uint32_t *pk = py + ((k - 1) & 1) * T::PX_WORDS;
             const int zi = z0 - 3 + k;  // plane k - 1
-            const uint4 r0 = *reinterpret_cast<const uint4 *>(px + (ty + 0) * TILE_X + 4 * q);
-            const uint4 r1 = *reinterpret_cast<const uint4 *>(px + (ty + 1) * TILE_X + 4 * q);
-            const uint4 r2 = *reinterpret_cast<const uint4 *>(px + (ty + 2) * TILE_X + 4 * q);
-            const uint4 r3 = *reinterpret_cast<const uint4 *>(px + (ty + 3) * TILE_X + 4 * q);
-            const uint4 r4 = *reinterpret_cast<const uint4 *>(px + (ty + 4) * TILE_X + 4 * q);
-            uint32_t p[4];
-            p[0] = r0.x + 4u * r1.x + 6u * r2.x + 4u * r3.x + r4.x;
-            p[1] = r0.y + 4u * r1.y + 6u * r2.y + 4u * r3.y + r4.y;
-            p[2] = r0.z + 4u * r1.z + 6u * r2.z + 4u * r3.z + r4.z;
-            p[3] = r0.w + 4u * r1.w + 6u * r2.w + 4u * r3.w + r4.w;
-            uint32_t s[4];
+            uint32_t p[8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int h = 0; h < 2; ++h) {
+                const uint4 r0 = *reinterpret_cast<const uint4 *>(pk + 32 * h + 0 * TILE_X);
+                const uint4 r1 = *reinterpret_cast<const uint4 *>(pk + 32 * h + 1 * TILE_X);
+                const uint4 r2 = *reinterpret_cast<const uint4 *>(pk + 32 * h + 2 * TILE_X);
+                const uint4 r3 = *reinterpret_cast<const uint4 *>(pk + 32 * h + 3 * TILE_X);
+                const uint4 r4 = *reinterpret_cast<const uint4 *>(pk + 32 * h + 4 * TILE_X);
+                p[4 * h + 0] = r0.x + 4u * r1.x + 6u * r2.x + 4u * r3.x + r4.x;
+                p[4 * h + 1] = r0.y + 4u * r1.y + 6u * r2.y + 4u * r3.y + r4.y;
+                p[4 * h + 2] = r0.z + 4u * r1.z + 6u * r2.z + 4u * r3.z + r4.z;
+                p[4 * h + 3] = r0.w + 4u * r1.w + 6u * r2.w + 4u * r3.w + r4.w;
+            }
+            uint32_t s[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
                 const uint32_t out = a0[j] + p[j];
                 a0[j] = a1[j] + 4u * p[j];
                 a1[j] = a2[j] + 6u * p[j];
@@ -406,59 +445,59 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
 // in 32-bit shared words; higher levels share words as two 16-bit counters,
 // and the thread whose increment takes such a counter to 0x8000 moves 0x8000
 // to the global bin, so a counter never exceeds 0x8000 + (increments in
-// flight) < 0x10000 and never carries into its neighbour.  With STORE the smoothed voxels are also
-// written (8-byte stores when rows are 8-byte aligned).  bind() fixes, per
-// tile, which of the thread's 4 voxels lie inside the volume.
+// flight) < 0x10000 and never carries into its neighbour.  With STORE the
+// smoothed voxels are also written (16-byte stores when rows are 16-byte
+// aligned).  bind() fixes, per tile, which of the thread's 8 voxels lie
+// inside the volume.
 template <bool STORE>
 struct HistEmit {
     uint32_t *sh;
     uint32_t *gh;
     uint16_t *sm;       // smoothed volume (STORE only)
     uint32_t X, Y;
-    uint32_t valid;     // bit j: voxel j of the quad is inside the volume
+    uint32_t valid;     // bit j: voxel j of the octet is inside the volume
     uint32_t copy;      // word offset of this half-warp's copy of the low levels
     uint16_t *row;      // &sm[y * X + xb] at z = 0
     size_t zstride;     // voxels per z-plane
-    bool vec;           // all 4 inside and 8-byte aligned
+    bool vec;           // all 8 inside and 16-byte aligned
     __device__ __forceinline__ void bind(int xb, int y) {
         valid = 0;
         if ((uint32_t)y < Y)
-            for (int j = 0; j < 4; ++j) valid |= ((uint32_t)(xb + j) < X ? 1u : 0u) << j;
+            for (int j = 0; j < 8; ++j) valid |= ((uint32_t)(xb + j) < X ? 1u : 0u) << j;
         copy = (threadIdx.x & 16u) ? (uint32_t)HIST_COPY1 : 0u;
         if (STORE) {
             zstride = (size_t)X * Y;
             row = sm + ((size_t)(valid ? (uint32_t)y : 0u) * X + (uint32_t)xb);
-            vec = valid == 0xFu && (X & 3u) == 0u;
+            vec = valid == 0xFFu && (X & 7u) == 0u;
         }
     }
     __device__ __forceinline__ void operator()(int z, bool live, const uint32_t *s) {
         if (!live) return;
-        const uint32_t vmax = max(max(s[0], s[1]), max(s[2], s[3]));
-        // warp-uniform fast path: 4 voxels inside, aligned row, low levels only
-        const bool fast = __all_sync(FULL, valid == 0xFu && (!STORE || vec) && vmax < (uint32_t)HIST_LOW);
+        const uint32_t vmax = max(max(max(s[0], s[1]), max(s[2], s[3])), max(max(s[4], s[5]), max(s[6], s[7])));
+        // warp-uniform fast path: 8 voxels inside, aligned row, low levels only
+        const bool fast = __all_sync(FULL, valid == 0xFFu && (!STORE || vec) && vmax < (uint32_t)HIST_LOW);
         if (fast) {
             if (STORE)
-                *reinterpret_cast<uint2 *>(row + (size_t)(uint32_t)z * zstride) =
-                    make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
+                *reinterpret_cast<uint4 *>(row + (size_t)(uint32_t)z * zstride) =
+                    make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
             uint32_t *hc = sh + copy;
-            atomicAdd(hc + s[0], 1u);
-            atomicAdd(hc + s[1], 1u);
-            atomicAdd(hc + s[2], 1u);
-            atomicAdd(hc + s[3], 1u);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) atomicAdd(hc + s[j], 1u);
             return;
         }
         if (STORE) {
             uint16_t *p = row + (size_t)(uint32_t)z * zstride;
             if (vec) {
-                *reinterpret_cast<uint2 *>(p) = make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
+                *reinterpret_cast<uint4 *>(p) =
+                    make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < 8; ++j)
                     if (valid & (1u << j)) p[j] = (uint16_t)s[j];
             }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 8; ++j) {
             if (valid & (1u << j)) {
                 const uint32_t v = s[j];
                 if (v < (uint32_t)HIST_LOW) {
@@ -649,7 +688,7 @@ __global__ void k_init(const BatchHdr *__restrict__ h) {
 }
 
 template <int TY>
-__global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist(const BatchHdr *__restrict__ h) {
+__global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist(const BatchHdr *__restrict__ h) {
     using T = Tile<TY>;
     extern __shared__ __align__(128) unsigned char dsm[];
     unsigned char *ring = dsm;
@@ -1472,14 +1511,14 @@ cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStre
         ++k;
     };
     rec();
-    k_smooth_hist<TY><<<p.grid_hist, 16 * TY, hist_smem_bytes(TY), s>>>(d);
+    k_smooth_hist<TY><<<p.grid_hist, Tile<TY>::NT, hist_smem_bytes(TY), s>>>(d);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t hist_smem_bytes(int tile_y) {
-    return tile_y == 8 ? Tile<8>::HIST_SMEM : (tile_y == 16 ? Tile<16>::HIST_SMEM : Tile<32>::HIST_SMEM);
+    return tile_y == 16 ? Tile<16>::HIST_SMEM : (tile_y == 32 ? Tile<32>::HIST_SMEM : Tile<64>::HIST_SMEM);
 }
 
 cudaError_t configure_kernels(int device, LaunchPlan &plan) {
@@ -1490,9 +1529,9 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
                              (int)hist_smem_bytes(TY));                                    \
     if (e != cudaSuccess) return e;                                                        \
 
-    SEG_CFG(8)
     SEG_CFG(16)
     SEG_CFG(32)
+    SEG_CFG(64)
 #undef SEG_CFG
     auto resident = [&](const void *fn, int threads, int *grid) -> cudaError_t {
         int per_sm = 0;
@@ -1518,9 +1557,9 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
 cudaError_t launch_tile_probe(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
     k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
     switch (p.tile_y) {
-        case 8: k_smooth_hist<8><<<p.grid_hist, 16 * 8, hist_smem_bytes(8), s>>>(d); break;
-        case 16: k_smooth_hist<16><<<p.grid_hist, 16 * 16, hist_smem_bytes(16), s>>>(d); break;
-        default: k_smooth_hist<32><<<p.grid_hist, 16 * 32, hist_smem_bytes(32), s>>>(d); break;
+        case 16: k_smooth_hist<16><<<p.grid_hist, Tile<16>::NT, hist_smem_bytes(16), s>>>(d); break;
+        case 32: k_smooth_hist<32><<<p.grid_hist, Tile<32>::NT, hist_smem_bytes(32), s>>>(d); break;
+        default: k_smooth_hist<64><<<p.grid_hist, Tile<64>::NT, hist_smem_bytes(64), s>>>(d); break;
     }
     return cudaGetLastError();
 }
@@ -1536,9 +1575,9 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
     cudaError_t e;
     switch (p.tile_y) {
-        case 8: e = launch_tile_kernels<8>(d, p, s, ev, k); break;
         case 16: e = launch_tile_kernels<16>(d, p, s, ev, k); break;
-        default: e = launch_tile_kernels<32>(d, p, s, ev, k); break;
+        case 32: e = launch_tile_kernels<32>(d, p, s, ev, k); break;
+        default: e = launch_tile_kernels<64>(d, p, s, ev, k); break;
     }
     if (e != cudaSuccess) return e;
     rec();
@@ -1590,7 +1629,7 @@ constexpr int NOALLOC_WORDS = HIST_BINS + ST_WORDS;  // 262,208 bytes per device
 // Every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
 
-constexpr int NOALLOC_TY = 32;
+constexpr int NOALLOC_TY = 64;
 constexpr int NOALLOC_TZ = 64;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
@@ -1602,7 +1641,7 @@ std::mutex g_noalloc_mu;
 
 // The histogram kernel with its one-volume descriptor passed by value.
 template <int TY>
-__global__ void __launch_bounds__(16 * TY, 1) k_smooth_hist_noalloc(const __grid_constant__ BatchHdr hdr) {
+__global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist_noalloc(const __grid_constant__ BatchHdr hdr) {
     using T = Tile<TY>;
     const BatchHdr *h = &hdr;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -1691,7 +1730,7 @@ extern "C" int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dim
     // the array keeps the previous call's contents: clear bins and counters
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * NOALLOC_WORDS, s);
     if (e == cudaSuccess) {
-        k_smooth_hist_noalloc<NOALLOC_TY><<<sms, 16 * NOALLOC_TY, hist_smem_bytes(NOALLOC_TY), s>>>(hdr);
+        k_smooth_hist_noalloc<NOALLOC_TY><<<sms, Tile<NOALLOC_TY>::NT, hist_smem_bytes(NOALLOC_TY), s>>>(hdr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)

@@ -108,7 +108,7 @@ struct Slot {
     BatchHdr *d_hdr = nullptr;
     uint32_t *h_stat = nullptr;  // pinned
     uint32_t *d_stat = nullptr;
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // tile_y 8/16/32
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // tile_y 16/32/64
     cudaEvent_t ev[NUM_KERNELS + 1] = {};
     Batch *busy = nullptr;
 };
@@ -275,7 +275,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     b.nvol = v;
 }
 
-int graph_index(int ty) { return ty == 8 ? 0 : (ty == 16 ? 1 : 2); }
+int graph_index(int ty) { return ty == 16 ? 0 : (ty == 32 ? 1 : 2); }
 
 // Enqueues descriptor upload, the pipeline and the status read-back.
 int enqueue_body(seg_ctx *ctx, Slot &s, uint32_t nvol) {
@@ -291,7 +291,7 @@ int enqueue_body(seg_ctx *ctx, Slot &s, uint32_t nvol) {
 // candidate tile shape on the batch's own data and keep the fastest.  The
 // pipeline's results do not depend on the tile shape.
 int tune_tiles(seg_ctx *ctx, Batch &b) {
-    static const int kTy[] = {16, 32};
+    static const int kTy[] = {32, 64};
     static const uint32_t kTz[] = {16, 32, 64};
     Slot &s = *b.slot;
     cudaEvent_t e0, e1;
@@ -545,7 +545,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
         return SEG_EINVAL;
     }
     if (cfg->flags & SEG_FORCE_TILE) {
-        if (cfg->tile_y != 8 && cfg->tile_y != 16 && cfg->tile_y != 32) return SEG_EINVAL;
+        if (cfg->tile_y != 16 && cfg->tile_y != 32 && cfg->tile_y != 64) return SEG_EINVAL;
         if (cfg->tile_z == 0) return SEG_EINVAL;
     }
     std::unique_ptr<seg_ctx> ctx(new seg_ctx());
@@ -563,7 +563,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     ctx->budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (uint64_t)(0.8 * (double)fr);
-    int ty = 32;
+    int ty = 64;
     uint32_t tz = 64;
     if (cfg->flags & SEG_FORCE_TILE) { ty = (int)cfg->tile_y; tz = cfg->tile_z; }
     ctx->tuned = (cfg->flags & SEG_FORCE_TILE) != 0;

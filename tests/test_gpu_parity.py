@@ -88,7 +88,7 @@ def test_wide_rows_reach_65536(seg, ctx):
     assert_matches_oracle(vol, lab, cells, thr, min_volume=1, what="X=65536")
 
 
-@pytest.mark.parametrize("ty,tz", [(8, 1), (8, 7), (16, 3), (16, 64), (32, 5), (32, 200)])
+@pytest.mark.parametrize("ty,tz", [(16, 1), (16, 7), (32, 3), (32, 64), (64, 5), (64, 200)])
 def test_tile_shape_invariance(seg, ty, tz):
     c = seg.seg_create(device=0, flags=seg.SEG_FORCE_TILE, tile_y=ty, tile_z=tz)
     try:
