@@ -352,26 +352,40 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
     // this thread's x-pass octets (row r, octet o of the 8 in a row); the
     // second one only for the first XITEMS - NT threads
     constexpr int EXTRA = T::XITEMS - T::NT;
-    const bool two = EXTRA > 0 && tid < EXTRA;
-    const int rA = tid >> 3, oA = tid & 7, rB = (tid + T::NT) >> 3, oB = tid & 7;
-    // an octet reads inputs x0 + 8 o - 2 .. x0 + 8 o + 9; inside the row it
-    // takes the staged words, at a volume edge it clamps every x
-    const bool fA = x0 + 8 * oA - 2 >= 0 && x0 + 8 * oA + 10 <= (int)X;
+    // this thread's x-pass octets (row r, octet o of the 8 in a row); the
+    // second one for the last EXTRA threads, which issue at most one copy
+    const bool two = EXTRA > 0 && tid >= T::NT - EXTRA;
+    const int rA = tid >> 3, oA = tid & 7, rB = (tid + EXTRA) >> 3, oB = tid & 7;
+    // an octet reads inputs x0 + 8 o - 2 .. x0 + 8 o + 9; at a volume edge
+    // the inputs outside [0, X) take the edge voxel's value
+    const int xa = x0 + 8 * oA - 2;           // first input of this thread's octets
+    const bool fA = xa >= 0 && xa + 12 <= (int)X;
     auto xitem = [&](const unsigned char *stage, const int8_t *sh, uint32_t *px, int r, int o, bool f, int zi) {
         const int s = sh[r];
         uint32_t v[12];
-        if (f && s >= 0) {
+        if (s >= 0) {
             const int off = r * T::ROWE + s + 8 * o;
             unpack12(reinterpret_cast<const uint32_t *>(stage) + (off >> 1), off & 1, v);
+            if (!f) {
+                // the window also holds x = 0 and x = X - 1 when the octet
+                // reaches past them (indices clamped for octets wholly past X,
+                // whose outputs are not used)
+                const uint16_t *st16 = reinterpret_cast<const uint16_t *>(stage) + r * T::ROWE;
+                const int jr = (int)X - 1 - xa;  // last input inside the row
+                const uint32_t vl = st16[min(max(2 - x0 + s, 0), T::ROWE - 1)];
+                const uint32_t vr = st16[min(max((int)X + 1 - x0 + s, 0), T::ROWE - 1)];
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    if (xa + j < 0) v[j] = vl;
+                    if (j > jr) v[j] = vr;
+                }
+            }
         } else {
-            const uint16_t *st16 = reinterpret_cast<const uint16_t *>(stage) + r * T::ROWE;
+            // a row read with plain loads: clamp every x
             const uint64_t rowg = ((uint64_t)min(max(zi, 0), (int)Z - 1) * Y +
                                    (uint64_t)min(max(y0 - 2 + r, 0), (int)Y - 1)) * X;
 #pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                const int x = min(max(x0 - 2 + 8 * o + j, 0), (int)X - 1);
-                v[j] = s >= 0 ? (uint32_t)st16[x - (x0 - 2) + s] : (uint32_t)__ldg(raw + rowg + x);
-            }
+            for (int j = 0; j < 12; ++j) v[j] = __ldg(raw + rowg + min(max(x0 - 2 + 8 * o + j, 0), (int)X - 1));
         }
         uint32_t out[8];
         xpass8(v, out);
