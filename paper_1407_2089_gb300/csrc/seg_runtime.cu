@@ -211,9 +211,28 @@ void layout_request(Request &r) {
 }
 
 // Builds the batch descriptor on the slot's pinned header.
+// z-chunk for a batch: the tuned one, halved (down to 8 planes) while the
+// batch would have fewer than two smoothing tiles per multiprocessor, so that
+// small batches still spread over the whole GPU.  A forced shape is kept.
+uint32_t batch_tile_z(const seg_ctx *ctx, const Batch &b) {
+    const uint32_t ty = (uint32_t)ctx->plan.tile_y;
+    uint32_t tz = ctx->tile_z;
+    if (ctx->cfg.flags & SEG_FORCE_TILE) return tz;
+    for (;;) {
+        uint64_t tiles = 0;
+        for (const Request *r : b.reqs)
+            for (uint32_t c = 0; c < r->C; ++c) {
+                const VolGeom &g = r->g[c];
+                tiles += cdiv(g.X, TILE_X) * cdiv(g.Y, ty) * cdiv(g.Z, tz);
+            }
+        if (tz <= 8 || tiles >= 2ull * (uint64_t)ctx->sms) return tz;
+        tz /= 2;
+    }
+}
+
 void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
-    const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = ctx->tile_z;
+    const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
     uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0;
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
