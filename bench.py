@@ -473,6 +473,7 @@ def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
     pool = torch.from_numpy(base.view(np.int16)).pin_memory()
     ctx = seg.seg_create(device=local, flags=flags, hbm_budget_bytes=120 * 10 ** 9, max_inflight=max_inflight)
     lat = []
+    phases = []
     vox = 0
     done_at = []
     lock = threading.Lock()
@@ -490,10 +491,13 @@ def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
                 continue
             rid, arrival, submit_wall, nvox = item
             st = seg.seg_wait(ctx, rid)
-            sub_ms, _, _, done_ms = seg.seg_request_times(ctx, rid)
+            sub_ms, adm_ms, lau_ms, done_ms = seg.seg_request_times(ctx, rid)
             if st != seg.SEG_DONE:
                 raise RuntimeError("request failed")
             lat.append((done_ms - sub_ms) + (submit_wall - arrival) * 1e3)
+            # where the time went: arrival -> submit returned (host wait and
+            # copy), -> launch (waiting for a slot), -> done (on the GPU)
+            phases.append(((submit_wall - arrival) * 1e3, lau_ms - sub_ms, done_ms - lau_ms))
             done_at.append(submit_wall + (done_ms - sub_ms) / 1e3)
             seg.seg_release(ctx, rid)
 
@@ -520,8 +524,11 @@ def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
     seg.seg_destroy(ctx)
     span = max(done_at) - t0
     lat = np.sort(np.array(lat))
+    ph = np.array(phases)
+    parts = {name: {"p50_ms": float(np.percentile(ph[:, i], 50)), "p99_ms": float(np.percentile(ph[:, i], 99))}
+             for i, name in enumerate(("submit", "wait_slot", "gpu"))}
     return {"requests": len(reqs), "rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "phases": parts,
             "achieved_gvox_s": vox / span / 1e9,
             "offered_gvox_s": vox / reqs[-1][0] / 1e9}
 

@@ -739,6 +739,17 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist(const BatchHdr *__res
     flush_hist<T::NT>(h, v, ndone, sh);
 }
 
+// Foreground bits of 8 consecutive smoothed voxels (a 16-byte load, two per
+// word, the lower x in the low half): bit j is set iff voxel j > t*.  The OR
+// of the four words bounds every voxel from above, so an octet of background
+// (almost all of a volume) is settled by one test.
+__device__ __forceinline__ uint32_t octet_bits(uint4 q, uint32_t t) {
+    const uint32_t ow = q.x | q.y | q.z | q.w;
+    if ((ow & 0xFFFFu) <= t && (ow >> 16) <= t) return 0u;
+    auto two = [t](uint32_t w) { return ((w & 0xFFFFu) > t ? 1u : 0u) | ((w >> 16) > t ? 2u : 0u); };
+    return two(q.x) | (two(q.y) << 2) | (two(q.z) << 4) | (two(q.w) << 6);
+}
+
 // Threshold + run count, streaming over the smoothed volume.  One block per
 // row tile, one warp per row at a time: foreground bits s > t* are gathered
 // into mask words (ballot, or 8 voxels per lane with 16-byte loads when rows
@@ -786,14 +797,7 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
                         if (xb >= X) break;
                         const uint32_t x = xb + 8u * (uint32_t)lane;
                         uint32_t bits = 0;
-                        if (x < X) {
-                            const uint32_t w4[4] = {q4[k][c].x, q4[k][c].y, q4[k][c].z, q4[k][c].w};
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                bits |= ((w4[j] & 0xFFFFu) > t ? 1u : 0u) << (2 * j);
-                                bits |= ((w4[j] >> 16) > t ? 1u : 0u) << (2 * j + 1);
-                            }
-                        }
+                        if (x < X) bits = octet_bits(q4[k][c], t);
                         uint32_t word = bits << (8 * (lane & 3));
                         word |= __shfl_xor_sync(FULL, word, 1);
                         word |= __shfl_xor_sync(FULL, word, 2);
@@ -833,14 +837,7 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
                         if (xb >= X) break;
                         const uint32_t x = xb + 8u * (uint32_t)lane;
                         uint32_t bits = 0;
-                        if (x < X) {
-                            const uint32_t w4[4] = {q4[c].x, q4[c].y, q4[c].z, q4[c].w};
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                bits |= ((w4[j] & 0xFFFFu) > t ? 1u : 0u) << (2 * j);
-                                bits |= ((w4[j] >> 16) > t ? 1u : 0u) << (2 * j + 1);
-                            }
-                        }
+                        if (x < X) bits = octet_bits(q4[c], t);
                         // lanes 4g..4g+3 hold the 32 bits of word g of this chunk
                         uint32_t word = bits << (8 * (lane & 3));
                         word |= __shfl_xor_sync(FULL, word, 1);
