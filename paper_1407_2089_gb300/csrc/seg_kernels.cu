@@ -1089,20 +1089,33 @@ __global__ void __launch_bounds__(BRICK_Y * BRICK_Z) k_union_local(const BatchHd
         soff[t] = loc;
         if (t == NT - 1) soff[NT] = n;
         if (ly == 0) gb[lz] = ib;
-        __syncthreads();
-        for (uint32_t l = t; l < n; l += NT) {
-            sx[l] = V.run_x[brick_global(l, soff, gb)];
+        // Each warp holds one plane of the brick (32 rows): it stages its own
+        // runs and unites its rows with their (y-1) neighbours, which lie in
+        // the same plane, synchronising with __syncwarp only.
+        const uint32_t pbeg = __shfl_sync(FULL, loc, 0), pend = __shfl_sync(FULL, loc + cnt, 31);
+        const uint32_t pg = __shfl_sync(FULL, ib, 0);  // global index of the plane's first run
+        for (uint32_t l = pbeg + ly; l < pend; l += BRICK_Y) {
+            sx[l] = V.run_x[pg + (l - pbeg)];
             sp[l] = l;
         }
-        __syncthreads();
+        __syncwarp();
         // Three phases, each followed by a full compression (every run points
         // at its root) so that no phase walks long paths: rows of one plane,
         // then the same row of the plane below, then the two diagonals.
         const uint32_t i1 = loc + cnt, lim = V.union_limit, u = t - BRICK_Y;
         bool ok = true;
         if (cnt && ly > 0) ok &= sm_unite_rows(sp, sx, loc, i1, soff[t - 1], soff[t], lim);  // (y-1, z)
-        __syncthreads();
-        sm_compress(sp, n, t, NT);
+        __syncwarp();
+        for (uint32_t l = pbeg + ly; l < pend; l += BRICK_Y) {  // compress this plane's runs
+            uint32_t r = sp[l];
+            if (r == l) continue;
+            uint32_t q = sp[r];
+            while (q != r) {
+                r = q;
+                q = sp[r];
+            }
+            sp[l] = r;
+        }
         __syncthreads();
         if (cnt && lz > 0) ok &= sm_unite_rows(sp, sx, loc, i1, soff[u], soff[u + 1], lim);  // (y, z-1)
         __syncthreads();
@@ -1315,7 +1328,7 @@ __device__ __forceinline__ void feat_global(seg_cell_features *f, unsigned long 
 // cells with one set of atomics per (tile, cell).
 constexpr int LABEL_RUNS = 2048;
 
-__global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__restrict__ h) {
+__global__ void __launch_bounds__(ROW_TILE, 6) k_label_features(const BatchHdr *__restrict__ h) {
     __shared__ VolIndex<&VolDev::rt_base> VI;
     VI.load(h);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1368,35 +1381,25 @@ __global__ void __launch_bounds__(ROW_TILE) k_label_features(const BatchHdr *__r
                 }
                 if (staged && ie - ib <= 16u) {
                     // few runs: every lane goes through the row's runs in
-                    // step (broadcast reads, no divergent walk) and fills its
-                    // 4 chunks of each 512-voxel segment
+                    // step (broadcast reads, no divergent walk) for each
+                    // 128-voxel segment, and fills its 4-voxel chunk
                     uint32_t j = ib;
-                    for (uint32_t seg = 0; seg < X; seg += 512) {
-                        uint32_t v[4][4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) v[c][q] = 0u;
-                        while (j < ie && (srx[j - rb] >> 16) < seg) ++j;
+                    for (uint32_t sb = 0; sb < X; sb += 128) {
+                        const uint32_t xb = sb + 4u * lane;
+                        uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+                        while (j < ie && (srx[j - rb] >> 16) < sb) ++j;
                         for (uint32_t k = j; k < ie; ++k) {
                             const uint32_t rx = srx[k - rb];
                             const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
-                            if (x0 >= seg + 512u) break;
-                            const uint32_t L = slab[k - rb];
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const uint32_t xb = seg + 128u * c + 4u * lane;
-                                if (x1 < xb || x0 > xb + 3u) continue;
-#pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    if (xb + q - x0 <= x1 - x0) v[c][q] = L;
-                            }
+                            if (x0 >= sb + 128u) break;
+                            if (x1 < xb || x0 > xb + 3u) continue;
+                            const uint32_t L = slab[k - rb], w = x1 - x0;
+                            if (xb - x0 <= w) v0 = L;
+                            if (xb + 1u - x0 <= w) v1 = L;
+                            if (xb + 2u - x0 <= w) v2 = L;
+                            if (xb + 3u - x0 <= w) v3 = L;
                         }
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const uint32_t xb = seg + 128u * c + 4u * lane;
-                            if (xb < X) __stcs(o4 + xb / 4, make_uint4(v[c][0], v[c][1], v[c][2], v[c][3]));
-                        }
+                        if (xb < X) __stcs(o4 + xb / 4, make_uint4(v0, v1, v2, v3));
                     }
                     continue;
                 }
