@@ -363,7 +363,18 @@ __device__ __forceinline__ void smooth_tile(const uint16_t *__restrict__ raw, ui
     auto xitem = [&](const unsigned char *stage, const int8_t *sh, uint32_t *px, int r, int o, bool f, int zi) {
         const int s = sh[r];
         uint32_t v[12];
-        if (s >= 0) {
+        if (f && s == 6) {
+            // rows of a 16-byte-aligned volume with X % 8 == 0: the octet's 12
+            // inputs are words 3..8 of the three 16-byte chunks o, o+1, o+2
+            const uint4 *c = reinterpret_cast<const uint4 *>(stage + r * T::ROWB) + o;
+            const uint4 c0 = c[0], c1 = c[1], c2 = c[2];
+            const uint32_t wd[6] = {c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                v[2 * k] = wd[k] & 0xFFFFu;
+                v[2 * k + 1] = wd[k] >> 16;
+            }
+        } else if (s >= 0) {
             const int off = r * T::ROWE + s + 8 * o;
             unpack12(reinterpret_cast<const uint32_t *>(stage) + (off >> 1), off & 1, v);
             if (!f) {
