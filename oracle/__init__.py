@@ -59,6 +59,15 @@ def _load():
                                        ctypes.c_uint32, u32p, vp, ctypes.c_uint64, u64p, u16p,
                                        u64p, u16p]
         lib.oracle_segment.restype = ctypes.c_int
+        for name in ("oracle_background", "oracle_denoise"):
+            getattr(lib, name).argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_uint32, u16p]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.oracle_box_pass.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_int, ctypes.c_uint32, u16p]
+        lib.oracle_box_pass.restype = ctypes.c_int
+        lib.oracle_median27.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u16p]
+        lib.oracle_median27.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -147,10 +156,43 @@ class OracleResult:
         return len(self.cells)
 
 
-def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
-            keep_smoothed: bool = False) -> OracleResult:
-    """The whole stage for one frame and channel (uint16 [Z,Y,X])."""
+def _vol_op(name, vol, *args):
     vol = np.ascontiguousarray(vol, dtype=np.uint16)
+    X, Y, Z = _dims(vol)
+    out = np.empty_like(vol)
+    rc = getattr(_load(), name)(_ptr(vol, ctypes.c_uint16), X, Y, Z, *args, _ptr(out, ctypes.c_uint16))
+    if rc:
+        raise RuntimeError("%s failed: %d" % (name, rc))
+    return out
+
+
+def box_pass(vol: np.ndarray, axis: int, r: int) -> np.ndarray:
+    """One rounded box pass of radius r along axis 0 = x, 1 = y, 2 = z."""
+    return _vol_op("oracle_box_pass", vol, int(axis), int(r))
+
+
+def background(vol: np.ndarray, r: int) -> np.ndarray:
+    """Background estimate of the denoise front end (Eq. 1): 3 box passes per axis."""
+    return _vol_op("oracle_background", vol, int(r))
+
+
+def median27(vol: np.ndarray) -> np.ndarray:
+    """3x3x3 median with replicate edges."""
+    return _vol_op("oracle_median27", vol)
+
+
+def denoise(vol: np.ndarray, r: int) -> np.ndarray:
+    """Denoised stem-cell image: median27(max(vol - background(vol, r), 0))."""
+    return _vol_op("oracle_denoise", vol, int(r))
+
+
+def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
+            keep_smoothed: bool = False, denoise_radius: int = 0) -> OracleResult:
+    """The whole stage for one frame and channel (uint16 [Z,Y,X]); with
+    denoise_radius > 0 the denoise front end runs first."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint16)
+    if denoise_radius:
+        vol = denoise(vol, denoise_radius)
     X, Y, Z = _dims(vol)
     n = vol.size
     labels = np.empty(vol.shape, dtype=np.uint32)

@@ -249,6 +249,101 @@ int oracle_filter_features(const uint32_t *prov, uint64_t ncomp, uint32_t X, uin
     return rc;
 }
 
+/* ------------------------------------------------------------------------
+ * Denoise front end for the stem-cell channel (Background Noise Removal,
+ * Eq. 1: observed = background + shot noise + signal).  The background B is
+ * a low-pass of the observed image; the paper names a Gaussian without a
+ * width.  Read here as three box filters of width w = 2r + 1 along x, then
+ * three along y, then three along z (three boxes approximate a Gaussian of
+ * variance 3 (w^2 - 1) / 12 per axis), each pass rounding to nearest,
+ * (sum + r) / w, with replicate edges.  The background is subtracted with a
+ * floor at 0 and the shot noise removed by the 3x3x3 median (the 14th of the
+ * 27 values, replicate edges).
+ * ------------------------------------------------------------------------ */
+
+/* One box pass of radius r along `axis` (0 = x, 1 = y, 2 = z). */
+int oracle_box_pass(const uint16_t *in, uint32_t X, uint32_t Y, uint32_t Z, int axis, uint32_t r,
+                    uint16_t *out) {
+    if (!in || !out || X == 0 || Y == 0 || Z == 0 || axis < 0 || axis > 2) return ORACLE_EINVAL;
+    const uint64_t w = 2 * (uint64_t)r + 1;
+    const int64_t len = axis == 0 ? X : (axis == 1 ? Y : Z);
+    for (uint64_t z = 0; z < Z; ++z)
+        for (uint64_t y = 0; y < Y; ++y)
+            for (uint64_t x = 0; x < X; ++x) {
+                const int64_t pos = axis == 0 ? (int64_t)x : (axis == 1 ? (int64_t)y : (int64_t)z);
+                uint64_t sum = 0;
+                for (int64_t k = -(int64_t)r; k <= (int64_t)r; ++k) {
+                    const int64_t q = clamp_i64(pos + k, len);
+                    const uint64_t xx = axis == 0 ? (uint64_t)q : x;
+                    const uint64_t yy = axis == 1 ? (uint64_t)q : y;
+                    const uint64_t zz = axis == 2 ? (uint64_t)q : z;
+                    sum += in[xx + X * (yy + Y * zz)];
+                }
+                out[x + X * (y + Y * z)] = (uint16_t)((sum + r) / w);
+            }
+    return ORACLE_OK;
+}
+
+/* Background estimate B: three box passes along x, three along y, three
+ * along z. */
+int oracle_background(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32_t r, uint16_t *b) {
+    if (!v || !b || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    uint64_t n = (uint64_t)X * Y * Z;
+    uint16_t *t = (uint16_t *)malloc(n * sizeof(uint16_t));
+    if (!t) return ORACLE_ENOMEM;
+    memcpy(b, v, n * sizeof(uint16_t));
+    int rc = ORACLE_OK;
+    for (int axis = 0; axis < 3 && rc == ORACLE_OK; ++axis)
+        for (int p = 0; p < 3 && rc == ORACLE_OK; ++p) {
+            rc = oracle_box_pass(b, X, Y, Z, axis, r, t);
+            memcpy(b, t, n * sizeof(uint16_t));
+        }
+    free(t);
+    return rc;
+}
+
+/* 3x3x3 median with replicate edges: the 14th smallest of the 27 values. */
+int oracle_median27(const uint16_t *d, uint32_t X, uint32_t Y, uint32_t Z, uint16_t *out) {
+    if (!d || !out || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                uint16_t w[27];
+                int m = 0;
+                for (int c = -1; c <= 1; ++c)
+                    for (int b = -1; b <= 1; ++b)
+                        for (int a = -1; a <= 1; ++a)
+                            w[m++] = d[clamp_i64(x + a, X) + X * (clamp_i64(y + b, Y) + Y * clamp_i64(z + c, Z))];
+                /* insertion sort */
+                for (int i = 1; i < 27; ++i) {
+                    uint16_t key = w[i];
+                    int j = i - 1;
+                    while (j >= 0 && w[j] > key) {
+                        w[j + 1] = w[j];
+                        --j;
+                    }
+                    w[j + 1] = key;
+                }
+                out[x + X * (y + Y * z)] = w[13];
+            }
+    return ORACLE_OK;
+}
+
+/* The denoised image: median27(max(v - B, 0)). */
+int oracle_denoise(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32_t r, uint16_t *out) {
+    if (!v || !out || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    uint64_t n = (uint64_t)X * Y * Z;
+    uint16_t *b = (uint16_t *)malloc(n * sizeof(uint16_t));
+    if (!b) return ORACLE_ENOMEM;
+    int rc = oracle_background(v, X, Y, Z, r, b);
+    if (rc == ORACLE_OK) {
+        for (uint64_t i = 0; i < n; ++i) b[i] = v[i] > b[i] ? (uint16_t)(v[i] - b[i]) : 0;
+        rc = oracle_median27(b, X, Y, Z, out);
+    }
+    free(b);
+    return rc;
+}
+
 /* The whole stage for one frame and channel: smooth, histogram, Otsu,
  * threshold (foreground iff s > t*), label, filter, features.
  * hist (65536 entries) and smoothed (n entries) are optional outputs. */

@@ -411,3 +411,94 @@ def test_single_frame_workload_counts():
     r = oracle.segment(vol, min_volume=30)
     assert 30 <= r.n_cells <= 40
     assert 300 < r.threshold < 1500
+
+
+# ---------------------------------------------------------------------------
+# Denoise front end (Background Noise Removal, Eq. 1): background by box
+# cascade, floor-at-zero subtraction, 3x3x3 median
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("r", [1, 2, 4, 8])
+def test_box_pass_matches_uniform_filter(r):
+    ndi = pytest.importorskip("scipy.ndimage")
+    # one pass = the mean over 2r+1 replicate-padded neighbours, rounded to
+    # nearest; w is odd, so no value lies exactly halfway
+    rng = np.random.default_rng(40 + r)
+    for shape in [(7, 9, 11), (3, 1, 20), (1, 5, 2)]:
+        v = rng.integers(0, 65536, size=shape).astype(np.uint16)
+        for axis in range(3):
+            got = oracle.box_pass(v, axis, r)
+            mean = ndi.uniform_filter1d(v.astype(np.float64), size=2 * r + 1, axis=2 - axis, mode="nearest")
+            assert np.array_equal(got, np.floor(mean + 0.5).astype(np.uint16)), (shape, axis)
+
+
+@pytest.mark.parametrize("r", [1, 3, 8])
+def test_box_cascade_impulse_is_three_fold_convolution(r):
+    # an impulse of height k w^3 far from the edges stays exact through three
+    # passes (every intermediate sum divides by w), giving k times the
+    # three-fold convolution of the box with itself
+    w = 2 * r + 1
+    k = 7
+    X = 8 * w
+    v = np.zeros((1, 1, X), dtype=np.uint16)
+    c = X // 2
+    v[0, 0, c] = k * w ** 3 if k * w ** 3 < 65536 else 0
+    if v[0, 0, c] == 0:
+        k = 65535 // w ** 3
+        v[0, 0, c] = k * w ** 3
+    out = v
+    for _ in range(3):
+        out = oracle.box_pass(out, 0, r)
+    kern = np.convolve(np.convolve(np.ones(w, dtype=np.int64), np.ones(w, dtype=np.int64)), np.ones(w, dtype=np.int64))
+    expect = np.zeros(X, dtype=np.int64)
+    expect[c - 3 * r: c + 3 * r + 1] = k * kern
+    assert np.array_equal(out[0, 0].astype(np.int64), expect)
+
+
+def test_background_keeps_constants_and_interior_ramps():
+    r = 3
+    flat = np.full((12, 13, 14), 777, dtype=np.uint16)
+    assert np.array_equal(oracle.background(flat, r), flat)
+    # a ramp along each axis in turn is reproduced wherever the windows of
+    # all nine passes stay inside the volume (symmetric sums of a linear
+    # function are exact multiples of w)
+    for axis in range(3):
+        n = 6 * 3 * r + 5
+        idx = np.arange(n, dtype=np.int64) * 5 + 100
+        shape = [3, 3, 3]
+        shape[2 - axis] = n
+        ramp = np.broadcast_to(idx.reshape([-1 if i == 2 - axis else 1 for i in range(3)]), shape)
+        ramp = np.ascontiguousarray(ramp, dtype=np.uint16)
+        b = oracle.background(ramp, r)
+        sl = [slice(None)] * 3
+        sl[2 - axis] = slice(3 * r, n - 3 * r)
+        assert np.array_equal(b[tuple(sl)], ramp[tuple(sl)]), axis
+
+
+def test_median27_matches_scipy():
+    ndi = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(44)
+    for shape in [(6, 7, 8), (1, 1, 5), (2, 3, 1), (4, 4, 4)]:
+        v = rng.integers(0, 65536, size=shape).astype(np.uint16)
+        assert np.array_equal(oracle.median27(v), ndi.median_filter(v, size=3, mode="nearest")), shape
+    # few distinct values: ties
+    v = rng.integers(0, 3, size=(9, 10, 11)).astype(np.uint16)
+    assert np.array_equal(oracle.median27(v), ndi.median_filter(v, size=3, mode="nearest"))
+
+
+def test_denoise_is_median_of_floored_difference():
+    ndi = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(45)
+    v = rng.integers(0, 4000, size=(10, 12, 14)).astype(np.uint16)
+    for r in (1, 4):
+        b = oracle.background(v, r).astype(np.int64)
+        d = np.maximum(v.astype(np.int64) - b, 0).astype(np.uint16)
+        assert np.array_equal(oracle.denoise(v, r), ndi.median_filter(d, size=3, mode="nearest"))
+
+
+def test_segment_with_denoise_is_segment_of_denoised():
+    vol, _ = synth.well_separated((48, 40, 20), seed=9, n_nuclei=6)
+    r = 4
+    a = oracle.segment(vol, min_volume=5, denoise_radius=r)
+    b = oracle.segment(oracle.denoise(vol, r), min_volume=5)
+    assert a.threshold == b.threshold and np.array_equal(a.labels, b.labels)
