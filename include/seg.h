@@ -103,6 +103,12 @@ typedef struct {
 
 typedef struct {
     uint32_t min_volume_voxels; /* keep cells with >= this many voxels (30)      */
+    /* 0: off.  1..32: the denoise front end of the stem-cell channel
+     * (Background Noise Removal, Eq. 1) runs before the smoothing: the
+     * background is three box filters of width 2r+1 along x, then y, then z
+     * (each rounding to nearest, replicate edges), it is subtracted with a
+     * floor at 0, and the 3x3x3 median of the difference is segmented. */
+    uint32_t denoise_radius;
 } seg_channel_params;
 
 /* Creates a context on cfg->device.  Allocates streams and descriptor buffers;

@@ -70,6 +70,16 @@ struct VolDev {
     uint32_t bk_base;         // first flat brick index
     uint32_t nbt;             // row pairs that cross a brick face (k_union tasks)
     uint32_t bt_base;         // first flat k_union task index
+    // denoise front end (dn_r > 0); raw then points at dn_out
+    const uint16_t *dn_src;   // observed image [Z][Y][X]
+    uint16_t *dn_a, *dn_b;    // box-pass ping-pong buffers (the background ends in dn_a)
+    uint16_t *dn_out;         // denoised image (the smoothing's input)
+    uint32_t dn_r;            // box radius, 0 = no denoise
+    uint32_t dn_mul;          // ceil(2^32 / (2 dn_r + 1)): division by the box width
+    uint32_t dn_n[3];         // box-pass items per axis (lines x chunks)
+    uint32_t dn_base0, dn_base1, dn_base2;  // first flat box item per axis
+    uint32_t dn_tiles;        // median tiles
+    uint32_t dn_tbase;        // first flat median tile
 };
 
 // Batch header, followed in memory by VolDev[nvol].
@@ -81,7 +91,9 @@ struct BatchHdr {
     uint32_t tile_y;     // rows of a smoothing tile
     uint32_t nbricks;    // union-find bricks over the batch
     uint32_t nbtasks;    // k_union tasks over the batch
-    uint32_t pad;
+    uint32_t dn_items[3];// denoise box-pass items per axis over the batch
+    uint32_t dn_tiles;   // denoise median tiles over the batch
+    uint32_t pad[3];
     VolDev vol[1];       // nvol entries
 };
 
@@ -90,7 +102,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 13;
+constexpr int NUM_KERNELS = 15;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {
@@ -106,6 +118,8 @@ struct LaunchPlan {
     int grid_ul;         // k_union_local
     int grid_task;       // k_union, k_flatten
     int grid_lab;        // k_label_features
+    int grid_box;        // k_box_pass
+    int grid_med;        // k_median27
 };
 
 // Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)
@@ -117,6 +131,11 @@ cudaError_t launch_pipeline(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaS
 
 // Only the tile-dependent part (init + smoothing/histogram), for tile tuning.
 cudaError_t launch_tile_probe(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);
+
+// Denoise front end of the volumes with dn_r > 0 (none: the kernels exit).
+constexpr int DN_CHUNK = 256;    // box-pass outputs per thread along a line
+constexpr int DN_MAX_R = 32;
+cudaError_t launch_denoise(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);
 
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);

@@ -34,14 +34,15 @@
 
 #include <algorithm>
 
+#include "median27_net.h"
 #include "seg_internal.h"
 
 namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
-    "init",        "smooth_hist_otsu", "threshold_runs", "scan_runs", "row_runs",
-    "union_local", "union",            "flatten",        "keep_count", "scan_keep",
-    "rank",        "label_features",   "gather_stat"};
+    "denoise_box", "denoise_median", "init",           "smooth_hist_otsu", "threshold_runs",
+    "scan_runs",   "row_runs",       "union_local",    "union",            "flatten",
+    "keep_count",  "scan_keep",      "rank",           "label_features",   "gather_stat"};
 
 namespace {
 
@@ -1528,6 +1529,106 @@ __global__ void k_gather_stat(const BatchHdr *__restrict__ h, uint32_t *out) {
         out[i] = h->vol[i / ST_WORDS].stat[i % ST_WORDS];
 }
 
+// ----------------------------------------------------------------------------
+// Denoise front end of the stem-cell channel (Background Noise Removal,
+// Eq. 1): background B by box passes, D = max(L - B, 0), 3x3x3 median of D
+// ----------------------------------------------------------------------------
+
+// (n + r) / w for n + r < 2^24 and w = 2r + 1 <= 65, as a multiply-high by
+// mul = ceil(2^32 / w) (division by an invariant integer, Granlund and
+// Montgomery 1994): the product's error n * (mul * w - 2^32) / (w 2^32) stays
+// below 2^-8 < 1/w, so the floor is exact.
+__device__ __forceinline__ uint32_t box_div(uint32_t n, uint32_t mul) { return __umulhi(n, mul); }
+
+// One rounded box pass of radius r along AXIS for every line chunk of the
+// volumes with the denoise front end.  Pass p (0..8) reads the observed image
+// (p = 0) or a ping-pong buffer and writes the other one; passes 0-2 run
+// along x, 3-5 along y, 6-8 along z, so the background ends in dn_a.
+// One thread per (line, chunk of DN_CHUNK outputs), consecutive threads on
+// consecutive lines; the window sum slides along the line with clamped
+// (replicate-edge) reads.
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_box_pass(const BatchHdr *__restrict__ h, int pass) {
+    __shared__ VolIndex<AXIS == 0 ? &VolDev::dn_base0 : (AXIS == 1 ? &VolDev::dn_base1 : &VolDev::dn_base2)> VI;
+    VI.load(h);
+    const uint32_t total = h->dn_items[AXIS];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
+        const VolDev &V = h->vol[VI.find(h, it)];
+        const uint32_t li = it - (AXIS == 0 ? V.dn_base0 : (AXIS == 1 ? V.dn_base1 : V.dn_base2));
+        const uint32_t X = V.X, Y = V.Y, Z = V.Z;
+        const uint32_t len = AXIS == 0 ? X : (AXIS == 1 ? Y : Z);
+        const uint32_t nlines = AXIS == 0 ? Y * Z : (AXIS == 1 ? X * Z : X * Y);
+        const uint32_t line = li % nlines, chunk = li / nlines;
+        size_t base, step;
+        if (AXIS == 0) {
+            base = (size_t)line * X;
+            step = 1;
+        } else if (AXIS == 1) {
+            base = (size_t)(line % X) + (size_t)X * Y * (line / X);
+            step = X;
+        } else {
+            base = line;
+            step = (size_t)X * Y;
+        }
+        const uint16_t *in = pass == 0 ? V.dn_src : ((pass & 1) ? V.dn_a : V.dn_b);
+        uint16_t *out = (pass & 1) ? V.dn_b : V.dn_a;
+        const int r = (int)V.dn_r, n = (int)len;
+        const int c0 = (int)chunk * DN_CHUNK, c1 = min(c0 + DN_CHUNK, n);
+        auto at = [&](int q) { return (uint32_t)in[base + (size_t)min(max(q, 0), n - 1) * step]; };
+        uint32_t sum = 0;
+        for (int q = c0 - r; q <= c0 + r; ++q) sum += at(q);
+        for (int q = c0; q < c1; ++q) {
+            out[base + (size_t)q * step] = (uint16_t)box_div(sum + (uint32_t)r, V.dn_mul);
+            sum += at(q + r + 1) - at(q - r);
+        }
+    }
+}
+
+// D = max(L - B, 0) staged per tile of 32 x 8 x 8 voxels (plus a one-voxel
+// halo, clamped), then the median of each voxel's 27 neighbours; the result
+// is the volume the smoothing reads.
+constexpr int MED_TX = 32, MED_TY = 8, MED_TZ = 8;
+
+__global__ void __launch_bounds__(MED_TX * MED_TY) k_median27(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::dn_tbase> VI;
+    __shared__ uint16_t d[MED_TZ + 2][MED_TY + 2][MED_TX + 2];
+    VI.load(h);
+    const int tx = threadIdx.x % MED_TX, ty = threadIdx.x / MED_TX;
+    for (uint32_t t = blockIdx.x; t < h->dn_tiles; t += gridDim.x) {
+        const VolDev &V = h->vol[VI.find(h, t)];
+        const uint32_t lt = t - V.dn_tbase;
+        const int X = (int)V.X, Y = (int)V.Y, Z = (int)V.Z;
+        const int ntx = (X + MED_TX - 1) / MED_TX, nty = (Y + MED_TY - 1) / MED_TY;
+        const int x0 = (int)(lt % ntx) * MED_TX, y0 = (int)((lt / ntx) % nty) * MED_TY;
+        const int z0 = (int)(lt / ((uint32_t)ntx * nty)) * MED_TZ;
+        __syncthreads();  // the previous tile is done with d
+        constexpr int NS = (MED_TZ + 2) * (MED_TY + 2) * (MED_TX + 2);
+        for (int i = threadIdx.x; i < NS; i += MED_TX * MED_TY) {
+            const int sx = i % (MED_TX + 2), sy = (i / (MED_TX + 2)) % (MED_TY + 2);
+            const int sz = i / ((MED_TX + 2) * (MED_TY + 2));
+            const int x = min(max(x0 - 1 + sx, 0), X - 1), y = min(max(y0 - 1 + sy, 0), Y - 1);
+            const int z = min(max(z0 - 1 + sz, 0), Z - 1);
+            const size_t g = (size_t)x + (size_t)X * ((size_t)y + (size_t)Y * z);
+            const uint32_t l = V.dn_src[g], b = V.dn_a[g];
+            d[sz][sy][sx] = (uint16_t)(l > b ? l - b : 0u);
+        }
+        __syncthreads();
+        const int x = x0 + tx, y = y0 + ty;
+        if (x >= X || y >= Y) continue;
+        for (int k = 0; k < MED_TZ && z0 + k < Z; ++k) {
+            uint32_t v[27];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) v[9 * c + 3 * b + a] = d[k + c][ty + b][tx + a];
+            V.dn_out[(size_t)x + (size_t)X * ((size_t)y + (size_t)Y * (z0 + k))] = (uint16_t)median27_net(v);
+        }
+    }
+}
+
 template <int TY>
 cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s,
                                 cudaEvent_t *ev, int &k) {
@@ -1576,6 +1677,8 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     if ((e = resident((const void *)k_flatten, ROW_TILE, &g2)) != cudaSuccess) return e;
     plan.grid_task = std::min(g1, g2);
     if ((e = resident((const void *)k_label_features, ROW_TILE, &plan.grid_lab)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_box_pass<1>, 256, &plan.grid_box)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_median27, MED_TX * MED_TY, &plan.grid_med)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1589,6 +1692,20 @@ cudaError_t launch_tile_probe(const BatchHdr *d, const LaunchPlan &p, cudaStream
     return cudaGetLastError();
 }
 
+static void launch_box_passes(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
+    for (int pass = 0; pass < 9; ++pass) {
+        if (pass < 3) k_box_pass<0><<<p.grid_box, 256, 0, s>>>(d, pass);
+        else if (pass < 6) k_box_pass<1><<<p.grid_box, 256, 0, s>>>(d, pass);
+        else k_box_pass<2><<<p.grid_box, 256, 0, s>>>(d, pass);
+    }
+}
+
+cudaError_t launch_denoise(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
+    launch_box_passes(d, p, s);
+    k_median27<<<p.grid_med, MED_TX * MED_TY, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s, cudaEvent_t *ev,
                             uint32_t *stat_out) {
     int k = 0;
@@ -1596,6 +1713,11 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
         if (ev) cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal);
         ++k;
     };
+    // denoise front end (its kernels find no items when no volume asks for it)
+    rec();
+    launch_box_passes(d, p, s);
+    rec();
+    k_median27<<<p.grid_med, MED_TX * MED_TY, 0, s>>>(d);
     rec();
     k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
     cudaError_t e;

@@ -41,11 +41,12 @@ struct Batch;
 // Geometry and footprint of one channel of a request.
 struct VolGeom {
     uint32_t X, Y, Z, W, rows, nrt;
+    uint32_t dn_r;   // denoise box radius, 0 = off
     uint64_t n, r_cap, k_cap;
     size_t scratch;  // bytes of per-batch scratch for this volume-channel
 };
 
-VolGeom geom(seg_dims d, uint32_t min_volume) {
+VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r) {
     VolGeom g;
     g.X = d.x; g.Y = d.y; g.Z = d.z;
     g.W = (uint32_t)cdiv(d.x, 32);
@@ -60,6 +61,8 @@ VolGeom geom(seg_dims d, uint32_t min_volume) {
     g.k_cap = std::max<uint64_t>(kc, 1);
     g.scratch = al(4ull * HIST_BINS) + al(2ull * g.n) + al(4ull * g.rows * g.W) + al(4ull * (g.rows + 1)) +
                 al(4ull * g.rows) + 2 * al(4ull * g.nrt) + 3 * al(4ull * g.r_cap);
+    g.dn_r = dn_r;
+    if (dn_r) g.scratch += 3 * al(2ull * g.n);  // two box-pass buffers + the denoised image
     return g;
 }
 
@@ -233,7 +236,7 @@ uint32_t batch_tile_z(const seg_ctx *ctx, const Batch &b) {
 void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
-    uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0;
+    uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0;
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
         for (uint32_t c = 0; c < r->C; ++c) {
@@ -243,6 +246,32 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.labels = r->labels(c);
             V.feat = r->feat(c);
             V.stat = r->stat(c);
+            V.dn_r = g.dn_r;
+            V.dn_src = V.raw;
+            V.dn_a = V.dn_b = V.dn_out = nullptr;
+            V.dn_mul = 0;
+            V.dn_n[0] = V.dn_n[1] = V.dn_n[2] = 0;
+            V.dn_tiles = 0;
+            if (g.dn_r) {
+                V.dn_a = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
+                V.dn_b = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
+                V.dn_out = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
+                V.raw = V.dn_out;  // the smoothing reads the denoised image
+                const uint64_t w = 2ull * g.dn_r + 1;
+                V.dn_mul = (uint32_t)(((1ull << 32) + w - 1) / w);
+                V.dn_n[0] = (uint32_t)((uint64_t)g.Y * g.Z * cdiv(g.X, DN_CHUNK));
+                V.dn_n[1] = (uint32_t)((uint64_t)g.X * g.Z * cdiv(g.Y, DN_CHUNK));
+                V.dn_n[2] = (uint32_t)((uint64_t)g.X * g.Y * cdiv(g.Z, DN_CHUNK));
+                V.dn_tiles = (uint32_t)(cdiv(g.X, 32) * cdiv(g.Y, 8) * cdiv(g.Z, 8));
+            }
+            V.dn_base0 = dn[0];
+            V.dn_base1 = dn[1];
+            V.dn_base2 = dn[2];
+            V.dn_tbase = dnt;
+            dn[0] += V.dn_n[0];
+            dn[1] += V.dn_n[1];
+            dn[2] += V.dn_n[2];
+            dnt += V.dn_tiles;
             V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
             V.smooth = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
             V.mask = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows * g.W);
@@ -289,6 +318,10 @@ void build_header(seg_ctx *ctx, Batch &b) {
     h->nrowtiles = rts;
     h->nbricks = bks;
     h->nbtasks = bts;
+    h->dn_items[0] = dn[0];
+    h->dn_items[1] = dn[1];
+    h->dn_items[2] = dn[2];
+    h->dn_tiles = dnt;
     h->tile_z = tz;
     h->tile_y = ty;
     b.nvol = v;
@@ -660,8 +693,10 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
     r->minvol.resize(channels);
     for (uint32_t c = 0; c < channels; ++c) {
         uint32_t m = per_channel ? per_channel[c].min_volume_voxels : 30u;
+        const uint32_t dr = per_channel ? per_channel[c].denoise_radius : 0u;
+        if (dr > (uint32_t)DN_MAX_R) return SEG_EINVAL;
         r->minvol[c] = m ? m : 1u;  // a cell has at least one voxel
-        r->g.push_back(geom(dims, r->minvol[c]));
+        r->g.push_back(geom(dims, r->minvol[c], dr));
     }
     r->thresh.assign(channels, 0);
     r->ncells.assign(channels, 0);
