@@ -329,6 +329,9 @@ def run_gpu(args):
     total_kernel_ms = sum(k["ms"] for k in kern.values())
     shares = {n: round(k["ms"] / total_kernel_ms, 4) for n, k in kern.items()} if total_kernel_ms else {}
     seg.seg_destroy(ctx)
+    denoise = None
+    if args.denoise_radius:
+        denoise = denoise_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.denoise_radius)
     forms = None
     if not args.no_forms:
         forms = {"batched": value / ws, "plain": plain_form(seg, torch, d_in, (X, Y, Z), local,
@@ -407,6 +410,7 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "forms_gvox_s_per_gpu": forms,
+            "denoise_front_end": denoise,
             "serving": serve,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
@@ -415,6 +419,63 @@ def run_gpu(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def denoise_run(seg, torch, d_in, dims, local, steps, radius):
+    """The same workload with the denoise front end of Eq. 1 on the
+    stem-cell channel (channel 0, box radius `radius`), batched as in the
+    main measurement.  Returns Gvoxels/s of the whole stage and the mean
+    per-step CUDA-event times of the front-end kernels."""
+    T, C = d_in.shape[0], d_in.shape[1]
+    X, Y, Z = dims
+    stream = torch.cuda.Stream()
+    ctx = seg.seg_create(device=local, flags=seg.SEG_PROFILE, batch_window_us=2_000_000,
+                         order_stream=stream.cuda_stream, max_inflight=1)
+    radii = [radius] + [0] * (C - 1)
+
+    def one_pass():
+        reqs = [seg.seg_submit_volume(ctx, d_in[t], dims=(X, Y, Z), channels=C, denoise_radius=radii)
+                for t in range(T)]
+        seg.seg_flush(ctx)
+        for r in reqs:
+            seg.seg_enqueue_wait(ctx, r, stream.cuda_stream)
+        return reqs
+
+    def finish(reqs):
+        for r in reqs:
+            if seg.seg_wait(ctx, r) != seg.SEG_DONE:
+                raise RuntimeError("request failed")
+            seg.seg_release(ctx, r)
+
+    for _ in range(2):
+        finish(one_pass())
+    torch.cuda.synchronize()
+    seg.seg_reset_stats(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pend = []
+    for _ in range(steps):
+        pend.append(one_pass())
+        if len(pend) > 1:
+            finish(pend.pop(0))
+    e1.record(stream)
+    for p in pend:
+        finish(p)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kern = seg.seg_get_stats(ctx)["kernels"]
+    seg.seg_destroy(ctx)
+    per = {n: kern[n]["ms"] / steps for n in ("denoise_box", "denoise_median")}
+    vox_dn = T * X * Y * Z  # voxels through the front end per step (channel 0)
+    front_ms = per["denoise_box"] + per["denoise_median"]
+    return {"radius": radius, "channels_denoised": 1, "gvox_s": d_in.numel() / (ms / 1e3) / 1e9,
+            "ms_per_step": ms, "front_end_ms_per_step": front_ms,
+            "front_end_gvox_s": vox_dn / (front_ms / 1e3) / 1e9 if front_ms else None,
+            "kernel_ms_per_step": per,
+            # algorithmic bytes of the front end: read the observed image,
+            # write the denoised one (4 B/voxel); the 9 box passes move 36 B
+            "front_end_hbm_frac": (vox_dn * 4.0 / (front_ms / 1e3) / 1e9) / peaks()[0] if front_ms else None}
 
 
 def plain_form(seg, torch, d_in, dims, local, steps):
@@ -545,6 +606,8 @@ def main():
     ap.add_argument("--frames", type=int, default=FRAMES,
                     help="time-lapse frames per step (fewer frames: a small case for profiling)")
     ap.add_argument("--tile", default="", help="force the tile height and z-chunk, e.g. 32,64")
+    ap.add_argument("--denoise-radius", type=int, default=8,
+                    help="also time the stage with the denoise front end on channel 0 (0 skips)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain per-frame comparison")

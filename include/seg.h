@@ -103,7 +103,7 @@ typedef struct {
 
 typedef struct {
     uint32_t min_volume_voxels; /* keep cells with >= this many voxels (30)      */
-    /* 0: off.  1..32: the denoise front end of the stem-cell channel
+    /* 0: off.  1..16: the denoise front end of the stem-cell channel
      * (Background Noise Removal, Eq. 1) runs before the smoothing: the
      * background is three box filters of width 2r+1 along x, then y, then z
      * (each rounding to nearest, replicate edges), it is subtracted with a

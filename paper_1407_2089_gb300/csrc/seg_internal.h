@@ -120,6 +120,7 @@ struct LaunchPlan {
     int grid_lab;        // k_label_features
     int grid_box;        // k_box_pass
     int grid_med;        // k_median27
+    bool denoise;        // some volume of the batch runs the denoise front end
 };
 
 // Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)
@@ -133,8 +134,8 @@ cudaError_t launch_pipeline(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaS
 cudaError_t launch_tile_probe(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);
 
 // Denoise front end of the volumes with dn_r > 0 (none: the kernels exit).
-constexpr int DN_CHUNK = 256;    // box-pass outputs per thread along a line
-constexpr int DN_MAX_R = 32;
+constexpr int DN_CHUNK = 128;    // box-pass positions per tile along a line
+constexpr int DN_MAX_R = 16;
 cudaError_t launch_denoise(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);
 
 // Histogram-kernel shared memory per block for a tile height.

@@ -1540,47 +1540,134 @@ __global__ void k_gather_stat(const BatchHdr *__restrict__ h, uint32_t *out) {
 // below 2^-8 < 1/w, so the floor is exact.
 __device__ __forceinline__ uint32_t box_div(uint32_t n, uint32_t mul) { return __umulhi(n, mul); }
 
-// One rounded box pass of radius r along AXIS for every line chunk of the
-// volumes with the denoise front end.  Pass p (0..8) reads the observed image
-// (p = 0) or a ping-pong buffer and writes the other one; passes 0-2 run
-// along x, 3-5 along y, 6-8 along z, so the background ends in dn_a.
-// One thread per (line, chunk of DN_CHUNK outputs), consecutive threads on
-// consecutive lines; the window sum slides along the line with clamped
-// (replicate-edge) reads.
+// The three rounded box passes of radius r along AXIS, for every tile of 64
+// lines x DN_CHUNK positions of the volumes with the denoise front end.  A
+// block loads its tile with a halo of 3r positions on each side (clamped to
+// the line) into shared memory, runs the three passes there -- pass k over
+// the positions the next one needs, each reading its input at positions
+// clamped to the line, which is the replicate edge of every pass -- and
+// writes the chunk.  Axis x reads dn_src and writes dn_a, y reads dn_a and
+// writes dn_b, z reads dn_b and writes the background into dn_a.  Shared
+// layout [position][lane], lanes padded to 66 so that both the lane-major
+// passes and the position-major copies of axis x avoid bank conflicts.
+constexpr int BOX_LANES = 64, BOX_PITCH = BOX_LANES + 2;
+constexpr int BOX_POS = DN_CHUNK + 6 * DN_MAX_R;
+constexpr size_t BOX_SMEM = 2ull * BOX_POS * BOX_PITCH * sizeof(uint16_t);
+
 template <int AXIS>
-__global__ void __launch_bounds__(256) k_box_pass(const BatchHdr *__restrict__ h, int pass) {
+__global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
     __shared__ VolIndex<AXIS == 0 ? &VolDev::dn_base0 : (AXIS == 1 ? &VolDev::dn_base1 : &VolDev::dn_base2)> VI;
+    extern __shared__ __align__(16) uint16_t bsm[];
+    uint16_t *bufA = bsm, *bufB = bsm + BOX_POS * BOX_PITCH;
     VI.load(h);
-    const uint32_t total = h->dn_items[AXIS];
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
+    const int t = threadIdx.x;
+    for (uint32_t it = blockIdx.x; it < h->dn_items[AXIS]; it += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, it)];
         const uint32_t li = it - (AXIS == 0 ? V.dn_base0 : (AXIS == 1 ? V.dn_base1 : V.dn_base2));
-        const uint32_t X = V.X, Y = V.Y, Z = V.Z;
-        const uint32_t len = AXIS == 0 ? X : (AXIS == 1 ? Y : Z);
-        const uint32_t nlines = AXIS == 0 ? Y * Z : (AXIS == 1 ? X * Z : X * Y);
-        const uint32_t line = li % nlines, chunk = li / nlines;
-        size_t base, step;
+        const int X = (int)V.X, Y = (int)V.Y, Z = (int)V.Z;
+        const int n = AXIS == 0 ? X : (AXIS == 1 ? Y : Z);
+        const int nchunk = (n + DN_CHUNK - 1) / DN_CHUNK;
+        const int group = (int)(li / (uint32_t)nchunk), chunk = (int)(li % (uint32_t)nchunk);
+        const int r = (int)V.dn_r;
+        const uint32_t mul = V.dn_mul;
+        const int c0 = chunk * DN_CHUNK, c1 = min(c0 + DN_CHUNK, n), base = c0 - 3 * r;
+        const int lo = max(base, 0), hi = min(c1 + 3 * r, n);  // loaded positions
+        // lane l of this group: its line's first element and the step along it
+        const int nxg = (X + BOX_LANES - 1) / BOX_LANES;
+        int nl;            // lanes of this group that exist
+        size_t gstart;     // element of lane 0 at position 0
+        size_t lstride, pstride;
         if (AXIS == 0) {
-            base = (size_t)line * X;
-            step = 1;
-        } else if (AXIS == 1) {
-            base = (size_t)(line % X) + (size_t)X * Y * (line / X);
-            step = X;
+            const int rows = Y * Z;
+            nl = min(BOX_LANES, rows - group * BOX_LANES);
+            gstart = (size_t)group * BOX_LANES * X;
+            lstride = (size_t)X;
+            pstride = 1;
         } else {
-            base = line;
-            step = (size_t)X * Y;
+            const int gx = group % nxg, other = group / nxg;
+            nl = min(BOX_LANES, X - gx * BOX_LANES);
+            lstride = 1;
+            if (AXIS == 1) {
+                gstart = (size_t)gx * BOX_LANES + (size_t)X * Y * other;
+                pstride = (size_t)X;
+            } else {
+                gstart = (size_t)gx * BOX_LANES + (size_t)X * other;
+                pstride = (size_t)X * Y;
+            }
         }
-        const uint16_t *in = pass == 0 ? V.dn_src : ((pass & 1) ? V.dn_a : V.dn_b);
-        uint16_t *out = (pass & 1) ? V.dn_b : V.dn_a;
-        const int r = (int)V.dn_r, n = (int)len;
-        const int c0 = (int)chunk * DN_CHUNK, c1 = min(c0 + DN_CHUNK, n);
-        auto at = [&](int q) { return (uint32_t)in[base + (size_t)min(max(q, 0), n - 1) * step]; };
-        uint32_t sum = 0;
-        for (int q = c0 - r; q <= c0 + r; ++q) sum += at(q);
-        for (int q = c0; q < c1; ++q) {
-            out[base + (size_t)q * step] = (uint16_t)box_div(sum + (uint32_t)r, V.dn_mul);
-            sum += at(q + r + 1) - at(q - r);
+        const uint16_t *src = AXIS == 0 ? V.dn_src : (AXIS == 1 ? V.dn_a : V.dn_b);
+        uint16_t *dst = AXIS == 1 ? V.dn_b : V.dn_a;
+        const int np = hi - lo;
+        __syncthreads();  // the previous tile is done with the buffers
+        // load: consecutive threads on consecutive elements in memory
+        if (AXIS == 0) {
+            // one warp per line (a row segment), lanes along it
+            const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+            for (int l = warp; l < nl; l += nw) {
+                const uint16_t *row = src + gstart + (size_t)l * lstride;
+                for (int q = lo + lane; q < hi; q += 32) bufA[(q - base) * BOX_PITCH + l] = row[q];
+            }
+        } else {
+            for (int i = t; i < np * BOX_LANES; i += blockDim.x) {
+                const int l = i % BOX_LANES, q = lo + i / BOX_LANES;
+                if (l < nl) bufA[(q - base) * BOX_PITCH + l] = src[gstart + (size_t)l * lstride + (size_t)q * pstride];
+            }
+        }
+        __syncthreads();
+        // three passes: A -> B over [c0-2r, c1+2r), B -> A over [c0-r, c1+r), A -> B over [c0, c1)
+        const int l = t % BOX_LANES, seg = t / BOX_LANES;
+        for (int k = 0; k < 3; ++k) {
+            const uint16_t *in = (k == 1) ? bufB : bufA;
+            uint16_t *out = (k == 1) ? bufA : bufB;
+            const int p0 = max(c0 - (2 - k) * r, 0), p1 = min(c1 + (2 - k) * r, n);
+            const int per = (p1 - p0 + 3) / 4;
+            const int q0 = p0 + seg * per, q1 = min(q0 + per, p1);
+            if (l < nl && q0 < q1) {
+                // every read lies in [q0 - r, q1 - 1 + r] clamped to the line,
+                // inside the positions the previous pass (or the load) covered
+                auto at = [&](int q) { return (uint32_t)in[(min(max(q, 0), n - 1) - base) * BOX_PITCH + l]; };
+                uint32_t sum = 0;
+                for (int q = q0 - r; q <= q0 + r; ++q) sum += at(q);
+                out[(q0 - base) * BOX_PITCH + l] = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                // positions q whose window [q - r - 1, q + r] needs no
+                // clamping run through three moving pointers
+                const int qa = min(max(q0 + 1, r + 1), q1), qb = max(min(q1, n - r), qa);
+                int q = q0 + 1;
+                for (; q < qa; ++q) {
+                    sum += at(q + r) - at(q - r - 1);
+                    out[(q - base) * BOX_PITCH + l] = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                }
+                const uint16_t *pin = in + (q + r - base) * BOX_PITCH + l;
+                const uint16_t *pout = in + (q - r - 1 - base) * BOX_PITCH + l;
+                uint16_t *po = out + (q - base) * BOX_PITCH + l;
+#pragma unroll 4
+                for (; q < qb; ++q) {
+                    sum += (uint32_t)*pin - (uint32_t)*pout;
+                    *po = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                    pin += BOX_PITCH;
+                    pout += BOX_PITCH;
+                    po += BOX_PITCH;
+                }
+                for (; q < q1; ++q) {
+                    sum += at(q + r) - at(q - r - 1);
+                    out[(q - base) * BOX_PITCH + l] = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                }
+            }
+            __syncthreads();
+        }
+        // store the chunk from B
+        const int nc = c1 - c0;
+        if (AXIS == 0) {
+            const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+            for (int ll = warp; ll < nl; ll += nw) {
+                uint16_t *row = dst + gstart + (size_t)ll * lstride;
+                for (int q = c0 + lane; q < c1; q += 32) row[q] = bufB[(q - base) * BOX_PITCH + ll];
+            }
+        } else {
+            for (int i = t; i < nc * BOX_LANES; i += blockDim.x) {
+                const int ll = i % BOX_LANES, q = c0 + i / BOX_LANES;
+                if (ll < nl) dst[gstart + (size_t)ll * lstride + (size_t)q * pstride] = bufB[(q - base) * BOX_PITCH + ll];
+            }
         }
     }
 }
@@ -1677,7 +1764,15 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     if ((e = resident((const void *)k_flatten, ROW_TILE, &g2)) != cudaSuccess) return e;
     plan.grid_task = std::min(g1, g2);
     if ((e = resident((const void *)k_label_features, ROW_TILE, &plan.grid_lab)) != cudaSuccess) return e;
-    if ((e = resident((const void *)k_box_pass<1>, 256, &plan.grid_box)) != cudaSuccess) return e;
+    for (const void *fn : {(const void *)k_box3<0>, (const void *)k_box3<1>, (const void *)k_box3<2>})
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BOX_SMEM)) != cudaSuccess)
+            return e;
+    {
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_box3<1>, 256, BOX_SMEM)) != cudaSuccess)
+            return e;
+        plan.grid_box = plan.sms * (per_sm > 0 ? per_sm : 1);
+    }
     if ((e = resident((const void *)k_median27, MED_TX * MED_TY, &plan.grid_med)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -1693,11 +1788,9 @@ cudaError_t launch_tile_probe(const BatchHdr *d, const LaunchPlan &p, cudaStream
 }
 
 static void launch_box_passes(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
-    for (int pass = 0; pass < 9; ++pass) {
-        if (pass < 3) k_box_pass<0><<<p.grid_box, 256, 0, s>>>(d, pass);
-        else if (pass < 6) k_box_pass<1><<<p.grid_box, 256, 0, s>>>(d, pass);
-        else k_box_pass<2><<<p.grid_box, 256, 0, s>>>(d, pass);
-    }
+    k_box3<0><<<p.grid_box, 256, BOX_SMEM, s>>>(d);
+    k_box3<1><<<p.grid_box, 256, BOX_SMEM, s>>>(d);
+    k_box3<2><<<p.grid_box, 256, BOX_SMEM, s>>>(d);
 }
 
 cudaError_t launch_denoise(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
@@ -1713,11 +1806,11 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
         if (ev) cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal);
         ++k;
     };
-    // denoise front end (its kernels find no items when no volume asks for it)
+    // denoise front end, for batches in which some volume asks for it
     rec();
-    launch_box_passes(d, p, s);
+    if (p.denoise) launch_box_passes(d, p, s);
     rec();
-    k_median27<<<p.grid_med, MED_TX * MED_TY, 0, s>>>(d);
+    if (p.denoise) k_median27<<<p.grid_med, MED_TX * MED_TY, 0, s>>>(d);
     rec();
     k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
     cudaError_t e;

@@ -111,7 +111,7 @@ struct Slot {
     BatchHdr *d_hdr = nullptr;
     uint32_t *h_stat = nullptr;  // pinned
     uint32_t *d_stat = nullptr;
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // tile_y 16/32/64
+    cudaGraphExec_t graph[6] = {};  // tile_y 16/32/64, without / with the denoise front end
     cudaEvent_t ev[NUM_KERNELS + 1] = {};
     Batch *busy = nullptr;
 };
@@ -259,9 +259,10 @@ void build_header(seg_ctx *ctx, Batch &b) {
                 V.raw = V.dn_out;  // the smoothing reads the denoised image
                 const uint64_t w = 2ull * g.dn_r + 1;
                 V.dn_mul = (uint32_t)(((1ull << 32) + w - 1) / w);
-                V.dn_n[0] = (uint32_t)((uint64_t)g.Y * g.Z * cdiv(g.X, DN_CHUNK));
-                V.dn_n[1] = (uint32_t)((uint64_t)g.X * g.Z * cdiv(g.Y, DN_CHUNK));
-                V.dn_n[2] = (uint32_t)((uint64_t)g.X * g.Y * cdiv(g.Z, DN_CHUNK));
+                // tiles of 64 lines x DN_CHUNK positions per axis
+                V.dn_n[0] = (uint32_t)(cdiv((uint64_t)g.Y * g.Z, 64) * cdiv(g.X, DN_CHUNK));
+                V.dn_n[1] = (uint32_t)(cdiv(g.X, 64) * g.Z * cdiv(g.Y, DN_CHUNK));
+                V.dn_n[2] = (uint32_t)(cdiv(g.X, 64) * g.Y * cdiv(g.Z, DN_CHUNK));
                 V.dn_tiles = (uint32_t)(cdiv(g.X, 32) * cdiv(g.Y, 8) * cdiv(g.Z, 8));
             }
             V.dn_base0 = dn[0];
@@ -327,7 +328,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     b.nvol = v;
 }
 
-int graph_index(int ty) { return ty == 16 ? 0 : (ty == 32 ? 1 : 2); }
+int graph_index(int ty, bool denoise) { return (ty == 16 ? 0 : (ty == 32 ? 1 : 2)) + (denoise ? 3 : 0); }
 
 // Enqueues descriptor upload, the pipeline and the status read-back.
 int enqueue_body(seg_ctx *ctx, Slot &s, uint32_t nvol) {
@@ -402,8 +403,9 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
         if (rc != SEG_OK) return rc;
     }
     build_header(ctx, b);
+    ctx->plan.denoise = s.h_hdr->dn_tiles > 0;
     if (ctx->graphs) {
-        cudaGraphExec_t &ge = s.graph[graph_index(ctx->plan.tile_y)];
+        cudaGraphExec_t &ge = s.graph[graph_index(ctx->plan.tile_y, ctx->plan.denoise)];
         if (!ge) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
@@ -624,6 +626,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->plan.tile_y = ty;
     ctx->plan.grid_hist = ctx->sms;  // one resident block per SM (176 KiB histogram)
     ctx->plan.grid_vols = ctx->sms;
+    ctx->plan.denoise = false;
     CK(configure_kernels(cfg->device, ctx->plan));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {

@@ -93,5 +93,5 @@ def test_time_lapse_frame_stem_cell_channel(seg, ctx):
 def test_radius_limit(seg, ctx):
     vol = np.zeros((4, 4, 4), dtype=np.uint16)
     with pytest.raises(seg.SegError) as e:
-        seg.seg_submit_volume(ctx, vol, denoise_radius=33)
+        seg.seg_submit_volume(ctx, vol, denoise_radius=17)
     assert e.value.code == seg.SEG_EINVAL
