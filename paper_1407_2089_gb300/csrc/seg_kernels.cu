@@ -1599,18 +1599,38 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
         uint16_t *dst = AXIS == 1 ? V.dn_b : V.dn_a;
         const int np = hi - lo;
         __syncthreads();  // the previous tile is done with the buffers
-        // load: consecutive threads on consecutive elements in memory
+        // load: consecutive threads on consecutive elements in memory, eight
+        // independent loads in flight per thread before the shared stores
+        constexpr int NB = 8;
         if (AXIS == 0) {
             // one warp per line (a row segment), lanes along it
             const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
             for (int l = warp; l < nl; l += nw) {
                 const uint16_t *row = src + gstart + (size_t)l * lstride;
-                for (int q = lo + lane; q < hi; q += 32) bufA[(q - base) * BOX_PITCH + l] = row[q];
+                for (int q0 = lo + lane; q0 < hi; q0 += 32 * NB) {
+                    uint16_t v[NB];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (q0 + 32 * j < hi) v[j] = row[q0 + 32 * j];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (q0 + 32 * j < hi) bufA[(q0 + 32 * j - base) * BOX_PITCH + l] = v[j];
+                }
             }
         } else {
-            for (int i = t; i < np * BOX_LANES; i += blockDim.x) {
-                const int l = i % BOX_LANES, q = lo + i / BOX_LANES;
-                if (l < nl) bufA[(q - base) * BOX_PITCH + l] = src[gstart + (size_t)l * lstride + (size_t)q * pstride];
+            const int total = np * BOX_LANES, nt = blockDim.x;
+            for (int i0 = t; i0 < total; i0 += nt * NB) {
+                uint16_t v[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const int i = i0 + j * nt, l = i % BOX_LANES, q = lo + i / BOX_LANES;
+                    if (i < total && l < nl) v[j] = src[gstart + (size_t)l * lstride + (size_t)q * pstride];
+                }
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const int i = i0 + j * nt, l = i % BOX_LANES, q = lo + i / BOX_LANES;
+                    if (i < total && l < nl) bufA[(q - base) * BOX_PITCH + l] = v[j];
+                }
             }
         }
         __syncthreads();
@@ -1627,7 +1647,12 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
                 // inside the positions the previous pass (or the load) covered
                 auto at = [&](int q) { return (uint32_t)in[(min(max(q, 0), n - 1) - base) * BOX_PITCH + l]; };
                 uint32_t sum = 0;
-                for (int q = q0 - r; q <= q0 + r; ++q) sum += at(q);
+                if (q0 - r >= 0 && q0 + r < n) {
+                    const uint16_t *pw = in + (q0 - r - base) * BOX_PITCH + l;
+                    for (int i = 0; i <= 2 * r; ++i) sum += pw[i * BOX_PITCH];
+                } else {
+                    for (int q = q0 - r; q <= q0 + r; ++q) sum += at(q);
+                }
                 out[(q0 - base) * BOX_PITCH + l] = (uint16_t)box_div(sum + (uint32_t)r, mul);
                 // positions q whose window [q - r - 1, q + r] needs no
                 // clamping run through three moving pointers
@@ -1677,7 +1702,7 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
 // is the volume the smoothing reads.
 constexpr int MED_TX = 32, MED_TY = 8, MED_TZ = 8;
 
-__global__ void __launch_bounds__(MED_TX * MED_TY) k_median27(const BatchHdr *__restrict__ h) {
+__global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr *__restrict__ h) {
     __shared__ VolIndex<&VolDev::dn_tbase> VI;
     __shared__ uint16_t d[MED_TZ + 2][MED_TY + 2][MED_TX + 2];
     VI.load(h);
@@ -1691,14 +1716,28 @@ __global__ void __launch_bounds__(MED_TX * MED_TY) k_median27(const BatchHdr *__
         const int z0 = (int)(lt / ((uint32_t)ntx * nty)) * MED_TZ;
         __syncthreads();  // the previous tile is done with d
         constexpr int NS = (MED_TZ + 2) * (MED_TY + 2) * (MED_TX + 2);
-        for (int i = threadIdx.x; i < NS; i += MED_TX * MED_TY) {
-            const int sx = i % (MED_TX + 2), sy = (i / (MED_TX + 2)) % (MED_TY + 2);
-            const int sz = i / ((MED_TX + 2) * (MED_TY + 2));
-            const int x = min(max(x0 - 1 + sx, 0), X - 1), y = min(max(y0 - 1 + sy, 0), Y - 1);
-            const int z = min(max(z0 - 1 + sz, 0), Z - 1);
-            const size_t g = (size_t)x + (size_t)X * ((size_t)y + (size_t)Y * z);
-            const uint32_t l = V.dn_src[g], b = V.dn_a[g];
-            d[sz][sy][sx] = (uint16_t)(l > b ? l - b : 0u);
+        // 14 elements per thread, loaded in two rounds of 7 pairs in flight
+        constexpr int NT = MED_TX * MED_TY, NB = 7;
+        for (int i0 = threadIdx.x; i0 < NS; i0 += NT * NB) {
+            uint16_t lv[NB], bv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const int i = i0 + j * NT;
+                if (i < NS) {
+                    const int sx = i % (MED_TX + 2), sy = (i / (MED_TX + 2)) % (MED_TY + 2);
+                    const int sz = i / ((MED_TX + 2) * (MED_TY + 2));
+                    const int x = min(max(x0 - 1 + sx, 0), X - 1), y = min(max(y0 - 1 + sy, 0), Y - 1);
+                    const int z = min(max(z0 - 1 + sz, 0), Z - 1);
+                    const size_t g = (size_t)x + (size_t)X * ((size_t)y + (size_t)Y * z);
+                    lv[j] = V.dn_src[g];
+                    bv[j] = V.dn_a[g];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const int i = i0 + j * NT;
+                if (i < NS) (&d[0][0][0])[i] = (uint16_t)(lv[j] > bv[j] ? lv[j] - bv[j] : 0);
+            }
         }
         __syncthreads();
         const int x = x0 + tx, y = y0 + ty;
