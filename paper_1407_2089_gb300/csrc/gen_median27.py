@@ -1,20 +1,24 @@
-"""Writes median27_net.h: a branch-free selection network for the median of
-27 values (the 14th smallest), used by the 3x3x3 median of the denoise
-front end.
+"""Writes median27_net.h: the selection networks of the 3x3x3 median of the
+denoise front end.
 
-Construction: Batcher's odd-even merge sort network on 32 inputs, with the
-inputs 27..31 held at +infinity.  A comparator whose upper input is known
-to be +infinity never exchanges and is dropped; one whose lower input is
-+infinity always exchanges and becomes a renaming.  Then only the
-comparators on which output 13 depends are kept, and a comparator one of
-whose outputs is not used afterwards keeps only its min or its max.
+* sort9: sorts the 9 values of one plane's 3x3 neighbourhood.
+* median3x9: the median (14th smallest) of 27 values given as three sorted
+  lists of 9 (the neighbourhoods of planes z-1, z, z+1).
+
+Each sorted plane list is used by three voxels along z, so a median costs
+one sort9 and one median3x9.  Both networks start from Batcher's odd-even
+merge sort (16 inputs with 7 held at +infinity for sort9; 64 inputs with
+the three lists in the blocks starting at 0, 16 and 32 for median3x9) and
+drop every comparator whose result follows from what is already known: a
++infinity input, the sorted order of the input lists, or the order earlier
+comparators established.  median3x9 then keeps only the comparators its
+output depends on, and a comparator one of whose outputs is not used keeps
+only its min or its max.
 
 Run: python gen_median27.py [output path]
 """
 import os
 import sys
-
-N, N_REAL, OUT = 32, 27, 13
 
 
 def batcher(n):
@@ -34,55 +38,117 @@ def batcher(n):
     return comps
 
 
-def network():
-    var = list(range(N))            # wire -> variable name index
-    inf = [w >= N_REAL for w in range(N)]
-    ops = []                        # (lo_var, hi_var) in program order
-    for i, j in batcher(N):
-        if inf[j]:
+def reduce(n, finite, sorted_groups):
+    """Batcher's network on n wires without the comparators whose outcome is
+    implied.  Returns (ops, var): ops are (lo, hi) variable pairs (after one,
+    lo holds the min and hi the max) and var maps output wire -> variable."""
+    le = [[i == j for j in range(n)] for i in range(n)]
+    for grp in sorted_groups:
+        for a in range(len(grp)):
+            for b in range(a + 1, len(grp)):
+                le[grp[a]][grp[b]] = True
+    for w in range(n):
+        if w not in finite:
+            for k in range(n):
+                le[k][w] = True
+
+    def close():
+        for k in range(n):
+            lk = le[k]
+            for i in range(n):
+                if le[i][k]:
+                    row = le[i]
+                    for j in range(n):
+                        if lk[j]:
+                            row[j] = True
+
+    close()
+    var = list(range(n))
+    ops = []
+    for i, j in batcher(n):
+        if le[i][j]:
             continue
-        if inf[i]:
+        if le[j][i]:
             var[i], var[j] = var[j], var[i]
-            inf[i], inf[j] = inf[j], inf[i]
+            le[i], le[j] = le[j], le[i]
+            for row in le:
+                row[i], row[j] = row[j], row[i]
             continue
         ops.append((var[i], var[j]))
-    # after a comparator (a, b): variable a holds the min, b the max
-    out_var = var[OUT]
-    need = {out_var}
-    kept = []
+        a, b = le[i][:], le[j][:]
+        ka = [le[k][i] for k in range(n)]
+        kb = [le[k][j] for k in range(n)]
+        le[i] = [x or y for x, y in zip(a, b)]
+        le[j] = [x and y for x, y in zip(a, b)]
+        for k in range(n):
+            le[k][i] = ka[k] and kb[k]
+            le[k][j] = ka[k] or kb[k]
+        le[i][j] = True
+        le[j][i] = False
+        le[i][i] = le[j][j] = True
+        close()
+    return ops, var
+
+
+def sort9():
+    ops, var = reduce(16, set(range(9)), [])
+    return ops, [var[w] for w in range(9)]
+
+
+def median3x9():
+    finite = set(range(0, 9)) | set(range(16, 25)) | set(range(32, 41))
+    groups = [list(range(0, 9)), list(range(16, 25)), list(range(32, 41))]
+    ops, var = reduce(64, finite, groups)
+    out = var[13]
+    need, kept = {out}, []
     for a, b in reversed(ops):
         na, nb = a in need, b in need
-        if not (na or nb):
-            continue
-        kept.append((a, b, na, nb))
-        need.add(a)
-        need.add(b)
+        if na or nb:
+            kept.append((a, b, na, nb))
+            need.update((a, b))
     kept.reverse()
-    return kept, out_var
+    return kept, out
+
+
+def _cmp(lines, v, a, b, na=True, nb=True):
+    if na and nb:
+        lines.append("    { const uint32_t t = min(%s[%d], %s[%d]); %s[%d] = max(%s[%d], %s[%d]); %s[%d] = t; }"
+                     % (v, a, v, b, v, b, v, a, v, b, v, a))
+    elif na:
+        lines.append("    %s[%d] = min(%s[%d], %s[%d]);" % (v, a, v, a, v, b))
+    else:
+        lines.append("    %s[%d] = max(%s[%d], %s[%d]);" % (v, b, v, a, v, b))
 
 
 def emit(path):
-    kept, out_var = network()
+    s_ops, s_out = sort9()
+    m_ops, m_out = median3x9()
     lines = [
-        "// Generated by gen_median27.py: median (14th smallest) of 27 values by",
-        "// a pruned odd-even merge network (%d comparators)." % len(kept),
+        "// Generated by gen_median27.py: sort9 (%d comparators) and the median of" % len(s_ops),
+        "// three sorted lists of 9 (%d comparators, pruned Batcher networks)." % len(m_ops),
         "#pragma once",
         "",
-        "__device__ __forceinline__ uint32_t median27_net(uint32_t *v) {",
+        "// Sorts v[0..8] in place (s[k] receives the k-th smallest).",
+        "__device__ __forceinline__ void sort9(const uint32_t *v, uint32_t *s) {",
+        "    uint32_t w[16];",
     ]
-    for a, b, na, nb in kept:
-        if na and nb:
-            lines.append("    { const uint32_t t = min(v[%d], v[%d]); v[%d] = max(v[%d], v[%d]); v[%d] = t; }"
-                         % (a, b, b, a, b, a))
-        elif na:
-            lines.append("    v[%d] = min(v[%d], v[%d]);" % (a, a, b))
-        else:
-            lines.append("    v[%d] = max(v[%d], v[%d]);" % (b, a, b))
-    lines.append("    return v[%d];" % out_var)
-    lines.append("}")
+    lines += ["    w[%d] = v[%d];" % (i, i) for i in range(9)]
+    for a, b in s_ops:
+        _cmp(lines, "w", a, b)
+    lines += ["    s[%d] = w[%d];" % (k, s_out[k]) for k in range(9)]
+    lines += ["}", "",
+              "// The 14th smallest of a[0..8], b[0..8], c[0..8], each sorted ascending.",
+              "__device__ __forceinline__ uint32_t median3x9(const uint32_t *a, const uint32_t *b, const uint32_t *c) {",
+              "    uint32_t w[64];"]
+    lines += ["    w[%d] = a[%d];" % (i, i) for i in range(9)]
+    lines += ["    w[%d] = b[%d];" % (16 + i, i) for i in range(9)]
+    lines += ["    w[%d] = c[%d];" % (32 + i, i) for i in range(9)]
+    for a, b, na, nb in m_ops:
+        _cmp(lines, "w", a, b, na, nb)
+    lines += ["    return w[%d];" % m_out, "}"]
     with open(path, "w") as f:
         f.write("\n".join(lines) + "\n")
-    return len(kept)
+    return len(s_ops), len(m_ops)
 
 
 if __name__ == "__main__":

@@ -1,133 +1,142 @@
-// Generated by gen_median27.py: median (14th smallest) of 27 values by
-// a pruned odd-even merge network (126 comparators).
+// Generated by gen_median27.py: sort9 (28 comparators) and the median of
+// three sorted lists of 9 (55 comparators, pruned Batcher networks).
 #pragma once
 
-__device__ __forceinline__ uint32_t median27_net(uint32_t *v) {
-    { const uint32_t t = min(v[0], v[1]); v[1] = max(v[0], v[1]); v[0] = t; }
-    { const uint32_t t = min(v[2], v[3]); v[3] = max(v[2], v[3]); v[2] = t; }
-    { const uint32_t t = min(v[4], v[5]); v[5] = max(v[4], v[5]); v[4] = t; }
-    { const uint32_t t = min(v[6], v[7]); v[7] = max(v[6], v[7]); v[6] = t; }
-    { const uint32_t t = min(v[8], v[9]); v[9] = max(v[8], v[9]); v[8] = t; }
-    { const uint32_t t = min(v[10], v[11]); v[11] = max(v[10], v[11]); v[10] = t; }
-    { const uint32_t t = min(v[12], v[13]); v[13] = max(v[12], v[13]); v[12] = t; }
-    { const uint32_t t = min(v[14], v[15]); v[15] = max(v[14], v[15]); v[14] = t; }
-    { const uint32_t t = min(v[16], v[17]); v[17] = max(v[16], v[17]); v[16] = t; }
-    { const uint32_t t = min(v[18], v[19]); v[19] = max(v[18], v[19]); v[18] = t; }
-    { const uint32_t t = min(v[20], v[21]); v[21] = max(v[20], v[21]); v[20] = t; }
-    { const uint32_t t = min(v[22], v[23]); v[23] = max(v[22], v[23]); v[22] = t; }
-    { const uint32_t t = min(v[24], v[25]); v[25] = max(v[24], v[25]); v[24] = t; }
-    { const uint32_t t = min(v[0], v[2]); v[2] = max(v[0], v[2]); v[0] = t; }
-    { const uint32_t t = min(v[1], v[3]); v[3] = max(v[1], v[3]); v[1] = t; }
-    { const uint32_t t = min(v[4], v[6]); v[6] = max(v[4], v[6]); v[4] = t; }
-    { const uint32_t t = min(v[5], v[7]); v[7] = max(v[5], v[7]); v[5] = t; }
-    { const uint32_t t = min(v[8], v[10]); v[10] = max(v[8], v[10]); v[8] = t; }
-    { const uint32_t t = min(v[9], v[11]); v[11] = max(v[9], v[11]); v[9] = t; }
-    { const uint32_t t = min(v[12], v[14]); v[14] = max(v[12], v[14]); v[12] = t; }
-    { const uint32_t t = min(v[13], v[15]); v[15] = max(v[13], v[15]); v[13] = t; }
-    { const uint32_t t = min(v[16], v[18]); v[18] = max(v[16], v[18]); v[16] = t; }
-    { const uint32_t t = min(v[17], v[19]); v[19] = max(v[17], v[19]); v[17] = t; }
-    { const uint32_t t = min(v[20], v[22]); v[22] = max(v[20], v[22]); v[20] = t; }
-    { const uint32_t t = min(v[21], v[23]); v[23] = max(v[21], v[23]); v[21] = t; }
-    { const uint32_t t = min(v[24], v[26]); v[26] = max(v[24], v[26]); v[24] = t; }
-    { const uint32_t t = min(v[1], v[2]); v[2] = max(v[1], v[2]); v[1] = t; }
-    { const uint32_t t = min(v[5], v[6]); v[6] = max(v[5], v[6]); v[5] = t; }
-    { const uint32_t t = min(v[9], v[10]); v[10] = max(v[9], v[10]); v[9] = t; }
-    { const uint32_t t = min(v[13], v[14]); v[14] = max(v[13], v[14]); v[13] = t; }
-    { const uint32_t t = min(v[17], v[18]); v[18] = max(v[17], v[18]); v[17] = t; }
-    { const uint32_t t = min(v[21], v[22]); v[22] = max(v[21], v[22]); v[21] = t; }
-    { const uint32_t t = min(v[25], v[26]); v[26] = max(v[25], v[26]); v[25] = t; }
-    { const uint32_t t = min(v[0], v[4]); v[4] = max(v[0], v[4]); v[0] = t; }
-    { const uint32_t t = min(v[1], v[5]); v[5] = max(v[1], v[5]); v[1] = t; }
-    { const uint32_t t = min(v[2], v[6]); v[6] = max(v[2], v[6]); v[2] = t; }
-    { const uint32_t t = min(v[3], v[7]); v[7] = max(v[3], v[7]); v[3] = t; }
-    { const uint32_t t = min(v[8], v[12]); v[12] = max(v[8], v[12]); v[8] = t; }
-    { const uint32_t t = min(v[9], v[13]); v[13] = max(v[9], v[13]); v[9] = t; }
-    { const uint32_t t = min(v[10], v[14]); v[14] = max(v[10], v[14]); v[10] = t; }
-    { const uint32_t t = min(v[11], v[15]); v[15] = max(v[11], v[15]); v[11] = t; }
-    { const uint32_t t = min(v[16], v[20]); v[20] = max(v[16], v[20]); v[16] = t; }
-    { const uint32_t t = min(v[17], v[21]); v[21] = max(v[17], v[21]); v[17] = t; }
-    { const uint32_t t = min(v[18], v[22]); v[22] = max(v[18], v[22]); v[18] = t; }
-    { const uint32_t t = min(v[19], v[23]); v[23] = max(v[19], v[23]); v[19] = t; }
-    { const uint32_t t = min(v[2], v[4]); v[4] = max(v[2], v[4]); v[2] = t; }
-    { const uint32_t t = min(v[3], v[5]); v[5] = max(v[3], v[5]); v[3] = t; }
-    { const uint32_t t = min(v[10], v[12]); v[12] = max(v[10], v[12]); v[10] = t; }
-    { const uint32_t t = min(v[11], v[13]); v[13] = max(v[11], v[13]); v[11] = t; }
-    { const uint32_t t = min(v[18], v[20]); v[20] = max(v[18], v[20]); v[18] = t; }
-    { const uint32_t t = min(v[19], v[21]); v[21] = max(v[19], v[21]); v[19] = t; }
-    { const uint32_t t = min(v[1], v[2]); v[2] = max(v[1], v[2]); v[1] = t; }
-    { const uint32_t t = min(v[3], v[4]); v[4] = max(v[3], v[4]); v[3] = t; }
-    { const uint32_t t = min(v[5], v[6]); v[6] = max(v[5], v[6]); v[5] = t; }
-    { const uint32_t t = min(v[9], v[10]); v[10] = max(v[9], v[10]); v[9] = t; }
-    { const uint32_t t = min(v[11], v[12]); v[12] = max(v[11], v[12]); v[11] = t; }
-    { const uint32_t t = min(v[13], v[14]); v[14] = max(v[13], v[14]); v[13] = t; }
-    { const uint32_t t = min(v[17], v[18]); v[18] = max(v[17], v[18]); v[17] = t; }
-    { const uint32_t t = min(v[19], v[20]); v[20] = max(v[19], v[20]); v[19] = t; }
-    { const uint32_t t = min(v[21], v[22]); v[22] = max(v[21], v[22]); v[21] = t; }
-    { const uint32_t t = min(v[25], v[26]); v[26] = max(v[25], v[26]); v[25] = t; }
-    { const uint32_t t = min(v[0], v[8]); v[8] = max(v[0], v[8]); v[0] = t; }
-    { const uint32_t t = min(v[1], v[9]); v[9] = max(v[1], v[9]); v[1] = t; }
-    { const uint32_t t = min(v[2], v[10]); v[10] = max(v[2], v[10]); v[2] = t; }
-    { const uint32_t t = min(v[3], v[11]); v[11] = max(v[3], v[11]); v[3] = t; }
-    { const uint32_t t = min(v[4], v[12]); v[12] = max(v[4], v[12]); v[4] = t; }
-    { const uint32_t t = min(v[5], v[13]); v[13] = max(v[5], v[13]); v[5] = t; }
-    { const uint32_t t = min(v[6], v[14]); v[14] = max(v[6], v[14]); v[6] = t; }
-    v[7] = min(v[7], v[15]);
-    { const uint32_t t = min(v[16], v[24]); v[24] = max(v[16], v[24]); v[16] = t; }
-    { const uint32_t t = min(v[17], v[25]); v[25] = max(v[17], v[25]); v[17] = t; }
-    { const uint32_t t = min(v[18], v[26]); v[26] = max(v[18], v[26]); v[18] = t; }
-    { const uint32_t t = min(v[4], v[8]); v[8] = max(v[4], v[8]); v[4] = t; }
-    { const uint32_t t = min(v[5], v[9]); v[9] = max(v[5], v[9]); v[5] = t; }
-    { const uint32_t t = min(v[6], v[10]); v[10] = max(v[6], v[10]); v[6] = t; }
-    { const uint32_t t = min(v[7], v[11]); v[11] = max(v[7], v[11]); v[7] = t; }
-    { const uint32_t t = min(v[20], v[24]); v[24] = max(v[20], v[24]); v[20] = t; }
-    { const uint32_t t = min(v[21], v[25]); v[25] = max(v[21], v[25]); v[21] = t; }
-    { const uint32_t t = min(v[22], v[26]); v[26] = max(v[22], v[26]); v[22] = t; }
-    { const uint32_t t = min(v[2], v[4]); v[4] = max(v[2], v[4]); v[2] = t; }
-    { const uint32_t t = min(v[3], v[5]); v[5] = max(v[3], v[5]); v[3] = t; }
-    { const uint32_t t = min(v[6], v[8]); v[8] = max(v[6], v[8]); v[6] = t; }
-    { const uint32_t t = min(v[7], v[9]); v[9] = max(v[7], v[9]); v[7] = t; }
-    { const uint32_t t = min(v[10], v[12]); v[12] = max(v[10], v[12]); v[10] = t; }
-    { const uint32_t t = min(v[11], v[13]); v[13] = max(v[11], v[13]); v[11] = t; }
-    { const uint32_t t = min(v[18], v[20]); v[20] = max(v[18], v[20]); v[18] = t; }
-    { const uint32_t t = min(v[19], v[21]); v[21] = max(v[19], v[21]); v[19] = t; }
-    { const uint32_t t = min(v[22], v[24]); v[24] = max(v[22], v[24]); v[22] = t; }
-    { const uint32_t t = min(v[23], v[25]); v[25] = max(v[23], v[25]); v[23] = t; }
-    { const uint32_t t = min(v[1], v[2]); v[2] = max(v[1], v[2]); v[1] = t; }
-    { const uint32_t t = min(v[3], v[4]); v[4] = max(v[3], v[4]); v[3] = t; }
-    { const uint32_t t = min(v[5], v[6]); v[6] = max(v[5], v[6]); v[5] = t; }
-    { const uint32_t t = min(v[7], v[8]); v[8] = max(v[7], v[8]); v[7] = t; }
-    { const uint32_t t = min(v[9], v[10]); v[10] = max(v[9], v[10]); v[9] = t; }
-    { const uint32_t t = min(v[11], v[12]); v[12] = max(v[11], v[12]); v[11] = t; }
-    { const uint32_t t = min(v[13], v[14]); v[14] = max(v[13], v[14]); v[13] = t; }
-    { const uint32_t t = min(v[17], v[18]); v[18] = max(v[17], v[18]); v[17] = t; }
-    { const uint32_t t = min(v[19], v[20]); v[20] = max(v[19], v[20]); v[19] = t; }
-    { const uint32_t t = min(v[21], v[22]); v[22] = max(v[21], v[22]); v[21] = t; }
-    { const uint32_t t = min(v[23], v[24]); v[24] = max(v[23], v[24]); v[23] = t; }
-    { const uint32_t t = min(v[25], v[26]); v[26] = max(v[25], v[26]); v[25] = t; }
-    v[16] = max(v[0], v[16]);
-    v[17] = max(v[1], v[17]);
-    v[18] = max(v[2], v[18]);
-    v[19] = max(v[3], v[19]);
-    v[20] = max(v[4], v[20]);
-    v[21] = max(v[5], v[21]);
-    v[22] = max(v[6], v[22]);
-    v[7] = min(v[7], v[23]);
-    v[8] = min(v[8], v[24]);
-    v[9] = min(v[9], v[25]);
-    v[10] = min(v[10], v[26]);
-    v[16] = max(v[8], v[16]);
-    v[17] = max(v[9], v[17]);
-    v[18] = max(v[10], v[18]);
-    v[11] = min(v[11], v[19]);
-    v[12] = min(v[12], v[20]);
-    v[13] = min(v[13], v[21]);
-    v[14] = min(v[14], v[22]);
-    v[11] = max(v[7], v[11]);
-    v[16] = max(v[12], v[16]);
-    v[13] = min(v[13], v[17]);
-    v[14] = min(v[14], v[18]);
-    v[13] = max(v[11], v[13]);
-    v[14] = min(v[14], v[16]);
-    v[13] = min(v[13], v[14]);
-    return v[13];
+// Sorts v[0..8] in place (s[k] receives the k-th smallest).
+__device__ __forceinline__ void sort9(const uint32_t *v, uint32_t *s) {
+    uint32_t w[16];
+    w[0] = v[0];
+    w[1] = v[1];
+    w[2] = v[2];
+    w[3] = v[3];
+    w[4] = v[4];
+    w[5] = v[5];
+    w[6] = v[6];
+    w[7] = v[7];
+    w[8] = v[8];
+    { const uint32_t t = min(w[0], w[1]); w[1] = max(w[0], w[1]); w[0] = t; }
+    { const uint32_t t = min(w[2], w[3]); w[3] = max(w[2], w[3]); w[2] = t; }
+    { const uint32_t t = min(w[4], w[5]); w[5] = max(w[4], w[5]); w[4] = t; }
+    { const uint32_t t = min(w[6], w[7]); w[7] = max(w[6], w[7]); w[6] = t; }
+    { const uint32_t t = min(w[0], w[2]); w[2] = max(w[0], w[2]); w[0] = t; }
+    { const uint32_t t = min(w[1], w[3]); w[3] = max(w[1], w[3]); w[1] = t; }
+    { const uint32_t t = min(w[4], w[6]); w[6] = max(w[4], w[6]); w[4] = t; }
+    { const uint32_t t = min(w[5], w[7]); w[7] = max(w[5], w[7]); w[5] = t; }
+    { const uint32_t t = min(w[1], w[2]); w[2] = max(w[1], w[2]); w[1] = t; }
+    { const uint32_t t = min(w[5], w[6]); w[6] = max(w[5], w[6]); w[5] = t; }
+    { const uint32_t t = min(w[0], w[4]); w[4] = max(w[0], w[4]); w[0] = t; }
+    { const uint32_t t = min(w[1], w[5]); w[5] = max(w[1], w[5]); w[1] = t; }
+    { const uint32_t t = min(w[2], w[6]); w[6] = max(w[2], w[6]); w[2] = t; }
+    { const uint32_t t = min(w[3], w[7]); w[7] = max(w[3], w[7]); w[3] = t; }
+    { const uint32_t t = min(w[2], w[4]); w[4] = max(w[2], w[4]); w[2] = t; }
+    { const uint32_t t = min(w[3], w[5]); w[5] = max(w[3], w[5]); w[3] = t; }
+    { const uint32_t t = min(w[1], w[2]); w[2] = max(w[1], w[2]); w[1] = t; }
+    { const uint32_t t = min(w[3], w[4]); w[4] = max(w[3], w[4]); w[3] = t; }
+    { const uint32_t t = min(w[5], w[6]); w[6] = max(w[5], w[6]); w[5] = t; }
+    { const uint32_t t = min(w[0], w[8]); w[8] = max(w[0], w[8]); w[0] = t; }
+    { const uint32_t t = min(w[4], w[8]); w[8] = max(w[4], w[8]); w[4] = t; }
+    { const uint32_t t = min(w[2], w[4]); w[4] = max(w[2], w[4]); w[2] = t; }
+    { const uint32_t t = min(w[3], w[5]); w[5] = max(w[3], w[5]); w[3] = t; }
+    { const uint32_t t = min(w[6], w[8]); w[8] = max(w[6], w[8]); w[6] = t; }
+    { const uint32_t t = min(w[1], w[2]); w[2] = max(w[1], w[2]); w[1] = t; }
+    { const uint32_t t = min(w[3], w[4]); w[4] = max(w[3], w[4]); w[3] = t; }
+    { const uint32_t t = min(w[5], w[6]); w[6] = max(w[5], w[6]); w[5] = t; }
+    { const uint32_t t = min(w[7], w[8]); w[8] = max(w[7], w[8]); w[7] = t; }
+    s[0] = w[0];
+    s[1] = w[1];
+    s[2] = w[2];
+    s[3] = w[3];
+    s[4] = w[4];
+    s[5] = w[5];
+    s[6] = w[6];
+    s[7] = w[7];
+    s[8] = w[8];
+}
+
+// The 14th smallest of a[0..8], b[0..8], c[0..8], each sorted ascending.
+__device__ __forceinline__ uint32_t median3x9(const uint32_t *a, const uint32_t *b, const uint32_t *c) {
+    uint32_t w[64];
+    w[0] = a[0];
+    w[1] = a[1];
+    w[2] = a[2];
+    w[3] = a[3];
+    w[4] = a[4];
+    w[5] = a[5];
+    w[6] = a[6];
+    w[7] = a[7];
+    w[8] = a[8];
+    w[16] = b[0];
+    w[17] = b[1];
+    w[18] = b[2];
+    w[19] = b[3];
+    w[20] = b[4];
+    w[21] = b[5];
+    w[22] = b[6];
+    w[23] = b[7];
+    w[24] = b[8];
+    w[32] = c[0];
+    w[33] = c[1];
+    w[34] = c[2];
+    w[35] = c[3];
+    w[36] = c[4];
+    w[37] = c[5];
+    w[38] = c[6];
+    w[39] = c[7];
+    w[40] = c[8];
+    { const uint32_t t = min(w[0], w[16]); w[16] = max(w[0], w[16]); w[0] = t; }
+    { const uint32_t t = min(w[1], w[17]); w[17] = max(w[1], w[17]); w[1] = t; }
+    { const uint32_t t = min(w[2], w[18]); w[18] = max(w[2], w[18]); w[2] = t; }
+    { const uint32_t t = min(w[3], w[19]); w[19] = max(w[3], w[19]); w[3] = t; }
+    { const uint32_t t = min(w[4], w[20]); w[20] = max(w[4], w[20]); w[4] = t; }
+    { const uint32_t t = min(w[5], w[21]); w[21] = max(w[5], w[21]); w[5] = t; }
+    { const uint32_t t = min(w[6], w[22]); w[22] = max(w[6], w[22]); w[6] = t; }
+    { const uint32_t t = min(w[7], w[23]); w[23] = max(w[7], w[23]); w[7] = t; }
+    { const uint32_t t = min(w[8], w[24]); w[24] = max(w[8], w[24]); w[8] = t; }
+    { const uint32_t t = min(w[8], w[16]); w[16] = max(w[8], w[16]); w[8] = t; }
+    { const uint32_t t = min(w[4], w[8]); w[8] = max(w[4], w[8]); w[4] = t; }
+    { const uint32_t t = min(w[5], w[17]); w[17] = max(w[5], w[17]); w[5] = t; }
+    { const uint32_t t = min(w[6], w[18]); w[18] = max(w[6], w[18]); w[6] = t; }
+    { const uint32_t t = min(w[7], w[19]); w[19] = max(w[7], w[19]); w[7] = t; }
+    { const uint32_t t = min(w[20], w[16]); w[16] = max(w[20], w[16]); w[20] = t; }
+    { const uint32_t t = min(w[2], w[4]); w[4] = max(w[2], w[4]); w[2] = t; }
+    { const uint32_t t = min(w[3], w[5]); w[5] = max(w[3], w[5]); w[3] = t; }
+    { const uint32_t t = min(w[6], w[8]); w[8] = max(w[6], w[8]); w[6] = t; }
+    { const uint32_t t = min(w[7], w[17]); w[17] = max(w[7], w[17]); w[7] = t; }
+    { const uint32_t t = min(w[18], w[20]); w[20] = max(w[18], w[20]); w[18] = t; }
+    { const uint32_t t = min(w[19], w[21]); w[21] = max(w[19], w[21]); w[19] = t; }
+    { const uint32_t t = min(w[22], w[16]); w[16] = max(w[22], w[16]); w[22] = t; }
+    { const uint32_t t = min(w[1], w[2]); w[2] = max(w[1], w[2]); w[1] = t; }
+    { const uint32_t t = min(w[3], w[4]); w[4] = max(w[3], w[4]); w[3] = t; }
+    { const uint32_t t = min(w[5], w[6]); w[6] = max(w[5], w[6]); w[5] = t; }
+    { const uint32_t t = min(w[7], w[8]); w[8] = max(w[7], w[8]); w[7] = t; }
+    { const uint32_t t = min(w[17], w[18]); w[18] = max(w[17], w[18]); w[17] = t; }
+    { const uint32_t t = min(w[19], w[20]); w[20] = max(w[19], w[20]); w[19] = t; }
+    { const uint32_t t = min(w[21], w[22]); w[22] = max(w[21], w[22]); w[21] = t; }
+    w[16] = max(w[23], w[16]);
+    w[32] = max(w[0], w[32]);
+    w[33] = max(w[1], w[33]);
+    w[34] = max(w[2], w[34]);
+    w[35] = max(w[3], w[35]);
+    w[36] = max(w[4], w[36]);
+    w[37] = max(w[5], w[37]);
+    w[38] = max(w[6], w[38]);
+    w[7] = min(w[7], w[39]);
+    w[8] = min(w[8], w[40]);
+    w[16] = min(w[16], w[32]);
+    w[24] = min(w[24], w[33]);
+    w[16] = max(w[8], w[16]);
+    w[24] = max(w[17], w[24]);
+    w[34] = max(w[18], w[34]);
+    w[19] = min(w[19], w[35]);
+    w[20] = min(w[20], w[36]);
+    w[21] = min(w[21], w[37]);
+    w[22] = min(w[22], w[38]);
+    w[19] = max(w[7], w[19]);
+    w[16] = max(w[20], w[16]);
+    w[21] = min(w[21], w[24]);
+    w[22] = min(w[22], w[34]);
+    w[21] = max(w[19], w[21]);
+    w[22] = min(w[22], w[16]);
+    w[21] = min(w[21], w[22]);
+    return w[21];
 }

@@ -1698,8 +1698,9 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
 }
 
 // D = max(L - B, 0) staged per tile of 32 x 8 x 8 voxels (plus a one-voxel
-// halo, clamped), then the median of each voxel's 27 neighbours; the result
-// is the volume the smoothing reads.
+// halo, clamped), then the median of each voxel's 27 neighbours from the
+// sorted 3x3 neighbourhoods of its three planes; the result is the volume
+// the smoothing reads.
 constexpr int MED_TX = 32, MED_TY = 8, MED_TZ = 8;
 
 __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr *__restrict__ h) {
@@ -1742,15 +1743,27 @@ __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr 
         __syncthreads();
         const int x = x0 + tx, y = y0 + ty;
         if (x >= X || y >= Y) continue;
+        // each plane's 3x3 neighbourhood is sorted once and serves the three
+        // voxels above, at and below it
+        auto plane = [&](int c, uint32_t *srt) {
+            uint32_t v[9];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) v[3 * b + a] = d[c][ty + b][tx + a];
+            sort9(v, srt);
+        };
+        uint32_t s0[9], s1[9], s2[9];
+        plane(0, s0);
+        plane(1, s1);
         for (int k = 0; k < MED_TZ && z0 + k < Z; ++k) {
-            uint32_t v[27];
+            plane(k + 2, s2);
+            V.dn_out[(size_t)x + (size_t)X * ((size_t)y + (size_t)Y * (z0 + k))] = (uint16_t)median3x9(s0, s1, s2);
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int b = 0; b < 3; ++b)
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) v[9 * c + 3 * b + a] = d[k + c][ty + b][tx + a];
-            V.dn_out[(size_t)x + (size_t)X * ((size_t)y + (size_t)Y * (z0 + k))] = (uint16_t)median27_net(v);
+            for (int i = 0; i < 9; ++i) {
+                s0[i] = s1[i];
+                s1[i] = s2[i];
+            }
         }
     }
 }
