@@ -56,8 +56,8 @@ def _load():
                                                ctypes.c_uint64, u64p]
         lib.oracle_filter_features.restype = ctypes.c_int
         lib.oracle_segment.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
-                                       ctypes.c_uint32, u32p, vp, ctypes.c_uint64, u64p, u16p,
-                                       u64p, u16p]
+                                       ctypes.c_uint32, ctypes.c_uint32, u32p, vp, ctypes.c_uint64, u64p,
+                                       u16p, u64p, u16p]
         lib.oracle_segment.restype = ctypes.c_int
         for name in ("oracle_background", "oracle_denoise"):
             getattr(lib, name).argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -68,6 +68,8 @@ def _load():
         lib.oracle_box_pass.restype = ctypes.c_int
         lib.oracle_median27.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u16p]
         lib.oracle_median27.restype = ctypes.c_int
+        lib.oracle_close.argtypes = [u8p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u8p]
+        lib.oracle_close.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -186,10 +188,22 @@ def denoise(vol: np.ndarray, r: int) -> np.ndarray:
     return _vol_op("oracle_denoise", vol, int(r))
 
 
+def close(mask: np.ndarray, rho: int) -> np.ndarray:
+    """Closing of a boolean [Z,Y,X] mask with the ball of radius rho (padded)."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    X, Y, Z = _dims(m)
+    out = np.empty_like(m)
+    rc = _load().oracle_close(_ptr(m, ctypes.c_uint8), X, Y, Z, int(rho), _ptr(out, ctypes.c_uint8))
+    if rc:
+        raise RuntimeError("oracle_close failed: %d" % rc)
+    return out.astype(bool)
+
+
 def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
-            keep_smoothed: bool = False, denoise_radius: int = 0) -> OracleResult:
+            keep_smoothed: bool = False, denoise_radius: int = 0, closing_radius: int = 0) -> OracleResult:
     """The whole stage for one frame and channel (uint16 [Z,Y,X]); with
-    denoise_radius > 0 the denoise front end runs first."""
+    denoise_radius > 0 the denoise front end runs first, with closing_radius
+    > 0 the foreground is closed with that ball before labelling."""
     vol = np.ascontiguousarray(vol, dtype=np.uint16)
     if denoise_radius:
         vol = denoise(vol, denoise_radius)
@@ -207,7 +221,7 @@ def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
     hist = np.zeros(65536, dtype=np.uint64) if keep_hist else None
     sm = np.empty_like(vol) if keep_smoothed else None
     rc = _load().oracle_segment(
-        _ptr(vol, ctypes.c_uint16), X, Y, Z, int(min_volume), _ptr(labels, ctypes.c_uint32),
+        _ptr(vol, ctypes.c_uint16), X, Y, Z, int(min_volume), int(closing_radius), _ptr(labels, ctypes.c_uint32),
         cells.ctypes.data, len(cells), _ptr(k, ctypes.c_uint64), _ptr(t, ctypes.c_uint16),
         _ptr(hist, ctypes.c_uint64) if hist is not None else None,
         _ptr(sm, ctypes.c_uint16) if sm is not None else None)

@@ -344,12 +344,66 @@ int oracle_denoise(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32
     return rc;
 }
 
+/* ------------------------------------------------------------------------
+ * Morphological closing of the foreground (Segmentation: a closing with a
+ * binary ball removes holes before the connected components).  The ball of
+ * radius rho holds the offsets with dx^2 + dy^2 + dz^2 <= rho^2 (voxel
+ * units).  The closing is taken on the volume padded with rho voxels of
+ * background on every side -- dilation, then erosion, then the original box
+ * -- so it contains the foreground it started from and has no border
+ * artefacts.
+ * ------------------------------------------------------------------------ */
+int oracle_close(const uint8_t *m, uint32_t X, uint32_t Y, uint32_t Z, uint32_t rho, uint8_t *out) {
+    if (!m || !out || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    const int64_t r = rho;
+    const int64_t PX = X + 2 * r, PY = Y + 2 * r, PZ = Z + 2 * r;
+    const uint64_t pn = (uint64_t)PX * PY * PZ;
+    uint8_t *a = (uint8_t *)calloc(pn, 1), *d = (uint8_t *)calloc(pn, 1);
+    if (!a || !d) { free(a); free(d); return ORACLE_ENOMEM; }
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x)
+                a[(x + r) + PX * ((y + r) + PY * (z + r))] = m[x + X * (y + Y * z)] ? 1 : 0;
+    /* dilation: any ball neighbour inside the padded box set */
+    for (int64_t z = 0; z < PZ; ++z)
+        for (int64_t y = 0; y < PY; ++y)
+            for (int64_t x = 0; x < PX; ++x) {
+                uint8_t v = 0;
+                for (int64_t c = -r; c <= r && !v; ++c)
+                    for (int64_t b = -r; b <= r && !v; ++b)
+                        for (int64_t e = -r; e <= r && !v; ++e) {
+                            if (e * e + b * b + c * c > r * r) continue;
+                            const int64_t xx = x + e, yy = y + b, zz = z + c;
+                            if (xx < 0 || yy < 0 || zz < 0 || xx >= PX || yy >= PY || zz >= PZ) continue;
+                            v = a[xx + PX * (yy + PY * zz)];
+                        }
+                d[x + PX * (y + PY * z)] = v;
+            }
+    /* erosion, read back inside the original box: every ball neighbour set
+     * (all of them lie inside the padded box) */
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                uint8_t v = 1;
+                for (int64_t c = -r; c <= r && v; ++c)
+                    for (int64_t b = -r; b <= r && v; ++b)
+                        for (int64_t e = -r; e <= r && v; ++e) {
+                            if (e * e + b * b + c * c > r * r) continue;
+                            v = d[(x + r + e) + PX * ((y + r + b) + PY * (z + r + c))];
+                        }
+                out[x + X * (y + Y * z)] = v;
+            }
+    free(a);
+    free(d);
+    return ORACLE_OK;
+}
+
 /* The whole stage for one frame and channel: smooth, histogram, Otsu,
  * threshold (foreground iff s > t*), label, filter, features.
  * hist (65536 entries) and smoothed (n entries) are optional outputs. */
 int oracle_segment(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32_t min_volume,
-                   uint32_t *labels, oracle_cell *cells, uint64_t cap, uint64_t *k_out,
-                   uint16_t *t_out, uint64_t *hist, uint16_t *smoothed) {
+                   uint32_t closing_radius, uint32_t *labels, oracle_cell *cells, uint64_t cap,
+                   uint64_t *k_out, uint16_t *t_out, uint64_t *hist, uint16_t *smoothed) {
     if (!v || !labels || !k_out || !t_out || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
     uint64_t n = (uint64_t)X * Y * Z;
     uint16_t *s = smoothed ? smoothed : (uint16_t *)malloc(n * sizeof(uint16_t));
@@ -364,6 +418,14 @@ int oracle_segment(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32
     uint16_t t = oracle_otsu(h);
     *t_out = t;
     for (uint64_t i = 0; i < n; ++i) m[i] = (uint8_t)(s[i] > t);
+    if (closing_radius) {
+        uint8_t *c = (uint8_t *)malloc(n);
+        if (!c) { rc = ORACLE_ENOMEM; goto done; }
+        rc = oracle_close(m, X, Y, Z, closing_radius, c);
+        memcpy(m, c, n);
+        free(c);
+        if (rc) goto done;
+    }
     int64_t nc = oracle_label26(m, X, Y, Z, labels);
     if (nc < 0) { rc = (int)nc; goto done; }
     rc = oracle_filter_features(labels, (uint64_t)nc, X, Y, Z, min_volume, labels, cells, cap, k_out);

@@ -502,3 +502,48 @@ def test_segment_with_denoise_is_segment_of_denoised():
     a = oracle.segment(vol, min_volume=5, denoise_radius=r)
     b = oracle.segment(oracle.denoise(vol, r), min_volume=5)
     assert a.threshold == b.threshold and np.array_equal(a.labels, b.labels)
+
+
+# ---------------------------------------------------------------------------
+# Closing with a binary ball (Segmentation): pinned to scipy on the padded
+# volume, and to the algebra of a closing
+# ---------------------------------------------------------------------------
+
+def _ball(rho):
+    g = np.arange(-rho, rho + 1)
+    return (g[:, None, None] ** 2 + g[None, :, None] ** 2 + g[None, None, :] ** 2) <= rho * rho
+
+
+@pytest.mark.parametrize("rho", [1, 2, 3])
+def test_close_matches_scipy_on_padded_volume(rho):
+    ndi = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(60 + rho)
+    for shape, p in [((9, 11, 13), 0.3), ((4, 20, 7), 0.5), ((1, 6, 30), 0.4), ((12, 12, 12), 0.1)]:
+        m = rng.uniform(size=shape) < p
+        padded = np.pad(m, rho)
+        ref = ndi.binary_closing(padded, structure=_ball(rho))[rho:-rho, rho:-rho, rho:-rho]
+        assert np.array_equal(oracle.close(m, rho), ref), (shape, rho)
+
+
+def test_close_algebra():
+    rng = np.random.default_rng(66)
+    m = rng.uniform(size=(10, 12, 14)) < 0.35
+    for rho in (1, 2):
+        c = oracle.close(m, rho)
+        assert np.all(c[m])                                  # extensive
+        assert np.array_equal(oracle.close(c, rho), c)       # idempotent
+    assert np.array_equal(oracle.close(m, 0), m)             # radius 0: identity
+    # a one-voxel hole inside a solid block is filled by the smallest ball
+    b = np.zeros((9, 9, 9), dtype=bool)
+    b[2:7, 2:7, 2:7] = True
+    b[4, 4, 4] = False
+    assert oracle.close(b, 1)[4, 4, 4]
+
+
+def test_segment_with_closing_labels_the_closed_mask():
+    ndi = pytest.importorskip("scipy.ndimage")
+    vol, _ = synth.well_separated((40, 36, 18), seed=11, n_nuclei=5)
+    r = oracle.segment(vol, min_volume=1, closing_radius=2, keep_smoothed=True)
+    closed = oracle.close(r.smoothed > r.threshold, 2)
+    lab, n = ndi.label(closed, structure=np.ones((3, 3, 3)))
+    assert n == r.labels.max() and np.array_equal(r.labels > 0, closed)
