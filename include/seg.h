@@ -109,6 +109,11 @@ typedef struct {
      * (each rounding to nearest, replicate edges), it is subtracted with a
      * floor at 0, and the 3x3x3 median of the difference is segmented. */
     uint32_t denoise_radius;
+    /* 0: off.  1..8: the foreground is closed with the binary ball of this
+     * radius (offsets with dx^2 + dy^2 + dz^2 <= r^2) before labelling,
+     * dilation then erosion on the volume padded with background, so the
+     * closed foreground contains the original (Segmentation section). */
+    uint32_t closing_radius;
 } seg_channel_params;
 
 /* Creates a context on cfg->device.  Allocates streams and descriptor buffers;
@@ -169,7 +174,7 @@ int seg_release(seg_ctx *ctx, seg_req req);
 int seg_request_times(seg_ctx *ctx, seg_req req, double *submit_ms, double *admit_ms,
                       double *launch_ms, double *done_ms);
 
-#define SEG_MAX_KERNELS 16
+#define SEG_MAX_KERNELS 32
 typedef struct {
     uint64_t batches;                 /* launch sequences completed            */
     uint64_t volumes;                 /* volume-channels segmented             */

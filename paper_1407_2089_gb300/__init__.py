@@ -37,7 +37,7 @@ SEG_NO_GRAPH = 0x4
 SEG_PROFILE = 0x8
 SEG_TEST_UNION_FAIL = 0x10
 
-SEG_MAX_KERNELS = 16
+SEG_MAX_KERNELS = 32
 
 
 class seg_dims(ctypes.Structure):
@@ -65,7 +65,8 @@ class seg_config(ctypes.Structure):
 
 
 class seg_channel_params(ctypes.Structure):
-    _fields_ = [("min_volume_voxels", ctypes.c_uint32), ("denoise_radius", ctypes.c_uint32)]
+    _fields_ = [("min_volume_voxels", ctypes.c_uint32), ("denoise_radius", ctypes.c_uint32),
+                ("closing_radius", ctypes.c_uint32)]
 
 
 class seg_stats(ctypes.Structure):
@@ -167,11 +168,11 @@ def _voxel_ptr(voxels):
     return voxels.data_ptr(), 1 if voxels.is_cuda else 0
 
 
-def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, denoise_radius=0):
+def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, denoise_radius=0, closing_radius=0):
     """Submits [C][Z][Y][X] (or [Z][Y][X]) uint16 voxels; returns the request id.
 
-    min_volume, denoise_radius: one int for every channel or a sequence of
-    per-channel ints (denoise_radius 0 = no denoise front end)."""
+    min_volume, denoise_radius, closing_radius: one int for every channel or
+    a sequence of per-channel ints (0 = no denoise front end / no closing)."""
     shape = tuple(voxels.shape)
     if dims is None:
         if len(shape) == 3:
@@ -186,7 +187,9 @@ def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, deno
     ptr, on_dev = _voxel_ptr(voxels)
     mv = [min_volume] * channels if np.isscalar(min_volume) else list(min_volume)
     dr = [denoise_radius] * channels if np.isscalar(denoise_radius) else list(denoise_radius)
-    params = (seg_channel_params * channels)(*[seg_channel_params(int(m), int(d)) for m, d in zip(mv, dr)])
+    cr = [closing_radius] * channels if np.isscalar(closing_radius) else list(closing_radius)
+    params = (seg_channel_params * channels)(*[seg_channel_params(int(m), int(d), int(c))
+                                               for m, d, c in zip(mv, dr, cr)])
     out = ctypes.c_uint64()
     _check(_lib.seg_submit_volume(ctx, ctypes.c_void_p(ptr), on_dev, seg_dims(*dims), channels,
                                   params, ctypes.byref(out)), "seg_submit_volume")
@@ -280,11 +283,12 @@ def seg_otsu_threshold_noalloc(voxels_ptr, dims, result_ptr, stream_ptr=None):
            "seg_otsu_threshold_noalloc")
 
 
-def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000, denoise_radius=0):
+def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000, denoise_radius=0, closing_radius=0):
     """Convenience: submit one volume, wait, read labels + cells of every channel, release.
 
     Returns a list (one entry per channel) of (labels, cells, threshold)."""
-    req = seg_submit_volume(ctx, voxels, min_volume=min_volume, denoise_radius=denoise_radius)
+    req = seg_submit_volume(ctx, voxels, min_volume=min_volume, denoise_radius=denoise_radius,
+                            closing_radius=closing_radius)
     seg_flush(ctx)
     try:
         st = seg_wait(ctx, req, timeout_ms)

@@ -80,6 +80,12 @@ struct VolDev {
     uint32_t dn_base0, dn_base1, dn_base2;  // first flat box item per axis
     uint32_t dn_tiles;        // median tiles
     uint32_t dn_tbase;        // first flat median tile
+    // closing of the foreground (cl_r > 0)
+    uint32_t *cl_ext;         // dilated mask on rows y in [-r, Y+r), z in [-r, Z+r), W + 2 words each
+    uint32_t cl_r;            // ball radius, 0 = no closing
+    uint32_t cl_n;            // dilation items (extended rows x words)
+    uint32_t cl_base;         // first flat dilation item
+    uint32_t cl_pad;
 };
 
 // Batch header, followed in memory by VolDev[nvol].
@@ -93,7 +99,8 @@ struct BatchHdr {
     uint32_t nbtasks;    // k_union tasks over the batch
     uint32_t dn_items[3];// denoise box-pass items per axis over the batch
     uint32_t dn_tiles;   // denoise median tiles over the batch
-    uint32_t pad[3];
+    uint32_t cl_items;   // closing dilation items over the batch
+    uint32_t pad[2];
     VolDev vol[1];       // nvol entries
 };
 
@@ -102,7 +109,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 15;
+constexpr int NUM_KERNELS = 17;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {
@@ -121,6 +128,7 @@ struct LaunchPlan {
     int grid_box;        // k_box_pass
     int grid_med;        // k_median27
     bool denoise;        // some volume of the batch runs the denoise front end
+    bool closing;        // some volume of the batch closes its foreground
 };
 
 // Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)
@@ -136,6 +144,7 @@ cudaError_t launch_tile_probe(const BatchHdr *d_hdr, const LaunchPlan &plan, cud
 // Denoise front end of the volumes with dn_r > 0 (none: the kernels exit).
 constexpr int DN_CHUNK = 128;    // box-pass positions per tile along a line
 constexpr int DN_MAX_R = 16;
+constexpr int CL_MAX_R = 8;      // closing ball radius limit
 cudaError_t launch_denoise(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);
 
 // Histogram-kernel shared memory per block for a tile height.

@@ -40,9 +40,10 @@
 namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
-    "denoise_box", "denoise_median", "init",           "smooth_hist_otsu", "threshold_runs",
-    "scan_runs",   "row_runs",       "union_local",    "union",            "flatten",
-    "keep_count",  "scan_keep",      "rank",           "label_features",   "gather_stat"};
+    "denoise_box", "denoise_median", "init",       "smooth_hist_otsu", "threshold_runs",
+    "dilate",      "erode",          "scan_runs",  "row_runs",         "union_local",
+    "union",       "flatten",        "keep_count", "scan_keep",        "rank",
+    "label_features", "gather_stat"};
 
 namespace {
 
@@ -1768,6 +1769,128 @@ __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr 
     }
 }
 
+// ----------------------------------------------------------------------------
+// Closing of the foreground with a binary ball (Segmentation section): the
+// ball of radius rho holds the offsets with dx^2 + dy^2 + dz^2 <= rho^2.  It
+// is split into rows: for each (dy, dz) with dy^2 + dz^2 <= rho^2 an x-run of
+// half-width floor(sqrt(rho^2 - dy^2 - dz^2)).  Dilation (OR) fills the
+// extended mask, which covers rho rows and planes of padding and one word
+// of padding on each side of every row; erosion (AND) reads it back for the
+// rows of the volume, so every ball around a voxel stays inside the
+// extended mask -- the closing of the padded volume, cut to the volume.
+// ----------------------------------------------------------------------------
+
+// x-run half-width of the ball for a row offset, -1 outside the ball.
+__device__ __forceinline__ int ball_rx(int rho, int dy, int dz) {
+    const int q = rho * rho - dy * dy - dz * dz;
+    if (q < 0) return -1;
+    int r = (int)sqrtf((float)q);
+    while (r * r > q) --r;
+    while ((r + 1) * (r + 1) <= q) ++r;
+    return r;
+}
+
+// OR (DIL) or AND of the 2 rx + 1 x-shifts of a bit word w1 with its
+// neighbours w0 (lower x) and w2 (higher x).
+template <bool DIL>
+__device__ __forceinline__ uint32_t smear(uint32_t w0, uint32_t w1, uint32_t w2, int rx) {
+    uint32_t acc = w1;
+    for (int k = 1; k <= rx; ++k) {
+        const uint32_t up = __funnelshift_r(w1, w2, k);    // bit b <- x + k
+        const uint32_t dn = __funnelshift_l(w0, w1, k);    // bit b <- x - k
+        acc = DIL ? (acc | up | dn) : (acc & up & dn);
+    }
+    return acc;
+}
+
+// One thread per word of the extended mask of every closing volume.
+__global__ void __launch_bounds__(256) k_dilate(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::cl_base> VI;
+    VI.load(h);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < h->cl_items; it += stride) {
+        const VolDev &V = h->vol[VI.find(h, it)];
+        const uint32_t li = it - V.cl_base;
+        const int rho = (int)V.cl_r, W = (int)V.W, WE = W + 2, Y = (int)V.Y, Z = (int)V.Z;
+        const int YE = Y + 2 * rho;
+        const int we = (int)(li % (uint32_t)WE), er = (int)(li / (uint32_t)WE);
+        const int y = er % YE - rho, z = er / YE - rho;
+        const int w = we - 1;  // word of the row, -1 and W are the padding words
+        auto word = [&](int yy, int zz, int ww) -> uint32_t {
+            if (yy < 0 || yy >= Y || zz < 0 || zz >= Z || ww < 0 || ww >= W) return 0u;
+            return V.mask[((size_t)zz * Y + yy) * W + ww];
+        };
+        uint32_t acc = 0;
+        for (int dz = -rho; dz <= rho; ++dz)
+            for (int dy = -rho; dy <= rho; ++dy) {
+                const int rx = ball_rx(rho, dy, dz);
+                if (rx < 0) continue;
+                const int yy = y + dy, zz = z + dz;
+                if (yy < 0 || yy >= Y || zz < 0 || zz >= Z) continue;
+                acc |= smear<true>(word(yy, zz, w - 1), word(yy, zz, w), word(yy, zz, w + 1), rx);
+            }
+        V.cl_ext[(size_t)er * WE + we] = acc;
+    }
+}
+
+// One block per row tile, one warp per row: the eroded row, its run starts
+// and the tile's run total (the closed foreground replaces the threshold
+// mask and the run counts of k_threshold_runs).
+__global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::rt_base> VI;
+    __shared__ uint32_t wsum[ROW_TILE / 32];
+    VI.load(h);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
+        const VolDev &V = h->vol[VI.find(h, rt)];
+        if (V.cl_r == 0) continue;  // the same for the whole block
+        const uint32_t lt = rt - V.rt_base, row0 = lt * ROW_TILE;
+        const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
+        const int rho = (int)V.cl_r, W = (int)V.W, WE = W + 2, Y = (int)V.Y;
+        const int YE = Y + 2 * rho;
+        uint32_t wtot = 0;
+        for (uint32_t rr = warp; rr < nrows; rr += ROW_TILE / 32) {
+            const uint32_t row = row0 + rr;
+            const int y = (int)(row % (uint32_t)Y), z = (int)(row / (uint32_t)Y);
+            uint32_t carry = 0, cnt = 0;
+            for (int w0 = 0; w0 < W; w0 += 32) {
+                const int w = w0 + lane;
+                uint32_t acc = 0xFFFFFFFFu;
+                if (w < W) {
+                    for (int dz = -rho; dz <= rho; ++dz)
+                        for (int dy = -rho; dy <= rho; ++dy) {
+                            const int rx = ball_rx(rho, dy, dz);
+                            if (rx < 0) continue;
+                            const uint32_t *e = V.cl_ext + ((size_t)(z + dz + rho) * YE + (y + dy + rho)) * WE + (w + 1);
+                            acc &= smear<false>(e[-1], e[0], e[1], rx);
+                        }
+                    const uint32_t x0 = 32u * (uint32_t)w;
+                    if (x0 + 32u > V.X) acc &= (1u << (V.X - x0)) - 1u;  // no bits past the row
+                    V.mask[(size_t)row * W + w] = acc;
+                } else {
+                    acc = 0u;
+                }
+                const uint32_t prev = __shfl_up_sync(FULL, acc, 1);
+                const uint32_t left = lane == 0 ? carry : (prev >> 31);
+                if (w < W) cnt += __popc(acc & ~((acc << 1) | left));
+                carry = __shfl_sync(FULL, acc, 31) >> 31;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+            if (lane == 0) V.rowoff[row] = cnt;
+            wtot += cnt;
+        }
+        if (lane == 0) wsum[warp] = wtot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int i = 0; i < ROW_TILE / 32; ++i) tot += wsum[i];
+            V.tsum[lt] = tot;
+        }
+        __syncthreads();
+    }
+}
+
 template <int TY>
 cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s,
                                 cudaEvent_t *ev, int &k) {
@@ -1874,6 +1997,11 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     if (e != cudaSuccess) return e;
     rec();
     k_threshold_runs<<<p.grid_thr, ROW_TILE, 0, s>>>(d);
+    // closing, for batches in which some volume asks for it
+    rec();
+    if (p.closing) k_dilate<<<p.grid_task, 256, 0, s>>>(d);
+    rec();
+    if (p.closing) k_erode<<<p.grid_thr, ROW_TILE, 0, s>>>(d);
     rec();
     k_tile_scan<0><<<p.grid_vols, 1024, 0, s>>>(d);
     rec();

@@ -42,11 +42,13 @@ struct Batch;
 struct VolGeom {
     uint32_t X, Y, Z, W, rows, nrt;
     uint32_t dn_r;   // denoise box radius, 0 = off
+    uint32_t cl_r;   // closing ball radius, 0 = off
+    uint64_t cl_words;  // words of the extended (padded) mask of the closing
     uint64_t n, r_cap, k_cap;
     size_t scratch;  // bytes of per-batch scratch for this volume-channel
 };
 
-VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r) {
+VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r) {
     VolGeom g;
     g.X = d.x; g.Y = d.y; g.Z = d.z;
     g.W = (uint32_t)cdiv(d.x, 32);
@@ -63,6 +65,9 @@ VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r) {
                 al(4ull * g.rows) + 2 * al(4ull * g.nrt) + 3 * al(4ull * g.r_cap);
     g.dn_r = dn_r;
     if (dn_r) g.scratch += 3 * al(2ull * g.n);  // two box-pass buffers + the denoised image
+    g.cl_r = cl_r;
+    g.cl_words = cl_r ? (uint64_t)(d.y + 2 * cl_r) * (d.z + 2 * cl_r) * (g.W + 2) : 0;
+    if (cl_r) g.scratch += al(4ull * g.cl_words);
     return g;
 }
 
@@ -111,7 +116,7 @@ struct Slot {
     BatchHdr *d_hdr = nullptr;
     uint32_t *h_stat = nullptr;  // pinned
     uint32_t *d_stat = nullptr;
-    cudaGraphExec_t graph[6] = {};  // tile_y 16/32/64, without / with the denoise front end
+    cudaGraphExec_t graph[12] = {};  // tile_y 16/32/64 x denoise front end x closing
     cudaEvent_t ev[NUM_KERNELS + 1] = {};
     Batch *busy = nullptr;
 };
@@ -236,7 +241,7 @@ uint32_t batch_tile_z(const seg_ctx *ctx, const Batch &b) {
 void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
-    uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0;
+    uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0, cl = 0;
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
         for (uint32_t c = 0; c < r->C; ++c) {
@@ -273,6 +278,16 @@ void build_header(seg_ctx *ctx, Batch &b) {
             dn[1] += V.dn_n[1];
             dn[2] += V.dn_n[2];
             dnt += V.dn_tiles;
+            V.cl_r = g.cl_r;
+            V.cl_ext = nullptr;
+            V.cl_n = 0;
+            V.cl_pad = 0;
+            if (g.cl_r) {
+                V.cl_ext = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.cl_words);
+                V.cl_n = (uint32_t)g.cl_words;
+            }
+            V.cl_base = cl;
+            cl += V.cl_n;
             V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
             V.smooth = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
             V.mask = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows * g.W);
@@ -323,12 +338,15 @@ void build_header(seg_ctx *ctx, Batch &b) {
     h->dn_items[1] = dn[1];
     h->dn_items[2] = dn[2];
     h->dn_tiles = dnt;
+    h->cl_items = cl;
     h->tile_z = tz;
     h->tile_y = ty;
     b.nvol = v;
 }
 
-int graph_index(int ty, bool denoise) { return (ty == 16 ? 0 : (ty == 32 ? 1 : 2)) + (denoise ? 3 : 0); }
+int graph_index(int ty, bool denoise, bool closing) {
+    return (ty == 16 ? 0 : (ty == 32 ? 1 : 2)) + (denoise ? 3 : 0) + (closing ? 6 : 0);
+}
 
 // Enqueues descriptor upload, the pipeline and the status read-back.
 int enqueue_body(seg_ctx *ctx, Slot &s, uint32_t nvol) {
@@ -404,8 +422,9 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
     }
     build_header(ctx, b);
     ctx->plan.denoise = s.h_hdr->dn_tiles > 0;
+    ctx->plan.closing = s.h_hdr->cl_items > 0;
     if (ctx->graphs) {
-        cudaGraphExec_t &ge = s.graph[graph_index(ctx->plan.tile_y, ctx->plan.denoise)];
+        cudaGraphExec_t &ge = s.graph[graph_index(ctx->plan.tile_y, ctx->plan.denoise, ctx->plan.closing)];
         if (!ge) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
@@ -627,6 +646,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->plan.grid_hist = ctx->sms;  // one resident block per SM (176 KiB histogram)
     ctx->plan.grid_vols = ctx->sms;
     ctx->plan.denoise = false;
+    ctx->plan.closing = false;
     CK(configure_kernels(cfg->device, ctx->plan));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
@@ -697,9 +717,10 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
     for (uint32_t c = 0; c < channels; ++c) {
         uint32_t m = per_channel ? per_channel[c].min_volume_voxels : 30u;
         const uint32_t dr = per_channel ? per_channel[c].denoise_radius : 0u;
-        if (dr > (uint32_t)DN_MAX_R) return SEG_EINVAL;
+        const uint32_t cr = per_channel ? per_channel[c].closing_radius : 0u;
+        if (dr > (uint32_t)DN_MAX_R || cr > (uint32_t)CL_MAX_R) return SEG_EINVAL;
         r->minvol[c] = m ? m : 1u;  // a cell has at least one voxel
-        r->g.push_back(geom(dims, r->minvol[c], dr));
+        r->g.push_back(geom(dims, r->minvol[c], dr, cr));
     }
     r->thresh.assign(channels, 0);
     r->ncells.assign(channels, 0);
@@ -913,6 +934,7 @@ int seg_get_stats(seg_ctx *ctx, seg_stats *out) {
     out->voxels = ctx->st_voxels;
     out->tile_y = (uint32_t)ctx->plan.tile_y;
     out->tile_z = ctx->tile_z;
+    static_assert(NUM_KERNELS <= SEG_MAX_KERNELS, "seg_stats holds SEG_MAX_KERNELS kernels");
     out->n_kernels = NUM_KERNELS;
     for (int k = 0; k < NUM_KERNELS; ++k) {
         std::snprintf(out->names[k], sizeof(out->names[k]), "%s", kKernelNames[k]);

@@ -60,4 +60,14 @@ def test_struct_layouts():
     assert ctypes.sizeof(seg.seg_cell_features) == 64
     assert ctypes.sizeof(seg.seg_dims) == 12
     assert ctypes.sizeof(seg.seg_config) == 48
-    assert ctypes.sizeof(seg.seg_channel_params) == 8
+    assert ctypes.sizeof(seg.seg_channel_params) == 12
+
+
+def test_binding_constants_match_header():
+    # the ctypes mirrors of the header's array sizes and flags
+    hdr = open(os.path.join(ROOT, "include", "seg.h")).read()
+    defs = dict(re.findall(r"#define\s+(SEG_[A-Z_]+)\s+\(?(-?0x[0-9a-fA-F]+|-?[0-9]+)u?\)?", hdr))
+    import paper_1407_2089_gb300 as seg
+    for name in ("SEG_MAX_KERNELS", "SEG_FORCE_TILE", "SEG_PLAIN", "SEG_NO_GRAPH", "SEG_PROFILE"):
+        assert name in defs, name
+        assert getattr(seg, name) == int(defs[name], 0), name
