@@ -329,9 +329,11 @@ def run_gpu(args):
     total_kernel_ms = sum(k["ms"] for k in kern.values())
     shares = {n: round(k["ms"] / total_kernel_ms, 4) for n, k in kern.items()} if total_kernel_ms else {}
     seg.seg_destroy(ctx)
-    denoise = None
+    denoise = closing = None
     if args.denoise_radius:
         denoise = denoise_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.denoise_radius)
+    if args.closing_radius:
+        closing = closing_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.closing_radius)
     forms = None
     if not args.no_forms:
         forms = {"batched": value / ws, "plain": plain_form(seg, torch, d_in, (X, Y, Z), local,
@@ -411,6 +413,7 @@ def run_gpu(args):
             "e2e": e2e,
             "forms_gvox_s_per_gpu": forms,
             "denoise_front_end": denoise,
+            "closing": closing,
             "serving": serve,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
@@ -421,20 +424,19 @@ def run_gpu(args):
     return 0
 
 
-def denoise_run(seg, torch, d_in, dims, local, steps, radius):
-    """The same workload with the denoise front end of Eq. 1 on the
-    stem-cell channel (channel 0, box radius `radius`), batched as in the
-    main measurement.  Returns Gvoxels/s of the whole stage and the mean
-    per-step CUDA-event times of the front-end kernels."""
+def option_run(seg, torch, d_in, dims, local, steps, denoise, closing):
+    """The same workload, batched as in the main measurement, with per-channel
+    options (denoise radii, closing radii).  Returns Gvoxels/s of the whole
+    stage, ms per step and the mean per-step CUDA-event time of every kernel."""
     T, C = d_in.shape[0], d_in.shape[1]
     X, Y, Z = dims
     stream = torch.cuda.Stream()
     ctx = seg.seg_create(device=local, flags=seg.SEG_PROFILE, batch_window_us=2_000_000,
                          order_stream=stream.cuda_stream, max_inflight=1)
-    radii = [radius] + [0] * (C - 1)
 
     def one_pass():
-        reqs = [seg.seg_submit_volume(ctx, d_in[t], dims=(X, Y, Z), channels=C, denoise_radius=radii)
+        reqs = [seg.seg_submit_volume(ctx, d_in[t], dims=(X, Y, Z), channels=C, denoise_radius=denoise,
+                                      closing_radius=closing)
                 for t in range(T)]
         seg.seg_flush(ctx)
         for r in reqs:
@@ -466,16 +468,32 @@ def denoise_run(seg, torch, d_in, dims, local, steps, radius):
     ms = e0.elapsed_time(e1) / steps
     kern = seg.seg_get_stats(ctx)["kernels"]
     seg.seg_destroy(ctx)
-    per = {n: kern[n]["ms"] / steps for n in ("denoise_box", "denoise_median")}
+    per = {n: k["ms"] / steps for n, k in kern.items()}
+    return d_in.numel() / (ms / 1e3) / 1e9, ms, per
+
+
+def denoise_run(seg, torch, d_in, dims, local, steps, radius):
+    """The denoise front end of Eq. 1 on the stem-cell channel (channel 0)."""
+    T, C = d_in.shape[0], d_in.shape[1]
+    X, Y, Z = dims
+    gv, ms, per = option_run(seg, torch, d_in, dims, local, steps, [radius] + [0] * (C - 1), 0)
     vox_dn = T * X * Y * Z  # voxels through the front end per step (channel 0)
     front_ms = per["denoise_box"] + per["denoise_median"]
-    return {"radius": radius, "channels_denoised": 1, "gvox_s": d_in.numel() / (ms / 1e3) / 1e9,
+    return {"radius": radius, "channels_denoised": 1, "gvox_s": gv,
             "ms_per_step": ms, "front_end_ms_per_step": front_ms,
             "front_end_gvox_s": vox_dn / (front_ms / 1e3) / 1e9 if front_ms else None,
-            "kernel_ms_per_step": per,
+            "kernel_ms_per_step": {n: per[n] for n in ("denoise_box", "denoise_median")},
             # algorithmic bytes of the front end: read the observed image,
-            # write the denoised one (4 B/voxel); the 9 box passes move 36 B
+            # write the denoised one (4 B/voxel); the box passes move 12 B
             "front_end_hbm_frac": (vox_dn * 4.0 / (front_ms / 1e3) / 1e9) / peaks()[0] if front_ms else None}
+
+
+def closing_run(seg, torch, d_in, dims, local, steps, radius):
+    """The closing of the foreground with a ball of `radius` on every channel."""
+    gv, ms, per = option_run(seg, torch, d_in, dims, local, steps, 0, radius)
+    close_ms = per["dilate"] + per["erode"]
+    return {"radius": radius, "gvox_s": gv, "ms_per_step": ms, "closing_ms_per_step": close_ms,
+            "kernel_ms_per_step": {n: per[n] for n in ("dilate", "erode")}}
 
 
 def plain_form(seg, torch, d_in, dims, local, steps):
@@ -608,6 +626,8 @@ def main():
     ap.add_argument("--tile", default="", help="force the tile height and z-chunk, e.g. 32,64")
     ap.add_argument("--denoise-radius", type=int, default=8,
                     help="also time the stage with the denoise front end on channel 0 (0 skips)")
+    ap.add_argument("--closing-radius", type=int, default=1,
+                    help="also time the stage with the foreground closed by this ball (0 skips)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain per-frame comparison")

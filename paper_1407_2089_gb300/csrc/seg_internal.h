@@ -83,7 +83,7 @@ struct VolDev {
     // closing of the foreground (cl_r > 0)
     uint32_t *cl_ext;         // dilated mask on rows y in [-r, Y+r), z in [-r, Z+r), W + 2 words each
     uint32_t cl_r;            // ball radius, 0 = no closing
-    uint32_t cl_n;            // dilation items (extended rows x words)
+    uint32_t cl_n;            // dilation items (words of the extended mask)
     uint32_t cl_base;         // first flat dilation item
     uint32_t cl_pad;
 };

@@ -1780,15 +1780,28 @@ __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr 
 // extended mask -- the closing of the padded volume, cut to the volume.
 // ----------------------------------------------------------------------------
 
-// x-run half-width of the ball for a row offset, -1 outside the ball.
-__device__ __forceinline__ int ball_rx(int rho, int dy, int dz) {
-    const int q = rho * rho - dy * dy - dz * dz;
-    if (q < 0) return -1;
-    int r = (int)sqrtf((float)q);
-    while (r * r > q) --r;
-    while ((r + 1) * (r + 1) <= q) ++r;
-    return r;
-}
+// x-run half-widths of the balls, per radius and row offset (-1 outside the
+// ball), filled once per block: rx^2 <= rho^2 - dy^2 - dz^2 < (rx + 1)^2.
+constexpr int CL_SPAN = 2 * CL_MAX_R + 1;
+
+struct BallTable {
+    int8_t rx[CL_MAX_R + 1][CL_SPAN][CL_SPAN];
+    __device__ __forceinline__ void fill() {
+        for (int i = threadIdx.x; i < (CL_MAX_R + 1) * CL_SPAN * CL_SPAN; i += blockDim.x) {
+            const int rho = i / (CL_SPAN * CL_SPAN), dy = (i / CL_SPAN) % CL_SPAN - CL_MAX_R;
+            const int dz = i % CL_SPAN - CL_MAX_R;
+            const int q = rho * rho - dy * dy - dz * dz;
+            int r = -1;
+            if (q >= 0)
+                while ((r + 1) * (r + 1) <= q) ++r;
+            (&rx[0][0][0])[i] = (int8_t)r;
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ int get(int rho, int dy, int dz) const {
+        return rx[rho][dy + CL_MAX_R][dz + CL_MAX_R];
+    }
+};
 
 // OR (DIL) or AND of the 2 rx + 1 x-shifts of a bit word w1 with its
 // neighbours w0 (lower x) and w2 (higher x).
@@ -1806,7 +1819,9 @@ __device__ __forceinline__ uint32_t smear(uint32_t w0, uint32_t w1, uint32_t w2,
 // One thread per word of the extended mask of every closing volume.
 __global__ void __launch_bounds__(256) k_dilate(const BatchHdr *__restrict__ h) {
     __shared__ VolIndex<&VolDev::cl_base> VI;
+    __shared__ BallTable BT;
     VI.load(h);
+    BT.fill();
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < h->cl_items; it += stride) {
         const VolDev &V = h->vol[VI.find(h, it)];
@@ -1816,19 +1831,20 @@ __global__ void __launch_bounds__(256) k_dilate(const BatchHdr *__restrict__ h) 
         const int we = (int)(li % (uint32_t)WE), er = (int)(li / (uint32_t)WE);
         const int y = er % YE - rho, z = er / YE - rho;
         const int w = we - 1;  // word of the row, -1 and W are the padding words
-        auto word = [&](int yy, int zz, int ww) -> uint32_t {
-            if (yy < 0 || yy >= Y || zz < 0 || zz >= Z || ww < 0 || ww >= W) return 0u;
-            return V.mask[((size_t)zz * Y + yy) * W + ww];
-        };
         uint32_t acc = 0;
-        for (int dz = -rho; dz <= rho; ++dz)
+        for (int dz = -rho; dz <= rho; ++dz) {
+            const int zz = z + dz;
+            if (zz < 0 || zz >= Z) continue;
             for (int dy = -rho; dy <= rho; ++dy) {
-                const int rx = ball_rx(rho, dy, dz);
-                if (rx < 0) continue;
-                const int yy = y + dy, zz = z + dz;
-                if (yy < 0 || yy >= Y || zz < 0 || zz >= Z) continue;
-                acc |= smear<true>(word(yy, zz, w - 1), word(yy, zz, w), word(yy, zz, w + 1), rx);
+                const int rx = BT.get(rho, dy, dz), yy = y + dy;
+                if (rx < 0 || yy < 0 || yy >= Y) continue;
+                const uint32_t *row = V.mask + ((size_t)zz * Y + yy) * W;
+                const uint32_t a0 = (w >= 1 && w - 1 < W) ? row[w - 1] : 0u;
+                const uint32_t a1 = (w >= 0 && w < W) ? row[w] : 0u;
+                const uint32_t a2 = (w + 1 >= 0 && w + 1 < W) ? row[w + 1] : 0u;
+                acc |= smear<true>(a0, a1, a2, rx);
             }
+        }
         V.cl_ext[(size_t)er * WE + we] = acc;
     }
 }
@@ -1838,8 +1854,10 @@ __global__ void __launch_bounds__(256) k_dilate(const BatchHdr *__restrict__ h) 
 // mask and the run counts of k_threshold_runs).
 __global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__ h) {
     __shared__ VolIndex<&VolDev::rt_base> VI;
+    __shared__ BallTable BT;
     __shared__ uint32_t wsum[ROW_TILE / 32];
     VI.load(h);
+    BT.fill();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, rt)];
@@ -1848,18 +1866,26 @@ __global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__
         const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
         const int rho = (int)V.cl_r, W = (int)V.W, WE = W + 2, Y = (int)V.Y;
         const int YE = Y + 2 * rho;
+        // rows of at most 16 words share a warp: segments of seg lanes
+        // (a power of two >= W), one row per segment
+        int seg = 32;
+        while (seg / 2 >= W && seg > 1) seg /= 2;
+        const int per = 32 / seg, sub = lane / seg, sl = lane % seg;
         uint32_t wtot = 0;
-        for (uint32_t rr = warp; rr < nrows; rr += ROW_TILE / 32) {
-            const uint32_t row = row0 + rr;
+        for (uint32_t rb = (uint32_t)warp * per; rb < nrows; rb += (ROW_TILE / 32) * per) {
+            const uint32_t rr = rb + (uint32_t)sub;
+            const bool live = rr < nrows;
+            const uint32_t row = row0 + (live ? rr : 0u);
             const int y = (int)(row % (uint32_t)Y), z = (int)(row / (uint32_t)Y);
             uint32_t carry = 0, cnt = 0;
-            for (int w0 = 0; w0 < W; w0 += 32) {
-                const int w = w0 + lane;
-                uint32_t acc = 0xFFFFFFFFu;
-                if (w < W) {
+            for (int w0 = 0; w0 < W; w0 += seg) {
+                const int w = w0 + sl;
+                uint32_t acc = 0u;
+                if (live && w < W) {
+                    acc = 0xFFFFFFFFu;
                     for (int dz = -rho; dz <= rho; ++dz)
                         for (int dy = -rho; dy <= rho; ++dy) {
-                            const int rx = ball_rx(rho, dy, dz);
+                            const int rx = BT.get(rho, dy, dz);
                             if (rx < 0) continue;
                             const uint32_t *e = V.cl_ext + ((size_t)(z + dz + rho) * YE + (y + dy + rho)) * WE + (w + 1);
                             acc &= smear<false>(e[-1], e[0], e[1], rx);
@@ -1867,19 +1893,19 @@ __global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__
                     const uint32_t x0 = 32u * (uint32_t)w;
                     if (x0 + 32u > V.X) acc &= (1u << (V.X - x0)) - 1u;  // no bits past the row
                     V.mask[(size_t)row * W + w] = acc;
-                } else {
-                    acc = 0u;
                 }
-                const uint32_t prev = __shfl_up_sync(FULL, acc, 1);
-                const uint32_t left = lane == 0 ? carry : (prev >> 31);
-                if (w < W) cnt += __popc(acc & ~((acc << 1) | left));
-                carry = __shfl_sync(FULL, acc, 31) >> 31;
+                const uint32_t prev = __shfl_up_sync(FULL, acc, 1, seg);
+                const uint32_t left = sl == 0 ? carry : (prev >> 31);
+                if (live && w < W) cnt += __popc(acc & ~((acc << 1) | left));
+                carry = __shfl_sync(FULL, acc, seg - 1, seg) >> 31;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
-            if (lane == 0) V.rowoff[row] = cnt;
-            wtot += cnt;
+            for (int o = seg / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+            if (live && sl == 0) {
+                V.rowoff[row] = cnt;
+                wtot += cnt;
+            }
         }
+        for (int o = 16; o > 0; o >>= 1) wtot += __shfl_xor_sync(FULL, wtot, o);
         if (lane == 0) wsum[warp] = wtot;
         __syncthreads();
         if (threadIdx.x == 0) {
