@@ -70,6 +70,9 @@ def _load():
         lib.oracle_median27.restype = ctypes.c_int
         lib.oracle_close.argtypes = [u8p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u8p]
         lib.oracle_close.restype = ctypes.c_int
+        lib.oracle_distance.argtypes = [u8p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_uint32, u32p]
+        lib.oracle_distance.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -144,14 +147,15 @@ def filter_features(prov: np.ndarray, ncomp: int, min_volume: int):
 
 
 class OracleResult:
-    __slots__ = ("labels", "cells", "threshold", "hist", "smoothed")
+    __slots__ = ("labels", "cells", "threshold", "hist", "smoothed", "distance")
 
-    def __init__(self, labels, cells, threshold, hist, smoothed):
+    def __init__(self, labels, cells, threshold, hist, smoothed, distance=None):
         self.labels = labels
         self.cells = cells
         self.threshold = threshold
         self.hist = hist
         self.smoothed = smoothed
+        self.distance = distance
 
     @property
     def n_cells(self):
@@ -199,11 +203,36 @@ def close(mask: np.ndarray, rho: int) -> np.ndarray:
     return out.astype(bool)
 
 
+def distance(mask: np.ndarray, weights=(16, 16, 25)) -> np.ndarray:
+    """Weighted squared distance (wx dx^2 + wy dy^2 + wz dz^2) of every voxel
+    of a boolean [Z,Y,X] mask to its nearest foreground voxel (brute force;
+    0xFFFFFFFF when there is no foreground)."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    X, Y, Z = _dims(m)
+    out = np.empty(m.shape, dtype=np.uint32)
+    rc = _load().oracle_distance(_ptr(m, ctypes.c_uint8), X, Y, Z, int(weights[0]), int(weights[1]),
+                                 int(weights[2]), _ptr(out, ctypes.c_uint32))
+    if rc:
+        raise RuntimeError("oracle_distance failed: %d" % rc)
+    return out
+
+
 def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
-            keep_smoothed: bool = False, denoise_radius: int = 0, closing_radius: int = 0) -> OracleResult:
+            keep_smoothed: bool = False, denoise_radius: int = 0, closing_radius: int = 0,
+            distance_weights=None) -> OracleResult:
     """The whole stage for one frame and channel (uint16 [Z,Y,X]); with
     denoise_radius > 0 the denoise front end runs first, with closing_radius
-    > 0 the foreground is closed with that ball before labelling."""
+    > 0 the foreground is closed with that ball before labelling, and with
+    distance_weights the distance map of the (closed) foreground is added."""
+    if distance_weights is not None:
+        r = segment(vol, min_volume, keep_hist, True, denoise_radius, closing_radius)
+        fg = r.smoothed > r.threshold
+        if closing_radius:
+            fg = close(fg, closing_radius)
+        r.distance = distance(fg, distance_weights)
+        if not keep_smoothed:
+            r.smoothed = None
+        return r
     vol = np.ascontiguousarray(vol, dtype=np.uint16)
     if denoise_radius:
         vol = denoise(vol, denoise_radius)

@@ -398,6 +398,49 @@ int oracle_close(const uint8_t *m, uint32_t X, uint32_t Y, uint32_t Z, uint32_t 
     return ORACLE_OK;
 }
 
+/* ------------------------------------------------------------------------
+ * Distance map of the foreground (Segmentation: the vasculature channel's
+ * distance map gives every voxel its distance to the nearest foreground
+ * voxel).  Squared Euclidean distance with integer axis weights (wx, wy,
+ * wz): d2(p) = min over foreground q of wx dx^2 + wy dy^2 + wz dz^2; with
+ * weights 16, 16, 25 this is 25 times the squared distance in um at the
+ * 0.8 x 0.8 x 1.0 um spacing.  No foreground at all: 0xFFFFFFFF everywhere.
+ * Plain definition: the minimum over every foreground voxel.
+ * ------------------------------------------------------------------------ */
+int oracle_distance(const uint8_t *m, uint32_t X, uint32_t Y, uint32_t Z, uint32_t wx, uint32_t wy,
+                    uint32_t wz, uint32_t *d2) {
+    if (!m || !d2 || X == 0 || Y == 0 || Z == 0) return ORACLE_EINVAL;
+    const uint64_t n = (uint64_t)X * Y * Z;
+    uint64_t nf = 0;
+    for (uint64_t i = 0; i < n; ++i) nf += m[i] ? 1 : 0;
+    uint32_t *fx = (uint32_t *)malloc((nf ? nf : 1) * 3 * sizeof(uint32_t));
+    if (!fx) return ORACLE_ENOMEM;
+    uint64_t k = 0;
+    for (uint64_t z = 0; z < Z; ++z)
+        for (uint64_t y = 0; y < Y; ++y)
+            for (uint64_t x = 0; x < X; ++x)
+                if (m[x + X * (y + Y * z)]) {
+                    fx[3 * k] = (uint32_t)x;
+                    fx[3 * k + 1] = (uint32_t)y;
+                    fx[3 * k + 2] = (uint32_t)z;
+                    ++k;
+                }
+    for (uint64_t z = 0; z < Z; ++z)
+        for (uint64_t y = 0; y < Y; ++y)
+            for (uint64_t x = 0; x < X; ++x) {
+                uint64_t best = UINT64_MAX;
+                for (uint64_t j = 0; j < nf; ++j) {
+                    const int64_t dx = (int64_t)x - fx[3 * j], dy = (int64_t)y - fx[3 * j + 1];
+                    const int64_t dz = (int64_t)z - fx[3 * j + 2];
+                    const uint64_t v = (uint64_t)(wx * dx * dx + wy * dy * dy + wz * dz * dz);
+                    if (v < best) best = v;
+                }
+                d2[x + X * (y + Y * z)] = nf ? (uint32_t)best : 0xFFFFFFFFu;
+            }
+    free(fx);
+    return ORACLE_OK;
+}
+
 /* The whole stage for one frame and channel: smooth, histogram, Otsu,
  * threshold (foreground iff s > t*), label, filter, features.
  * hist (65536 entries) and smoothed (n entries) are optional outputs. */

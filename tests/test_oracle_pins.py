@@ -547,3 +547,30 @@ def test_segment_with_closing_labels_the_closed_mask():
     closed = oracle.close(r.smoothed > r.threshold, 2)
     lab, n = ndi.label(closed, structure=np.ones((3, 3, 3)))
     assert n == r.labels.max() and np.array_equal(r.labels > 0, closed)
+
+
+# ---------------------------------------------------------------------------
+# Distance map of the foreground (vasculature channel): brute-force minimum,
+# pinned to scipy's exact Euclidean distance transform with the voxel spacing
+# ---------------------------------------------------------------------------
+
+def test_distance_matches_scipy_edt():
+    ndi = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(70)
+    for shape, p in [((6, 9, 11), 0.05), ((1, 7, 20), 0.1), ((9, 9, 9), 0.01), ((4, 13, 5), 0.3)]:
+        m = rng.uniform(size=shape) < p
+        m.flat[rng.integers(m.size)] = True
+        d2 = oracle.distance(m, (16, 16, 25))
+        # scipy: distance to the nearest zero, sampling per axis (z, y, x) in um
+        e = ndi.distance_transform_edt(~m, sampling=(1.0, 0.8, 0.8))
+        assert np.array_equal(d2, np.rint(25.0 * e * e).astype(np.uint32)), shape
+
+
+def test_distance_special_cases():
+    m = np.zeros((3, 4, 5), dtype=bool)
+    assert np.all(oracle.distance(m) == 0xFFFFFFFF)         # no foreground
+    m[1, 2, 3] = True
+    d2 = oracle.distance(m, (1, 2, 3))
+    z, y, x = np.meshgrid(np.arange(3), np.arange(4), np.arange(5), indexing="ij")
+    assert np.array_equal(d2, (x - 3) ** 2 + 2 * (y - 2) ** 2 + 3 * (z - 1) ** 2)
+    assert np.all(oracle.distance(np.ones((2, 2, 2), dtype=bool)) == 0)
