@@ -329,11 +329,14 @@ def run_gpu(args):
     total_kernel_ms = sum(k["ms"] for k in kern.values())
     shares = {n: round(k["ms"] / total_kernel_ms, 4) for n, k in kern.items()} if total_kernel_ms else {}
     seg.seg_destroy(ctx)
-    denoise = closing = None
+    denoise = closing = distmap = None
     if args.denoise_radius:
         denoise = denoise_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.denoise_radius)
     if args.closing_radius:
         closing = closing_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.closing_radius)
+    if args.distance_weights != "0":
+        distmap = distance_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)),
+                               [int(a) for a in args.distance_weights.split(",")])
     forms = None
     if not args.no_forms:
         forms = {"batched": value / ws, "plain": plain_form(seg, torch, d_in, (X, Y, Z), local,
@@ -414,6 +417,7 @@ def run_gpu(args):
             "forms_gvox_s_per_gpu": forms,
             "denoise_front_end": denoise,
             "closing": closing,
+            "distance_map": distmap,
             "serving": serve,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
@@ -424,10 +428,11 @@ def run_gpu(args):
     return 0
 
 
-def option_run(seg, torch, d_in, dims, local, steps, denoise, closing):
+def option_run(seg, torch, d_in, dims, local, steps, denoise, closing, distance_weights=None):
     """The same workload, batched as in the main measurement, with per-channel
-    options (denoise radii, closing radii).  Returns Gvoxels/s of the whole
-    stage, ms per step and the mean per-step CUDA-event time of every kernel."""
+    options (denoise radii, closing radii, distance-map weights).  Returns
+    Gvoxels/s of the whole stage, ms per step and the mean per-step
+    CUDA-event time of every kernel."""
     T, C = d_in.shape[0], d_in.shape[1]
     X, Y, Z = dims
     stream = torch.cuda.Stream()
@@ -436,7 +441,7 @@ def option_run(seg, torch, d_in, dims, local, steps, denoise, closing):
 
     def one_pass():
         reqs = [seg.seg_submit_volume(ctx, d_in[t], dims=(X, Y, Z), channels=C, denoise_radius=denoise,
-                                      closing_radius=closing)
+                                      closing_radius=closing, distance_weights=distance_weights)
                 for t in range(T)]
         seg.seg_flush(ctx)
         for r in reqs:
@@ -494,6 +499,30 @@ def closing_run(seg, torch, d_in, dims, local, steps, radius):
     close_ms = per["dilate"] + per["erode"]
     return {"radius": radius, "gvox_s": gv, "ms_per_step": ms, "closing_ms_per_step": close_ms,
             "kernel_ms_per_step": {n: per[n] for n in ("dilate", "erode")}}
+
+
+def distance_run(seg, torch, d_in, dims, local, steps, weights):
+    """The distance map of the vessel channel (the last one) with the given
+    weights; every channel otherwise as in the main measurement."""
+    T, C = d_in.shape[0], d_in.shape[1]
+    X, Y, Z = dims
+    gv, ms, per = option_run(seg, torch, d_in, dims, local, steps, 0, 0,
+                             [None] * (C - 1) + [tuple(weights)])
+    vox = T * X * Y * Z  # voxels with a distance map per step
+    names = ("dist_x", "dist_z", "dist_y")
+    dist_ms = sum(per[n] for n in names)
+    # algorithmic bytes per voxel: the x pass reads the mask bit and writes a
+    # uint32; each line pass reads and writes one uint32 (its stack traffic
+    # is not counted); mask to map at least 4.125 B
+    algo = {"dist_x": 4.125, "dist_z": 8.0, "dist_y": 8.0}
+    peak = peaks()[0]
+    return {"weights": list(weights), "channels": 1, "gvox_s": gv, "ms_per_step": ms,
+            "distance_ms_per_step": dist_ms,
+            "distance_gvox_s": vox / (dist_ms / 1e3) / 1e9 if dist_ms else None,
+            "kernel_ms_per_step": {n: per[n] for n in names},
+            "kernel_hbm_frac": {n: (vox * algo[n] / (per[n] / 1e3) / 1e9) / peak if per[n] else None
+                                for n in names},
+            "stage_hbm_frac": (vox * 4.125 / (dist_ms / 1e3) / 1e9) / peak if dist_ms else None}
 
 
 def plain_form(seg, torch, d_in, dims, local, steps):
@@ -628,6 +657,9 @@ def main():
                     help="also time the stage with the denoise front end on channel 0 (0 skips)")
     ap.add_argument("--closing-radius", type=int, default=1,
                     help="also time the stage with the foreground closed by this ball (0 skips)")
+    ap.add_argument("--distance-weights", default="16,16,25",
+                    help="also time the vessel-channel distance map with these weights of dx^2, dy^2, "
+                         "dz^2 (0.8 x 0.8 x 1.0 um in 0.2 um units; 0 skips)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain per-frame comparison")

@@ -17,6 +17,10 @@
  *     above it), 26-connectivity, survivors numbered 1..K by their lowest
  *     linear voxel index.  The default limit, 30 voxels, is 19 um^3 at the
  *     0.8 x 0.8 x 1.0 um spacing of the Methods section.
+ *     Optional steps of the same section: closing of the foreground with a
+ *     binary ball before labelling, and (vessel channel) a distance map from
+ *     every voxel to the nearest foreground voxel, here the exact weighted
+ *     squared Euclidean distance.
  *   - Tracking, Eq. 6 uses each cell's voxel count; the per-cell record
  *     (count, inclusive bounding box, int64 coordinate sums) is what the
  *     later stages consume.
@@ -114,6 +118,16 @@ typedef struct {
      * dilation then erosion on the volume padded with background, so the
      * closed foreground contains the original (Segmentation section). */
     uint32_t closing_radius;
+    /* {0, 0, 0}: off.  Otherwise every voxel gets the weighted squared
+     * distance wx*dx^2 + wy*dy^2 + wz*dz^2 (uint32, exact) to the nearest
+     * voxel of the channel's final (closed) foreground, 0 on the foreground,
+     * 0xFFFFFFFF everywhere when the foreground is empty: the vessel-channel
+     * distance map of the Segmentation section, read back with
+     * seg_read_distance.  Weights are the squared voxel spacing in any common
+     * unit (16, 16, 25 is 0.8 x 0.8 x 1.0 um in units of 0.2 um); each must be
+     * >= 1 and wx(X-1)^2 + wy(Y-1)^2 + wz(Z-1)^2 < 0xFFFFFFFF, else
+     * seg_submit_volume returns SEG_EINVAL. */
+    uint32_t distance_weights[3];
 } seg_channel_params;
 
 /* Creates a context on cfg->device.  Allocates streams and descriptor buffers;
@@ -157,6 +171,13 @@ int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream);
  * SEG_EINVAL, SEG_ENOENT, SEG_ECUDA. */
 int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
                     uint64_t dst_elems, int dst_on_device);
+
+/* Copies channel `channel`'s distance map (X*Y*Z uint32, layout of the
+ * labels) to dst (host, or device when dst_on_device = 1).  Blocks until the
+ * copy is complete.  Errors: SEG_EINVAL also when the channel was submitted
+ * without distance weights; otherwise as seg_read_labels. */
+int seg_read_distance(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
+                      uint64_t dst_elems, int dst_on_device);
 
 /* Copies channel `channel`'s cells (label order) to host memory dst (cap
  * entries) and reports n_cells and the Otsu level t* (foreground = s > t*).

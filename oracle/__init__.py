@@ -217,6 +217,22 @@ def distance(mask: np.ndarray, weights=(16, 16, 25)) -> np.ndarray:
     return out
 
 
+def distance_at(mask: np.ndarray, points, weights=(16, 16, 25)) -> np.ndarray:
+    """The same weighted squared distance, evaluated only at the given
+    (z, y, x) points: for each, the minimum over all foreground voxels
+    (brute force; 0xFFFFFFFF when there is no foreground)."""
+    fz, fy, fx = (a.astype(np.int64) for a in np.nonzero(mask))
+    wx, wy, wz = (int(w) for w in weights)
+    out = np.empty(len(points), dtype=np.uint32)
+    for i, (z, y, x) in enumerate(points):
+        if len(fx) == 0:
+            out[i] = 0xFFFFFFFF
+            continue
+        d = wx * (fx - int(x)) ** 2 + wy * (fy - int(y)) ** 2 + wz * (fz - int(z)) ** 2
+        out[i] = int(d.min())
+    return out
+
+
 def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
             keep_smoothed: bool = False, denoise_radius: int = 0, closing_radius: int = 0,
             distance_weights=None) -> OracleResult:

@@ -66,7 +66,7 @@ class seg_config(ctypes.Structure):
 
 class seg_channel_params(ctypes.Structure):
     _fields_ = [("min_volume_voxels", ctypes.c_uint32), ("denoise_radius", ctypes.c_uint32),
-                ("closing_radius", ctypes.c_uint32)]
+                ("closing_radius", ctypes.c_uint32), ("distance_weights", ctypes.c_uint32 * 3)]
 
 
 class seg_stats(ctypes.Structure):
@@ -80,7 +80,7 @@ class seg_stats(ctypes.Structure):
 
 
 EXPORTS = ["seg_create", "seg_destroy", "seg_submit_volume", "seg_flush", "seg_poll",
-           "seg_enqueue_wait", "seg_read_labels", "seg_read_features", "seg_release",
+           "seg_enqueue_wait", "seg_read_labels", "seg_read_distance", "seg_read_features", "seg_release",
            "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror",
            "seg_otsu_threshold_noalloc"]
 
@@ -96,6 +96,7 @@ def _bind(lib):
         "seg_poll": [vp, u64, u32, P(i32)],
         "seg_enqueue_wait": [vp, u64, vp],
         "seg_read_labels": [vp, u64, u32, vp, u64, i32],
+        "seg_read_distance": [vp, u64, u32, vp, u64, i32],
         "seg_read_features": [vp, u64, u32, vp, u64, P(u64), P(ctypes.c_uint16)],
         "seg_release": [vp, u64],
         "seg_request_times": [vp, u64, P(ctypes.c_double), P(ctypes.c_double),
@@ -168,11 +169,14 @@ def _voxel_ptr(voxels):
     return voxels.data_ptr(), 1 if voxels.is_cuda else 0
 
 
-def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, denoise_radius=0, closing_radius=0):
+def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, denoise_radius=0, closing_radius=0,
+                      distance_weights=None):
     """Submits [C][Z][Y][X] (or [Z][Y][X]) uint16 voxels; returns the request id.
 
     min_volume, denoise_radius, closing_radius: one int for every channel or
-    a sequence of per-channel ints (0 = no denoise front end / no closing)."""
+    a sequence of per-channel ints (0 = no denoise front end / no closing).
+    distance_weights: None (no distance map), one (wx, wy, wz) for every
+    channel, or a per-channel sequence of triples or None."""
     shape = tuple(voxels.shape)
     if dims is None:
         if len(shape) == 3:
@@ -188,8 +192,16 @@ def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, deno
     mv = [min_volume] * channels if np.isscalar(min_volume) else list(min_volume)
     dr = [denoise_radius] * channels if np.isscalar(denoise_radius) else list(denoise_radius)
     cr = [closing_radius] * channels if np.isscalar(closing_radius) else list(closing_radius)
-    params = (seg_channel_params * channels)(*[seg_channel_params(int(m), int(d), int(c))
-                                               for m, d, c in zip(mv, dr, cr)])
+    if distance_weights is None or (len(distance_weights) == 3 and np.isscalar(distance_weights[0])):
+        dw = [distance_weights] * channels
+    else:
+        dw = list(distance_weights)
+    dw = [(0, 0, 0) if w is None else tuple(int(a) for a in w) for w in dw]
+    if len(mv) != channels or len(dr) != channels or len(cr) != channels or len(dw) != channels:
+        raise ValueError("per-channel parameter lists must have one entry per channel")
+    params = (seg_channel_params * channels)(
+        *[seg_channel_params(int(m), int(d), int(c), (ctypes.c_uint32 * 3)(*w))
+          for m, d, c, w in zip(mv, dr, cr, dw)])
     out = ctypes.c_uint64()
     _check(_lib.seg_submit_volume(ctx, ctypes.c_void_p(ptr), on_dev, seg_dims(*dims), channels,
                                   params, ctypes.byref(out)), "seg_submit_volume")
@@ -229,6 +241,18 @@ def seg_read_labels(ctx, req, channel, out):
     else:
         ptr, n, dev = out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
     _check(_lib.seg_read_labels(ctx, req, channel, ctypes.c_void_p(ptr), n, dev), "seg_read_labels")
+    return out
+
+
+def seg_read_distance(ctx, req, channel, out):
+    """Copies the channel's distance map into `out` (as seg_read_labels)."""
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.uint32 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be C-contiguous uint32")
+        ptr, n, dev = out.ctypes.data, out.size, 0
+    else:
+        ptr, n, dev = out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
+    _check(_lib.seg_read_distance(ctx, req, channel, ctypes.c_void_p(ptr), n, dev), "seg_read_distance")
     return out
 
 
@@ -283,12 +307,14 @@ def seg_otsu_threshold_noalloc(voxels_ptr, dims, result_ptr, stream_ptr=None):
            "seg_otsu_threshold_noalloc")
 
 
-def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000, denoise_radius=0, closing_radius=0):
+def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000, denoise_radius=0, closing_radius=0,
+            distance_weights=None):
     """Convenience: submit one volume, wait, read labels + cells of every channel, release.
 
-    Returns a list (one entry per channel) of (labels, cells, threshold)."""
+    Returns a list (one entry per channel) of (labels, cells, threshold), with
+    the distance map (or None) as a fourth entry when distance_weights is given."""
     req = seg_submit_volume(ctx, voxels, min_volume=min_volume, denoise_radius=denoise_radius,
-                            closing_radius=closing_radius)
+                            closing_radius=closing_radius, distance_weights=distance_weights)
     seg_flush(ctx)
     try:
         st = seg_wait(ctx, req, timeout_ms)
@@ -301,7 +327,17 @@ def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000, deno
             lab = np.empty(shape[-3:], dtype=np.uint32) if labels_out is None else labels_out[c]
             seg_read_labels(ctx, req, c, lab)
             cells, t = seg_read_features(ctx, req, c)
-            out.append((lab, cells, t))
+            if distance_weights is None:
+                out.append((lab, cells, t))
+                continue
+            wc = distance_weights
+            if not (len(wc) == 3 and np.isscalar(wc[0])):
+                wc = wc[c]
+            dist = None
+            if wc is not None and any(wc):
+                dist = np.empty(shape[-3:], dtype=np.uint32)
+                seg_read_distance(ctx, req, c, dist)
+            out.append((lab, cells, t, dist))
         return out
     finally:
         seg_release(ctx, req)

@@ -86,6 +86,15 @@ struct VolDev {
     uint32_t cl_n;            // dilation items (words of the extended mask)
     uint32_t cl_base;         // first flat dilation item
     uint32_t cl_pad;
+    // distance map of the final foreground (dt_w[0] > 0)
+    uint32_t *dt_out;         // [Z][Y][X] weighted squared distances (output)
+    uint32_t *dt_g;           // [Z][Y][X] x-pass distances, then the z pass's stack values
+    uint32_t *dt_h;           // [Z][Y][X] z-pass distances, then the y pass's stack values
+    uint16_t *dt_sp;          // [Z][Y][X] stack positions of a line pass
+    uint32_t dt_w[3];         // weights of dx^2, dy^2, dz^2; 0 = no distance map
+    uint32_t dt_rbase;        // first flat x-pass row (rows of the mask)
+    uint32_t dt_zbase;        // first flat z line (X * Y lines)
+    uint32_t dt_ybase;        // first flat y line (X * Z lines)
 };
 
 // Batch header, followed in memory by VolDev[nvol].
@@ -100,7 +109,10 @@ struct BatchHdr {
     uint32_t dn_items[3];// denoise box-pass items per axis over the batch
     uint32_t dn_tiles;   // denoise median tiles over the batch
     uint32_t cl_items;   // closing dilation items over the batch
-    uint32_t pad[2];
+    uint32_t dt_rows;    // distance-map x-pass rows over the batch
+    uint32_t dt_zlines;  // distance-map z lines over the batch
+    uint32_t dt_ylines;  // distance-map y lines over the batch
+    uint32_t pad[3];
     VolDev vol[1];       // nvol entries
 };
 
@@ -109,7 +121,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 17;
+constexpr int NUM_KERNELS = 20;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {
@@ -129,6 +141,8 @@ struct LaunchPlan {
     int grid_med;        // k_median27
     bool denoise;        // some volume of the batch runs the denoise front end
     bool closing;        // some volume of the batch closes its foreground
+    bool distance;       // some volume of the batch has a distance map
+    int grid_dist;       // k_dist_x, k_dist_line
 };
 
 // Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)

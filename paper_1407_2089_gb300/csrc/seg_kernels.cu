@@ -27,6 +27,7 @@
 //   rank            label of each kept root = 1 + its rank in raster order
 //   label_features  per-voxel labels (coalesced uint32 rows) and per-cell
 //                   count / bbox / coordinate sums
+#include <climits>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -41,9 +42,9 @@ namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
     "denoise_box", "denoise_median", "init",       "smooth_hist_otsu", "threshold_runs",
-    "dilate",      "erode",          "scan_runs",  "row_runs",         "union_local",
-    "union",       "flatten",        "keep_count", "scan_keep",        "rank",
-    "label_features", "gather_stat"};
+    "dilate",      "erode",          "dist_x",     "dist_z",           "dist_y",
+    "scan_runs",   "row_runs",       "union_local", "union",           "flatten",
+    "keep_count",  "scan_keep",      "rank",       "label_features",   "gather_stat"};
 
 namespace {
 
@@ -1917,6 +1918,178 @@ __global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// Distance map of the final foreground (Segmentation section: for every voxel
+// the distance to the nearest foreground voxel of the vessel channel).  The
+// weighted squared Euclidean distance min over foreground voxels p of
+// wx (x - px)^2 + wy (y - py)^2 + wz (z - pz)^2 is separable: a pass along x
+// gives, per row, the distance to the row's nearest foreground voxel; each
+// following pass along an axis a takes, per line, the lower envelope
+// out(q) = min_i f(i) + w_a (q - i)^2 of the previous pass's values f (the
+// lower envelope of parabolas of Felzenszwalb and Huttenlocher, "Distance
+// transforms of sampled functions").  Every comparison is made exactly in
+// 64-bit integers, so the map equals the brute-force minimum.
+
+constexpr uint32_t DT_INF = 0xFFFFFFFFu;  // no foreground reachable
+
+// One warp per mask row of every distance volume: g(x) = wx d^2 with d the
+// distance along the row to its nearest foreground voxel, DT_INF when the row
+// has none.  Lane l of a step writes x = 32 w + l, so each store is 128
+// contiguous bytes.
+__global__ void __launch_bounds__(256) k_dist_x(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::dt_rbase> VI;
+    VI.load(h);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = blockDim.x >> 5;
+    for (uint32_t it = blockIdx.x * nw + (threadIdx.x >> 5); it < h->dt_rows; it += gridDim.x * nw) {
+        const VolDev &V = h->vol[VI.find(h, it)];
+        if (V.dt_w[0] == 0u) continue;  // never taken: such volumes own no rows
+        const uint32_t row = it - V.dt_rbase;
+        const int W = (int)V.W, X = (int)V.X;
+        const uint32_t wx = V.dt_w[0];
+        const uint32_t *m = V.mask + (size_t)row * W;
+        uint32_t *g = V.dt_g + (size_t)row * X;
+        int left = -1;  // last foreground x before the current chunk of 32 words
+        for (int c0 = 0; c0 < W; c0 += 32) {
+            const int w = c0 + lane;
+            const uint32_t word = w < W ? m[w] : 0u;
+            // first foreground x after this chunk (INT_MAX: none)
+            int right = INT_MAX;
+            for (int c1 = c0 + 32; c1 < W; c1 += 32) {
+                const uint32_t wd = c1 + lane < W ? m[c1 + lane] : 0u;
+                const uint32_t b = __ballot_sync(FULL, wd != 0u);
+                if (b) {
+                    const int l = __ffs(b) - 1;
+                    right = 32 * (c1 + l) + __ffs(__shfl_sync(FULL, wd, l)) - 1;
+                    break;
+                }
+            }
+            // last foreground x at or before word w; first one at or after it
+            int pre = word ? 32 * w + 31 - __clz(word) : -1;
+            int suf = word ? 32 * w + __ffs(word) - 1 : INT_MAX;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int a = __shfl_up_sync(FULL, pre, o);
+                const int b = __shfl_down_sync(FULL, suf, o);
+                if (lane >= o) pre = max(pre, a);
+                if (lane + o < 32) suf = min(suf, b);
+            }
+            int lprev = __shfl_up_sync(FULL, pre, 1);
+            int rnext = __shfl_down_sync(FULL, suf, 1);
+            lprev = lane == 0 ? left : max(lprev, left);
+            rnext = lane == 31 ? right : min(rnext, right);
+            left = max(left, __shfl_sync(FULL, pre, 31));
+            const int nword = min(32, W - c0);
+            for (int j = 0; j < nword; ++j) {
+                const uint32_t wd = __shfl_sync(FULL, word, j);
+                const int lp = __shfl_sync(FULL, lprev, j), rn = __shfl_sync(FULL, rnext, j);
+                const int xb = 32 * (c0 + j), x = xb + lane;
+                if (x < X) {
+                    const uint32_t lo = wd & (0xFFFFFFFFu >> (31 - lane));  // bits <= lane
+                    const uint32_t hi = wd >> lane;                          // bits >= lane
+                    const int l = lo ? xb + 31 - __clz(lo) : lp;
+                    const int r = hi ? x + __ffs(hi) - 1 : rn;
+                    uint32_t d = 0xFFFFFFFFu;
+                    if (l >= 0) d = (uint32_t)(x - l);
+                    if (r != INT_MAX) d = min(d, (uint32_t)(r - x));
+                    g[x] = d == 0xFFFFFFFFu ? DT_INF : wx * d * d;
+                }
+            }
+        }
+    }
+}
+
+// Lower envelope of one line of L values f (stride apart), weight w:
+// out(q) = min_i f(i) + w (q - i)^2 over the i with f(i) != DT_INF, DT_INF
+// when there is none.  Parabola i is A(i) - 2 w q i + w q^2 with
+// A(i) = f(i) + w i^2; the forward sweep keeps the parabolas that are lowest
+// somewhere (a stack), dropping the top one p1 (below it p0) when the new
+// parabola q meets p1 no later than p1 meets p0:
+//   (A(q) - A(p1)) (p1 - p0) <= (A(p1) - A(p0)) (q - p1),
+// the crossing points compared by cross-multiplication.  Stack entry k is
+// written over element k of the line itself (f value) and of sp (position):
+// k <= q always, so no value still to be read is overwritten.  The second
+// sweep walks the stack while the next parabola is no higher at q.
+// Magnitudes: A < 2^33 and positions < 2^16, so the products stay below 2^49.
+__device__ __forceinline__ void dist_line(uint32_t *__restrict__ f, uint16_t *__restrict__ sp,
+                                          uint32_t *__restrict__ out, size_t stride, int L, uint32_t w) {
+    const int64_t W = w;
+    int k = -1;
+    int64_t p0 = 0, a0 = 0, p1 = 0, a1 = 0;  // stack entries k - 1 and k
+    for (int q = 0; q < L; ++q) {
+        const uint32_t fq = f[(size_t)q * stride];
+        if (fq == DT_INF) continue;
+        const int64_t aq = (int64_t)fq + W * q * q;
+        while (k >= 1 && (aq - a1) * (p1 - p0) <= (a1 - a0) * (q - p1)) {
+            --k;
+            p1 = p0;
+            a1 = a0;
+            if (k >= 1) {
+                p0 = sp[(size_t)(k - 1) * stride];
+                a0 = (int64_t)f[(size_t)(k - 1) * stride] + W * p0 * p0;
+            }
+        }
+        ++k;
+        sp[(size_t)k * stride] = (uint16_t)q;
+        if (k != q) f[(size_t)k * stride] = fq;
+        p0 = p1;
+        a0 = a1;
+        p1 = q;
+        a1 = aq;
+    }
+    if (k < 0) {
+        for (int q = 0; q < L; ++q) out[(size_t)q * stride] = DT_INF;
+        return;
+    }
+    const int top = k;
+    int j = 0;
+    int64_t pj = sp[0], fj = f[0], pn = 0, fn = 0;
+    if (top >= 1) {
+        pn = sp[stride];
+        fn = f[stride];
+    }
+    for (int q = 0; q < L; ++q) {
+        int64_t vj = fj + W * (q - pj) * (q - pj);
+        while (j < top) {
+            const int64_t vn = fn + W * (q - pn) * (q - pn);
+            if (vn > vj) break;
+            ++j;
+            pj = pn;
+            fj = fn;
+            vj = vn;
+            if (j < top) {
+                pn = sp[(size_t)(j + 1) * stride];
+                fn = f[(size_t)(j + 1) * stride];
+            }
+        }
+        out[(size_t)q * stride] = (uint32_t)vj;
+    }
+}
+
+// One thread per line along z (AXIS 2: g -> h) or y (AXIS 1: h -> the
+// distance map); consecutive threads take consecutive x, so every step of a
+// warp reads or writes 32 neighbouring words.
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_dist_line(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<AXIS == 2 ? &VolDev::dt_zbase : &VolDev::dt_ybase> VI;
+    VI.load(h);
+    const uint32_t items = AXIS == 2 ? h->dt_zlines : h->dt_ylines;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        const VolDev &V = h->vol[VI.find(h, it)];
+        if (V.dt_w[0] == 0u) continue;  // never taken: such volumes own no lines
+        const uint32_t li = it - (AXIS == 2 ? V.dt_zbase : V.dt_ybase);
+        const uint32_t x = li % V.X, u = li / V.X;  // u = y (z lines) or z (y lines)
+        const size_t plane = (size_t)V.X * V.Y;
+        if (AXIS == 2) {
+            const size_t o = (size_t)u * V.X + x;
+            dist_line(V.dt_g + o, V.dt_sp + o, V.dt_h + o, plane, (int)V.Z, V.dt_w[2]);
+        } else {
+            const size_t o = (size_t)u * plane + x;
+            dist_line(V.dt_h + o, V.dt_sp + o, V.dt_out + o, V.X, (int)V.Y, V.dt_w[1]);
+        }
+    }
+}
+
 template <int TY>
 cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s,
                                 cudaEvent_t *ev, int &k) {
@@ -1975,6 +2148,10 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
         plan.grid_box = plan.sms * (per_sm > 0 ? per_sm : 1);
     }
     if ((e = resident((const void *)k_median27, MED_TX * MED_TY, &plan.grid_med)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_dist_x, 256, &g1)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_dist_line<2>, 256, &g2)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_dist_line<1>, 256, &g3)) != cudaSuccess) return e;
+    plan.grid_dist = std::min(g1, std::min(g2, g3));
     return cudaSuccess;
 }
 
@@ -2028,6 +2205,14 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     if (p.closing) k_dilate<<<p.grid_task, 256, 0, s>>>(d);
     rec();
     if (p.closing) k_erode<<<p.grid_thr, ROW_TILE, 0, s>>>(d);
+    // distance map of the final foreground, for batches in which some volume
+    // asks for it
+    rec();
+    if (p.distance) k_dist_x<<<p.grid_dist, 256, 0, s>>>(d);
+    rec();
+    if (p.distance) k_dist_line<2><<<p.grid_dist, 256, 0, s>>>(d);
+    rec();
+    if (p.distance) k_dist_line<1><<<p.grid_dist, 256, 0, s>>>(d);
     rec();
     k_tile_scan<0><<<p.grid_vols, 1024, 0, s>>>(d);
     rec();

@@ -44,11 +44,12 @@ struct VolGeom {
     uint32_t dn_r;   // denoise box radius, 0 = off
     uint32_t cl_r;   // closing ball radius, 0 = off
     uint64_t cl_words;  // words of the extended (padded) mask of the closing
+    uint32_t dt_w[3];   // distance-map weights, {0, 0, 0} = off
     uint64_t n, r_cap, k_cap;
     size_t scratch;  // bytes of per-batch scratch for this volume-channel
 };
 
-VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r) {
+VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, const uint32_t *dt_w) {
     VolGeom g;
     g.X = d.x; g.Y = d.y; g.Z = d.z;
     g.W = (uint32_t)cdiv(d.x, 32);
@@ -68,6 +69,9 @@ VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r) {
     g.cl_r = cl_r;
     g.cl_words = cl_r ? (uint64_t)(d.y + 2 * cl_r) * (d.z + 2 * cl_r) * (g.W + 2) : 0;
     if (cl_r) g.scratch += al(4ull * g.cl_words);
+    for (int a = 0; a < 3; ++a) g.dt_w[a] = dt_w ? dt_w[a] : 0u;
+    // distance map: two uint32 line-pass buffers and the uint16 stack positions
+    if (g.dt_w[0]) g.scratch += 2 * al(4ull * g.n) + al(2ull * g.n);
     return g;
 }
 
@@ -82,6 +86,7 @@ struct Request {
     char *block = nullptr;               // labels | feat | stat | [input]
     size_t block_bytes = 0;
     size_t off_labels = 0, off_feat = 0, off_stat = 0, off_input = 0;
+    std::vector<size_t> off_dist;         // per channel; SIZE_MAX = no distance map
     size_t per_labels = 0, per_feat = 0;  // bytes per channel
     bool owns_input = false;
     bool admitted = false;
@@ -102,6 +107,9 @@ struct Request {
     uint32_t *labels(uint32_t c) const {
         return reinterpret_cast<uint32_t *>(block + off_labels + c * per_labels);
     }
+    uint32_t *dist(uint32_t c) const {
+        return off_dist[c] == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(block + off_dist[c]);
+    }
     seg_cell_features *feat(uint32_t c) const {
         return reinterpret_cast<seg_cell_features *>(block + off_feat + c * per_feat);
     }
@@ -116,7 +124,7 @@ struct Slot {
     BatchHdr *d_hdr = nullptr;
     uint32_t *h_stat = nullptr;  // pinned
     uint32_t *d_stat = nullptr;
-    cudaGraphExec_t graph[12] = {};  // tile_y 16/32/64 x denoise front end x closing
+    cudaGraphExec_t graph[24] = {};  // tile_y 16/32/64 x denoise x closing x distance map
     cudaEvent_t ev[NUM_KERNELS + 1] = {};
     Batch *busy = nullptr;
 };
@@ -210,6 +218,12 @@ void layout_request(Request &r) {
     off += r.per_feat * r.C;
     r.off_stat = off;
     off += al(4ull * ST_WORDS * r.C);
+    r.off_dist.assign(r.C, SIZE_MAX);
+    for (uint32_t c = 0; c < r.C; ++c)
+        if (r.g[c].dt_w[0]) {
+            r.off_dist[c] = off;
+            off += al(4ull * g.n);
+        }
     r.off_input = off;
     if (r.owns_input) off += al(2ull * g.n * r.C);
     r.block_bytes = off;
@@ -242,6 +256,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
     uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0, cl = 0;
+    uint32_t dtr = 0, dtz = 0, dty = 0;
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
         for (uint32_t c = 0; c < r->C; ++c) {
@@ -288,6 +303,21 @@ void build_header(seg_ctx *ctx, Batch &b) {
             }
             V.cl_base = cl;
             cl += V.cl_n;
+            V.dt_out = r->dist(c);
+            V.dt_g = V.dt_h = nullptr;
+            V.dt_sp = nullptr;
+            for (int a = 0; a < 3; ++a) V.dt_w[a] = g.dt_w[a];
+            V.dt_rbase = dtr;
+            V.dt_zbase = dtz;
+            V.dt_ybase = dty;
+            if (g.dt_w[0]) {
+                V.dt_g = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.n);
+                V.dt_h = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.n);
+                V.dt_sp = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
+                dtr += g.rows;
+                dtz += g.X * g.Y;
+                dty += g.X * g.Z;
+            }
             V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
             V.smooth = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
             V.mask = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows * g.W);
@@ -339,13 +369,16 @@ void build_header(seg_ctx *ctx, Batch &b) {
     h->dn_items[2] = dn[2];
     h->dn_tiles = dnt;
     h->cl_items = cl;
+    h->dt_rows = dtr;
+    h->dt_zlines = dtz;
+    h->dt_ylines = dty;
     h->tile_z = tz;
     h->tile_y = ty;
     b.nvol = v;
 }
 
-int graph_index(int ty, bool denoise, bool closing) {
-    return (ty == 16 ? 0 : (ty == 32 ? 1 : 2)) + (denoise ? 3 : 0) + (closing ? 6 : 0);
+int graph_index(int ty, bool denoise, bool closing, bool distance) {
+    return (ty == 16 ? 0 : (ty == 32 ? 1 : 2)) + (denoise ? 3 : 0) + (closing ? 6 : 0) + (distance ? 12 : 0);
 }
 
 // Enqueues descriptor upload, the pipeline and the status read-back.
@@ -423,8 +456,10 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
     build_header(ctx, b);
     ctx->plan.denoise = s.h_hdr->dn_tiles > 0;
     ctx->plan.closing = s.h_hdr->cl_items > 0;
+    ctx->plan.distance = s.h_hdr->dt_rows > 0;
     if (ctx->graphs) {
-        cudaGraphExec_t &ge = s.graph[graph_index(ctx->plan.tile_y, ctx->plan.denoise, ctx->plan.closing)];
+        cudaGraphExec_t &ge =
+            s.graph[graph_index(ctx->plan.tile_y, ctx->plan.denoise, ctx->plan.closing, ctx->plan.distance)];
         if (!ge) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
@@ -514,6 +549,7 @@ void worker_main(seg_ctx *ctx) {
                 b->slot = free_slot;
                 b->ctx = ctx;
                 uint32_t nv = 0;
+                uint64_t dt_lines = 0;
                 const uint32_t max_req = ctx->plain ? 1u : 0xFFFFFFFFu;
                 // FIFO, except that a request still waiting for memory does not
                 // hold back admitted ones queued behind it
@@ -526,6 +562,14 @@ void worker_main(seg_ctx *ctx) {
                         break;
                     }
                     if (nv + r->C > ctx->cap_vols) {
+                        rest.push_back(r);
+                        break;
+                    }
+                    // the distance map's flat line indices stay 32-bit
+                    uint64_t rl = 0;
+                    for (uint32_t c = 0; c < r->C; ++c)
+                        if (r->g[c].dt_w[0]) rl += (uint64_t)r->g[c].X * std::max(r->g[c].Y, r->g[c].Z);
+                    if (!b->reqs.empty() && dt_lines + rl > 0xFFFFFFFFull) {
                         rest.push_back(r);
                         break;
                     }
@@ -544,6 +588,7 @@ void worker_main(seg_ctx *ctx) {
                     r->launched = true;
                     r->t_launch = ctx->now();
                     nv += r->C;
+                    dt_lines += rl;
                     b->voxels += r->g[0].n * r->C;
                     b->reqs.push_back(r);
                 }
@@ -647,6 +692,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->plan.grid_vols = ctx->sms;
     ctx->plan.denoise = false;
     ctx->plan.closing = false;
+    ctx->plan.distance = false;
     CK(configure_kernels(cfg->device, ctx->plan));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
@@ -719,8 +765,26 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
         const uint32_t dr = per_channel ? per_channel[c].denoise_radius : 0u;
         const uint32_t cr = per_channel ? per_channel[c].closing_radius : 0u;
         if (dr > (uint32_t)DN_MAX_R || cr > (uint32_t)CL_MAX_R) return SEG_EINVAL;
+        const uint32_t *dw = per_channel ? per_channel[c].distance_weights : nullptr;
+        if (dw && (dw[0] | dw[1] | dw[2])) {
+            // every weight >= 1 and the largest distance below the 0xFFFFFFFF marker
+            if (!dw[0] || !dw[1] || !dw[2]) return SEG_EINVAL;
+            const unsigned __int128 dmax =
+                (unsigned __int128)dw[0] * (dims.x - 1ull) * (dims.x - 1ull) +
+                (unsigned __int128)dw[1] * (dims.y - 1ull) * (dims.y - 1ull) +
+                (unsigned __int128)dw[2] * (dims.z - 1ull) * (dims.z - 1ull);
+            if (dmax >= 0xFFFFFFFFull) return SEG_EINVAL;
+        } else {
+            dw = nullptr;
+        }
         r->minvol[c] = m ? m : 1u;  // a cell has at least one voxel
-        r->g.push_back(geom(dims, r->minvol[c], dr, cr));
+        r->g.push_back(geom(dims, r->minvol[c], dr, cr, dw));
+    }
+    {
+        uint64_t rl = 0;
+        for (uint32_t c = 0; c < channels; ++c)
+            if (r->g[c].dt_w[0]) rl += (uint64_t)dims.x * std::max(dims.y, dims.z);
+        if (rl > 0xFFFFFFFFull) return SEG_ETOOBIG;  // distance-map lines of one launch
     }
     r->thresh.assign(channels, 0);
     r->ncells.assign(channels, 0);
@@ -856,6 +920,28 @@ int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst, 
                                     ctx->read_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
     return cuda_fail(e, "seg_read_labels");
+}
+
+int seg_read_distance(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst, uint64_t dst_elems,
+                      int dst_on_device) {
+    if (!ctx || !dst) return SEG_EINVAL;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (r->state == SEG_PENDING) return SEG_ENOTREADY;
+        if (r->state == SEG_FAILED) return SEG_EFAILED;
+    }
+    if (channel >= r->C || !r->dist(channel)) return SEG_EINVAL;
+    const uint64_t n = r->g[channel].n;
+    if (dst_elems < n) return SEG_ESMALL;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpyAsync(dst, r->dist(channel), 4ull * n,
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    ctx->read_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
+    return cuda_fail(e, "seg_read_distance");
 }
 
 int seg_read_features(seg_ctx *ctx, seg_req req, uint32_t channel, seg_cell_features *dst, uint64_t cap,

@@ -574,3 +574,13 @@ def test_distance_special_cases():
     z, y, x = np.meshgrid(np.arange(3), np.arange(4), np.arange(5), indexing="ij")
     assert np.array_equal(d2, (x - 3) ** 2 + 2 * (y - 2) ** 2 + 3 * (z - 1) ** 2)
     assert np.all(oracle.distance(np.ones((2, 2, 2), dtype=bool)) == 0)
+
+
+def test_distance_at_agrees_with_the_full_map():
+    # the sampled form used at full size gives the full map's values
+    rng = np.random.default_rng(71)
+    for shape, p in [((5, 8, 13), 0.03), ((3, 3, 3), 0.0), ((7, 2, 9), 0.2)]:
+        m = rng.uniform(size=shape) < p
+        pts = [tuple(int(rng.integers(s)) for s in shape) for _ in range(25)]
+        d2 = oracle.distance(m, (7, 3, 11))
+        assert np.array_equal(oracle.distance_at(m, pts, (7, 3, 11)), np.array([d2[q] for q in pts], np.uint32))
