@@ -509,19 +509,21 @@ def distance_run(seg, torch, d_in, dims, local, steps, weights):
     gv, ms, per = option_run(seg, torch, d_in, dims, local, steps, 0, 0,
                              [None] * (C - 1) + [tuple(weights)])
     vox = T * X * Y * Z  # voxels with a distance map per step
-    names = ("dist_x", "dist_z", "dist_y")
+    names = ("dist_xy", "dist_xy_1024", "dist_x", "dist_y", "dist_z", "dist_z_long")
     dist_ms = sum(per[n] for n in names)
-    # algorithmic bytes per voxel: the x pass reads the mask bit and writes a
-    # uint32; each line pass reads and writes one uint32 (its stack traffic
-    # is not counted); mask to map at least 4.125 B
-    algo = {"dist_x": 4.125, "dist_z": 8.0, "dist_y": 8.0}
+    # algorithmic bytes per voxel: the x (or fused x+y) pass reads the mask bit
+    # and writes a uint32; each line pass reads and writes one uint32 (stack
+    # traffic is not counted); mask to map at least 4.125 B
+    algo = {"dist_xy": 4.125, "dist_xy_1024": 4.125, "dist_x": 4.125, "dist_y": 8.0, "dist_z": 8.0,
+            "dist_z_long": 8.0}
     peak = peaks()[0]
     return {"weights": list(weights), "channels": 1, "gvox_s": gv, "ms_per_step": ms,
             "distance_ms_per_step": dist_ms,
             "distance_gvox_s": vox / (dist_ms / 1e3) / 1e9 if dist_ms else None,
             "kernel_ms_per_step": {n: per[n] for n in names},
-            "kernel_hbm_frac": {n: (vox * algo[n] / (per[n] / 1e3) / 1e9) / peak if per[n] else None
-                                for n in names},
+            # kernels that took this workload (the others only launch and exit)
+            "kernel_hbm_frac": {n: (vox * algo[n] / (per[n] / 1e3) / 1e9) / peak
+                                for n in names if per[n] > 0.05 * dist_ms},
             "stage_hbm_frac": (vox * 4.125 / (dist_ms / 1e3) / 1e9) / peak if dist_ms else None}
 
 

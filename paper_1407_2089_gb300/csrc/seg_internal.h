@@ -88,14 +88,29 @@ struct VolDev {
     uint32_t cl_pad;
     // distance map of the final foreground (dt_w[0] > 0)
     uint32_t *dt_out;         // [Z][Y][X] weighted squared distances (output)
-    uint32_t *dt_g;           // [Z][Y][X] x-pass distances, then the z pass's stack values
-    uint32_t *dt_h;           // [Z][Y][X] z-pass distances, then the y pass's stack values
-    uint16_t *dt_sp;          // [Z][Y][X] stack positions of a line pass
+    uint32_t *dt_h;           // [Z][Y][X] distances of the x and y passes
+    uint32_t *dt_g;           // [Z][Y][X] x-pass distances (long-line path only)
+    uint16_t *dt_sp;          // [Z][Y][X] stack positions (long-line path only)
     uint32_t dt_w[3];         // weights of dx^2, dy^2, dz^2; 0 = no distance map
-    uint32_t dt_rbase;        // first flat x-pass row (rows of the mask)
-    uint32_t dt_zbase;        // first flat z line (X * Y lines)
-    uint32_t dt_ybase;        // first flat y line (X * Z lines)
+    uint32_t dt_base[6];      // first flat item of this volume in each DtKernel
+    uint32_t dt_zlt;          // lines of a k_dist_z tile (32, 64, 96 or 128)
+    uint32_t dt_pad;
 };
+
+// The distance-map kernels and their work items.  A volume takes the fused
+// x+y kernel when its lines along y fit one block (Y <= 1024, X < 65536), the
+// shared-memory z kernel when its lines along z do (Z <= 256); otherwise the
+// long-line kernels, which keep their stacks in global memory.
+enum DtKernel : int {
+    DT_XY16 = 0,  // k_dist_xy<16>: (mask word, z) tiles, Y <= 512
+    DT_XY32 = 1,  // k_dist_xy<32>: (mask word, z) tiles, 512 < Y <= 1024
+    DT_X = 2,     // k_dist_x: mask rows (long y lines)
+    DT_Y = 3,     // k_dist_line<1>: y lines (long y lines)
+    DT_Z = 4,     // k_dist_z: (mask word, y group) tiles, Z <= 256
+    DT_ZL = 5,    // k_dist_line<2>: z lines (Z > 256)
+    DT_NK = 6,
+};
+constexpr int DZ_ELEMS = 8192;   // k_dist_z shared stack entries per block
 
 // Batch header, followed in memory by VolDev[nvol].
 struct BatchHdr {
@@ -109,10 +124,7 @@ struct BatchHdr {
     uint32_t dn_items[3];// denoise box-pass items per axis over the batch
     uint32_t dn_tiles;   // denoise median tiles over the batch
     uint32_t cl_items;   // closing dilation items over the batch
-    uint32_t dt_rows;    // distance-map x-pass rows over the batch
-    uint32_t dt_zlines;  // distance-map z lines over the batch
-    uint32_t dt_ylines;  // distance-map y lines over the batch
-    uint32_t pad[3];
+    uint32_t dt_items[DT_NK]; // distance-map items per DtKernel over the batch
     VolDev vol[1];       // nvol entries
 };
 
@@ -121,7 +133,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 20;
+constexpr int NUM_KERNELS = 23;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {
@@ -143,6 +155,9 @@ struct LaunchPlan {
     bool closing;        // some volume of the batch closes its foreground
     bool distance;       // some volume of the batch has a distance map
     int grid_dist;       // k_dist_x, k_dist_line
+    int grid_dxy16;      // k_dist_xy<16>
+    int grid_dxy32;      // k_dist_xy<32>
+    int grid_dz;         // k_dist_z
 };
 
 // Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)

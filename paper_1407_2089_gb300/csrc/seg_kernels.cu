@@ -42,9 +42,10 @@ namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
     "denoise_box", "denoise_median", "init",       "smooth_hist_otsu", "threshold_runs",
-    "dilate",      "erode",          "dist_x",     "dist_z",           "dist_y",
-    "scan_runs",   "row_runs",       "union_local", "union",           "flatten",
-    "keep_count",  "scan_keep",      "rank",       "label_features",   "gather_stat"};
+    "dilate",      "erode",          "dist_xy",    "dist_xy_1024",     "dist_x",
+    "dist_y",      "dist_z",         "dist_z_long", "scan_runs",       "row_runs",
+    "union_local", "union",          "flatten",    "keep_count",       "scan_keep",
+    "rank",        "label_features", "gather_stat"};
 
 namespace {
 
@@ -1927,24 +1928,71 @@ __global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__
 // following pass along an axis a takes, per line, the lower envelope
 // out(q) = min_i f(i) + w_a (q - i)^2 of the previous pass's values f (the
 // lower envelope of parabolas of Felzenszwalb and Huttenlocher, "Distance
-// transforms of sampled functions").  Every comparison is made exactly in
-// 64-bit integers, so the map equals the brute-force minimum.
+// transforms of sampled functions").  Parabola i is A(i) - 2 w q i + w q^2
+// with A(i) = f(i) + w i^2, so the parabolas lowest somewhere are the
+// vertices of the lower convex hull of the points (i, A(i)).  Every
+// comparison is exact in integers, so the map equals the brute-force minimum.
+// Submission checks wx (X-1)^2 + wy (Y-1)^2 + wz (Z-1)^2 < 2^32 - 1, and f of
+// a pass is at most the sum of the earlier axes' terms, so A(i) and every
+// value f(i) + w (q - i)^2 at positions inside the volume fit in 32 bits.
+//
+// Paths: k_dist_xy (x and y passes fused, lines along y in shared memory)
+// then k_dist_z (z pass in shared memory); for lines too long for a block,
+// k_dist_x, k_dist_line<1> and k_dist_line<2> keep their stacks in global
+// memory.
 
 constexpr uint32_t DT_INF = 0xFFFFFFFFu;  // no foreground reachable
+constexpr uint16_t DX_NONE = 0xFFFFu;     // row without foreground (k_dist_xy)
 
-// One warp per mask row of every distance volume: g(x) = wx d^2 with d the
-// distance along the row to its nearest foreground voxel, DT_INF when the row
-// has none.  Lane l of a step writes x = 32 w + l, so each store is 128
-// contiguous bytes.
+// Flat work index of DtKernel K over the batch (as VolIndex).
+template <int K>
+struct DtIndex {
+    uint32_t base[SMEM_VOLS];
+    __device__ __forceinline__ void load(const BatchHdr *__restrict__ h) {
+        if (h->nvol <= SMEM_VOLS)
+            for (uint32_t i = threadIdx.x; i < h->nvol; i += blockDim.x) base[i] = h->vol[i].dt_base[K];
+        __syncthreads();
+    }
+    __device__ __forceinline__ uint32_t find(const BatchHdr *__restrict__ h, uint32_t t) const {
+        const uint32_t nv = h->nvol;
+        uint32_t lo = 0, hi = nv;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const uint32_t b = nv <= SMEM_VOLS ? base[mid] : h->vol[mid].dt_base[K];
+            if (b <= t) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+};
+
+// Point (pm, am) lies on or above the segment from (pa, aa) to (pc, ac),
+// pa < pm < pc: parabola pm is nowhere strictly below both others and leaves
+// the lower envelope.  In the form ac (pm - pa) + aa (pc - pm) <= am (pc - pa)
+// every product is of two unsigned 32-bit numbers (A < 2^32, positions
+// < 2^16), so each side stays below 2^49.
+__device__ __forceinline__ bool dt_covered(uint32_t pa, uint32_t aa, uint32_t pm, uint32_t am, uint32_t pc,
+                                           uint32_t ac) {
+    const uint64_t lhs = (uint64_t)ac * (pm - pa) + (uint64_t)aa * (pc - pm);
+    return lhs <= (uint64_t)am * (pc - pa);
+}
+
+__device__ __forceinline__ uint32_t dt_sq(int d) {
+    const uint32_t u = (uint32_t)abs(d);
+    return u * u;
+}
+
+// Long-line path, x pass.  One warp per mask row of every such volume:
+// g(x) = wx d^2 with d the distance along the row to its nearest foreground
+// voxel, DT_INF when the row has none.  Lane l of a step writes
+// x = 32 w + l, so each store is 128 contiguous bytes.
 __global__ void __launch_bounds__(256) k_dist_x(const BatchHdr *__restrict__ h) {
-    __shared__ VolIndex<&VolDev::dt_rbase> VI;
+    __shared__ DtIndex<DT_X> VI;
     VI.load(h);
     const int lane = threadIdx.x & 31;
     const uint32_t nw = blockDim.x >> 5;
-    for (uint32_t it = blockIdx.x * nw + (threadIdx.x >> 5); it < h->dt_rows; it += gridDim.x * nw) {
+    for (uint32_t it = blockIdx.x * nw + (threadIdx.x >> 5); it < h->dt_items[DT_X]; it += gridDim.x * nw) {
         const VolDev &V = h->vol[VI.find(h, it)];
-        if (V.dt_w[0] == 0u) continue;  // never taken: such volumes own no rows
-        const uint32_t row = it - V.dt_rbase;
+        const uint32_t row = it - V.dt_base[DT_X];
         const int W = (int)V.W, X = (int)V.X;
         const uint32_t wx = V.dt_w[0];
         const uint32_t *m = V.mask + (size_t)row * W;
@@ -1999,42 +2047,36 @@ __global__ void __launch_bounds__(256) k_dist_x(const BatchHdr *__restrict__ h) 
     }
 }
 
-// Lower envelope of one line of L values f (stride apart), weight w:
-// out(q) = min_i f(i) + w (q - i)^2 over the i with f(i) != DT_INF, DT_INF
-// when there is none.  Parabola i is A(i) - 2 w q i + w q^2 with
-// A(i) = f(i) + w i^2; the forward sweep keeps the parabolas that are lowest
-// somewhere (a stack), dropping the top one p1 (below it p0) when the new
-// parabola q meets p1 no later than p1 meets p0:
-//   (A(q) - A(p1)) (p1 - p0) <= (A(p1) - A(p0)) (q - p1),
-// the crossing points compared by cross-multiplication.  Stack entry k is
-// written over element k of the line itself (f value) and of sp (position):
-// k <= q always, so no value still to be read is overwritten.  The second
-// sweep walks the stack while the next parabola is no higher at q.
-// Magnitudes: A < 2^33 and positions < 2^16, so the products stay below 2^49.
+// Long-line path: lower envelope of one line of L values f (stride apart),
+// weight w: out(q) = min_i f(i) + w (q - i)^2 over the i with f(i) != DT_INF,
+// DT_INF when there is none.  The forward sweep keeps the hull vertices on a
+// stack, dropping the top one while dt_covered; stack entry k is written over
+// element k of the line itself (f value) and of sp (position): k <= q always,
+// so no value still to be read is overwritten.  The second sweep walks the
+// stack while the next parabola is no higher at q.
 __device__ __forceinline__ void dist_line(uint32_t *__restrict__ f, uint16_t *__restrict__ sp,
                                           uint32_t *__restrict__ out, size_t stride, int L, uint32_t w) {
-    const int64_t W = w;
     int k = -1;
-    int64_t p0 = 0, a0 = 0, p1 = 0, a1 = 0;  // stack entries k - 1 and k
+    uint32_t p0 = 0, a0 = 0, p1 = 0, a1 = 0;  // stack entries k - 1 and k
     for (int q = 0; q < L; ++q) {
         const uint32_t fq = f[(size_t)q * stride];
         if (fq == DT_INF) continue;
-        const int64_t aq = (int64_t)fq + W * q * q;
-        while (k >= 1 && (aq - a1) * (p1 - p0) <= (a1 - a0) * (q - p1)) {
+        const uint32_t aq = fq + w * dt_sq(q);
+        while (k >= 1 && dt_covered(p0, a0, p1, a1, (uint32_t)q, aq)) {
             --k;
             p1 = p0;
             a1 = a0;
             if (k >= 1) {
                 p0 = sp[(size_t)(k - 1) * stride];
-                a0 = (int64_t)f[(size_t)(k - 1) * stride] + W * p0 * p0;
+                a0 = f[(size_t)(k - 1) * stride] + w * p0 * p0;
             }
         }
         ++k;
         sp[(size_t)k * stride] = (uint16_t)q;
-        if (k != q) f[(size_t)k * stride] = fq;
+        f[(size_t)k * stride] = fq;
         p0 = p1;
         a0 = a1;
-        p1 = q;
+        p1 = (uint32_t)q;
         a1 = aq;
     }
     if (k < 0) {
@@ -2043,15 +2085,15 @@ __device__ __forceinline__ void dist_line(uint32_t *__restrict__ f, uint16_t *__
     }
     const int top = k;
     int j = 0;
-    int64_t pj = sp[0], fj = f[0], pn = 0, fn = 0;
+    uint32_t pj = sp[0], fj = f[0], pn = 0u, fn = 0u;
     if (top >= 1) {
         pn = sp[stride];
         fn = f[stride];
     }
     for (int q = 0; q < L; ++q) {
-        int64_t vj = fj + W * (q - pj) * (q - pj);
+        uint32_t vj = fj + w * dt_sq(q - (int)pj);
         while (j < top) {
-            const int64_t vn = fn + W * (q - pn) * (q - pn);
+            const uint32_t vn = fn + w * dt_sq(q - (int)pn);
             if (vn > vj) break;
             ++j;
             pj = pn;
@@ -2062,30 +2104,375 @@ __device__ __forceinline__ void dist_line(uint32_t *__restrict__ f, uint16_t *__
                 fn = f[(size_t)(j + 1) * stride];
             }
         }
-        out[(size_t)q * stride] = (uint32_t)vj;
+        out[(size_t)q * stride] = vj;
     }
 }
 
-// One thread per line along z (AXIS 2: g -> h) or y (AXIS 1: h -> the
-// distance map); consecutive threads take consecutive x, so every step of a
-// warp reads or writes 32 neighbouring words.
+// Long-line path: one thread per line along y (AXIS 1: g -> h) or z
+// (AXIS 2: h -> the distance map); consecutive threads take consecutive x,
+// so every step of a warp touches 32 neighbouring words.
 template <int AXIS>
 __global__ void __launch_bounds__(256) k_dist_line(const BatchHdr *__restrict__ h) {
-    __shared__ VolIndex<AXIS == 2 ? &VolDev::dt_zbase : &VolDev::dt_ybase> VI;
+    constexpr int K = AXIS == 1 ? DT_Y : DT_ZL;
+    __shared__ DtIndex<K> VI;
     VI.load(h);
-    const uint32_t items = AXIS == 2 ? h->dt_zlines : h->dt_ylines;
-    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < h->dt_items[K]; it += gridDim.x * blockDim.x) {
         const VolDev &V = h->vol[VI.find(h, it)];
-        if (V.dt_w[0] == 0u) continue;  // never taken: such volumes own no lines
-        const uint32_t li = it - (AXIS == 2 ? V.dt_zbase : V.dt_ybase);
-        const uint32_t x = li % V.X, u = li / V.X;  // u = y (z lines) or z (y lines)
+        const uint32_t li = it - V.dt_base[K];
+        const uint32_t x = li % V.X, u = li / V.X;  // u = z (y lines) or y (z lines)
         const size_t plane = (size_t)V.X * V.Y;
-        if (AXIS == 2) {
-            const size_t o = (size_t)u * V.X + x;
-            dist_line(V.dt_g + o, V.dt_sp + o, V.dt_h + o, plane, (int)V.Z, V.dt_w[2]);
-        } else {
+        if (AXIS == 1) {
             const size_t o = (size_t)u * plane + x;
-            dist_line(V.dt_h + o, V.dt_sp + o, V.dt_out + o, V.X, (int)V.Y, V.dt_w[1]);
+            dist_line(V.dt_g + o, V.dt_sp + o, V.dt_h + o, V.X, (int)V.Y, V.dt_w[1]);
+        } else {
+            const size_t o = (size_t)u * V.X + x;
+            dist_line(V.dt_h + o, V.dt_sp + o, V.dt_out + o, plane, (int)V.Z, V.dt_w[2]);
+        }
+    }
+}
+
+// x and y passes fused: one block per (mask word w, plane z) of every volume
+// whose lines along y fit (Y <= 32 NB, X < 65536).  Lane l follows the line
+// x = 32 w + l along y; warp b holds band b of it, BL = ceil(Y / NB)
+// consecutive y.
+//   1. x pass: a warp reads each of its band's mask rows whole (so the
+//      nearest foreground voxels left and right of the word are found too) and
+//      stores dx, the distance along x to the row's nearest foreground voxel
+//      (DX_NONE: none), in shared memory.
+//   2. Each band builds the lower hull of its points (y, A(y)),
+//      A(y) = wx dx(y)^2 + wy y^2, on a stack in shared memory.
+//   3. Hulls of neighbouring band groups merge in log2(NB) rounds: the lower
+//      common tangent of two hulls separated along y is found by dropping the
+//      left hull's last vertex or the right hull's first while it is covered
+//      by the segment from its neighbour to the other hull; each band keeps
+//      the contiguous range [lo, hi) of its stack that survives.
+//   4. Each band evaluates its outputs: the vertex lowest at the band's first
+//      y is reached by walking from the band's own vertices (along the hull
+//      the values at one y fall, then rise), then the walk goes on forward as
+//      y grows.  Values at y inside the volume stay below 2^32 (the weights
+//      were checked against the volume's extent), so step 4 is 32-bit.
+// The result, min over foreground (x', y', z) of wx (x-x')^2 + wy (y-y')^2,
+// goes to dt_h.
+template <int NB>
+__global__ void __launch_bounds__(NB * 32, NB == 16 ? 3 : 1) k_dist_xy(const BatchHdr *__restrict__ h) {
+    constexpr int K = NB == 16 ? DT_XY16 : DT_XY32;
+    constexpr int YCAP = 32 * NB;
+    extern __shared__ __align__(16) uint16_t xsm[];
+    uint16_t *sdx = xsm;              // [YCAP][32] x distances
+    uint16_t *sst = xsm + YCAP * 32;  // [YCAP][32] band stacks (positions y)
+    __shared__ uint16_t slo[NB][32], shi[NB][32];
+    __shared__ DtIndex<K> VI;
+    VI.load(h);
+    const int lane = threadIdx.x & 31, b = threadIdx.x >> 5;
+    for (uint32_t it = blockIdx.x; it < h->dt_items[K]; it += gridDim.x) {
+        const VolDev &V = h->vol[VI.find(h, it)];
+        const uint32_t li = it - V.dt_base[K];
+        const int W = (int)V.W, X = (int)V.X, Y = (int)V.Y;
+        const int w = (int)(li % (uint32_t)W), z = (int)(li / (uint32_t)W);
+        const int BL = (Y + NB - 1) / NB;
+        const int x = 32 * w + lane;
+        const uint32_t wx = V.dt_w[0], wy = V.dt_w[1];
+        const int ys = min(b * BL, Y), ye = min(ys + BL, Y);
+        // 1. x distances of this band's rows
+        auto put_dx = [&](int y, uint32_t own, int lc, int rc) {
+            uint32_t dx = DX_NONE;
+            if (x < X) {
+                const uint32_t lo = own & (0xFFFFFFFFu >> (31 - lane));  // bits <= lane
+                const uint32_t hi = own >> lane;                          // bits >= lane
+                const int l = lo ? 32 * w + 31 - __clz(lo) : lc;
+                const int r = hi ? x + __ffs(hi) - 1 : rc;
+                uint32_t d = 0xFFFFFFFFu;
+                if (l >= 0) d = (uint32_t)(x - l);
+                if (r != INT_MAX) d = min(d, (uint32_t)(r - x));
+                if (d != 0xFFFFFFFFu) dx = d;  // d <= X - 1 < DX_NONE
+            }
+            sdx[y * 32 + lane] = (uint16_t)dx;
+        };
+        const uint32_t *mb = V.mask + ((size_t)z * Y + ys) * W;
+        if (W <= 32) {
+            // rows of at most 32 words: lane l holds word l of 8 rows at a
+            // time, the 8 loads issued before any is used
+            for (int r0 = 0; r0 < ye - ys; r0 += 8) {
+            uint32_t rw[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                rw[u] = (r0 + u < ye - ys && lane < W) ? mb[(size_t)(r0 + u) * W + lane] : 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int r = r0 + u;
+                if (r >= ye - ys) break;
+                const uint32_t wd = rw[u];
+                const uint32_t nz = __ballot_sync(FULL, wd != 0u);
+                const uint32_t own = __shfl_sync(FULL, wd, w);
+                const uint32_t below = nz & ((1u << w) - 1u);
+                const uint32_t above = w >= 31 ? 0u : nz & ~((2u << w) - 1u);
+                int lc = -1, rc = INT_MAX;  // nearest foreground x left / right of word w
+                if (below) {
+                    const int j = 31 - __clz(below);
+                    lc = 32 * j + 31 - __clz(__shfl_sync(FULL, wd, j));
+                }
+                if (above) {
+                    const int j = __ffs(above) - 1;
+                    rc = 32 * j + __ffs(__shfl_sync(FULL, wd, j)) - 1;
+                }
+                put_dx(ys + r, own, lc, rc);
+            }
+            }
+        } else {
+            for (int y = ys; y < ye; ++y) {
+                const uint32_t *m = mb + (size_t)(y - ys) * W;
+                uint32_t own = 0u;
+                int lc = -1, rc = INT_MAX;
+                for (int c0 = 0; c0 < W; c0 += 32) {
+                    const uint32_t wd = c0 + lane < W ? m[c0 + lane] : 0u;
+                    const uint32_t nz = __ballot_sync(FULL, wd != 0u);
+                    const int rel = w - c0;  // word w's place in this chunk
+                    if (rel >= 0 && rel < 32) own = __shfl_sync(FULL, wd, rel);
+                    const uint32_t below = rel <= 0 ? 0u : (rel >= 32 ? nz : nz & ((1u << rel) - 1u));
+                    const uint32_t above = rel < 0 ? nz : (rel >= 31 ? 0u : nz & ~((2u << rel) - 1u));
+                    if (below) {
+                        const int j = 31 - __clz(below);
+                        lc = 32 * (c0 + j) + 31 - __clz(__shfl_sync(FULL, wd, j));
+                    }
+                    if (above && rc == INT_MAX) {
+                        const int j = __ffs(above) - 1;
+                        rc = 32 * (c0 + j) + __ffs(__shfl_sync(FULL, wd, j)) - 1;
+                    }
+                }
+                put_dx(y, own, lc, rc);
+            }
+        }
+        // (own rows only: each lane reads back what it wrote)
+        auto fval = [&](int p) -> uint32_t {  // wx dx(p)^2 of a row with foreground
+            const uint32_t d = sdx[p * 32 + lane];
+            return wx * d * d;
+        };
+        auto A = [&](uint32_t p) -> uint32_t { return fval((int)p) + wy * p * p; };
+        // 2. the band's lower hull
+        int k = -1;
+        uint32_t p0 = 0, a0 = 0, p1 = 0, a1 = 0;  // stack entries k - 1 and k
+        for (int q = ys; q < ye; ++q) {
+            const uint32_t d = sdx[q * 32 + lane];
+            if (d == DX_NONE) continue;
+            const uint32_t aq = wx * d * d + wy * dt_sq(q);
+            while (k >= 1 && dt_covered(p0, a0, p1, a1, (uint32_t)q, aq)) {
+                --k;
+                p1 = p0;
+                a1 = a0;
+                if (k >= 1) {
+                    p0 = sst[(ys + k - 1) * 32 + lane];
+                    a0 = A(p0);
+                }
+            }
+            ++k;
+            sst[(ys + k) * 32 + lane] = (uint16_t)q;
+            p0 = p1;
+            a0 = a1;
+            p1 = (uint32_t)q;
+            a1 = aq;
+        }
+        slo[b][lane] = 0;
+        shi[b][lane] = (uint16_t)(k + 1);
+        __syncthreads();
+        auto pos = [&](int bb, int i) -> int { return sst[(min(bb * BL, Y) + i) * 32 + lane]; };
+        auto empty = [&](int bb) -> bool { return slo[bb][lane] >= shi[bb][lane]; };
+        // 3. merge rounds: band b = (2g + 1) s joins [b - s, b) and [b, b + s)
+        for (int s = 1; s < NB; s <<= 1) {
+            if ((b & (2 * s - 1)) == s) {
+                int bl = b - 1, br = b;
+                while (bl >= b - s && empty(bl)) --bl;
+                while (br < b + s && empty(br)) ++br;
+                if (bl >= b - s && br < b + s) {
+                    int il = shi[bl][lane] - 1, ir = slo[br][lane];
+                    uint32_t pL = pos(bl, il), aL = A(pL), pR = pos(br, ir), aR = A(pR);
+                    for (bool moved = true; moved;) {
+                        moved = false;
+                        for (;;) {  // the left hull's last vertex
+                            int pb = bl, pi = il - 1;
+                            if (pi < (int)slo[pb][lane]) {
+                                do --pb; while (pb >= b - s && empty(pb));
+                                if (pb < b - s) break;
+                                pi = shi[pb][lane] - 1;
+                            }
+                            const uint32_t pP = pos(pb, pi), aP = A(pP);
+                            if (!dt_covered(pP, aP, pL, aL, pR, aR)) break;
+                            bl = pb; il = pi; pL = pP; aL = aP;
+                            moved = true;
+                        }
+                        for (;;) {  // the right hull's first vertex
+                            int nb = br, ni = ir + 1;
+                            if (ni >= (int)shi[nb][lane]) {
+                                do ++nb; while (nb < b + s && empty(nb));
+                                if (nb >= b + s) break;
+                                ni = slo[nb][lane];
+                            }
+                            const uint32_t pN = pos(nb, ni), aN = A(pN);
+                            if (!dt_covered(pL, aL, pR, aR, pN, aN)) break;
+                            br = nb; ir = ni; pR = pN; aR = aN;
+                            moved = true;
+                        }
+                    }
+                    shi[bl][lane] = (uint16_t)(il + 1);
+                    for (int bb = bl + 1; bb < b; ++bb) shi[bb][lane] = slo[bb][lane];
+                    slo[br][lane] = (uint16_t)ir;
+                    for (int bb = b; bb < br; ++bb) slo[bb][lane] = shi[bb][lane];
+                }
+            }
+            __syncthreads();
+        }
+        // 4. outputs of this band
+        if (x < X && ys < ye) {
+            uint32_t *out = V.dt_h + (size_t)z * Y * X + x;
+            // a surviving vertex near the band: its own first, else the
+            // nearest band's to the left (last), else to the right (first)
+            int cb = b, ci = 0;
+            bool any = true;
+            if (!empty(b)) {
+                ci = slo[b][lane];
+            } else {
+                cb = b - 1;
+                while (cb >= 0 && empty(cb)) --cb;
+                if (cb >= 0) {
+                    ci = shi[cb][lane] - 1;
+                } else {
+                    cb = b + 1;
+                    while (cb < NB && empty(cb)) ++cb;
+                    if (cb < NB) ci = slo[cb][lane]; else any = false;
+                }
+            }
+            if (!any) {
+                for (int q = ys; q < ye; ++q) out[(size_t)q * X] = DT_INF;
+            } else {
+                auto val = [&](uint32_t f, int p, int q) -> uint32_t {
+                    const uint32_t d = (uint32_t)abs(q - p);
+                    return f + wy * d * d;
+                };
+                int pc = pos(cb, ci);
+                uint32_t fc = fval(pc);
+                for (;;) {  // back while the previous vertex is lower at ys
+                    int pb = cb, pi = ci - 1;
+                    if (pi < (int)slo[pb][lane]) {
+                        do --pb; while (pb >= 0 && empty(pb));
+                        if (pb < 0) break;
+                        pi = shi[pb][lane] - 1;
+                    }
+                    const int pp = pos(pb, pi);
+                    const uint32_t fp = fval(pp);
+                    if (val(fp, pp, ys) >= val(fc, pc, ys)) break;
+                    cb = pb; ci = pi; pc = pp; fc = fp;
+                }
+                // the next vertex (none: pn < 0)
+                int nb = cb, ni = ci + 1, pn = -1;
+                uint32_t fn = 0u;
+                auto load_next = [&]() {
+                    if (ni >= (int)shi[nb][lane]) {
+                        do ++nb; while (nb < NB && empty(nb));
+                        if (nb >= NB) { pn = -1; return; }
+                        ni = slo[nb][lane];
+                    }
+                    pn = pos(nb, ni);
+                    fn = fval(pn);
+                };
+                load_next();
+                for (int q = ys; q < ye; ++q) {
+                    uint32_t vc = val(fc, pc, q);
+                    while (pn >= 0) {
+                        const uint32_t vn = val(fn, pn, q);
+                        if (vn > vc) break;
+                        pc = pn;
+                        fc = fn;
+                        vc = vn;
+                        ++ni;
+                        load_next();
+                    }
+                    out[(size_t)q * X] = vc;
+                }
+            }
+        }
+        __syncthreads();  // the next tile reuses the shared arrays
+    }
+}
+
+// z pass: one block per (mask word w, group of lt / 32 rows) of every volume
+// with Z <= 256 (lt lines, lt Z <= DZ_ELEMS).  Thread t < lt follows the
+// line x = 32 w + (t & 31), y = y0 + (t >> 5) along z: it loads the line's
+// dt_h values into shared memory (entry q at q lt + t, the loads independent
+// of each other), builds the lower hull over them in place (as dist_line),
+// then writes the distance map.  Positions (< 256) are bytes, four entries of
+// a line to a 32-bit word, so a warp's lanes always touch distinct banks.
+// Values at z inside the volume stay below 2^32, so the second sweep is
+// 32-bit.  Each thread touches only its own entries.
+__global__ void __launch_bounds__(128) k_dist_z(const BatchHdr *__restrict__ h) {
+    extern __shared__ __align__(16) uint32_t zsm[];
+    uint32_t *sf = zsm;                                              // [DZ_ELEMS] values
+    uint8_t *spb = reinterpret_cast<uint8_t *>(zsm + DZ_ELEMS);      // positions
+    __shared__ DtIndex<DT_Z> VI;
+    VI.load(h);
+    const int t = threadIdx.x;
+    for (uint32_t it = blockIdx.x; it < h->dt_items[DT_Z]; it += gridDim.x) {
+        const VolDev &V = h->vol[VI.find(h, it)];
+        const uint32_t li = it - V.dt_base[DT_Z];
+        const int W = (int)V.W, X = (int)V.X, Y = (int)V.Y, Z = (int)V.Z, lt = (int)V.dt_zlt;
+        const int w = (int)(li % (uint32_t)W), y = (int)(li / (uint32_t)W) * (lt >> 5) + (t >> 5);
+        const int x = 32 * w + (t & 31);
+        if (t >= lt || x >= X || y >= Y) continue;
+        const size_t plane = (size_t)X * Y;
+        const uint32_t *in = V.dt_h + (size_t)y * X + x;
+        uint32_t *out = V.dt_out + (size_t)y * X + x;
+        uint32_t *f = sf + t;
+        auto pos = [&](int k) -> uint8_t & { return spb[(((k >> 2) * lt + t) << 2) + (k & 3)]; };
+#pragma unroll 8
+        for (int q = 0; q < Z; ++q) f[q * lt] = in[(size_t)q * plane];
+        const uint32_t wz = V.dt_w[2];
+        int k = -1;
+        uint32_t p0 = 0, a0 = 0, p1 = 0, a1 = 0;  // stack entries k - 1 and k
+        for (int q = 0; q < Z; ++q) {
+            const uint32_t fq = f[q * lt];
+            if (fq == DT_INF) continue;
+            const uint32_t aq = fq + wz * dt_sq(q);
+            while (k >= 1 && dt_covered(p0, a0, p1, a1, (uint32_t)q, aq)) {
+                --k;
+                p1 = p0;
+                a1 = a0;
+                if (k >= 1) {
+                    p0 = pos(k - 1);
+                    a0 = f[(k - 1) * lt] + wz * p0 * p0;
+                }
+            }
+            ++k;
+            pos(k) = (uint8_t)q;
+            f[k * lt] = fq;
+            p0 = p1;
+            a0 = a1;
+            p1 = (uint32_t)q;
+            a1 = aq;
+        }
+        if (k < 0) {
+            for (int q = 0; q < Z; ++q) out[(size_t)q * plane] = DT_INF;
+            continue;
+        }
+        const int top = k;
+        int j = 0;
+        uint32_t pj = pos(0), fj = f[0], pn = 0u, fn = 0u;
+        if (top >= 1) {
+            pn = pos(1);
+            fn = f[lt];
+        }
+        for (int q = 0; q < Z; ++q) {
+            uint32_t vj = fj + wz * dt_sq(q - (int)pj);
+            while (j < top) {
+                const uint32_t vn = fn + wz * dt_sq(q - (int)pn);
+                if (vn > vj) break;
+                ++j;
+                pj = pn;
+                fj = fn;
+                vj = vn;
+                if (j < top) {
+                    pn = pos(j + 1);
+                    fn = f[(j + 1) * lt];
+                }
+            }
+            out[(size_t)q * plane] = vj;
         }
     }
 }
@@ -2103,6 +2490,11 @@ cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStre
 }
 
 }  // namespace
+
+// k_dist_xy<NB>: x distances and band stacks, 32 lines x 32 NB rows, uint16
+static size_t dxy_smem(int nb) { return 2ull * 2 * 32 * 32 * (size_t)nb; }
+// k_dist_z: uint32 values and byte positions (rows of four, padded)
+constexpr size_t DZ_SMEM = 5ull * DZ_ELEMS + 512;
 
 size_t hist_smem_bytes(int tile_y) {
     return tile_y == 16 ? Tile<16>::HIST_SMEM : (tile_y == 32 ? Tile<32>::HIST_SMEM : Tile<64>::HIST_SMEM);
@@ -2152,6 +2544,25 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     if ((e = resident((const void *)k_dist_line<2>, 256, &g2)) != cudaSuccess) return e;
     if ((e = resident((const void *)k_dist_line<1>, 256, &g3)) != cudaSuccess) return e;
     plan.grid_dist = std::min(g1, std::min(g2, g3));
+    if ((e = cudaFuncSetAttribute(k_dist_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DZ_SMEM)) !=
+        cudaSuccess)
+        return e;
+    {
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_z, 128, DZ_SMEM)) != cudaSuccess)
+            return e;
+        plan.grid_dz = plan.sms * (per_sm > 0 ? per_sm : 1);
+    }
+    for (int nb : {16, 32}) {
+        const void *fn = nb == 16 ? (const void *)k_dist_xy<16> : (const void *)k_dist_xy<32>;
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dxy_smem(nb))) !=
+            cudaSuccess)
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nb * 32, dxy_smem(nb))) != cudaSuccess)
+            return e;
+        (nb == 16 ? plan.grid_dxy16 : plan.grid_dxy32) = plan.sms * (per_sm > 0 ? per_sm : 1);
+    }
     return cudaSuccess;
 }
 
@@ -2208,11 +2619,17 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     // distance map of the final foreground, for batches in which some volume
     // asks for it
     rec();
+    if (p.distance) k_dist_xy<16><<<p.grid_dxy16, 16 * 32, dxy_smem(16), s>>>(d);
+    rec();
+    if (p.distance) k_dist_xy<32><<<p.grid_dxy32, 32 * 32, dxy_smem(32), s>>>(d);
+    rec();
     if (p.distance) k_dist_x<<<p.grid_dist, 256, 0, s>>>(d);
     rec();
-    if (p.distance) k_dist_line<2><<<p.grid_dist, 256, 0, s>>>(d);
-    rec();
     if (p.distance) k_dist_line<1><<<p.grid_dist, 256, 0, s>>>(d);
+    rec();
+    if (p.distance) k_dist_z<<<p.grid_dz, 128, DZ_SMEM, s>>>(d);
+    rec();
+    if (p.distance) k_dist_line<2><<<p.grid_dist, 256, 0, s>>>(d);
     rec();
     k_tile_scan<0><<<p.grid_vols, 1024, 0, s>>>(d);
     rec();

@@ -49,6 +49,27 @@ struct VolGeom {
     size_t scratch;  // bytes of per-batch scratch for this volume-channel
 };
 
+// Distance-map path of a volume: the fused x+y kernel for lines along y of
+// at most 512 or 1024 voxels (and X < 65536, so x distances fit 16 bits),
+// else the long-line x and y kernels; the shared-memory z kernel for Z <= 256
+// with `lt` lines per tile (32 x (lt / 32) rows, lt * Z <= DZ_ELEMS), else the
+// long-line z kernel.
+struct DtPath {
+    int xy;     // DT_XY16, DT_XY32 or DT_X (long-line x and y kernels)
+    int z;      // DT_Z or DT_ZL
+    uint32_t lt;
+    bool long_y() const { return xy == DT_X; }
+    bool needs_stack() const { return xy == DT_X || z == DT_ZL; }
+};
+
+DtPath dt_path(uint32_t X, uint32_t Y, uint32_t Z) {
+    DtPath p;
+    p.xy = X >= 65536u ? DT_X : (Y <= 512u ? DT_XY16 : (Y <= 1024u ? DT_XY32 : DT_X));
+    p.lt = std::min<uint32_t>(128u, (uint32_t)DZ_ELEMS / Z / 32u * 32u);
+    p.z = p.lt >= 32u ? DT_Z : DT_ZL;
+    return p;
+}
+
 VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, const uint32_t *dt_w) {
     VolGeom g;
     g.X = d.x; g.Y = d.y; g.Z = d.z;
@@ -70,8 +91,14 @@ VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, cons
     g.cl_words = cl_r ? (uint64_t)(d.y + 2 * cl_r) * (d.z + 2 * cl_r) * (g.W + 2) : 0;
     if (cl_r) g.scratch += al(4ull * g.cl_words);
     for (int a = 0; a < 3; ++a) g.dt_w[a] = dt_w ? dt_w[a] : 0u;
-    // distance map: two uint32 line-pass buffers and the uint16 stack positions
-    if (g.dt_w[0]) g.scratch += 2 * al(4ull * g.n) + al(2ull * g.n);
+    // distance map: the x+y pass result; the long-line kernels also need the
+    // x-pass result and the stack positions
+    if (g.dt_w[0]) {
+        const DtPath p = dt_path(d.x, d.y, d.z);
+        g.scratch += al(4ull * g.n);
+        if (p.long_y()) g.scratch += al(4ull * g.n);
+        if (p.needs_stack()) g.scratch += al(2ull * g.n);
+    }
     return g;
 }
 
@@ -256,7 +283,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
     uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0, cl = 0;
-    uint32_t dtr = 0, dtz = 0, dty = 0;
+    uint32_t dtb[DT_NK] = {0, 0, 0, 0, 0, 0};
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
         for (uint32_t c = 0; c < r->C; ++c) {
@@ -306,17 +333,29 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.dt_out = r->dist(c);
             V.dt_g = V.dt_h = nullptr;
             V.dt_sp = nullptr;
+            V.dt_zlt = 0;
+            V.dt_pad = 0;
             for (int a = 0; a < 3; ++a) V.dt_w[a] = g.dt_w[a];
-            V.dt_rbase = dtr;
-            V.dt_zbase = dtz;
-            V.dt_ybase = dty;
+            for (int k = 0; k < DT_NK; ++k) V.dt_base[k] = dtb[k];
             if (g.dt_w[0]) {
-                V.dt_g = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.n);
+                const DtPath p = dt_path(g.X, g.Y, g.Z);
                 V.dt_h = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.n);
-                V.dt_sp = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
-                dtr += g.rows;
-                dtz += g.X * g.Y;
-                dty += g.X * g.Z;
+                if (p.long_y()) {
+                    V.dt_g = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.n);
+                    dtb[DT_X] += g.rows;
+                    dtb[DT_Y] += g.X * g.Z;
+                } else {
+                    dtb[p.xy] += g.W * g.Z;
+                }
+                if (p.needs_stack()) {
+                    V.dt_sp = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
+                }
+                if (p.z == DT_Z) {
+                    V.dt_zlt = p.lt;
+                    dtb[DT_Z] += g.W * (uint32_t)cdiv(g.Y, p.lt / 32u);
+                } else {
+                    dtb[DT_ZL] += g.X * g.Y;
+                }
             }
             V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
             V.smooth = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
@@ -369,9 +408,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     h->dn_items[2] = dn[2];
     h->dn_tiles = dnt;
     h->cl_items = cl;
-    h->dt_rows = dtr;
-    h->dt_zlines = dtz;
-    h->dt_ylines = dty;
+    for (int k = 0; k < DT_NK; ++k) h->dt_items[k] = dtb[k];
     h->tile_z = tz;
     h->tile_y = ty;
     b.nvol = v;
@@ -456,7 +493,8 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
     build_header(ctx, b);
     ctx->plan.denoise = s.h_hdr->dn_tiles > 0;
     ctx->plan.closing = s.h_hdr->cl_items > 0;
-    ctx->plan.distance = s.h_hdr->dt_rows > 0;
+    ctx->plan.distance = false;
+    for (int k = 0; k < DT_NK; ++k) ctx->plan.distance |= s.h_hdr->dt_items[k] > 0;
     if (ctx->graphs) {
         cudaGraphExec_t &ge =
             s.graph[graph_index(ctx->plan.tile_y, ctx->plan.denoise, ctx->plan.closing, ctx->plan.distance)];

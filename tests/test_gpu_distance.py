@@ -53,14 +53,26 @@ def check(seg, ctx, vol, w, min_volume=1, closing_radius=0, what=""):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 2), (31, 1, 7), (33, 40, 3), (70, 9, 30), (1100, 6, 5),
-                                  (64, 64, 16), (40, 300, 4), (3, 5, 600)])
+                                  (64, 64, 16), (40, 300, 4), (9, 512, 3), (5, 700, 3), (4, 1024, 2),
+                                  (4, 1100, 2), (40, 7, 80), (33, 9, 100), (35, 5, 200), (3, 5, 257),
+                                  (3, 5, 600)])
 @pytest.mark.parametrize("w", [(16, 16, 25), (1, 1, 1), (7, 3, 11)])
 def test_ragged_shapes(seg, ctx, dims, w):
-    # rows of 1..35 mask words (more than one warp chunk), lines along y and
-    # z longer than a few hundred voxels, sparse foreground (rows, lines and
-    # planes without any) and unequal weights that catch a swapped axis
+    # rows of 1..35 mask words (more than one warp chunk); lines along y up to
+    # 512 and up to 1024 voxels (the fused x+y kernel's two block shapes) and
+    # longer (the long-line kernels); lines along z for each tile height of
+    # the z kernel (128, 96, 64 and 32 lines) and longer than 256; sparse
+    # foreground (rows, lines and planes without any); unequal weights that
+    # catch a swapped axis
     vol = boxes(dims, sum(dims) + w[1], n=3)
     check(seg, ctx, vol, w, what="%s w=%s" % (dims, w))
+
+
+def test_widest_rows(seg, ctx):
+    # X = 65536: x distances no longer fit 16 bits, so the long-line x and y
+    # kernels take the volume
+    vol = boxes((65536, 1, 1), 17, n=2)
+    check(seg, ctx, vol, (1, 1, 1), what="X=65536")
 
 
 def test_empty_foreground(seg, ctx):
