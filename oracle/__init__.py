@@ -7,9 +7,10 @@ its Python binding) never imports it, and the two share no code.
 The arithmetic lives in ``seg_oracle.c`` (plain single-threaded C, built by
 ``oracle/build.py``); this module only marshals numpy arrays through ctypes.
 Every function follows the paper's Segmentation section (Otsu thresholding,
-connected components, minimum volume) and Background Noise Removal section
-(Eq. 1, Gaussian low-pass read as binomial smoothing); see the C file for the
-exact readings.
+connected components, minimum volume, closing, distance map) and Background
+Noise Removal section (Eq. 1, Gaussian low-pass read as binomial smoothing;
+the stem-cell denoise front end; the MRF vessel denoise of Eqs. 2-3); see
+the C file for the exact readings.
 
 Parity status: every function is pinned by tests/test_oracle_pins.py against
 brute force, closed forms, exact-rational Otsu and library routines.
@@ -73,6 +74,18 @@ def _load():
         lib.oracle_distance.argtypes = [u8p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_uint32, u32p]
         lib.oracle_distance.restype = ctypes.c_int
+        lib.oracle_mrf_delta.argtypes = [u16p, ctypes.c_uint64]
+        lib.oracle_mrf_delta.restype = ctypes.c_uint32
+        lib.oracle_mrf_laplacian.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u64p]
+        lib.oracle_mrf_laplacian.restype = ctypes.c_uint64
+        lib.oracle_mrf_limit.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+        lib.oracle_mrf_limit.restype = ctypes.c_double
+        lib.oracle_mrf_step.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                        u16p]
+        lib.oracle_mrf_step.restype = ctypes.c_int
+        lib.oracle_mrf.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u16p,
+                                   u32p]
+        lib.oracle_mrf.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -147,7 +160,7 @@ def filter_features(prov: np.ndarray, ncomp: int, min_volume: int):
 
 
 class OracleResult:
-    __slots__ = ("labels", "cells", "threshold", "hist", "smoothed", "distance")
+    __slots__ = ("labels", "cells", "threshold", "hist", "smoothed", "distance", "denoised", "mrf_steps")
 
     def __init__(self, labels, cells, threshold, hist, smoothed, distance=None):
         self.labels = labels
@@ -156,6 +169,8 @@ class OracleResult:
         self.hist = hist
         self.smoothed = smoothed
         self.distance = distance
+        self.denoised = None
+        self.mrf_steps = None
 
     @property
     def n_cells(self):
@@ -233,13 +248,59 @@ def distance_at(mask: np.ndarray, points, weights=(16, 16, 25)) -> np.ndarray:
     return out
 
 
+def mrf_delta(vol: np.ndarray) -> int:
+    """Delta of Eq. 3: the smallest gap between two distinct voxel values (0: fewer than two)."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint16)
+    return int(_load().oracle_mrf_delta(_ptr(vol, ctypes.c_uint16), vol.size))
+
+
+def mrf_laplacian(vol: np.ndarray):
+    """(S, M) of the noise estimate: the summed absolute response of the
+    per-plane mask [1 -2 1; -2 4 -2; 1 -2 1] over plane interiors, and M,
+    the number of interior voxels."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint16)
+    X, Y, Z = _dims(vol)
+    m = np.zeros(1, dtype=np.uint64)
+    s = _load().oracle_mrf_laplacian(_ptr(vol, ctypes.c_uint16), X, Y, Z, _ptr(m, ctypes.c_uint64))
+    return int(s), int(m[0])
+
+
+def mrf_limit(s: int, m: int, n: int) -> float:
+    """N sigma^2, sigma = sqrt(pi / 2) S / (6 M): the bound of Eq. 2 on the summed squares."""
+    return float(_load().oracle_mrf_limit(int(s), int(m), int(n)))
+
+
+def mrf_step(vol: np.ndarray, delta: int) -> np.ndarray:
+    """One step of Eq. 3 (six neighbour sign votes, step delta, clamped)."""
+    return _vol_op("oracle_mrf_step", vol, int(delta))
+
+
+def mrf(vol: np.ndarray, max_iter: int):
+    """The MRF vessel denoise of Eqs. 2-3: (denoised image, steps kept)."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint16)
+    X, Y, Z = _dims(vol)
+    out = np.empty_like(vol)
+    it = np.zeros(1, dtype=np.uint32)
+    rc = _load().oracle_mrf(_ptr(vol, ctypes.c_uint16), X, Y, Z, int(max_iter), _ptr(out, ctypes.c_uint16),
+                            _ptr(it, ctypes.c_uint32))
+    if rc:
+        raise RuntimeError("oracle_mrf failed: %d" % rc)
+    return out, int(it[0])
+
+
 def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,
             keep_smoothed: bool = False, denoise_radius: int = 0, closing_radius: int = 0,
-            distance_weights=None) -> OracleResult:
+            distance_weights=None, mrf_iterations: int = 0) -> OracleResult:
     """The whole stage for one frame and channel (uint16 [Z,Y,X]); with
-    denoise_radius > 0 the denoise front end runs first, with closing_radius
+    denoise_radius > 0 the denoise front end runs first, with mrf_iterations
+    > 0 the MRF vessel denoise (at most that many steps), with closing_radius
     > 0 the foreground is closed with that ball before labelling, and with
     distance_weights the distance map of the (closed) foreground is added."""
+    if mrf_iterations:
+        den, it = mrf(vol, mrf_iterations)
+        r = segment(den, min_volume, keep_hist, keep_smoothed, denoise_radius, closing_radius, distance_weights)
+        r.denoised, r.mrf_steps = den, it
+        return r
     if distance_weights is not None:
         r = segment(vol, min_volume, keep_hist, True, denoise_radius, closing_radius)
         fg = r.smoothed > r.threshold

@@ -6,6 +6,7 @@ propagation, per-label enumeration), closed forms (impulse response, exact
 rational Otsu, symmetric sums), invariants and library special cases
 (numpy.bincount, scipy.ndimage.label with the full 3x3x3 structure).
 """
+import math
 import os
 from fractions import Fraction
 
@@ -584,3 +585,142 @@ def test_distance_at_agrees_with_the_full_map():
         pts = [tuple(int(rng.integers(s)) for s in shape) for _ in range(25)]
         d2 = oracle.distance(m, (7, 3, 11))
         assert np.array_equal(oracle.distance_at(m, pts, (7, 3, 11)), np.array([d2[q] for q in pts], np.uint32))
+
+
+# ---- MRF vessel denoise (Background Noise Removal, Eqs. 2-3) ---------------
+
+def test_mrf_delta_is_the_smallest_gap():
+    rng = np.random.default_rng(80)
+    for levels in ([7], [3, 10], [0, 65535], [5, 9, 12, 40000]):
+        v = rng.choice(np.array(levels, np.uint16), size=(3, 4, 5))
+        v.flat[: len(levels)] = levels  # every level present
+        u = np.unique(v)
+        want = int(np.diff(u.astype(np.int64)).min()) if len(u) > 1 else 0
+        assert oracle.mrf_delta(v) == want
+    v = rng.integers(100, 4000, size=(6, 7, 8)).astype(np.uint16)
+    assert oracle.mrf_delta(v) == int(np.diff(np.unique(v).astype(np.int64)).min())
+
+
+def test_mrf_laplacian_matches_convolution():
+    ndi = pytest.importorskip("scipy.ndimage")
+    mask = np.array([[1, -2, 1], [-2, 4, -2], [1, -2, 1]], np.int64)
+    rng = np.random.default_rng(81)
+    for shape in [(3, 9, 11), (1, 3, 3), (2, 5, 40), (4, 2, 7), (2, 8, 2)]:
+        v = rng.integers(0, 65536, size=shape).astype(np.uint16)
+        s = 0
+        for plane in v.astype(np.int64):
+            r = ndi.convolve(plane, mask, mode="constant")[1:-1, 1:-1]
+            s += int(np.abs(r).sum())
+        Z, Y, X = shape
+        assert oracle.mrf_laplacian(v) == (s, Z * max(X - 2, 0) * max(Y - 2, 0)), shape
+
+
+def test_mrf_noise_estimate_recovers_sigma():
+    # Immerkaer's estimate is unbiased for white Gaussian noise on a flat image
+    rng = np.random.default_rng(82)
+    for sigma in (10.0, 30.0):
+        v = np.rint(rng.normal(1000, sigma, size=(8, 96, 96))).astype(np.uint16)
+        s, m = oracle.mrf_laplacian(v)
+        est = math.sqrt(oracle.mrf_limit(s, m, v.size) / v.size)
+        assert abs(est - sigma) < 0.05 * sigma, (sigma, est)
+
+
+def test_mrf_limit_closed_form():
+    # one spike of height h inside a zero plane: all nine mask responses are
+    # interior, |response| sums to 16 h
+    h = 300
+    v = np.zeros((2, 7, 9), np.uint16)
+    v[1, 3, 4] = h
+    s, m = oracle.mrf_laplacian(v)
+    assert (s, m) == (16 * h, 2 * 5 * 7)
+    sigma = math.sqrt(math.pi / 2) * 16 * h / (6 * m)
+    assert oracle.mrf_limit(s, m, v.size) == pytest.approx(v.size * sigma * sigma, rel=1e-15)
+    assert oracle.mrf_limit(0, 0, 10) == 0.0
+
+
+def test_mrf_step_special_cases():
+    # constant: fixed
+    c = np.full((3, 4, 5), 77, np.uint16)
+    assert np.array_equal(oracle.mrf_step(c, 1), c)
+    # spike: it drops by delta, its six face neighbours rise by delta
+    v = np.zeros((5, 5, 5), np.uint16)
+    v[2, 2, 2] = 9
+    s = oracle.mrf_step(v, 4).astype(np.int64)
+    want = np.zeros((5, 5, 5), np.int64)
+    want[2, 2, 2] = 5
+    for dz, dy, dx in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]:
+        want[2 + dz, 2 + dy, 2 + dx] = 4
+    assert np.array_equal(s, want)
+    # ramp along x: the interior is fixed (one vote each way); the low end
+    # rises and the high end falls (its outer neighbour votes 0)
+    r = np.broadcast_to(np.arange(6, dtype=np.uint16) * 3, (2, 3, 6)).copy()
+    s = oracle.mrf_step(r, 3)
+    assert np.array_equal(s[..., 1:-1], r[..., 1:-1])
+    assert np.all(s[..., 0] == 3) and np.all(s[..., -1] == 12)
+
+
+def test_mrf_step_invariants():
+    rng = np.random.default_rng(83)
+    v = rng.integers(0, 50, size=(5, 6, 7)).astype(np.uint16)
+    d = oracle.mrf_delta(v)
+    s = oracle.mrf_step(v, d).astype(np.int64)
+    diff = s - v.astype(np.int64)
+    assert set(np.unique(diff)) <= {-d, 0, d}
+    # strict local maxima (over in-volume face neighbours) fall, minima rise
+    p = np.pad(v.astype(np.int64), 1, mode="edge")
+    nb = [p[1:-1, 1:-1, :-2], p[1:-1, 1:-1, 2:], p[1:-1, :-2, 1:-1], p[1:-1, 2:, 1:-1], p[:-2, 1:-1, 1:-1],
+          p[2:, 1:-1, 1:-1]]
+    c = v.astype(np.int64)
+    # (replicated edges equal the centre and vote 0, as the outside does)
+    higher = sum((n > c).astype(int) for n in nb)
+    lower = sum((n < c).astype(int) for n in nb)
+    assert np.all(diff[(lower > 0) & (higher == 0)] == -d)
+    assert np.all(diff[(higher > 0) & (lower == 0)] == d)
+    # mirror symmetry along each axis
+    for ax in range(3):
+        assert np.array_equal(oracle.mrf_step(np.flip(v, ax).copy(), d), np.flip(s, ax).astype(np.uint16))
+
+
+def test_mrf_iteration_stops():
+    rng = np.random.default_rng(84)
+    # constant: no step changes anything
+    c = np.full((4, 5, 6), 300, np.uint16)
+    out, it = oracle.mrf(c, 10)
+    assert it == 0 and np.array_equal(out, c)
+    # planes without interior (Y = 2): sigma = 0, the first step already
+    # strays from the original, so nothing is kept
+    v = rng.integers(0, 100, size=(3, 2, 9)).astype(np.uint16)
+    out, it = oracle.mrf(v, 10)
+    assert it == 0 and np.array_equal(out, v)
+    # noisy flat image: the kept steps are exactly the repeated step while the
+    # summed squares stay within N sigma^2, and fewer steps are a prefix
+    v = np.rint(rng.normal(500, 20, size=(4, 24, 24))).astype(np.uint16)
+    d = oracle.mrf_delta(v)
+    s, m = oracle.mrf_laplacian(v)
+    lim = oracle.mrf_limit(s, m, v.size)
+    cur, want = v, 0
+    while want < 200:
+        nxt = oracle.mrf_step(cur, d)
+        e = int(((nxt.astype(np.int64) - v.astype(np.int64)) ** 2).sum())
+        if np.array_equal(nxt, cur) or float(e) > lim:
+            break
+        cur, want = nxt, want + 1
+    out, it = oracle.mrf(v, 200)
+    assert it == want and np.array_equal(out, cur) and 0 < it < 200
+    out3, it3 = oracle.mrf(v, 3)
+    assert it3 == 3
+    p = v
+    for _ in range(3):
+        p = oracle.mrf_step(p, d)
+    assert np.array_equal(out3, p)
+
+
+def test_segment_with_mrf_is_segment_of_denoised():
+    rng = np.random.default_rng(85)
+    v = np.rint(rng.normal(200, 25, size=(12, 30, 40))).clip(0, 65535).astype(np.uint16)
+    v[4:8, 10:20, 5:35] += 1500
+    r = oracle.segment(v, min_volume=5, mrf_iterations=20)
+    den, it = oracle.mrf(v, 20)
+    assert r.mrf_steps == it and np.array_equal(r.denoised, den)
+    ref = oracle.segment(den, min_volume=5)
+    assert np.array_equal(r.labels, ref.labels) and r.threshold == ref.threshold
