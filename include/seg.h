@@ -128,6 +128,20 @@ typedef struct {
      * >= 1 and wx(X-1)^2 + wy(Y-1)^2 + wz(Z-1)^2 < 0xFFFFFFFF, else
      * seg_submit_volume returns SEG_EINVAL. */
     uint32_t distance_weights[3];
+    /* 0: off.  1..1000: the MRF denoise of the vessel channel (Background
+     * Noise Removal, Eqs. 2-3) runs before the smoothing, at most this many
+     * steps: every voxel moves by Delta (the smallest gap between two
+     * distinct input levels) towards the majority of its six face
+     * neighbours (a neighbour votes +1 if higher, -1 if lower, 0 if equal
+     * or outside the volume), all voxels at once, clamped to [0, 65535];
+     * a step is kept while the root-mean-square difference from the input
+     * stays within the noise level sigma = sqrt(pi/2) S / (6 M), S the
+     * summed absolute response of the plane mask [1 -2 1; -2 4 -2; 1 -2 1]
+     * over the M interior voxels of the z-planes (binary64: the step is kept
+     * iff (double)sum d^2 <= (N sigma) sigma); the iteration also stops at a
+     * step that changes nothing.  Not combined with denoise_radius
+     * (SEG_EINVAL). */
+    uint32_t mrf_iterations;
 } seg_channel_params;
 
 /* Creates a context on cfg->device.  Allocates streams and descriptor buffers;
@@ -178,6 +192,15 @@ int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
  * without distance weights; otherwise as seg_read_labels. */
 int seg_read_distance(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
                       uint64_t dst_elems, int dst_on_device);
+
+/* Copies the image channel `channel` was segmented from after its denoise
+ * (front end or MRF; X*Y*Z uint16, layout of the input) to dst (host, or
+ * device when dst_on_device = 1); *mrf_steps (optional) gets the number of
+ * MRF steps kept (0 for the front end).  Blocks until the copy is complete.
+ * Errors: SEG_EINVAL also when the channel has neither denoise; otherwise as
+ * seg_read_labels. */
+int seg_read_denoised(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst, uint64_t dst_elems,
+                      int dst_on_device, uint32_t *mrf_steps);
 
 /* Copies channel `channel`'s cells (label order) to host memory dst (cap
  * entries) and reports n_cells and the Otsu level t* (foreground = s > t*).

@@ -66,7 +66,8 @@ class seg_config(ctypes.Structure):
 
 class seg_channel_params(ctypes.Structure):
     _fields_ = [("min_volume_voxels", ctypes.c_uint32), ("denoise_radius", ctypes.c_uint32),
-                ("closing_radius", ctypes.c_uint32), ("distance_weights", ctypes.c_uint32 * 3)]
+                ("closing_radius", ctypes.c_uint32), ("distance_weights", ctypes.c_uint32 * 3),
+                ("mrf_iterations", ctypes.c_uint32)]
 
 
 class seg_stats(ctypes.Structure):
@@ -80,7 +81,8 @@ class seg_stats(ctypes.Structure):
 
 
 EXPORTS = ["seg_create", "seg_destroy", "seg_submit_volume", "seg_flush", "seg_poll",
-           "seg_enqueue_wait", "seg_read_labels", "seg_read_distance", "seg_read_features", "seg_release",
+           "seg_enqueue_wait", "seg_read_labels", "seg_read_distance", "seg_read_denoised",
+           "seg_read_features", "seg_release",
            "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror",
            "seg_otsu_threshold_noalloc"]
 
@@ -97,6 +99,7 @@ def _bind(lib):
         "seg_enqueue_wait": [vp, u64, vp],
         "seg_read_labels": [vp, u64, u32, vp, u64, i32],
         "seg_read_distance": [vp, u64, u32, vp, u64, i32],
+        "seg_read_denoised": [vp, u64, u32, vp, u64, i32, P(u32)],
         "seg_read_features": [vp, u64, u32, vp, u64, P(u64), P(ctypes.c_uint16)],
         "seg_release": [vp, u64],
         "seg_request_times": [vp, u64, P(ctypes.c_double), P(ctypes.c_double),
@@ -170,13 +173,14 @@ def _voxel_ptr(voxels):
 
 
 def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, denoise_radius=0, closing_radius=0,
-                      distance_weights=None):
+                      distance_weights=None, mrf_iterations=0):
     """Submits [C][Z][Y][X] (or [Z][Y][X]) uint16 voxels; returns the request id.
 
     min_volume, denoise_radius, closing_radius: one int for every channel or
     a sequence of per-channel ints (0 = no denoise front end / no closing).
     distance_weights: None (no distance map), one (wx, wy, wz) for every
-    channel, or a per-channel sequence of triples or None."""
+    channel, or a per-channel sequence of triples or None.  mrf_iterations:
+    step limit of the MRF vessel denoise (0 = off), one int or per channel."""
     shape = tuple(voxels.shape)
     if dims is None:
         if len(shape) == 3:
@@ -197,11 +201,12 @@ def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, deno
     else:
         dw = list(distance_weights)
     dw = [(0, 0, 0) if w is None else tuple(int(a) for a in w) for w in dw]
-    if len(mv) != channels or len(dr) != channels or len(cr) != channels or len(dw) != channels:
+    mi = [mrf_iterations] * channels if np.isscalar(mrf_iterations) else list(mrf_iterations)
+    if any(len(a) != channels for a in (mv, dr, cr, dw, mi)):
         raise ValueError("per-channel parameter lists must have one entry per channel")
     params = (seg_channel_params * channels)(
-        *[seg_channel_params(int(m), int(d), int(c), (ctypes.c_uint32 * 3)(*w))
-          for m, d, c, w in zip(mv, dr, cr, dw)])
+        *[seg_channel_params(int(m), int(d), int(c), (ctypes.c_uint32 * 3)(*w), int(i))
+          for m, d, c, w, i in zip(mv, dr, cr, dw, mi)])
     out = ctypes.c_uint64()
     _check(_lib.seg_submit_volume(ctx, ctypes.c_void_p(ptr), on_dev, seg_dims(*dims), channels,
                                   params, ctypes.byref(out)), "seg_submit_volume")
@@ -256,6 +261,21 @@ def seg_read_distance(ctx, req, channel, out):
     return out
 
 
+def seg_read_denoised(ctx, req, channel, out):
+    """Copies the channel's denoised image into `out` (a numpy uint16 array or
+    a torch int16/uint16 tensor); returns the number of MRF steps kept."""
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.uint16 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be C-contiguous uint16")
+        ptr, n, dev = out.ctypes.data, out.size, 0
+    else:
+        ptr, n, dev = out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
+    steps = ctypes.c_uint32()
+    _check(_lib.seg_read_denoised(ctx, req, channel, ctypes.c_void_p(ptr), n, dev, ctypes.byref(steps)),
+           "seg_read_denoised")
+    return steps.value
+
+
 def seg_read_features(ctx, req, channel):
     """Returns (cells structured array of FEATURE_DTYPE, otsu threshold)."""
     n = ctypes.c_uint64()
@@ -308,13 +328,14 @@ def seg_otsu_threshold_noalloc(voxels_ptr, dims, result_ptr, stream_ptr=None):
 
 
 def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000, denoise_radius=0, closing_radius=0,
-            distance_weights=None):
+            distance_weights=None, mrf_iterations=0):
     """Convenience: submit one volume, wait, read labels + cells of every channel, release.
 
     Returns a list (one entry per channel) of (labels, cells, threshold), with
     the distance map (or None) as a fourth entry when distance_weights is given."""
     req = seg_submit_volume(ctx, voxels, min_volume=min_volume, denoise_radius=denoise_radius,
-                            closing_radius=closing_radius, distance_weights=distance_weights)
+                            closing_radius=closing_radius, distance_weights=distance_weights,
+                            mrf_iterations=mrf_iterations)
     seg_flush(ctx)
     try:
         st = seg_wait(ctx, req, timeout_ms)

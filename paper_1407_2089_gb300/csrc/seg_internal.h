@@ -18,6 +18,14 @@ enum StatWord : uint32_t {
     ST_CELLS = 2,      // number of surviving cells K
     ST_TILES_DONE = 3, // smoothing tiles whose histogram share is merged
     ST_ERROR = 4,      // error bits (ERR_*)
+    ST_MRF_STEPS = 5,  // MRF denoise: steps kept
+    ST_MRF_SEL = 6,    // MRF denoise: result buffer (0 input, 1 mrf_buf[0], 2 mrf_buf[1])
+    ST_MRF_DONE = 7,   // MRF denoise: stopped
+    ST_MRF_DELTA = 8,  // MRF denoise: step size (0: fewer than two levels)
+    ST_MRF_CNT = 9,    // MRF denoise: tiles done in the current launch
+    ST_MRF_CHG = 10,   // MRF denoise: some voxel changed in the current step
+    ST_MRF_E = 12,     // MRF denoise: uint64 at words 12-13, Laplacian sum S, then sum d^2
+    ST_MRF_LIMIT = 14, // MRF denoise: binary64 bound N sigma^2 at words 14-15
     ST_WORDS = 16,
 };
 
@@ -95,6 +103,15 @@ struct VolDev {
     uint32_t dt_base[6];      // first flat item of this volume in each DtKernel
     uint32_t dt_zlt;          // lines of a k_dist_z tile (32, 64, 96 or 128)
     uint32_t dt_pad;
+    // MRF vessel denoise (mrf_max > 0); raw is rewritten on the device to the
+    // kept image before the smoothing reads it
+    const uint16_t *mrf_in;   // the input I^0 [Z][Y][X]
+    uint16_t *mrf_buf[2];     // steps: it 0 reads mrf_in, it > 0 mrf_buf[it & 1]; writes mrf_buf[(it + 1) & 1]
+    uint32_t *mrf_bits;       // 2048 words: levels present in the input
+    uint32_t mrf_max;         // step limit, 0 = off
+    uint32_t mrf_tiles;       // tiles of MRF_TILE octets (8 x-consecutive voxels)
+    uint32_t mrf_tbase;       // first flat MRF tile
+    uint32_t mrf_pad;
 };
 
 // The distance-map kernels and their work items.  A volume takes the fused
@@ -111,6 +128,8 @@ enum DtKernel : int {
     DT_NK = 6,
 };
 constexpr int DZ_ELEMS = 8192;   // k_dist_z shared stack entries per block
+constexpr int MRF_TILE = 256;    // octets per MRF tile (one per thread)
+constexpr uint32_t MRF_MAX_ITER = 1000;
 
 // Batch header, followed in memory by VolDev[nvol].
 struct BatchHdr {
@@ -125,6 +144,8 @@ struct BatchHdr {
     uint32_t dn_tiles;   // denoise median tiles over the batch
     uint32_t cl_items;   // closing dilation items over the batch
     uint32_t dt_items[DT_NK]; // distance-map items per DtKernel over the batch
+    uint32_t mrf_tiles;       // MRF tiles over the batch
+    uint32_t mrf_pad;
     VolDev vol[1];       // nvol entries
 };
 
@@ -133,7 +154,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 23;
+constexpr int NUM_KERNELS = 25;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {
@@ -158,6 +179,8 @@ struct LaunchPlan {
     int grid_dxy16;      // k_dist_xy<16>
     int grid_dxy32;      // k_dist_xy<32>
     int grid_dz;         // k_dist_z
+    int grid_mrf;        // k_mrf_stats, k_mrf_step
+    uint32_t mrf_iters;  // k_mrf_step launches: the largest step limit in the batch (0: none)
 };
 
 // Enqueues the whole pipeline for a batch whose header lives at d_hdr (device)

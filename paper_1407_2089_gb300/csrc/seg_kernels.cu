@@ -41,7 +41,8 @@
 namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
-    "denoise_box", "denoise_median", "init",       "smooth_hist_otsu", "threshold_runs",
+    "denoise_box", "denoise_median", "init",       "mrf_stats",        "mrf_iterate",
+    "smooth_hist_otsu", "threshold_runs",
     "dilate",      "erode",          "dist_xy",    "dist_xy_1024",     "dist_x",
     "dist_y",      "dist_z",         "dist_z_long", "scan_runs",       "row_runs",
     "union_local", "union",          "flatten",    "keep_count",       "scan_keep",
@@ -713,6 +714,8 @@ __global__ void k_init(const BatchHdr *__restrict__ h) {
         const uint32_t v = (uint32_t)(i / per), j = (uint32_t)(i % per);
         reinterpret_cast<uint4 *>(h->vol[v].hist)[j] = make_uint4(0, 0, 0, 0);
         if (j < ST_WORDS / 4) reinterpret_cast<uint4 *>(h->vol[v].stat)[j] = make_uint4(0, 0, 0, 0);
+        if (j < 2048 / 4 && h->vol[v].mrf_bits)
+            reinterpret_cast<uint4 *>(h->vol[v].mrf_bits)[j] = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -1920,6 +1923,226 @@ __global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// MRF vessel denoise (Background Noise Removal, Eqs. 2-3).  Every step moves
+// each voxel by Delta towards the majority of its six face neighbours (Eq. 3:
+// a neighbour votes +1 if higher, -1 if lower, 0 if equal or outside the
+// volume; the paired terms of the printed equation read as the two
+// neighbours' votes), all voxels at once, clamped to [0, 65535].  A step is
+// kept while the root-mean-square difference from the input stays within the
+// noise level sigma estimated from the input with a Laplacian mask (Eq. 2).
+// Delta is the smallest gap between two distinct input levels.  One tile is
+// MRF_TILE octets (8 x-consecutive voxels of a row) of one volume.
+
+__device__ __forceinline__ int mrf_sgn(int32_t d) { return (d > 0) - (d < 0); }
+
+// Block sum of one uint64 per thread (MRF_TILE threads); thread 0 gets it.
+__device__ __forceinline__ unsigned long long mrf_block_sum(unsigned long long v, unsigned long long *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long s = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < MRF_TILE / 32; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+// Levels present in the input (bitmap, set once per level) and the noise
+// estimate's sum S over every z-plane's interior of |[1 -2 1; -2 4 -2;
+// 1 -2 1] * I| (Immerkaer's mask), added into the volume's ST_MRF_E words.
+__global__ void __launch_bounds__(MRF_TILE) k_mrf_stats(const BatchHdr *__restrict__ h) {
+    __shared__ VolIndex<&VolDev::mrf_tbase> VI;
+    __shared__ unsigned long long red[MRF_TILE / 32];
+    VI.load(h);
+    for (uint32_t t = blockIdx.x; t < h->mrf_tiles; t += gridDim.x) {
+        const VolDev &V = h->vol[VI.find(h, t)];
+        const uint32_t X = V.X, Y = V.Y, OX = (X + 7) >> 3;
+        const uint32_t o = (t - V.mrf_tbase) * MRF_TILE + threadIdx.x;
+        unsigned long long s = 0;
+        if (o < V.rows * OX) {
+            const uint32_t row = o / OX, x0 = 8 * (o % OX), y = row % Y;
+            const uint16_t *r0 = V.mrf_in + (size_t)row * X;
+            const uint32_t xe = min(x0 + 8u, X);
+            for (uint32_t x = x0; x < xe; ++x) {
+                const uint32_t v = r0[x], bit = 1u << (v & 31u);
+                if (!(V.mrf_bits[v >> 5] & bit)) atomicOr(V.mrf_bits + (v >> 5), bit);
+            }
+            if (y >= 1 && y + 1 < Y) {
+                const uint16_t *rm = r0 - X, *rp = r0 + X;
+                for (uint32_t x = max(x0, 1u); x < xe && x + 1 < X; ++x) {
+                    const int32_t a = (int32_t)rm[x - 1] - 2 * (int32_t)rm[x] + (int32_t)rm[x + 1];
+                    const int32_t b = (int32_t)r0[x - 1] - 2 * (int32_t)r0[x] + (int32_t)r0[x + 1];
+                    const int32_t c = (int32_t)rp[x - 1] - 2 * (int32_t)rp[x] + (int32_t)rp[x + 1];
+                    s += (unsigned long long)abs(a - 2 * b + c);
+                }
+            }
+        }
+        s = mrf_block_sum(s, red);
+        if (threadIdx.x == 0 && s) atomicAdd(reinterpret_cast<unsigned long long *>(V.stat + ST_MRF_E), s);
+    }
+}
+
+// One warp per MRF volume: Delta from the levels present, and the bound
+// N sigma^2 of Eq. 2 from S in binary64 with every operation rounded as
+// written (sigma = (sqrt(pi/2) S) / (6 M), bound = (N sigma) sigma, M the
+// number of plane-interior voxels).  Fewer than two levels: nothing to do,
+// the input is kept.
+__global__ void k_mrf_prep(const BatchHdr *__restrict__ h) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t v = blockIdx.x; v < h->nvol; v += gridDim.x) {
+        const VolDev &V = h->vol[v];
+        if (V.mrf_max == 0) continue;
+        // lane l scans levels [2048 l, 2048 l + 2048)
+        int first = -1, last = -1;
+        uint32_t gap = 0xFFFFFFFFu;
+        for (int i = 0; i < 64; ++i) {
+            const uint32_t w = V.mrf_bits[64 * lane + i];
+            if (!w) continue;
+            const int pos0 = 32 * (64 * lane + i);
+            const int lo = pos0 + __ffs(w) - 1, hi = pos0 + 31 - __clz(w);
+            if (first < 0) first = lo;
+            if (last >= 0) gap = min(gap, (uint32_t)(lo - last));
+            int prev = lo;
+            for (uint32_t m = w & (w - 1u); m && gap > 1u; m &= m - 1u) {
+                const int p = pos0 + __ffs(m) - 1;
+                gap = min(gap, (uint32_t)(p - prev));
+                prev = p;
+            }
+            last = hi;
+        }
+        int gl = -1;  // last level seen over the lanes before
+        uint32_t delta = 0xFFFFFFFFu;
+        for (int l = 0; l < 32; ++l) {
+            const int f = __shfl_sync(FULL, first, l), la = __shfl_sync(FULL, last, l);
+            const uint32_t g = __shfl_sync(FULL, gap, l);
+            if (f < 0) continue;
+            if (gl >= 0) delta = min(delta, (uint32_t)(f - gl));
+            delta = min(delta, g);
+            gl = la;
+        }
+        if (lane == 0) {
+            uint32_t *st = V.stat;
+            unsigned long long *e = reinterpret_cast<unsigned long long *>(st + ST_MRF_E);
+            const unsigned long long s = *e;
+            const unsigned long long m =
+                (unsigned long long)V.Z * (V.X >= 2 ? V.X - 2 : 0) * (V.Y >= 2 ? V.Y - 2 : 0);
+            const unsigned long long n = (unsigned long long)V.X * V.Y * V.Z;
+            double limit = 0.0;
+            if (m) {
+                const double half_pi = 3.14159265358979323846 / 2.0;
+                const double sigma = __ddiv_rn(__dmul_rn(__dsqrt_rn(half_pi), __ull2double_rn(s)),
+                                               __dmul_rn(6.0, __ull2double_rn(m)));
+                limit = __dmul_rn(__dmul_rn(__ull2double_rn(n), sigma), sigma);
+            }
+            *reinterpret_cast<double *>(st + ST_MRF_LIMIT) = limit;
+            *e = 0ull;
+            st[ST_MRF_CNT] = 0u;
+            st[ST_MRF_CHG] = 0u;
+            st[ST_MRF_STEPS] = 0u;
+            st[ST_MRF_SEL] = 0u;
+            st[ST_MRF_DELTA] = delta == 0xFFFFFFFFu ? 0u : delta;
+            st[ST_MRF_DONE] = delta == 0xFFFFFFFFu ? 1u : 0u;
+        }
+    }
+}
+
+// Step `it` of every MRF volume not yet stopped: reads mrf_in (it = 0) or
+// mrf_buf[it & 1], writes mrf_buf[(it + 1) & 1], and adds the step's
+// sum (I^{it+1} - I^0)^2 and whether anything changed to the volume's
+// status words.  The block that finishes the volume's last tile decides:
+// stop at a step that changes nothing or strays too far (keeping I^it), or
+// at the step limit; when stopping it points the volume's raw input for the
+// smoothing (in the device copy of the batch descriptor) at the kept image.
+__global__ void __launch_bounds__(MRF_TILE) k_mrf_step(const BatchHdr *__restrict__ h, uint32_t it) {
+    __shared__ VolIndex<&VolDev::mrf_tbase> VI;
+    __shared__ unsigned long long red[MRF_TILE / 32];
+    __shared__ uint32_t chg_any;  // some voxel of the tile changed (0 between tiles)
+    if (threadIdx.x == 0) chg_any = 0u;
+    VI.load(h);  // (its barrier orders the store above)
+    for (uint32_t t = blockIdx.x; t < h->mrf_tiles; t += gridDim.x) {
+        const uint32_t vi = VI.find(h, t);
+        const VolDev &V = h->vol[vi];
+        uint32_t *st = V.stat;
+        if (it >= V.mrf_max || st[ST_MRF_DONE]) continue;  // the same for the whole block
+        const uint32_t X = V.X, Y = V.Y, Z = V.Z, OX = (X + 7) >> 3;
+        const size_t plane = (size_t)X * Y;
+        const uint16_t *cur = it == 0 ? V.mrf_in : V.mrf_buf[it & 1u];
+        uint16_t *nxt = V.mrf_buf[(it + 1u) & 1u];
+        const int32_t delta = (int32_t)st[ST_MRF_DELTA];
+        const uint32_t o = (t - V.mrf_tbase) * MRF_TILE + threadIdx.x;
+        unsigned long long e = 0;
+        bool changed = false;
+        if (o < V.rows * OX) {
+            const uint32_t row = o / OX, x0 = 8 * (o % OX), y = row % Y, z = row / Y;
+            const size_t base = (size_t)row * X;
+            const uint16_t *c0 = cur + base;
+            const uint16_t *ym = y > 0 ? c0 - X : nullptr, *yp = y + 1 < Y ? c0 + X : nullptr;
+            const uint16_t *zm = z > 0 ? c0 - plane : nullptr, *zp = z + 1 < Z ? c0 + plane : nullptr;
+            const uint16_t *org = V.mrf_in + base;
+            const uint32_t xe = min(x0 + 8u, X);
+            int32_t left = x0 > 0 ? (int32_t)c0[x0 - 1] : -1;
+            for (uint32_t x = x0; x < xe; ++x) {
+                const int32_t c = c0[x];
+                const int32_t right = x + 1 < X ? (int32_t)c0[x + 1] : -1;
+                int votes = 0;
+                if (left >= 0) votes += mrf_sgn(left - c);
+                if (right >= 0) votes += mrf_sgn(right - c);
+                if (ym) votes += mrf_sgn((int32_t)ym[x] - c);
+                if (yp) votes += mrf_sgn((int32_t)yp[x] - c);
+                if (zm) votes += mrf_sgn((int32_t)zm[x] - c);
+                if (zp) votes += mrf_sgn((int32_t)zp[x] - c);
+                const int32_t nv = min(max(c + delta * mrf_sgn(votes), 0), 65535);
+                nxt[base + x] = (uint16_t)nv;
+                const int32_t d = nv - (int32_t)org[x];
+                e += (unsigned long long)((int64_t)d * d);
+                changed |= nv != c;
+                left = c;
+            }
+        }
+        if (changed) chg_any = 1u;  // benign race: every writer stores 1
+        e = mrf_block_sum(e, red);  // (its barriers also order chg_any)
+        if (threadIdx.x == 0) {
+            unsigned long long *E = reinterpret_cast<unsigned long long *>(st + ST_MRF_E);
+            if (e) atomicAdd(E, e);
+            if (chg_any) atomicOr(st + ST_MRF_CHG, 1u);
+            chg_any = 0u;
+            __threadfence();
+            if (atomicAdd(st + ST_MRF_CNT, 1u) == V.mrf_tiles - 1u) {
+                // every tile of this volume is in: decide
+                __threadfence();
+                const unsigned long long sum = atomicAdd(E, 0ull);
+                const uint32_t chg = atomicAdd(st + ST_MRF_CHG, 0u);
+                const double limit = *reinterpret_cast<const volatile double *>(st + ST_MRF_LIMIT);
+                uint32_t sel, steps, done;
+                if (!chg || __ull2double_rn(sum) > limit) {
+                    done = 1u;  // keep I^it
+                    steps = it;
+                    sel = it == 0 ? 0u : 1u + (it & 1u);
+                } else {
+                    steps = it + 1u;
+                    sel = 1u + ((it + 1u) & 1u);
+                    done = it + 1u >= V.mrf_max ? 1u : 0u;
+                }
+                st[ST_MRF_STEPS] = steps;
+                st[ST_MRF_SEL] = sel;
+                st[ST_MRF_DONE] = done;
+                if (done) {
+                    // the smoothing reads the kept image: the descriptor is
+                    // the device copy made for this launch sequence
+                    VolDev &W = const_cast<VolDev &>(V);
+                    W.raw = sel == 0 ? V.mrf_in : V.mrf_buf[sel - 1u];
+                }
+                *E = 0ull;
+                st[ST_MRF_CHG] = 0u;
+                st[ST_MRF_CNT] = 0u;
+            }
+        }
+        __syncthreads();  // chg_any and red are reused by the next tile
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Distance map of the final foreground (Segmentation section: for every voxel
 // the distance to the nearest foreground voxel of the vessel channel).  The
 // weighted squared Euclidean distance min over foreground voxels p of
@@ -2544,6 +2767,9 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     if ((e = resident((const void *)k_dist_line<2>, 256, &g2)) != cudaSuccess) return e;
     if ((e = resident((const void *)k_dist_line<1>, 256, &g3)) != cudaSuccess) return e;
     plan.grid_dist = std::min(g1, std::min(g2, g3));
+    if ((e = resident((const void *)k_mrf_stats, MRF_TILE, &g1)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_mrf_step, MRF_TILE, &g2)) != cudaSuccess) return e;
+    plan.grid_mrf = std::min(g1, g2);
     if ((e = cudaFuncSetAttribute(k_dist_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DZ_SMEM)) !=
         cudaSuccess)
         return e;
@@ -2602,6 +2828,14 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     if (p.denoise) k_median27<<<p.grid_med, MED_TX * MED_TY, 0, s>>>(d);
     rec();
     k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
+    // MRF vessel denoise, for batches in which some volume asks for it
+    rec();
+    if (p.mrf_iters) {
+        k_mrf_stats<<<p.grid_mrf, MRF_TILE, 0, s>>>(d);
+        k_mrf_prep<<<p.grid_vols, 32, 0, s>>>(d);
+    }
+    rec();
+    for (uint32_t it = 0; it < p.mrf_iters; ++it) k_mrf_step<<<p.grid_mrf, MRF_TILE, 0, s>>>(d, it);
     cudaError_t e;
     switch (p.tile_y) {
         case 16: e = launch_tile_kernels<16>(d, p, s, ev, k); break;

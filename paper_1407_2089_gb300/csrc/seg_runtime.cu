@@ -19,6 +19,7 @@
 #include <cstring>
 #include <deque>
 #include <memory>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -45,6 +46,7 @@ struct VolGeom {
     uint32_t cl_r;   // closing ball radius, 0 = off
     uint64_t cl_words;  // words of the extended (padded) mask of the closing
     uint32_t dt_w[3];   // distance-map weights, {0, 0, 0} = off
+    uint32_t mrf_max;   // MRF denoise step limit, 0 = off
     uint64_t n, r_cap, k_cap;
     size_t scratch;  // bytes of per-batch scratch for this volume-channel
 };
@@ -70,7 +72,8 @@ DtPath dt_path(uint32_t X, uint32_t Y, uint32_t Z) {
     return p;
 }
 
-VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, const uint32_t *dt_w) {
+VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, const uint32_t *dt_w,
+             uint32_t mrf_max) {
     VolGeom g;
     g.X = d.x; g.Y = d.y; g.Z = d.z;
     g.W = (uint32_t)cdiv(d.x, 32);
@@ -86,7 +89,9 @@ VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, cons
     g.scratch = al(4ull * HIST_BINS) + al(2ull * g.n) + al(4ull * g.rows * g.W) + al(4ull * (g.rows + 1)) +
                 al(4ull * g.rows) + 2 * al(4ull * g.nrt) + 3 * al(4ull * g.r_cap);
     g.dn_r = dn_r;
-    if (dn_r) g.scratch += 3 * al(2ull * g.n);  // two box-pass buffers + the denoised image
+    if (dn_r) g.scratch += 2 * al(2ull * g.n);  // two box-pass buffers (the denoised image persists)
+    g.mrf_max = mrf_max;
+    if (mrf_max) g.scratch += al(4ull * 2048);  // levels present in the input
     g.cl_r = cl_r;
     g.cl_words = cl_r ? (uint64_t)(d.y + 2 * cl_r) * (d.z + 2 * cl_r) * (g.W + 2) : 0;
     if (cl_r) g.scratch += al(4ull * g.cl_words);
@@ -114,6 +119,8 @@ struct Request {
     size_t block_bytes = 0;
     size_t off_labels = 0, off_feat = 0, off_stat = 0, off_input = 0;
     std::vector<size_t> off_dist;         // per channel; SIZE_MAX = no distance map
+    std::vector<size_t> off_den;          // per channel; SIZE_MAX = no denoise (front end: 1 image, MRF: 2)
+    std::vector<uint32_t> mrf_steps, mrf_sel;
     size_t per_labels = 0, per_feat = 0;  // bytes per channel
     bool owns_input = false;
     bool admitted = false;
@@ -134,6 +141,10 @@ struct Request {
     uint32_t *labels(uint32_t c) const {
         return reinterpret_cast<uint32_t *>(block + off_labels + c * per_labels);
     }
+    uint16_t *den(uint32_t c, int k = 0) const {
+        return off_den[c] == SIZE_MAX ? nullptr
+                                      : reinterpret_cast<uint16_t *>(block + off_den[c]) + (size_t)k * g[c].n;
+    }
     uint32_t *dist(uint32_t c) const {
         return off_dist[c] == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(block + off_dist[c]);
     }
@@ -151,7 +162,7 @@ struct Slot {
     BatchHdr *d_hdr = nullptr;
     uint32_t *h_stat = nullptr;  // pinned
     uint32_t *d_stat = nullptr;
-    cudaGraphExec_t graph[24] = {};  // tile_y 16/32/64 x denoise x closing x distance map
+    std::map<uint64_t, cudaGraphExec_t> graph;  // by graph_key of the launch plan
     cudaEvent_t ev[NUM_KERNELS + 1] = {};
     Batch *busy = nullptr;
 };
@@ -163,6 +174,7 @@ struct Batch {
     size_t scratch_bytes = 0;
     uint32_t nvol = 0;
     uint64_t voxels = 0;
+    uint32_t mrf_iters = 0;  // MRF steps launched (the largest limit in the batch)
     std::atomic<bool> done{false};
     int launch_err = SEG_OK;
     struct seg_ctx *ctx = nullptr;
@@ -251,6 +263,12 @@ void layout_request(Request &r) {
             r.off_dist[c] = off;
             off += al(4ull * g.n);
         }
+    r.off_den.assign(r.C, SIZE_MAX);
+    for (uint32_t c = 0; c < r.C; ++c)
+        if (r.g[c].dn_r || r.g[c].mrf_max) {
+            r.off_den[c] = off;
+            off += al(2ull * g.n * (r.g[c].mrf_max ? 2 : 1));
+        }
     r.off_input = off;
     if (r.owns_input) off += al(2ull * g.n * r.C);
     r.block_bytes = off;
@@ -284,6 +302,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
     uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0, cl = 0;
     uint32_t dtb[DT_NK] = {0, 0, 0, 0, 0, 0};
+    uint32_t mrft = 0, mrf_iters = 0;
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
         for (uint32_t c = 0; c < r->C; ++c) {
@@ -302,7 +321,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
             if (g.dn_r) {
                 V.dn_a = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
                 V.dn_b = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
-                V.dn_out = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
+                V.dn_out = r->den(c);
                 V.raw = V.dn_out;  // the smoothing reads the denoised image
                 const uint64_t w = 2ull * g.dn_r + 1;
                 V.dn_mul = (uint32_t)(((1ull << 32) + w - 1) / w);
@@ -330,6 +349,21 @@ void build_header(seg_ctx *ctx, Batch &b) {
             }
             V.cl_base = cl;
             cl += V.cl_n;
+            V.mrf_in = V.raw;
+            V.mrf_buf[0] = V.mrf_buf[1] = nullptr;
+            V.mrf_bits = nullptr;
+            V.mrf_max = g.mrf_max;
+            V.mrf_tiles = 0;
+            V.mrf_pad = 0;
+            V.mrf_tbase = mrft;
+            if (g.mrf_max) {
+                V.mrf_buf[0] = r->den(c, 0);
+                V.mrf_buf[1] = r->den(c, 1);
+                V.mrf_bits = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * 2048);
+                V.mrf_tiles = (uint32_t)cdiv((uint64_t)g.rows * cdiv(g.X, 8), MRF_TILE);
+                mrft += V.mrf_tiles;
+                mrf_iters = std::max(mrf_iters, g.mrf_max);
+            }
             V.dt_out = r->dist(c);
             V.dt_g = V.dt_h = nullptr;
             V.dt_sp = nullptr;
@@ -409,13 +443,18 @@ void build_header(seg_ctx *ctx, Batch &b) {
     h->dn_tiles = dnt;
     h->cl_items = cl;
     for (int k = 0; k < DT_NK; ++k) h->dt_items[k] = dtb[k];
+    h->mrf_tiles = mrft;
+    h->mrf_pad = 0;
+    b.mrf_iters = mrf_iters;
     h->tile_z = tz;
     h->tile_y = ty;
     b.nvol = v;
 }
 
-int graph_index(int ty, bool denoise, bool closing, bool distance) {
-    return (ty == 16 ? 0 : (ty == 32 ? 1 : 2)) + (denoise ? 3 : 0) + (closing ? 6 : 0) + (distance ? 12 : 0);
+// A captured graph fixes which optional kernels launch and how many MRF steps.
+uint64_t graph_key(const LaunchPlan &p) {
+    return (uint64_t)p.tile_y | (uint64_t)p.denoise << 8 | (uint64_t)p.closing << 9 | (uint64_t)p.distance << 10 |
+           (uint64_t)p.mrf_iters << 16;
 }
 
 // Enqueues descriptor upload, the pipeline and the status read-back.
@@ -495,9 +534,9 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
     ctx->plan.closing = s.h_hdr->cl_items > 0;
     ctx->plan.distance = false;
     for (int k = 0; k < DT_NK; ++k) ctx->plan.distance |= s.h_hdr->dt_items[k] > 0;
+    ctx->plan.mrf_iters = b.mrf_iters;
     if (ctx->graphs) {
-        cudaGraphExec_t &ge =
-            s.graph[graph_index(ctx->plan.tile_y, ctx->plan.denoise, ctx->plan.closing, ctx->plan.distance)];
+        cudaGraphExec_t &ge = s.graph[graph_key(ctx->plan)];
         if (!ge) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
@@ -533,6 +572,8 @@ void finalize_batch(seg_ctx *ctx, Slot &s) {
             r->thresh[c] = w[ST_THRESH];
             r->ncells[c] = w[ST_CELLS];
             r->errbits[c] = w[ST_ERROR];
+            r->mrf_steps[c] = w[ST_MRF_STEPS];
+            r->mrf_sel[c] = w[ST_MRF_SEL];
             if (w[ST_ERROR]) bad = true;
         }
         r->state = bad ? SEG_FAILED : SEG_DONE;
@@ -731,6 +772,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->plan.denoise = false;
     ctx->plan.closing = false;
     ctx->plan.distance = false;
+    ctx->plan.mrf_iters = 0;
     CK(configure_kernels(cfg->device, ctx->plan));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
@@ -772,7 +814,7 @@ int seg_destroy(seg_ctx *ctx) {
     }
     for (Slot &s : ctx->slots) {
         for (auto &g : s.graph)
-            if (g) cudaGraphExecDestroy(g);
+            if (g.second) cudaGraphExecDestroy(g.second);
         for (auto &e : s.ev)
             if (e) cudaEventDestroy(e);
         if (s.h_hdr) cudaFreeHost(s.h_hdr);
@@ -815,8 +857,10 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
         } else {
             dw = nullptr;
         }
+        const uint32_t mi = per_channel ? per_channel[c].mrf_iterations : 0u;
+        if (mi > MRF_MAX_ITER || (mi && dr)) return SEG_EINVAL;
         r->minvol[c] = m ? m : 1u;  // a cell has at least one voxel
-        r->g.push_back(geom(dims, r->minvol[c], dr, cr, dw));
+        r->g.push_back(geom(dims, r->minvol[c], dr, cr, dw, mi));
     }
     {
         uint64_t rl = 0;
@@ -826,6 +870,8 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
     }
     r->thresh.assign(channels, 0);
     r->ncells.assign(channels, 0);
+    r->mrf_steps.assign(channels, 0);
+    r->mrf_sel.assign(channels, 0);
     r->errbits.assign(channels, 0);
     r->owns_input = !on_device;
     if (on_device) r->user_dev = voxels;
@@ -958,6 +1004,35 @@ int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst, 
                                     ctx->read_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
     return cuda_fail(e, "seg_read_labels");
+}
+
+int seg_read_denoised(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst, uint64_t dst_elems,
+                      int dst_on_device, uint32_t *mrf_steps) {
+    if (!ctx || !dst) return SEG_EINVAL;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (r->state == SEG_PENDING) return SEG_ENOTREADY;
+        if (r->state == SEG_FAILED) return SEG_EFAILED;
+    }
+    if (channel >= r->C || !r->den(channel)) return SEG_EINVAL;
+    const uint64_t n = r->g[channel].n;
+    if (dst_elems < n) return SEG_ESMALL;
+    // the front end's image, or the MRF image that was kept
+    const uint16_t *src = r->den(channel);
+    if (r->g[channel].mrf_max) {
+        const uint32_t sel = r->mrf_sel[channel];
+        src = sel == 0 ? r->input(channel) : r->den(channel, (int)sel - 1);
+    }
+    if (mrf_steps) *mrf_steps = r->mrf_steps[channel];
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpyAsync(dst, src, 2ull * n,
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    ctx->read_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
+    return cuda_fail(e, "seg_read_denoised");
 }
 
 int seg_read_distance(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst, uint64_t dst_elems,

@@ -60,7 +60,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(seg.seg_cell_features) == 64
     assert ctypes.sizeof(seg.seg_dims) == 12
     assert ctypes.sizeof(seg.seg_config) == 48
-    assert ctypes.sizeof(seg.seg_channel_params) == 24
+    assert ctypes.sizeof(seg.seg_channel_params) == 28
 
 
 def test_binding_constants_match_header():
