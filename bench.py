@@ -329,11 +329,13 @@ def run_gpu(args):
     total_kernel_ms = sum(k["ms"] for k in kern.values())
     shares = {n: round(k["ms"] / total_kernel_ms, 4) for n, k in kern.items()} if total_kernel_ms else {}
     seg.seg_destroy(ctx)
-    denoise = closing = distmap = None
+    denoise = closing = distmap = mrfd = None
     if args.denoise_radius:
         denoise = denoise_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.denoise_radius)
     if args.closing_radius:
         closing = closing_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.closing_radius)
+    if args.mrf_iterations:
+        mrfd = mrf_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 3)), args.mrf_iterations)
     if args.distance_weights != "0":
         distmap = distance_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)),
                                [int(a) for a in args.distance_weights.split(",")])
@@ -418,6 +420,7 @@ def run_gpu(args):
             "denoise_front_end": denoise,
             "closing": closing,
             "distance_map": distmap,
+            "mrf_denoise": mrfd,
             "serving": serve,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
@@ -428,7 +431,7 @@ def run_gpu(args):
     return 0
 
 
-def option_run(seg, torch, d_in, dims, local, steps, denoise, closing, distance_weights=None):
+def option_run(seg, torch, d_in, dims, local, steps, denoise, closing, distance_weights=None, mrf_iterations=0):
     """The same workload, batched as in the main measurement, with per-channel
     options (denoise radii, closing radii, distance-map weights).  Returns
     Gvoxels/s of the whole stage, ms per step and the mean per-step
@@ -441,7 +444,8 @@ def option_run(seg, torch, d_in, dims, local, steps, denoise, closing, distance_
 
     def one_pass():
         reqs = [seg.seg_submit_volume(ctx, d_in[t], dims=(X, Y, Z), channels=C, denoise_radius=denoise,
-                                      closing_radius=closing, distance_weights=distance_weights)
+                                      closing_radius=closing, distance_weights=distance_weights,
+                                      mrf_iterations=mrf_iterations)
                 for t in range(T)]
         seg.seg_flush(ctx)
         for r in reqs:
@@ -525,6 +529,24 @@ def distance_run(seg, torch, d_in, dims, local, steps, weights):
             "kernel_hbm_frac": {n: (vox * algo[n] / (per[n] / 1e3) / 1e9) / peak
                                 for n in names if per[n] > 0.05 * dist_ms},
             "stage_hbm_frac": (vox * 4.125 / (dist_ms / 1e3) / 1e9) / peak if dist_ms else None}
+
+
+def mrf_run(seg, torch, d_in, dims, local, steps, iters):
+    """The MRF vessel denoise (Eqs. 2-3) on the vessel channel (the last one),
+    at most `iters` steps; every channel otherwise as in the main measurement."""
+    T, C = d_in.shape[0], d_in.shape[1]
+    X, Y, Z = dims
+    gv, ms, per = option_run(seg, torch, d_in, dims, local, steps, 0, 0, None, [0] * (C - 1) + [iters])
+    vox = T * X * Y * Z  # voxels through the MRF denoise per step
+    mrf_ms = per["mrf_stats"] + per["mrf_iterate"]
+    # algorithmic bytes: the statistics pass reads the input once (2 B); each
+    # step reads the current image and the input and writes the next (6 B)
+    return {"max_steps": iters, "channels": 1, "gvox_s": gv, "ms_per_step": ms,
+            "mrf_ms_per_step": mrf_ms,
+            "kernel_ms_per_step": {n: per[n] for n in ("mrf_stats", "mrf_iterate")},
+            "ms_per_mrf_step": per["mrf_iterate"] / iters if iters else None,
+            "step_hbm_frac": ((vox * 6.0 * iters / (per["mrf_iterate"] / 1e3) / 1e9) / peaks()[0]
+                              if per["mrf_iterate"] else None)}
 
 
 def plain_form(seg, torch, d_in, dims, local, steps):
@@ -659,6 +681,8 @@ def main():
                     help="also time the stage with the denoise front end on channel 0 (0 skips)")
     ap.add_argument("--closing-radius", type=int, default=1,
                     help="also time the stage with the foreground closed by this ball (0 skips)")
+    ap.add_argument("--mrf-iterations", type=int, default=20,
+                    help="also time the stage with the MRF vessel denoise, at most this many steps (0 skips)")
     ap.add_argument("--distance-weights", default="16,16,25",
                     help="also time the vessel-channel distance map with these weights of dx^2, dy^2, "
                          "dz^2 (0.8 x 0.8 x 1.0 um in 0.2 um units; 0 skips)")

@@ -109,9 +109,11 @@ struct VolDev {
     uint16_t *mrf_buf[2];     // steps: it 0 reads mrf_in, it > 0 mrf_buf[it & 1]; writes mrf_buf[(it + 1) & 1]
     uint32_t *mrf_bits;       // 2048 words: levels present in the input
     uint32_t mrf_max;         // step limit, 0 = off
-    uint32_t mrf_tiles;       // tiles of MRF_TILE octets (8 x-consecutive voxels)
-    uint32_t mrf_tbase;       // first flat MRF tile
-    uint32_t mrf_pad;
+    uint32_t mrf_tiles;       // k_mrf_stats tiles of MRF_TILE octets (8 x-consecutive voxels)
+    uint32_t mrf_tbase;       // first flat k_mrf_stats tile
+    uint32_t mrf_ctiles;      // k_mrf_step tiles: MRF_TX octets x MRF_TY rows, all of z
+    uint32_t mrf_cbase;       // first flat k_mrf_step tile
+    uint32_t mrf_vec;         // 1: X % 8 == 0 and the input 16-byte aligned (octets load as uint4)
 };
 
 // The distance-map kernels and their work items.  A volume takes the fused
@@ -128,7 +130,9 @@ enum DtKernel : int {
     DT_NK = 6,
 };
 constexpr int DZ_ELEMS = 8192;   // k_dist_z shared stack entries per block
-constexpr int MRF_TILE = 256;    // octets per MRF tile (one per thread)
+constexpr int MRF_TILE = 256;    // octets per k_mrf_stats tile (one per thread)
+constexpr int MRF_TX = 32;       // k_mrf_step tile: octets along x (one warp) ...
+constexpr int MRF_TY = 8;        // ... times rows, walked down z
 constexpr uint32_t MRF_MAX_ITER = 1000;
 
 // Batch header, followed in memory by VolDev[nvol].
@@ -144,8 +148,8 @@ struct BatchHdr {
     uint32_t dn_tiles;   // denoise median tiles over the batch
     uint32_t cl_items;   // closing dilation items over the batch
     uint32_t dt_items[DT_NK]; // distance-map items per DtKernel over the batch
-    uint32_t mrf_tiles;       // MRF tiles over the batch
-    uint32_t mrf_pad;
+    uint32_t mrf_tiles;       // k_mrf_stats tiles over the batch
+    uint32_t mrf_ctiles;      // k_mrf_step tiles over the batch
     VolDev vol[1];       // nvol entries
 };
 
@@ -179,7 +183,8 @@ struct LaunchPlan {
     int grid_dxy16;      // k_dist_xy<16>
     int grid_dxy32;      // k_dist_xy<32>
     int grid_dz;         // k_dist_z
-    int grid_mrf;        // k_mrf_stats, k_mrf_step
+    int grid_mrf;        // k_mrf_stats
+    int grid_mrfs;       // k_mrf_step
     uint32_t mrf_iters;  // k_mrf_step launches: the largest step limit in the batch (0: none)
 };
 

@@ -1948,39 +1948,99 @@ __device__ __forceinline__ unsigned long long mrf_block_sum(unsigned long long v
     return s;
 }
 
-// Levels present in the input (bitmap, set once per level) and the noise
-// estimate's sum S over every z-plane's interior of |[1 -2 1; -2 4 -2;
-// 1 -2 1] * I| (Immerkaer's mask), added into the volume's ST_MRF_E words.
+// The 8 voxels of an octet at p (16-byte aligned when `vec`), else the first
+// n of them.
+__device__ __forceinline__ void mrf_load8(const uint16_t *p, bool vec, uint32_t n, int32_t *v) {
+    if (vec) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[2 * j] = (int32_t)(w[j] & 0xFFFFu);
+            v[2 * j + 1] = (int32_t)(w[j] >> 16);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (uint32_t)j < n ? (int32_t)p[j] : 0;
+    }
+}
+
+// Levels present in the input and the noise estimate's sum S over every
+// z-plane's interior of |[1 -2 1; -2 4 -2; 1 -2 1] * I| (Immerkaer's mask),
+// added into the volume's ST_MRF_E words.  The levels collect in a shared
+// bitmap, merged into the volume's (nonzero words only) when the block moves
+// to another volume and at its end.
 __global__ void __launch_bounds__(MRF_TILE) k_mrf_stats(const BatchHdr *__restrict__ h) {
-    __shared__ VolIndex<&VolDev::mrf_tbase> VI;
     __shared__ unsigned long long red[MRF_TILE / 32];
-    VI.load(h);
-    for (uint32_t t = blockIdx.x; t < h->mrf_tiles; t += gridDim.x) {
-        const VolDev &V = h->vol[VI.find(h, t)];
-        const uint32_t X = V.X, Y = V.Y, OX = (X + 7) >> 3;
-        const uint32_t o = (t - V.mrf_tbase) * MRF_TILE + threadIdx.x;
-        unsigned long long s = 0;
-        if (o < V.rows * OX) {
-            const uint32_t row = o / OX, x0 = 8 * (o % OX), y = row % Y;
-            const uint16_t *r0 = V.mrf_in + (size_t)row * X;
-            const uint32_t xe = min(x0 + 8u, X);
-            for (uint32_t x = x0; x < xe; ++x) {
-                const uint32_t v = r0[x], bit = 1u << (v & 31u);
-                if (!(V.mrf_bits[v >> 5] & bit)) atomicOr(V.mrf_bits + (v >> 5), bit);
-            }
-            if (y >= 1 && y + 1 < Y) {
-                const uint16_t *rm = r0 - X, *rp = r0 + X;
-                for (uint32_t x = max(x0, 1u); x < xe && x + 1 < X; ++x) {
-                    const int32_t a = (int32_t)rm[x - 1] - 2 * (int32_t)rm[x] + (int32_t)rm[x + 1];
-                    const int32_t b = (int32_t)r0[x - 1] - 2 * (int32_t)r0[x] + (int32_t)r0[x + 1];
-                    const int32_t c = (int32_t)rp[x - 1] - 2 * (int32_t)rp[x] + (int32_t)rp[x + 1];
-                    s += (unsigned long long)abs(a - 2 * b + c);
-                }
+    __shared__ uint32_t sbits[2048];
+    for (int i = threadIdx.x; i < 2048; i += MRF_TILE) sbits[i] = 0u;
+    // a contiguous range of tiles per block, so it meets few volumes
+    const uint32_t T = h->mrf_tiles, G = gridDim.x;
+    const uint32_t tb = (uint32_t)(((uint64_t)T * blockIdx.x) / G);
+    const uint32_t te = (uint32_t)(((uint64_t)T * (blockIdx.x + 1)) / G);
+    uint32_t vi = 0;
+    while (vi + 1 < h->nvol && tb >= h->vol[vi + 1].mrf_tbase) ++vi;
+    unsigned long long s = 0;
+    __syncthreads();
+    auto flush = [&]() {  // this block's levels and sum for volume vi
+        const unsigned long long tot = mrf_block_sum(s, red);  // (barriers order sbits too)
+        s = 0;
+        const VolDev &V = h->vol[vi];
+        if (threadIdx.x == 0 && tot) atomicAdd(reinterpret_cast<unsigned long long *>(V.stat + ST_MRF_E), tot);
+        for (int i = threadIdx.x; i < 2048; i += MRF_TILE) {
+            const uint32_t w = sbits[i];
+            if (w) {
+                atomicOr(V.mrf_bits + i, w);
+                sbits[i] = 0u;
             }
         }
-        s = mrf_block_sum(s, red);
-        if (threadIdx.x == 0 && s) atomicAdd(reinterpret_cast<unsigned long long *>(V.stat + ST_MRF_E), s);
+        __syncthreads();
+    };
+    for (uint32_t t = tb; t < te; ++t) {
+        if (vi + 1 < h->nvol && t >= h->vol[vi + 1].mrf_tbase) {
+            flush();
+            do ++vi; while (vi + 1 < h->nvol && t >= h->vol[vi + 1].mrf_tbase);
+        }
+        const VolDev &V = h->vol[vi];
+        const uint32_t X = V.X, Y = V.Y, OX = (X + 7) >> 3;
+        const uint32_t o = (t - V.mrf_tbase) * MRF_TILE + threadIdx.x;
+        if (o >= V.rows * OX) continue;
+        const uint32_t row = o / OX, x0 = 8 * (o % OX), y = row % Y;
+        const uint16_t *r0 = V.mrf_in + (size_t)row * X + x0;
+        const uint32_t n = min(8u, X - x0);
+        const bool vec = n == 8u && V.mrf_vec;  // (mrf_buf is always aligned)
+        int32_t c[8];
+        mrf_load8(r0, vec, n, c);
+        for (uint32_t j = 0; j < n; ++j) atomicOr(sbits + (c[j] >> 5), 1u << (c[j] & 31));
+        if (y >= 1 && y + 1 < Y) {
+            int32_t a[8], b[8];
+            mrf_load8(r0 - X, vec, n, a);
+            mrf_load8(r0 + X, vec, n, b);
+            // second differences along x of the three rows, then along y
+            int32_t l0 = 0, la = 0, lb = 0, r0v = 0, ra = 0, rb = 0;
+            if (x0 > 0) {
+                l0 = r0[-1];
+                la = r0[-1 - (int)X];
+                lb = r0[-1 + (int)X];
+            }
+            if (x0 + 8 < X) {
+                r0v = r0[8];
+                ra = r0[8 - (int)X];
+                rb = r0[8 + (int)X];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t x = x0 + j;
+                if (x < 1 || x + 1 >= X || (uint32_t)j >= n) continue;
+                const int32_t cl = j > 0 ? c[j - 1] : l0, cr = j < 7 ? c[j + 1] : r0v;
+                const int32_t al = j > 0 ? a[j - 1] : la, ar = j < 7 ? a[j + 1] : ra;
+                const int32_t bl = j > 0 ? b[j - 1] : lb, br = j < 7 ? b[j + 1] : rb;
+                const int32_t da = al - 2 * a[j] + ar, dc = cl - 2 * c[j] + cr, db = bl - 2 * b[j] + br;
+                s += (unsigned long long)abs(da - 2 * dc + db);
+            }
+        }
     }
+    if (tb < te) flush();
 }
 
 // One warp per MRF volume: Delta from the levels present, and the bound
@@ -2047,75 +2107,163 @@ __global__ void k_mrf_prep(const BatchHdr *__restrict__ h) {
     }
 }
 
+// Octet helpers of the step kernel: 8 voxels packed two to a word.
+__device__ __forceinline__ uint4 mrf_oct(const uint16_t *p, bool vec, uint32_t n) {
+    if (vec) return *reinterpret_cast<const uint4 *>(p);
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t j = 0; j < n; ++j) w[j >> 1] |= (uint32_t)p[j] << (16 * (j & 1));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ void mrf_unpack(uint4 q, int32_t *v) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[2 * j] = (int32_t)(w[j] & 0xFFFFu);
+        v[2 * j + 1] = (int32_t)(w[j] >> 16);
+    }
+}
+
+// Eq. 3 on one octet c (n voxels valid; FULL: n = 8): left / right are the
+// x neighbours of its end voxels (-1: outside the volume), ym, yp, zm, zp
+// the octets of the neighbouring rows and planes (null: outside).  Adds the
+// octet's sum (I^{n+1} - I^0)^2 to e and whether it changed to `changed`;
+// returns the new octet (voxels past n are zero).
+template <bool FULL>
+__device__ __forceinline__ uint4 mrf_update(uint4 c, int32_t left, int32_t right, const uint4 *ym, const uint4 *yp,
+                                            const uint4 *zm, const uint4 *zp, uint4 org, int32_t delta, uint32_t n,
+                                            unsigned long long &e, bool &changed) {
+    int32_t v[8], nb[8];
+    int votes[8];
+    mrf_unpack(c, v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int32_t l = k > 0 ? v[k - 1] : left;
+        const int32_t r = k < 7 ? (FULL || (uint32_t)(k + 1) < n ? v[k + 1] : -1) : right;
+        votes[k] = (l >= 0 ? mrf_sgn(l - v[k]) : 0) + (r >= 0 ? mrf_sgn(r - v[k]) : 0);
+    }
+    const uint4 *rows[4] = {ym, yp, zm, zp};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!rows[q]) continue;
+        mrf_unpack(*rows[q], nb);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) votes[k] += mrf_sgn(nb[k] - v[k]);
+    }
+    mrf_unpack(org, nb);
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!FULL && (uint32_t)k >= n) continue;
+        const int32_t nv = min(max(v[k] + delta * mrf_sgn(votes[k]), 0), 65535);
+        const uint32_t d = (uint32_t)abs(nv - nb[k]);
+        e += (unsigned long long)d * d;
+        changed |= nv != v[k];
+        w[k >> 1] |= (uint32_t)nv << (16 * (k & 1));
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ int32_t mrf_clamp1(int32_t d) { return min(max(d, -1), 1); }  // sgn of an integer
+
+// Eq. 3 on a whole octet with comparisons shared where two voxels compare
+// with each other: inside the octet each x pair is compared once, and along
+// z the comparison of a voxel with the plane above is, negated, the next
+// plane's comparison with the plane below (za: in, the previous plane's
+// comparisons with its plane above, or 0 at z = 0; out, this plane's).
+__device__ __forceinline__ uint4 mrf_update_full(uint4 c, int32_t left, int32_t right, const uint4 *ym,
+                                                 const uint4 *yp, const uint4 *zp, int32_t *za, uint4 org,
+                                                 int32_t delta, unsigned long long &e, bool &changed) {
+    int32_t v[8], nb[8], votes[8];
+    mrf_unpack(c, v);
+    int32_t px[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) px[k] = mrf_clamp1(v[k + 1] - v[k]);
+    votes[0] = (left >= 0 ? mrf_clamp1(left - v[0]) : 0) + px[0] - za[0];
+#pragma unroll
+    for (int k = 1; k < 7; ++k) votes[k] = px[k] - px[k - 1] - za[k];
+    votes[7] = (right >= 0 ? mrf_clamp1(right - v[7]) : 0) - px[6] - za[7];
+    if (ym) {
+        mrf_unpack(*ym, nb);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) votes[k] += mrf_clamp1(nb[k] - v[k]);
+    }
+    if (yp) {
+        mrf_unpack(*yp, nb);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) votes[k] += mrf_clamp1(nb[k] - v[k]);
+    }
+    if (zp) {
+        mrf_unpack(*zp, nb);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            za[k] = mrf_clamp1(nb[k] - v[k]);
+            votes[k] += za[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) za[k] = 0;
+    }
+    mrf_unpack(org, nb);
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int32_t a = min(max(v[2 * j] + delta * mrf_clamp1(votes[2 * j]), 0), 65535);
+        const int32_t b = min(max(v[2 * j + 1] + delta * mrf_clamp1(votes[2 * j + 1]), 0), 65535);
+        const uint32_t da = (uint32_t)abs(a - nb[2 * j]), db = (uint32_t)abs(b - nb[2 * j + 1]);
+        e += (unsigned long long)da * da + (unsigned long long)db * db;
+        w[j] = (uint32_t)a | (uint32_t)b << 16;
+    }
+    const uint4 r = make_uint4(w[0], w[1], w[2], w[3]);
+    changed |= ((r.x ^ c.x) | (r.y ^ c.y) | (r.z ^ c.z) | (r.w ^ c.w)) != 0u;
+    return r;
+}
+
 // Step `it` of every MRF volume not yet stopped: reads mrf_in (it = 0) or
 // mrf_buf[it & 1], writes mrf_buf[(it + 1) & 1], and adds the step's
 // sum (I^{it+1} - I^0)^2 and whether anything changed to the volume's
-// status words.  The block that finishes the volume's last tile decides:
-// stop at a step that changes nothing or strays too far (keeping I^it), or
-// at the step limit; when stopping it points the volume's raw input for the
-// smoothing (in the device copy of the batch descriptor) at the kept image.
-__global__ void __launch_bounds__(MRF_TILE) k_mrf_step(const BatchHdr *__restrict__ h, uint32_t it) {
-    __shared__ VolIndex<&VolDev::mrf_tbase> VI;
-    __shared__ unsigned long long red[MRF_TILE / 32];
-    __shared__ uint32_t chg_any;  // some voxel of the tile changed (0 between tiles)
+// status words.  A tile is MRF_TX octets x MRF_TY rows walked down z: each
+// thread keeps its octet of planes z - 1, z, z + 1 in registers, the rows
+// y - 1 and y + 1 come from the neighbouring threads through shared memory
+// and the x neighbours by shuffles, so every voxel of the current image is
+// read from memory about once per step.  Blocks take contiguous tile ranges
+// and flush their sums once per volume; the block whose flush completes a
+// volume decides: stop at a step that changes nothing or strays too far
+// (keeping I^it), or at the step limit; when stopping it points the volume's
+// raw input for the smoothing (in the device copy of the batch descriptor)
+// at the kept image.
+__global__ void __launch_bounds__(MRF_TX * MRF_TY, 3) k_mrf_step(const BatchHdr *__restrict__ h, uint32_t it) {
+    __shared__ uint4 srow[MRF_TY + 2][MRF_TX];  // plane z, rows y0 - 1 .. y0 + MRF_TY
+    __shared__ unsigned long long red[MRF_TX * MRF_TY / 32];
+    __shared__ uint32_t chg_any;  // some voxel of the block's tiles changed (0 between volumes)
     if (threadIdx.x == 0) chg_any = 0u;
-    VI.load(h);  // (its barrier orders the store above)
-    for (uint32_t t = blockIdx.x; t < h->mrf_tiles; t += gridDim.x) {
-        const uint32_t vi = VI.find(h, t);
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const uint32_t T = h->mrf_ctiles, G = gridDim.x;
+    const uint32_t tb = (uint32_t)(((uint64_t)T * blockIdx.x) / G);
+    const uint32_t te = (uint32_t)(((uint64_t)T * (blockIdx.x + 1)) / G);
+    uint32_t vi = 0;
+    while (vi + 1 < h->nvol && tb >= h->vol[vi + 1].mrf_cbase) ++vi;
+    unsigned long long e = 0;
+    bool changed = false;
+    uint32_t ntile = 0;
+    __syncthreads();
+    auto flush = [&]() {  // this block's tiles of volume vi
+        if (changed) chg_any = 1u;  // benign race: every writer stores 1
+        const unsigned long long sum = mrf_block_sum(e, red);  // (its barriers also order chg_any)
         const VolDev &V = h->vol[vi];
         uint32_t *st = V.stat;
-        if (it >= V.mrf_max || st[ST_MRF_DONE]) continue;  // the same for the whole block
-        const uint32_t X = V.X, Y = V.Y, Z = V.Z, OX = (X + 7) >> 3;
-        const size_t plane = (size_t)X * Y;
-        const uint16_t *cur = it == 0 ? V.mrf_in : V.mrf_buf[it & 1u];
-        uint16_t *nxt = V.mrf_buf[(it + 1u) & 1u];
-        const int32_t delta = (int32_t)st[ST_MRF_DELTA];
-        const uint32_t o = (t - V.mrf_tbase) * MRF_TILE + threadIdx.x;
-        unsigned long long e = 0;
-        bool changed = false;
-        if (o < V.rows * OX) {
-            const uint32_t row = o / OX, x0 = 8 * (o % OX), y = row % Y, z = row / Y;
-            const size_t base = (size_t)row * X;
-            const uint16_t *c0 = cur + base;
-            const uint16_t *ym = y > 0 ? c0 - X : nullptr, *yp = y + 1 < Y ? c0 + X : nullptr;
-            const uint16_t *zm = z > 0 ? c0 - plane : nullptr, *zp = z + 1 < Z ? c0 + plane : nullptr;
-            const uint16_t *org = V.mrf_in + base;
-            const uint32_t xe = min(x0 + 8u, X);
-            int32_t left = x0 > 0 ? (int32_t)c0[x0 - 1] : -1;
-            for (uint32_t x = x0; x < xe; ++x) {
-                const int32_t c = c0[x];
-                const int32_t right = x + 1 < X ? (int32_t)c0[x + 1] : -1;
-                int votes = 0;
-                if (left >= 0) votes += mrf_sgn(left - c);
-                if (right >= 0) votes += mrf_sgn(right - c);
-                if (ym) votes += mrf_sgn((int32_t)ym[x] - c);
-                if (yp) votes += mrf_sgn((int32_t)yp[x] - c);
-                if (zm) votes += mrf_sgn((int32_t)zm[x] - c);
-                if (zp) votes += mrf_sgn((int32_t)zp[x] - c);
-                const int32_t nv = min(max(c + delta * mrf_sgn(votes), 0), 65535);
-                nxt[base + x] = (uint16_t)nv;
-                const int32_t d = nv - (int32_t)org[x];
-                e += (unsigned long long)((int64_t)d * d);
-                changed |= nv != c;
-                left = c;
-            }
-        }
-        if (changed) chg_any = 1u;  // benign race: every writer stores 1
-        e = mrf_block_sum(e, red);  // (its barriers also order chg_any)
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && ntile) {
             unsigned long long *E = reinterpret_cast<unsigned long long *>(st + ST_MRF_E);
-            if (e) atomicAdd(E, e);
+            if (sum) atomicAdd(E, sum);
             if (chg_any) atomicOr(st + ST_MRF_CHG, 1u);
-            chg_any = 0u;
             __threadfence();
-            if (atomicAdd(st + ST_MRF_CNT, 1u) == V.mrf_tiles - 1u) {
+            if (atomicAdd(st + ST_MRF_CNT, ntile) + ntile == V.mrf_ctiles) {
                 // every tile of this volume is in: decide
                 __threadfence();
-                const unsigned long long sum = atomicAdd(E, 0ull);
+                const unsigned long long tot = atomicAdd(E, 0ull);
                 const uint32_t chg = atomicAdd(st + ST_MRF_CHG, 0u);
                 const double limit = *reinterpret_cast<const volatile double *>(st + ST_MRF_LIMIT);
                 uint32_t sel, steps, done;
-                if (!chg || __ull2double_rn(sum) > limit) {
+                if (!chg || __ull2double_rn(tot) > limit) {
                     done = 1u;  // keep I^it
                     steps = it;
                     sel = it == 0 ? 0u : 1u + (it & 1u);
@@ -2138,8 +2286,80 @@ __global__ void __launch_bounds__(MRF_TILE) k_mrf_step(const BatchHdr *__restric
                 st[ST_MRF_CNT] = 0u;
             }
         }
-        __syncthreads();  // chg_any and red are reused by the next tile
+        if (threadIdx.x == 0) chg_any = 0u;
+        e = 0;
+        changed = false;
+        ntile = 0;
+        __syncthreads();
+    };
+    for (uint32_t t = tb; t < te; ++t) {
+        if (vi + 1 < h->nvol && t >= h->vol[vi + 1].mrf_cbase) {
+            flush();
+            do ++vi; while (vi + 1 < h->nvol && t >= h->vol[vi + 1].mrf_cbase);
+        }
+        const VolDev &V = h->vol[vi];
+        // volumes that stopped (or never started) are left alone; the flag
+        // was set by an earlier launch, so it is the same for every thread
+        if (it >= V.mrf_max || V.stat[ST_MRF_DONE]) continue;
+        ++ntile;
+        const uint32_t X = V.X, Y = V.Y, Z = V.Z, OX = (X + 7) >> 3;
+        const uint32_t ntx = (OX + MRF_TX - 1) / MRF_TX;
+        const uint32_t lt = t - V.mrf_cbase;
+        const uint32_t ox = (lt % ntx) * MRF_TX + lx, y0 = (lt / ntx) * MRF_TY, y = y0 + ly;
+        const uint32_t x0 = 8 * ox;
+        const bool live = ox < OX && y < Y;
+        const uint32_t n = live ? min(8u, X - x0) : 0u;
+        const bool vec = n == 8u && V.mrf_vec;  // (mrf_buf is always aligned)
+        const size_t plane = (size_t)X * Y;
+        const uint16_t *cur = it == 0 ? V.mrf_in : V.mrf_buf[it & 1u];
+        uint16_t *nxt = V.mrf_buf[(it + 1u) & 1u];
+        const int32_t delta = (int32_t)V.stat[ST_MRF_DELTA];
+        const size_t off = (size_t)y * X + x0;  // this octet in plane 0
+        // halo rows of the tile (loaded by the first and last warp)
+        const bool hrow = (ly == 0 && y0 > 0) || (ly == MRF_TY - 1 && y0 + MRF_TY < Y);
+        const uint32_t hy = ly == 0 ? y0 - 1 : y0 + MRF_TY;
+        const uint32_t hn = (hrow && ox < OX) ? min(8u, X - x0) : 0u;
+        const size_t hoff = (size_t)hy * X + x0;
+        uint4 below = make_uint4(0, 0, 0, 0), c = below, above = below;
+        int32_t za[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // full octets: comparisons with the plane above
+        if (n) c = mrf_oct(cur + off, vec, n);
+        if (n && Z > 1) above = mrf_oct(cur + plane + off, vec, n);
+        for (uint32_t z = 0; z < Z; ++z) {
+            const size_t zo = (size_t)z * plane;
+            srow[ly + 1][lx] = c;
+            if (hn) srow[ly == 0 ? 0 : MRF_TY + 1][lx] = mrf_oct(cur + zo + hoff, hn == 8u && V.mrf_vec, hn);
+            // x neighbours: the next octets of the row, or memory at the tile's ends
+            const uint32_t lnb = __shfl_up_sync(FULL, c.w >> 16, 1);
+            const uint32_t rnb = __shfl_down_sync(FULL, c.x & 0xFFFFu, 1);
+            __syncthreads();
+            if (n) {
+                const int32_t left = x0 == 0 ? -1 : (lx > 0 ? (int32_t)lnb : (int32_t)cur[zo + off - 1]);
+                const int32_t right = x0 + 8 >= X ? -1 : (lx < 31 ? (int32_t)rnb : (int32_t)cur[zo + off + 8]);
+                const uint4 *ym = y > 0 ? &srow[ly][lx] : nullptr;
+                const uint4 *yp = y + 1 < Y ? &srow[ly + 2][lx] : nullptr;
+                const uint4 org = mrf_oct(V.mrf_in + zo + off, vec, n);
+                uint4 res;
+                if (n == 8u)
+                    res = mrf_update_full(c, left, right, ym, yp, z + 1 < Z ? &above : nullptr, za, org, delta, e,
+                                          changed);
+                else
+                    res = mrf_update<false>(c, left, right, ym, yp, z > 0 ? &below : nullptr,
+                                            z + 1 < Z ? &above : nullptr, org, delta, n, e, changed);
+                uint16_t *dst = nxt + zo + off;
+                if (vec) {
+                    *reinterpret_cast<uint4 *>(dst) = res;
+                } else {
+                    const uint32_t w[4] = {res.x, res.y, res.z, res.w};
+                    for (uint32_t k = 0; k < n; ++k) dst[k] = (uint16_t)(w[k >> 1] >> (16 * (k & 1)));
+                }
+            }
+            below = c;
+            c = above;
+            if (n && z + 2 < Z) above = mrf_oct(cur + zo + 2 * plane + off, vec, n);
+            __syncthreads();  // srow is rewritten for the next plane
+        }
     }
+    if (tb < te) flush();
 }
 
 // ---------------------------------------------------------------------------
@@ -2767,9 +2987,8 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     if ((e = resident((const void *)k_dist_line<2>, 256, &g2)) != cudaSuccess) return e;
     if ((e = resident((const void *)k_dist_line<1>, 256, &g3)) != cudaSuccess) return e;
     plan.grid_dist = std::min(g1, std::min(g2, g3));
-    if ((e = resident((const void *)k_mrf_stats, MRF_TILE, &g1)) != cudaSuccess) return e;
-    if ((e = resident((const void *)k_mrf_step, MRF_TILE, &g2)) != cudaSuccess) return e;
-    plan.grid_mrf = std::min(g1, g2);
+    if ((e = resident((const void *)k_mrf_stats, MRF_TILE, &plan.grid_mrf)) != cudaSuccess) return e;
+    if ((e = resident((const void *)k_mrf_step, MRF_TX * MRF_TY, &plan.grid_mrfs)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_dist_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DZ_SMEM)) !=
         cudaSuccess)
         return e;
@@ -2835,7 +3054,7 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
         k_mrf_prep<<<p.grid_vols, 32, 0, s>>>(d);
     }
     rec();
-    for (uint32_t it = 0; it < p.mrf_iters; ++it) k_mrf_step<<<p.grid_mrf, MRF_TILE, 0, s>>>(d, it);
+    for (uint32_t it = 0; it < p.mrf_iters; ++it) k_mrf_step<<<p.grid_mrfs, MRF_TX * MRF_TY, 0, s>>>(d, it);
     cudaError_t e;
     switch (p.tile_y) {
         case 16: e = launch_tile_kernels<16>(d, p, s, ev, k); break;

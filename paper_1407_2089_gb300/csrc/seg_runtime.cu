@@ -302,7 +302,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
     uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0, cl = 0;
     uint32_t dtb[DT_NK] = {0, 0, 0, 0, 0, 0};
-    uint32_t mrft = 0, mrf_iters = 0;
+    uint32_t mrft = 0, mrfc = 0, mrf_iters = 0;
     char *sp = b.scratch;
     for (Request *r : b.reqs) {
         for (uint32_t c = 0; c < r->C; ++c) {
@@ -354,14 +354,18 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.mrf_bits = nullptr;
             V.mrf_max = g.mrf_max;
             V.mrf_tiles = 0;
-            V.mrf_pad = 0;
+            V.mrf_vec = (g.X % 8u == 0u && (reinterpret_cast<uintptr_t>(V.mrf_in) & 15u) == 0u) ? 1u : 0u;
             V.mrf_tbase = mrft;
+            V.mrf_ctiles = 0;
+            V.mrf_cbase = mrfc;
             if (g.mrf_max) {
                 V.mrf_buf[0] = r->den(c, 0);
                 V.mrf_buf[1] = r->den(c, 1);
                 V.mrf_bits = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * 2048);
                 V.mrf_tiles = (uint32_t)cdiv((uint64_t)g.rows * cdiv(g.X, 8), MRF_TILE);
                 mrft += V.mrf_tiles;
+                V.mrf_ctiles = (uint32_t)(cdiv(cdiv(g.X, 8), MRF_TX) * cdiv(g.Y, MRF_TY));
+                mrfc += V.mrf_ctiles;
                 mrf_iters = std::max(mrf_iters, g.mrf_max);
             }
             V.dt_out = r->dist(c);
@@ -444,7 +448,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     h->cl_items = cl;
     for (int k = 0; k < DT_NK; ++k) h->dt_items[k] = dtb[k];
     h->mrf_tiles = mrft;
-    h->mrf_pad = 0;
+    h->mrf_ctiles = mrfc;
     b.mrf_iters = mrf_iters;
     h->tile_z = tz;
     h->tile_y = ty;

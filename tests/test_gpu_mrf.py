@@ -153,3 +153,23 @@ def test_vessel_frame_full_size(seg, ctx):
     vol = synth.TimeLapse(frames=1).frame(0, 1)
     steps = run(seg, ctx, vol, 30, min_volume=30, what="vessel frame")
     assert steps > 0
+
+
+def test_unaligned_device_input(seg, ctx):
+    # a device input 2 bytes past a 16-byte boundary takes the scalar loads
+    import torch
+    vol = vessels((48, 20, 6), 31)
+    flat = torch.zeros(vol.size + 8, dtype=torch.int16, device="cuda:0")
+    flat[1:1 + vol.size] = torch.from_numpy(vol.reshape(-1).view(np.int16)).cuda()
+    d = flat[1:1 + vol.size].view(vol.shape)
+    assert d.data_ptr() % 16 == 2
+    req = seg.seg_submit_volume(ctx, d, min_volume=5, mrf_iterations=9)
+    seg.seg_flush(ctx)
+    try:
+        assert seg.seg_wait(ctx, req) == seg.SEG_DONE
+        den = np.empty(vol.shape, np.uint16)
+        steps = seg.seg_read_denoised(ctx, req, 0, den)
+    finally:
+        seg.seg_release(ctx, req)
+    want, wsteps = oracle.mrf(vol, 9)
+    assert steps == wsteps and np.array_equal(den, want)
