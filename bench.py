@@ -55,7 +55,7 @@ KERNEL_BYTES_PER_VOXEL = {
 # than L2); the per-launch figure scales with the voxels a launch processes
 # since every 512x512x64 volume is tiled the same way.
 KERNEL_TRAFFIC_BYTES_PER_VOXEL = {
-    "smooth_hist_otsu": 7.54,      # 5.70 read (halo lines re-read) + 1.84 smoothed write
+    "smooth_hist_otsu": 7.69,      # 5.88 read (halo lines re-read) + 1.81 smoothed write
 }
 
 
