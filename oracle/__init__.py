@@ -86,6 +86,15 @@ def _load():
         lib.oracle_mrf.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u16p,
                                    u32p]
         lib.oracle_mrf.restype = ctypes.c_int
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.oracle_reg_sums.argtypes = [u16p, u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, i32p, u64p]
+        lib.oracle_reg_sums.restype = None
+        lib.oracle_normcov.argtypes = [u64p, ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_normcov.restype = ctypes.c_double
+        lib.oracle_register.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_uint32, i32p, i32p, ctypes.c_uint32, i32p, vp,
+                                        ctypes.c_uint32, u32p]
+        lib.oracle_register.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -286,6 +295,52 @@ def mrf(vol: np.ndarray, max_iter: int):
     if rc:
         raise RuntimeError("oracle_mrf failed: %d" % rc)
     return out, int(it[0])
+
+
+EDGE_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("shift", "<i4", (3,)), ("pad0", "<u4"),
+                       ("score", "<f8"), ("in_tree", "<u4"), ("pad1", "<u4")])
+assert EDGE_DTYPE.itemsize == 40
+
+
+def reg_sums(A: np.ndarray, B: np.ndarray, d) -> np.ndarray:
+    """(N, Sa, Sb, Saa, Sbb, Sab) over the voxels tile A (origin 0) shares with
+    tile B placed at origin d = (dx, dy, dz) in A's coordinates."""
+    A = np.ascontiguousarray(A, dtype=np.uint16)
+    B = np.ascontiguousarray(B, dtype=np.uint16)
+    X, Y, Z = _dims(A)
+    dd = np.array(d, dtype=np.int32)
+    out = np.zeros(6, dtype=np.uint64)
+    _load().oracle_reg_sums(_ptr(A, ctypes.c_uint16), _ptr(B, ctypes.c_uint16), X, Y, Z,
+                            _ptr(dd, ctypes.c_int32), _ptr(out, ctypes.c_uint64))
+    return out
+
+
+def normcov(sums):
+    """Eq. 4 (Pearson correlation) from the six sums; None when undefined."""
+    s = np.ascontiguousarray(sums, dtype=np.uint64)
+    ok = ctypes.c_int()
+    r = _load().oracle_normcov(_ptr(s, ctypes.c_uint64), ctypes.byref(ok))
+    return float(r) if ok.value else None
+
+
+def register(tiles, stage, radius, root=0):
+    """Montage registration: (delta [n, 3] int32, edges structured array)."""
+    tiles = [np.ascontiguousarray(t, dtype=np.uint16) for t in tiles]
+    X, Y, Z = _dims(tiles[0])
+    n = len(tiles)
+    ptrs = (ctypes.c_void_p * n)(*[t.ctypes.data for t in tiles])
+    st = np.ascontiguousarray(stage, dtype=np.int32).reshape(n, 3)
+    rad = np.ascontiguousarray(radius, dtype=np.int32)
+    delta = np.zeros((n, 3), dtype=np.int32)
+    cap = n * (n - 1) // 2
+    edges = np.zeros(max(cap, 1), dtype=EDGE_DTYPE)
+    ne = np.zeros(1, dtype=np.uint32)
+    rc = _load().oracle_register(ptrs, n, X, Y, Z, _ptr(st, ctypes.c_int32), _ptr(rad, ctypes.c_int32),
+                                 int(root), _ptr(delta, ctypes.c_int32), edges.ctypes.data, cap,
+                                 _ptr(ne, ctypes.c_uint32))
+    if rc:
+        raise RuntimeError("oracle_register failed: %d" % rc)
+    return delta, edges[: int(ne[0])].copy()
 
 
 def segment(vol: np.ndarray, min_volume: int = 30, keep_hist: bool = False,

@@ -573,6 +573,175 @@ int oracle_mrf(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32_t m
     return ORACLE_OK;
 }
 
+/* ---- Montage registration (Registration section, Eq. 4) -------------------
+ *
+ * Overlapping tiles of a montage are placed at their stage positions; each
+ * overlapping pair is scored at every shift of the second tile inside a
+ * window around its stage position by the normalized covariance of Eq. 4
+ * over the voxels the two tiles then share; each pair keeps its best shift;
+ * a maximum spanning tree of the pair graph (dropping the lowest-scoring
+ * edges) anchors one tile and gives every other tile the sum of the shifts
+ * along its tree path.  Readings:
+ *   - normcov(A, B) = sum (A - muA)(B - muB) / (sigmaA sigmaB) over the
+ *     overlap is read as the Pearson correlation, sigma the root of the
+ *     summed squared deviations, so the score does not grow with the size of
+ *     the overlap (which changes with the shift).  From exact integer sums:
+ *     num = N Sab - Sa Sb, va = N Saa - Sa^2, vb = N Sbb - Sb^2 (128-bit),
+ *     rho = (double)num / sqrt((double)va * (double)vb); undefined when the
+ *     overlap is empty or va or vb is 0.
+ *   - A pair is an edge when its stage boxes overlap.  Its shift s (of the
+ *     second tile, b > a) runs over [-r, r] per axis, z outermost, then y,
+ *     then x; the first shift with the largest defined score is kept.  An
+ *     edge with no defined score stays out of the tree.
+ *   - The maximum spanning tree is Kruskal's: edges by score, highest first,
+ *     ties by (a, b); the root keeps its stage position; delta(b) =
+ *     delta(a) + s over a tree edge (a, b), delta(a) = delta(b) - s; tiles
+ *     outside the root's tree keep delta 0.
+ */
+typedef struct {
+    uint32_t a, b;
+    int32_t shift[3];
+    uint32_t pad0;
+    double score;
+    uint32_t in_tree;
+    uint32_t pad1;
+} oracle_edge;
+
+/* Sums over the voxels shared by tile A (origin 0) and tile B placed with its
+ * origin at d in A's coordinates: out = {N, Sa, Sb, Saa, Sbb, Sab}. */
+void oracle_reg_sums(const uint16_t *A, const uint16_t *B, uint32_t X, uint32_t Y, uint32_t Z, const int32_t *d,
+                     uint64_t *out) {
+    int64_t lo[3], hi[3];
+    const int64_t D[3] = {X, Y, Z};
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = d[k] > 0 ? d[k] : 0;
+        hi[k] = d[k] + D[k] < D[k] ? d[k] + D[k] : D[k];
+    }
+    uint64_t n = 0, sa = 0, sb = 0, saa = 0, sbb = 0, sab = 0;
+    for (int64_t z = lo[2]; z < hi[2]; ++z)
+        for (int64_t y = lo[1]; y < hi[1]; ++y)
+            for (int64_t x = lo[0]; x < hi[0]; ++x) {
+                const uint64_t a = A[x + X * (y + Y * z)];
+                const uint64_t b = B[(x - d[0]) + X * ((y - d[1]) + Y * (z - d[2]))];
+                ++n;
+                sa += a;
+                sb += b;
+                saa += a * a;
+                sbb += b * b;
+                sab += a * b;
+            }
+    out[0] = n; out[1] = sa; out[2] = sb; out[3] = saa; out[4] = sbb; out[5] = sab;
+}
+
+/* Eq. 4 as read above from the six sums; *defined = 0 when undefined. */
+double oracle_normcov(const uint64_t *s, int *defined) {
+    const __int128 n = (__int128)s[0];
+    const __int128 num = n * (__int128)s[5] - (__int128)s[1] * (__int128)s[2];
+    const __int128 va = n * (__int128)s[3] - (__int128)s[1] * (__int128)s[1];
+    const __int128 vb = n * (__int128)s[4] - (__int128)s[2] * (__int128)s[2];
+    if (s[0] == 0 || va == 0 || vb == 0) {
+        *defined = 0;
+        return 0.0;
+    }
+    *defined = 1;
+    return (double)num / sqrt((double)va * (double)vb);
+}
+
+static uint32_t uf_find(uint32_t *p, uint32_t i) {
+    while (p[i] != i) i = p[i];
+    return i;
+}
+
+int oracle_register(const uint16_t *const *tiles, uint32_t nt, uint32_t X, uint32_t Y, uint32_t Z,
+                    const int32_t *stage, const int32_t *radius, uint32_t root, int32_t *delta,
+                    oracle_edge *edges, uint32_t cap, uint32_t *n_edges) {
+    if (!tiles || !stage || !radius || !delta || nt == 0 || root >= nt || X == 0 || Y == 0 || Z == 0)
+        return ORACLE_EINVAL;
+    const int64_t D[3] = {X, Y, Z};
+    uint32_t ne = 0;
+    for (uint32_t a = 0; a < nt; ++a)
+        for (uint32_t b = a + 1; b < nt; ++b) {
+            int overlap = 1;
+            for (int k = 0; k < 3; ++k) {
+                const int64_t o = (int64_t)stage[3 * b + k] - stage[3 * a + k];
+                if (o >= D[k] || -o >= D[k]) overlap = 0;
+            }
+            if (!overlap) continue;
+            if (ne < cap && edges) {
+                oracle_edge *e = &edges[ne];
+                memset(e, 0, sizeof(*e));
+                e->a = a;
+                e->b = b;
+                e->score = -2.0;  /* no defined score */
+                for (int32_t sz = -radius[2]; sz <= radius[2]; ++sz)
+                    for (int32_t sy = -radius[1]; sy <= radius[1]; ++sy)
+                        for (int32_t sx = -radius[0]; sx <= radius[0]; ++sx) {
+                            const int32_t d[3] = {stage[3 * b] - stage[3 * a] + sx,
+                                                  stage[3 * b + 1] - stage[3 * a + 1] + sy,
+                                                  stage[3 * b + 2] - stage[3 * a + 2] + sz};
+                            uint64_t sums[6];
+                            oracle_reg_sums(tiles[a], tiles[b], X, Y, Z, d, sums);
+                            int ok;
+                            const double r = oracle_normcov(sums, &ok);
+                            if (ok && r > e->score) {
+                                e->score = r;
+                                e->shift[0] = sx;
+                                e->shift[1] = sy;
+                                e->shift[2] = sz;
+                            }
+                        }
+            }
+            ++ne;
+        }
+    if (n_edges) *n_edges = ne;
+    if (ne > cap || !edges) return ne > cap ? ORACLE_ESMALL : ORACLE_OK;
+    /* Kruskal: edges by score, highest first, ties by (a, b) (selection order) */
+    uint32_t *order = (uint32_t *)malloc((ne ? ne : 1) * sizeof(uint32_t));
+    uint32_t *par = (uint32_t *)malloc(nt * sizeof(uint32_t));
+    if (!order || !par) {
+        free(order);
+        free(par);
+        return ORACLE_ENOMEM;
+    }
+    for (uint32_t i = 0; i < ne; ++i) order[i] = i;
+    for (uint32_t i = 0; i < ne; ++i)  /* insertion sort: stable, so ties keep (a, b) order */
+        for (uint32_t j = i; j > 0 && edges[order[j]].score > edges[order[j - 1]].score; --j) {
+            const uint32_t t = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = t;
+        }
+    for (uint32_t i = 0; i < nt; ++i) par[i] = i;
+    for (uint32_t i = 0; i < ne; ++i) {
+        oracle_edge *e = &edges[order[i]];
+        if (e->score < -1.5) continue;  /* undefined */
+        const uint32_t ra = uf_find(par, e->a), rb = uf_find(par, e->b);
+        if (ra == rb) continue;
+        par[ra] = rb;
+        e->in_tree = 1;
+    }
+    /* deltas along the tree from the root (repeated sweeps until nothing changes) */
+    uint8_t *known = (uint8_t *)calloc(nt, 1);
+    for (uint32_t i = 0; i < 3 * nt; ++i) delta[i] = 0;
+    known[root] = 1;
+    for (int grew = 1; grew;) {
+        grew = 0;
+        for (uint32_t i = 0; i < ne; ++i) {
+            const oracle_edge *e = &edges[i];
+            if (!e->in_tree || known[e->a] == known[e->b]) continue;
+            if (known[e->a])
+                for (int k = 0; k < 3; ++k) delta[3 * e->b + k] = delta[3 * e->a + k] + e->shift[k];
+            else
+                for (int k = 0; k < 3; ++k) delta[3 * e->a + k] = delta[3 * e->b + k] - e->shift[k];
+            known[e->a] = known[e->b] = 1;
+            grew = 1;
+        }
+    }
+    free(known);
+    free(order);
+    free(par);
+    return ORACLE_OK;
+}
+
 /* The whole stage for one frame and channel: smooth, histogram, Otsu,
  * threshold (foreground iff s > t*), label, filter, features.
  * hist (65536 entries) and smoothed (n entries) are optional outputs. */

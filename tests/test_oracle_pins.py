@@ -724,3 +724,110 @@ def test_segment_with_mrf_is_segment_of_denoised():
     assert r.mrf_steps == it and np.array_equal(r.denoised, den)
     ref = oracle.segment(den, min_volume=5)
     assert np.array_equal(r.labels, ref.labels) and r.threshold == ref.threshold
+
+
+# ---- montage registration (Registration section, Eq. 4) --------------------
+
+def _montage(rng, grid, dims, overlap, jitter, radius):
+    """Tiles cut from one textured global volume at true positions; the stage
+    positions are the true ones moved by at most `radius` voxels per axis."""
+    X, Y, Z = dims
+    nx, ny = grid
+    step = (X - overlap[0], Y - overlap[1])
+    true, stage = [], []
+    for j in range(ny):
+        for i in range(nx):
+            s = np.array([i * step[0], j * step[1], 0])
+            t = s + rng.integers(-jitter, jitter + 1, size=3) * np.array([1, 1, 0])
+            t[2] = rng.integers(0, radius[2] + 1)
+            true.append(t + np.array([radius[0], radius[1], 0]))
+            stage.append(s + np.array([radius[0], radius[1], 0]))
+    true, stage = np.array(true), np.array(stage)
+    ext = true.max(axis=0) + np.array(dims) + 1
+    G = rng.integers(0, 4000, size=(ext[2], ext[1], ext[0])).astype(np.uint16)
+    tiles = [G[t[2]:t[2] + Z, t[1]:t[1] + Y, t[0]:t[0] + X].copy() for t in true]
+    return tiles, true, stage
+
+
+def test_reg_sums_brute_force():
+    rng = np.random.default_rng(90)
+    X, Y, Z = 9, 7, 5
+    A = rng.integers(0, 65536, size=(Z, Y, X)).astype(np.uint16)
+    B = rng.integers(0, 65536, size=(Z, Y, X)).astype(np.uint16)
+    for d in [(0, 0, 0), (3, -2, 1), (-8, 6, -4), (9, 0, 0), (2, 2, 5), (-4, -6, 0)]:
+        n = sa = sb = saa = sbb = sab = 0
+        for z in range(Z):
+            for y in range(Y):
+                for x in range(X):
+                    bx, by, bz = x - d[0], y - d[1], z - d[2]
+                    if 0 <= bx < X and 0 <= by < Y and 0 <= bz < Z:
+                        a, b = int(A[z, y, x]), int(B[bz, by, bx])
+                        n, sa, sb, saa, sbb, sab = n + 1, sa + a, sb + b, saa + a * a, sbb + b * b, sab + a * b
+        assert list(oracle.reg_sums(A, B, d)) == [n, sa, sb, saa, sbb, sab], d
+
+
+def test_normcov_special_cases():
+    rng = np.random.default_rng(91)
+    A = rng.integers(0, 30000, size=(4, 6, 8)).astype(np.uint16)
+    assert oracle.normcov(oracle.reg_sums(A, A, (0, 0, 0))) == pytest.approx(1.0, abs=1e-15)
+    B = (2 * A.astype(np.int64) + 7).astype(np.uint16)
+    assert oracle.normcov(oracle.reg_sums(A, B, (0, 0, 0))) == pytest.approx(1.0, abs=1e-15)
+    C = (60000 - A.astype(np.int64)).astype(np.uint16)
+    assert oracle.normcov(oracle.reg_sums(A, C, (0, 0, 0))) == pytest.approx(-1.0, abs=1e-15)
+    assert oracle.normcov(oracle.reg_sums(A, np.full_like(A, 5), (0, 0, 0))) is None  # no variance
+    assert oracle.normcov(oracle.reg_sums(A, A, (8, 0, 0))) is None                   # no overlap
+    D = rng.integers(0, 65536, size=A.shape).astype(np.uint16)
+    d = (2, -1, 1)
+    a = A[1:, :5, 2:].astype(np.float64).ravel()
+    b = D[:3, 1:, :6].astype(np.float64).ravel()
+    assert oracle.normcov(oracle.reg_sums(A, D, d)) == pytest.approx(np.corrcoef(a, b)[0, 1], abs=1e-12)
+
+
+def test_register_recovers_planted_offsets():
+    rng = np.random.default_rng(92)
+    radius = (3, 3, 2)
+    # relative shifts of neighbours stay inside the window (jitter 1 per tile)
+    tiles, true, stage = _montage(rng, (3, 2), (40, 36, 12), (9, 8), 1, radius)
+    delta, edges = oracle.register(tiles, stage, radius, root=0)
+    assert np.array_equal(delta, (true - stage) - (true - stage)[0])
+    # a tree edge's shift is the difference of its tiles' corrections
+    for e in edges[edges["in_tree"] == 1]:
+        assert np.array_equal(delta[e["b"]] - delta[e["a"]], e["shift"])
+    assert (edges["in_tree"] == 1).sum() == len(tiles) - 1
+    # another root moves every correction by the same amount
+    d2, _ = oracle.register(tiles, stage, radius, root=4)
+    assert np.array_equal(d2 - d2[0], delta)
+
+
+def test_register_tree_is_maximum():
+    # the tree has the largest total score among all spanning trees of the
+    # pair graph (brute force over edge subsets)
+    import itertools
+    rng = np.random.default_rng(93)
+    radius = (2, 2, 1)
+    tiles, true, stage = _montage(rng, (2, 2), (30, 30, 8), (8, 8), 1, radius)
+    # noisier copies so that scores differ
+    tiles = [np.clip(t.astype(np.int64) + rng.integers(-3000, 3000, size=t.shape), 0, 65535).astype(np.uint16)
+             for t in tiles]
+    _, edges = oracle.register(tiles, stage, radius, root=0)
+    n = len(tiles)
+    best = None
+    for sub in itertools.combinations(range(len(edges)), n - 1):
+        p = list(range(n))
+
+        def f(i):
+            while p[i] != i:
+                i = p[i]
+            return i
+        ok = True
+        for k in sub:
+            ra, rb = f(int(edges[k]["a"])), f(int(edges[k]["b"]))
+            if ra == rb:
+                ok = False
+                break
+            p[ra] = rb
+        if ok:
+            w = sum(edges[k]["score"] for k in sub)
+            best = w if best is None else max(best, w)
+    chosen = edges[edges["in_tree"] == 1]["score"].sum()
+    assert len(edges[edges["in_tree"] == 1]) == n - 1 and chosen == pytest.approx(best, abs=1e-12)
