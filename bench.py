@@ -329,11 +329,13 @@ def run_gpu(args):
     total_kernel_ms = sum(k["ms"] for k in kern.values())
     shares = {n: round(k["ms"] / total_kernel_ms, 4) for n, k in kern.items()} if total_kernel_ms else {}
     seg.seg_destroy(ctx)
-    denoise = closing = distmap = mrfd = None
+    denoise = closing = distmap = mrfd = reg = None
     if args.denoise_radius:
         denoise = denoise_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.denoise_radius)
     if args.closing_radius:
         closing = closing_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 5)), args.closing_radius)
+    if args.register:
+        reg = registration_run(seg, torch, local)
     if args.mrf_iterations:
         mrfd = mrf_run(seg, torch, d_in, (X, Y, Z), local, max(1, min(args.steps, 3)), args.mrf_iterations)
     if args.distance_weights != "0":
@@ -421,6 +423,7 @@ def run_gpu(args):
             "closing": closing,
             "distance_map": distmap,
             "mrf_denoise": mrfd,
+            "registration": reg,
             "serving": serve,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
@@ -547,6 +550,60 @@ def mrf_run(seg, torch, d_in, dims, local, steps, iters):
             "ms_per_mrf_step": per["mrf_iterate"] / iters if iters else None,
             "step_hbm_frac": ((vox * 6.0 * iters / (per["mrf_iterate"] / 1e3) / 1e9) / peaks()[0]
                               if per["mrf_iterate"] else None)}
+
+
+def registration_run(seg, torch, local, grid=(3, 3), dims=(1024, 1024, 64), overlap=0.1, radius=(4, 4, 1),
+                     reps=3):
+    """Montage registration (Eq. 4 + maximum spanning tree): tiles cut on the
+    GPU from one seeded noise volume at planted positions, stage positions
+    off by up to half the window; the whole call is timed (wall clock,
+    synchronous)."""
+    import synth
+    rng = np.random.default_rng(synth.mix_seed(4, 7))
+    X, Y, Z = dims
+    ov = (int(round(X * overlap)), int(round(Y * overlap)))
+    true, stage = [], []
+    for j in range(grid[1]):
+        for i in range(grid[0]):
+            st = np.array([i * (X - ov[0]) + radius[0], j * (Y - ov[1]) + radius[1], 0])
+            t = st + np.array([rng.integers(-(radius[0] // 2), radius[0] // 2 + 1),
+                               rng.integers(-(radius[1] // 2), radius[1] // 2 + 1), rng.integers(0, radius[2] + 1)])
+            true.append(t)
+            stage.append(st)
+    true, stage = np.array(true), np.array(stage)
+    ext = true.max(axis=0) + np.array(dims) + 1
+    g = torch.Generator(device="cuda:%d" % local)
+    g.manual_seed(int(synth.mix_seed(4, 8)) & 0x7FFFFFFF)
+    G = torch.randint(0, 3000, (int(ext[2]), int(ext[1]), int(ext[0])), generator=g, device="cuda:%d" % local,
+                      dtype=torch.int32)
+    tiles = [G[t[2]:t[2] + Z, t[1]:t[1] + Y, t[0]:t[0] + X].to(torch.int16).contiguous() for t in true]
+    del G
+    torch.cuda.synchronize()
+    seg.seg_register_montage(tiles, stage, radius)  # warm-up
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        delta, edges = seg.seg_register_montage(tiles, stage, radius)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.median(ts))
+    # products of the correlation: every shift's shared box, summed
+    prod = 0
+    for e in edges:
+        d0 = stage[e["b"]] - stage[e["a"]]
+        for sz in range(-radius[2], radius[2] + 1):
+            for sy in range(-radius[1], radius[1] + 1):
+                for sx in range(-radius[0], radius[0] + 1):
+                    n = 1
+                    for k, (d, D) in enumerate(zip(d0 + np.array([sx, sy, sz]), dims)):
+                        n *= max(0, min(D, d + D) - max(0, d))
+                    prod += n
+    ok = bool(np.array_equal(delta, (true - stage) - (true - stage)[0]))
+    del tiles
+    torch.cuda.empty_cache()
+    return {"tiles": int(np.prod(grid)), "tile_dims": list(dims), "overlap": overlap, "radius": list(radius),
+            "edges": int(len(edges)), "ms_per_registration": ms, "products": int(prod),
+            "gproducts_s": prod / (ms / 1e3) / 1e9, "planted_offsets_recovered": ok}
 
 
 def plain_form(seg, torch, d_in, dims, local, steps):
@@ -681,6 +738,8 @@ def main():
                     help="also time the stage with the denoise front end on channel 0 (0 skips)")
     ap.add_argument("--closing-radius", type=int, default=1,
                     help="also time the stage with the foreground closed by this ball (0 skips)")
+    ap.add_argument("--register", type=int, default=1,
+                    help="also time the montage registration of a 3x3 montage of 1024x1024x64 tiles (0 skips)")
     ap.add_argument("--mrf-iterations", type=int, default=20,
                     help="also time the stage with the MRF vessel denoise, at most this many steps (0 skips)")
     ap.add_argument("--distance-weights", default="16,16,25",

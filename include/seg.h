@@ -267,6 +267,45 @@ int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dims, uint32_t
 /* Human-readable text for a return code (static storage). */
 const char *seg_strerror(int code);
 
+/* ---- montage registration (Registration section, Eq. 4) ----------------- */
+
+typedef struct {
+    int32_t x, y, z;
+} seg_offset;
+
+/* One overlapping pair of tiles, 40 bytes. */
+typedef struct {
+    uint32_t a, b;     /* tiles, a < b, whose stage boxes overlap          */
+    seg_offset shift;  /* best shift of tile b away from its stage position */
+    uint32_t pad0;
+    double score;      /* normcov at that shift; -2 when no shift had one   */
+    uint32_t in_tree;  /* 1: edge of the maximum spanning tree              */
+    uint32_t pad1;
+} seg_montage_edge;
+
+#define SEG_REG_MAX_RXY 12 /* search half-width limits along x and y, and z */
+#define SEG_REG_MAX_RZ 6
+
+/* Registers n_tiles tiles of one montage (all dims.x * dims.y * dims.z
+ * uint16, [Z][Y][X]; tiles[i] a host pointer, or a device pointer on
+ * `device` when on_device = 1) placed at stage[i] (voxels, one global frame).
+ * Every pair whose stage boxes overlap is scored at each shift s of the
+ * second tile with |s.x|, |s.y| <= radius.x, radius.y (<= SEG_REG_MAX_RXY)
+ * and |s.z| <= radius.z (<= SEG_REG_MAX_RZ): normcov (Eq. 4, read as the
+ * Pearson correlation (N Sab - Sa Sb) / sqrt((N Saa - Sa^2)(N Sbb - Sb^2))
+ * over the voxels the two tiles then share, exact integer sums, binary64
+ * ratio), and keeps the first best shift in z, y, x order.  A maximum
+ * spanning tree of the pairs (Kruskal, ties by (a, b)) anchors tile `root`;
+ * delta[i] gets the correction of tile i (stage + delta is its registered
+ * position; 0 for tiles the tree does not reach).  edges (cap edges_cap)
+ * gets the pairs in (a, b) order and *n_edges their number.  Blocks until
+ * done.  Errors: SEG_EINVAL (null pointer, zero size, root >= n_tiles, a
+ * radius outside its limit), SEG_ETOOBIG (a tile of 2^32 voxels or more),
+ * SEG_ESMALL (edges_cap < *n_edges: nothing else is written), SEG_ECUDA. */
+int seg_register_montage(int device, const uint16_t *const *tiles, int on_device, uint32_t n_tiles,
+                         seg_dims dims, const seg_offset *stage, seg_offset radius, uint32_t root,
+                         seg_offset *delta, seg_montage_edge *edges, uint32_t edges_cap, uint32_t *n_edges);
+
 #ifdef __cplusplus
 }
 #endif

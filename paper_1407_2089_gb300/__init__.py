@@ -38,6 +38,8 @@ SEG_PROFILE = 0x8
 SEG_TEST_UNION_FAIL = 0x10
 
 SEG_MAX_KERNELS = 32
+SEG_REG_MAX_RXY = 12
+SEG_REG_MAX_RZ = 6
 
 
 class seg_dims(ctypes.Structure):
@@ -70,6 +72,14 @@ class seg_channel_params(ctypes.Structure):
                 ("mrf_iterations", ctypes.c_uint32)]
 
 
+class seg_offset(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int32), ("y", ctypes.c_int32), ("z", ctypes.c_int32)]
+
+
+MONTAGE_EDGE_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("shift", "<i4", (3,)), ("pad0", "<u4"),
+                               ("score", "<f8"), ("in_tree", "<u4"), ("pad1", "<u4")])
+
+
 class seg_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_uint64), ("volumes", ctypes.c_uint64),
                 ("voxels", ctypes.c_uint64), ("tile_y", ctypes.c_uint32),
@@ -84,7 +94,7 @@ EXPORTS = ["seg_create", "seg_destroy", "seg_submit_volume", "seg_flush", "seg_p
            "seg_enqueue_wait", "seg_read_labels", "seg_read_distance", "seg_read_denoised",
            "seg_read_features", "seg_release",
            "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror",
-           "seg_otsu_threshold_noalloc"]
+           "seg_otsu_threshold_noalloc", "seg_register_montage"]
 
 
 def _bind(lib):
@@ -107,6 +117,8 @@ def _bind(lib):
         "seg_get_stats": [vp, P(seg_stats)],
         "seg_reset_stats": [vp],
         "seg_otsu_threshold_noalloc": [vp, seg_dims, vp, vp],
+        "seg_register_montage": [i32, P(vp), i32, u32, seg_dims, P(seg_offset), seg_offset, u32, P(seg_offset),
+                                 vp, u32, P(u32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -362,3 +374,37 @@ def segment(ctx, voxels, min_volume=30, labels_out=None, timeout_ms=600000, deno
         return out
     finally:
         seg_release(ctx, req)
+
+
+def seg_register_montage(tiles, stage, radius, root=0, device=0):
+    """Registers the montage tiles (a list of equal-shape [Z][Y][X] uint16
+    numpy arrays, or CUDA int16/uint16 tensors on `device`) placed at
+    stage[i] = (x, y, z); radius = (rx, ry, rz) half-widths of the search.
+    Returns (delta [n, 3] int32, edges structured array of MONTAGE_EDGE_DTYPE)."""
+    n = len(tiles)
+    if n == 0:
+        raise ValueError("no tiles")
+    on_dev = not isinstance(tiles[0], np.ndarray)
+    keep = []
+    ptrs = (ctypes.c_void_p * n)()
+    for i, t in enumerate(tiles):
+        if on_dev:
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("device tiles must be contiguous CUDA tensors")
+            ptrs[i] = t.data_ptr()
+        else:
+            a = np.ascontiguousarray(t, dtype=np.uint16)
+            keep.append(a)
+            ptrs[i] = a.ctypes.data
+    Z, Y, X = tuple(tiles[0].shape)
+    st = (seg_offset * n)(*[seg_offset(int(p[0]), int(p[1]), int(p[2])) for p in stage])
+    delta = (seg_offset * n)()
+    cap = n * (n - 1) // 2
+    edges = np.zeros(max(cap, 1), dtype=MONTAGE_EDGE_DTYPE)
+    ne = ctypes.c_uint32()
+    _check(_lib.seg_register_montage(int(device), ptrs, 1 if on_dev else 0, n, seg_dims(X, Y, Z), st,
+                                     seg_offset(*[int(v) for v in radius]), int(root), delta,
+                                     ctypes.c_void_p(edges.ctypes.data), cap, ctypes.byref(ne)),
+           "seg_register_montage")
+    d = np.array([[o.x, o.y, o.z] for o in delta], dtype=np.int32)
+    return d, edges[: ne.value].copy()

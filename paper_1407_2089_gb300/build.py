@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libseg.so")
-SOURCES = ["seg_kernels.cu", "seg_runtime.cu"]
+SOURCES = ["seg_kernels.cu", "seg_runtime.cu", "seg_montage.cu"]
 HEADERS = [os.path.join(CSRC, "seg_internal.h"), os.path.join(INCLUDE, "seg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,7 +33,7 @@ def _stale(out, deps):
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-pthread", "-I", INCLUDE,
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-pthread,-ffp-contract=off", "-I", INCLUDE,
              "-I", CSRC] + ARCH + list(extra_flags)
     if verbose:
         flags += ["-Xptxas", "-v"]

@@ -1,0 +1,406 @@
+// seg_montage.cu -- montage registration (Registration section, Eq. 4):
+// overlapping tiles are scored at every shift of a search window by the
+// normalized covariance of their shared voxels, each overlapping pair keeps
+// its best shift, and a maximum spanning tree of the pairs gives every tile
+// its correction relative to an anchored one.
+//
+// Per pair and shift s the score needs six exact integer sums over the
+// shared box: N, Sa, Sb, Saa, Sbb and Sab.  The GPU computes
+//   * Sab for all shifts at once (k_reg_corr): a block stages a sub-box of
+//     tile a and the matching region of tile b widened by the window (b
+//     zero outside its box, so no bounds test per product), and each thread
+//     takes shifts, summing the products over the sub-box from shared
+//     memory;
+//   * Sa, Saa (tile a) and Sb, Sbb (tile b) from prefix sums: along x per
+//     row (k_reg_rowpre), along y per x-range and plane (k_reg_q), then per
+//     shift over the planes of its box (k_reg_box), because the shared box
+//     varies only at its faces.
+// The host then forms the Pearson correlation in 128-bit integers and
+// binary64, picks the first best shift in z, y, x order, builds the maximum
+// spanning tree (Kruskal) and sums the shifts from the root.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "seg.h"
+
+namespace {
+
+constexpr int RC_TX = 32, RC_TY = 8, RC_TZ = 4;  // tile-a sub-box of a k_reg_corr block
+constexpr int RC_THREADS = 256;
+
+// Half-open range [lo, hi) of one axis.
+struct Range {
+    int lo, hi;
+};
+
+// Shared range along one axis for tile b's origin at d in tile a's frame:
+// in a's coordinates (side 0) or in b's (side 1).
+__host__ __device__ inline Range shared_range(int d, int D, int side) {
+    if (side == 0) return Range{d > 0 ? d : 0, d + D < D ? d + D : D};
+    return Range{-d > 0 ? -d : 0, D - d < D ? D - d : D};
+}
+
+// Sab for every shift: block = sub-box of tile a's search region U (in a's
+// coordinates).  Shift index si = ((sz + rz) SY + (sy + ry)) SX + (sx + rx).
+__global__ void __launch_bounds__(RC_THREADS) k_reg_corr(const uint16_t *__restrict__ A, const uint16_t *__restrict__ B,
+                                                         int X, int Y, int Z, int3 u0, int3 u1, int3 d0, int3 r,
+                                                         unsigned long long *__restrict__ sab) {
+    extern __shared__ uint16_t rsm[];
+    const int BX = RC_TX + 2 * r.x, BY = RC_TY + 2 * r.y, BZ = RC_TZ + 2 * r.z;
+    uint16_t *As = rsm;                          // [RC_TZ][RC_TY][RC_TX]
+    uint16_t *Bs = rsm + RC_TX * RC_TY * RC_TZ;  // [BZ][BY][BX]
+    const int nbx = (u1.x - u0.x + RC_TX - 1) / RC_TX, nby = (u1.y - u0.y + RC_TY - 1) / RC_TY;
+    const int bi = (int)blockIdx.x;
+    const int ax0 = u0.x + (bi % nbx) * RC_TX, ay0 = u0.y + ((bi / nbx) % nby) * RC_TY;
+    const int az0 = u0.z + (bi / (nbx * nby)) * RC_TZ;
+    for (int i = threadIdx.x; i < RC_TX * RC_TY * RC_TZ; i += RC_THREADS) {
+        const int x = ax0 + i % RC_TX, y = ay0 + (i / RC_TX) % RC_TY, z = az0 + i / (RC_TX * RC_TY);
+        As[i] = (x < u1.x && y < u1.y && z < u1.z) ? A[((size_t)z * Y + y) * X + x] : (uint16_t)0;
+    }
+    // b coordinates of a's sub-box under every shift: a - d0 - s
+    const int bx0 = ax0 - d0.x - r.x, by0 = ay0 - d0.y - r.y, bz0 = az0 - d0.z - r.z;
+    for (int i = threadIdx.x; i < BX * BY * BZ; i += RC_THREADS) {
+        const int x = bx0 + i % BX, y = by0 + (i / BX) % BY, z = bz0 + i / (BX * BY);
+        Bs[i] = (x >= 0 && x < X && y >= 0 && y < Y && z >= 0 && z < Z) ? B[((size_t)z * Y + y) * X + x]
+                                                                       : (uint16_t)0;
+    }
+    __syncthreads();
+    const int SX = 2 * r.x + 1, SY = 2 * r.y + 1, S = SX * SY * (2 * r.z + 1);
+    for (int si = threadIdx.x; si < S; si += RC_THREADS) {
+        const int sx = si % SX - r.x, sy = (si / SX) % SY - r.y, sz = si / (SX * SY) - r.z;
+        unsigned long long acc = 0;
+        for (int z = 0; z < RC_TZ; ++z)
+            for (int y = 0; y < RC_TY; ++y) {
+                const uint16_t *ar = As + (z * RC_TY + y) * RC_TX;
+                const uint16_t *br = Bs + ((z - sz + r.z) * BY + (y - sy + r.y)) * BX + (r.x - sx);
+#pragma unroll
+                for (int x = 0; x < RC_TX; ++x) acc += (unsigned long long)((uint32_t)ar[x] * (uint32_t)br[x]);
+            }
+        if (acc) atomicAdd(sab + si, acc);
+    }
+}
+
+// Prefix sums along x of v and v^2 over the region U of one tile: row
+// (y, z) of U at (z - u0.z) UY + (y - u0.y), W = u1.x - u0.x + 1 entries.
+__global__ void k_reg_rowpre(const uint16_t *__restrict__ T, int X, int Y, int3 u0, int3 u1,
+                             unsigned long long *__restrict__ p1, unsigned long long *__restrict__ p2) {
+    const int UY = u1.y - u0.y, rows = UY * (u1.z - u0.z), W = u1.x - u0.x + 1;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+        const int y = u0.y + row % UY, z = u0.z + row / UY;
+        const uint16_t *t = T + ((size_t)z * Y + y) * X;
+        unsigned long long a = 0, b = 0;
+        unsigned long long *q1 = p1 + (size_t)row * W, *q2 = p2 + (size_t)row * W;
+        q1[0] = 0;
+        q2[0] = 0;
+        for (int x = u0.x; x < u1.x; ++x) {
+            const unsigned long long v = t[x];
+            a += v;
+            b += v * v;
+            q1[x - u0.x + 1] = a;
+            q2[x - u0.x + 1] = b;
+        }
+    }
+}
+
+// For every x-shift and plane of U: prefix along y of the rows' sums over the
+// shift's x-range.  Q[(sxi (UZ) + z - u0.z) (UY + 1) + j].
+__global__ void k_reg_q(const unsigned long long *__restrict__ p1, const unsigned long long *__restrict__ p2,
+                        int X, int3 u0, int3 u1, int d0x, int rx, int side, unsigned long long *__restrict__ q1,
+                        unsigned long long *__restrict__ q2) {
+    const int UY = u1.y - u0.y, UZ = u1.z - u0.z, W = u1.x - u0.x + 1, SX = 2 * rx + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < SX * UZ; i += gridDim.x * blockDim.x) {
+        const int sxi = i / UZ, zz = i % UZ;
+        const Range xr = shared_range(d0x + sxi - rx, X, side);
+        unsigned long long *o1 = q1 + (size_t)i * (UY + 1), *o2 = q2 + (size_t)i * (UY + 1);
+        o1[0] = 0;
+        o2[0] = 0;
+        unsigned long long a = 0, b = 0;
+        const bool any = xr.lo < xr.hi;
+        const int l = any ? xr.lo - u0.x : 0, h = any ? xr.hi - u0.x : 0;
+        for (int j = 0; j < UY; ++j) {
+            const size_t row = (size_t)(zz * UY + j) * W;
+            if (any) {
+                a += p1[row + h] - p1[row + l];
+                b += p2[row + h] - p2[row + l];
+            }
+            o1[j + 1] = a;
+            o2[j + 1] = b;
+        }
+    }
+}
+
+// Per shift: the sums of v and v^2 over the tile's shared box.
+__global__ void k_reg_box(const unsigned long long *__restrict__ q1, const unsigned long long *__restrict__ q2,
+                          int X, int Y, int Z, int3 u0, int3 u1, int3 d0, int3 r, int side,
+                          unsigned long long *__restrict__ s1, unsigned long long *__restrict__ s2) {
+    const int UY = u1.y - u0.y, UZ = u1.z - u0.z;
+    const int SX = 2 * r.x + 1, SY = 2 * r.y + 1, S = SX * SY * (2 * r.z + 1);
+    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < S; si += gridDim.x * blockDim.x) {
+        const int sxi = si % SX, sy = (si / SX) % SY - r.y, sz = si / (SX * SY) - r.z;
+        const Range xr = shared_range(d0.x + sxi - r.x, X, side);
+        const Range yr = shared_range(d0.y + sy, Y, side), zr = shared_range(d0.z + sz, Z, side);
+        unsigned long long a = 0, b = 0;
+        if (xr.lo < xr.hi && yr.lo < yr.hi && zr.lo < zr.hi) {
+            for (int z = zr.lo; z < zr.hi; ++z) {
+                const size_t q = (size_t)(sxi * UZ + (z - u0.z)) * (UY + 1);
+                a += q1[q + (yr.hi - u0.y)] - q1[q + (yr.lo - u0.y)];
+                b += q2[q + (yr.hi - u0.y)] - q2[q + (yr.lo - u0.y)];
+            }
+        }
+        s1[si] = a;
+        s2[si] = b;
+    }
+}
+
+int fail(cudaError_t e) {
+    if (e == cudaSuccess) return SEG_OK;
+    cudaGetLastError();
+    return SEG_ECUDA;
+}
+
+#define RK(call)                                 \
+    do {                                         \
+        const cudaError_t e__ = (call);          \
+        if (e__ != cudaSuccess) return fail(e__); \
+    } while (0)
+
+// Device buffers of one registration call, freed on every return path.
+struct Scratch {
+    std::vector<void *> ptrs;
+    cudaStream_t s = nullptr;
+    ~Scratch() {
+        for (void *p : ptrs) cudaFree(p);
+        if (s) cudaStreamDestroy(s);
+    }
+    template <class T>
+    cudaError_t alloc(T **p, size_t n) {
+        void *q = nullptr;
+        const cudaError_t e = cudaMalloc(&q, n ? n * sizeof(T) : 1);
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = static_cast<T *>(q);
+        return e;
+    }
+};
+
+// Search region of one side (0: tile a, 1: tile b) in that tile's frame:
+// the union over the window of the shared boxes.
+void side_region(const int *d0, const int *r, const int *D, int side, int3 &u0, int3 &u1) {
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        const Range a = shared_range(d0[k] - r[k], D[k], side), b = shared_range(d0[k] + r[k], D[k], side);
+        lo[k] = std::min(a.lo, b.lo);
+        hi[k] = std::max(a.hi, b.hi);
+        if (lo[k] > hi[k]) hi[k] = lo[k];
+    }
+    u0 = make_int3(lo[0], lo[1], lo[2]);
+    u1 = make_int3(hi[0], hi[1], hi[2]);
+}
+
+// Entries of the prefix buffers one side of a pair needs.
+void side_sizes(const int *D, const int *d0, const int *r, int side, size_t &np, size_t &nq) {
+    int3 u0, u1;
+    side_region(d0, r, D, side, u0, u1);
+    const size_t UX = (size_t)(u1.x - u0.x), UY = (size_t)(u1.y - u0.y), UZ = (size_t)(u1.z - u0.z);
+    np = UY * UZ * (UX + 1);
+    nq = (size_t)(2 * r[0] + 1) * UZ * (UY + 1);
+}
+
+// Prefix buffers (p1, p2 along x; q1, q2 along y), sized for the largest side.
+struct Prefix {
+    unsigned long long *p1, *p2, *q1, *q2;
+};
+
+// Sa, Saa (side 0) or Sb, Sbb (side 1) of every shift.
+int side_sums(Scratch &sc, const Prefix &pf, const uint16_t *T, const int *D, const int *d0, const int *r, int side,
+              unsigned long long *s1, unsigned long long *s2) {
+    int3 u0, u1;
+    side_region(d0, r, D, side, u0, u1);
+    const int UX = u1.x - u0.x, UY = u1.y - u0.y, UZ = u1.z - u0.z;
+    const int SX = 2 * r[0] + 1, S = SX * (2 * r[1] + 1) * (2 * r[2] + 1);
+    if (UX <= 0 || UY <= 0 || UZ <= 0) {
+        RK(cudaMemsetAsync(s1, 0, S * sizeof(unsigned long long), sc.s));
+        RK(cudaMemsetAsync(s2, 0, S * sizeof(unsigned long long), sc.s));
+        return SEG_OK;
+    }
+    unsigned long long *p1 = pf.p1, *p2 = pf.p2, *q1 = pf.q1, *q2 = pf.q2;
+    const int rows = UY * UZ;
+    k_reg_rowpre<<<(rows + 255) / 256, 256, 0, sc.s>>>(T, D[0], D[1], u0, u1, p1, p2);
+    k_reg_q<<<(SX * UZ + 127) / 128, 128, 0, sc.s>>>(p1, p2, D[0], u0, u1, d0[0], r[0], side, q1, q2);
+    k_reg_box<<<(S + 127) / 128, 128, 0, sc.s>>>(q1, q2, D[0], D[1], D[2], u0, u1, make_int3(d0[0], d0[1], d0[2]),
+                                                 make_int3(r[0], r[1], r[2]), side, s1, s2);
+    RK(cudaGetLastError());
+    return SEG_OK;
+}
+
+uint32_t uf_root(std::vector<uint32_t> &p, uint32_t i) {
+    while (p[i] != i) {
+        p[i] = p[p[i]];
+        i = p[i];
+    }
+    return i;
+}
+
+}  // namespace
+
+extern "C" int seg_register_montage(int device, const uint16_t *const *tiles, int on_device, uint32_t n_tiles,
+                                    seg_dims dims, const seg_offset *stage, seg_offset radius, uint32_t root,
+                                    seg_offset *delta, seg_montage_edge *edges, uint32_t edges_cap,
+                                    uint32_t *n_edges) {
+    if (!tiles || !stage || !delta || !n_edges || n_tiles == 0 || root >= n_tiles || dims.x == 0 || dims.y == 0 ||
+        dims.z == 0)
+        return SEG_EINVAL;
+    if (radius.x < 0 || radius.y < 0 || radius.z < 0 || radius.x > SEG_REG_MAX_RXY || radius.y > SEG_REG_MAX_RXY ||
+        radius.z > SEG_REG_MAX_RZ)
+        return SEG_EINVAL;
+    for (uint32_t i = 0; i < n_tiles; ++i)
+        if (!tiles[i]) return SEG_EINVAL;
+    const uint64_t n = (uint64_t)dims.x * dims.y * dims.z;
+    if (n >= (1ull << 32) || dims.x > 0x7FFFFFFFu || dims.y > 0x7FFFFFFFu || dims.z > 0x7FFFFFFFu)
+        return SEG_ETOOBIG;
+    const int D[3] = {(int)dims.x, (int)dims.y, (int)dims.z};
+    const int r[3] = {radius.x, radius.y, radius.z};
+    // pairs whose stage boxes overlap, in (a, b) order
+    std::vector<seg_montage_edge> E;
+    for (uint32_t a = 0; a < n_tiles; ++a)
+        for (uint32_t b = a + 1; b < n_tiles; ++b) {
+            const int64_t o[3] = {(int64_t)stage[b].x - stage[a].x, (int64_t)stage[b].y - stage[a].y,
+                                  (int64_t)stage[b].z - stage[a].z};
+            bool ov = true;
+            for (int k = 0; k < 3; ++k) ov = ov && o[k] < D[k] && -o[k] < D[k];
+            if (!ov) continue;
+            seg_montage_edge e;
+            std::memset(&e, 0, sizeof(e));
+            e.a = a;
+            e.b = b;
+            e.score = -2.0;
+            E.push_back(e);
+        }
+    *n_edges = (uint32_t)E.size();
+    if (E.size() > edges_cap || (!edges && !E.empty())) return SEG_ESMALL;
+
+    Scratch sc;
+    RK(cudaSetDevice(device));
+    RK(cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking));
+    // the tiles on the device
+    std::vector<const uint16_t *> dt(n_tiles);
+    if (on_device) {
+        for (uint32_t i = 0; i < n_tiles; ++i) dt[i] = tiles[i];
+    } else {
+        for (uint32_t i = 0; i < n_tiles; ++i) {
+            uint16_t *p;
+            RK(sc.alloc(&p, n));
+            RK(cudaMemcpyAsync(p, tiles[i], 2 * n, cudaMemcpyHostToDevice, sc.s));
+            dt[i] = p;
+        }
+    }
+    const int SX = 2 * r[0] + 1, SY = 2 * r[1] + 1, S = SX * SY * (2 * r[2] + 1);
+    unsigned long long *dsum;  // Sab, Sa, Saa, Sb, Sbb of every shift
+    RK(sc.alloc(&dsum, 5 * (size_t)S));
+    std::vector<unsigned long long> hs(5 * (size_t)S);
+    size_t np = 1, nq = 1;
+    for (const seg_montage_edge &e : E) {
+        const int d0[3] = {stage[e.b].x - stage[e.a].x, stage[e.b].y - stage[e.a].y, stage[e.b].z - stage[e.a].z};
+        for (int side = 0; side < 2; ++side) {
+            size_t a, b;
+            side_sizes(D, d0, r, side, a, b);
+            np = std::max(np, a);
+            nq = std::max(nq, b);
+        }
+    }
+    Prefix pf;
+    RK(sc.alloc(&pf.p1, np));
+    RK(sc.alloc(&pf.p2, np));
+    RK(sc.alloc(&pf.q1, nq));
+    RK(sc.alloc(&pf.q2, nq));
+    const size_t smem = sizeof(uint16_t) * ((size_t)RC_TX * RC_TY * RC_TZ +
+                                            (size_t)(RC_TX + 2 * r[0]) * (RC_TY + 2 * r[1]) * (RC_TZ + 2 * r[2]));
+    RK(cudaFuncSetAttribute(k_reg_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (seg_montage_edge &e : E) {
+        const int d0[3] = {stage[e.b].x - stage[e.a].x, stage[e.b].y - stage[e.a].y, stage[e.b].z - stage[e.a].z};
+        RK(cudaMemsetAsync(dsum, 0, S * sizeof(unsigned long long), sc.s));
+        int3 u0, u1;
+        side_region(d0, r, D, 0, u0, u1);
+        if (u1.x > u0.x && u1.y > u0.y && u1.z > u0.z) {
+            const int nb = ((u1.x - u0.x + RC_TX - 1) / RC_TX) * ((u1.y - u0.y + RC_TY - 1) / RC_TY) *
+                           ((u1.z - u0.z + RC_TZ - 1) / RC_TZ);
+            k_reg_corr<<<nb, RC_THREADS, smem, sc.s>>>(dt[e.a], dt[e.b], D[0], D[1], D[2], u0, u1,
+                                                       make_int3(d0[0], d0[1], d0[2]), make_int3(r[0], r[1], r[2]),
+                                                       dsum);
+            RK(cudaGetLastError());
+        }
+        int rc = side_sums(sc, pf, dt[e.a], D, d0, r, 0, dsum + S, dsum + 2 * (size_t)S);
+        if (rc != SEG_OK) return rc;
+        rc = side_sums(sc, pf, dt[e.b], D, d0, r, 1, dsum + 3 * (size_t)S, dsum + 4 * (size_t)S);
+        if (rc != SEG_OK) return rc;
+        RK(cudaMemcpyAsync(hs.data(), dsum, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, sc.s));
+        RK(cudaStreamSynchronize(sc.s));
+        // the first best shift in z, y, x order
+        for (int si = 0; si < S; ++si) {
+            const int s[3] = {si % SX - r[0], (si / SX) % SY - r[1], si / (SX * SY) - r[2]};
+            uint64_t cnt = 1;
+            for (int k = 0; k < 3; ++k) {
+                const Range q = shared_range(d0[k] + s[k], D[k], 0);
+                cnt *= (uint64_t)(q.hi > q.lo ? q.hi - q.lo : 0);
+            }
+            if (cnt == 0) continue;
+            const unsigned long long sab = hs[si], sa = hs[S + si], saa = hs[2 * (size_t)S + si];
+            const unsigned long long sb = hs[3 * (size_t)S + si], sbb = hs[4 * (size_t)S + si];
+            const __int128 N = (__int128)cnt;
+            const __int128 num = N * (__int128)sab - (__int128)sa * (__int128)sb;
+            const __int128 va = N * (__int128)saa - (__int128)sa * (__int128)sa;
+            const __int128 vb = N * (__int128)sbb - (__int128)sb * (__int128)sb;
+            if (va == 0 || vb == 0) continue;
+            const double rho = (double)num / std::sqrt((double)va * (double)vb);
+            if (rho > e.score) {
+                e.score = rho;
+                e.shift.x = s[0];
+                e.shift.y = s[1];
+                e.shift.z = s[2];
+            }
+        }
+    }
+    // maximum spanning tree: scores highest first, ties by (a, b)
+    std::vector<uint32_t> order(E.size());
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t i, uint32_t j) { return E[i].score > E[j].score; });
+    std::vector<uint32_t> par(n_tiles);
+    std::iota(par.begin(), par.end(), 0u);
+    std::vector<std::vector<uint32_t>> adj(n_tiles);
+    for (uint32_t i : order) {
+        seg_montage_edge &e = E[i];
+        if (e.score < -1.5) continue;  // no defined score
+        const uint32_t ra = uf_root(par, e.a), rb = uf_root(par, e.b);
+        if (ra == rb) continue;
+        par[ra] = rb;
+        e.in_tree = 1;
+        adj[e.a].push_back(i);
+        adj[e.b].push_back(i);
+    }
+    // corrections from the root along the tree
+    for (uint32_t i = 0; i < n_tiles; ++i) delta[i] = seg_offset{0, 0, 0};
+    std::vector<uint8_t> seen(n_tiles, 0);
+    std::vector<uint32_t> todo{root};
+    seen[root] = 1;
+    while (!todo.empty()) {
+        const uint32_t t = todo.back();
+        todo.pop_back();
+        for (uint32_t i : adj[t]) {
+            const seg_montage_edge &e = E[i];
+            const uint32_t o = e.a == t ? e.b : e.a;
+            if (seen[o]) continue;
+            const int sg = e.a == t ? 1 : -1;  // delta(b) = delta(a) + shift
+            delta[o] = seg_offset{delta[t].x + sg * e.shift.x, delta[t].y + sg * e.shift.y,
+                                  delta[t].z + sg * e.shift.z};
+            seen[o] = 1;
+            todo.push_back(o);
+        }
+    }
+    if (!E.empty()) std::memcpy(edges, E.data(), E.size() * sizeof(seg_montage_edge));
+    return SEG_OK;
+}
