@@ -11,10 +11,10 @@
 //     zero outside its box, so no bounds test per product), and each thread
 //     takes shifts, summing the products over the sub-box from shared
 //     memory;
-//   * Sa, Saa (tile a) and Sb, Sbb (tile b) from prefix sums: along x per
-//     row (k_reg_rowpre), along y per x-range and plane (k_reg_q), then per
-//     shift over the planes of its box (k_reg_box), because the shared box
-//     varies only at its faces.
+//   * Sa, Saa (tile a) and Sb, Sbb (tile b) from the x-range sums of every
+//     row (k_reg_rows), their prefixes along y per x-range and plane
+//     (k_reg_q), then per shift a sum over the planes of its box
+//     (k_reg_box), because the shared box varies only at its faces.
 // The host then forms the Pearson correlation in 128-bit integers and
 // binary64, picks the first best shift in z, y, x order, builds the maximum
 // spanning tree (Kruskal) and sums the shifts from the root.
@@ -86,52 +86,106 @@ __global__ void __launch_bounds__(RC_THREADS) k_reg_corr(const uint16_t *__restr
     }
 }
 
-// Prefix sums along x of v and v^2 over the region U of one tile: row
-// (y, z) of U at (z - u0.z) UY + (y - u0.y), W = u1.x - u0.x + 1 entries.
-__global__ void k_reg_rowpre(const uint16_t *__restrict__ T, int X, int Y, int3 u0, int3 u1,
-                             unsigned long long *__restrict__ p1, unsigned long long *__restrict__ p2) {
-    const int UY = u1.y - u0.y, rows = UY * (u1.z - u0.z), W = u1.x - u0.x + 1;
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+// Per row (y, z) of the region U of one tile and x-shift sxi: the sums of v
+// and v^2 over the shift's x-range, R[sxi rows + row] with row =
+// (z - u0.z) UY + (y - u0.y).  One warp per row: the part of the row every
+// x-range shares (the core) is summed by all lanes and reduced; lane sxi then
+// adds its range's voxels outside the core (at most 2 rx of them).
+__global__ void k_reg_rows(const uint16_t *__restrict__ T, int X, int Y, int3 u0, int3 u1, int d0x, int rx, int side,
+                           unsigned long long *__restrict__ r1, unsigned long long *__restrict__ r2) {
+    const int UY = u1.y - u0.y, rows = UY * (u1.z - u0.z), SX = 2 * rx + 1;
+    const int lane = threadIdx.x & 31;
+    const Range first = shared_range(d0x - rx, X, side), last = shared_range(d0x + rx, X, side);
+    // ranges move monotonically with the shift: the core is [max lo, min hi)
+    const int clo = max(first.lo, last.lo), chi = min(first.hi, last.hi);
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nw) {
         const int y = u0.y + row % UY, z = u0.z + row / UY;
         const uint16_t *t = T + ((size_t)z * Y + y) * X;
         unsigned long long a = 0, b = 0;
-        unsigned long long *q1 = p1 + (size_t)row * W, *q2 = p2 + (size_t)row * W;
-        q1[0] = 0;
-        q2[0] = 0;
-        for (int x = u0.x; x < u1.x; ++x) {
+        for (int x = clo + lane; x < chi; x += 32) {
             const unsigned long long v = t[x];
             a += v;
             b += v * v;
-            q1[x - u0.x + 1] = a;
-            q2[x - u0.x + 1] = b;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+            b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        }
+        if (lane < SX) {
+            const Range q = shared_range(d0x + lane - rx, X, side);
+            if (clo >= chi) {  // no core: the whole range
+                a = b = 0;
+                for (int x = q.lo; x < q.hi; ++x) {
+                    const unsigned long long v = t[x];
+                    a += v;
+                    b += v * v;
+                }
+            } else if (q.lo >= q.hi) {
+                a = b = 0;
+            } else {
+                for (int x = q.lo; x < clo; ++x) {
+                    const unsigned long long v = t[x];
+                    a += v;
+                    b += v * v;
+                }
+                for (int x = chi; x < q.hi; ++x) {
+                    const unsigned long long v = t[x];
+                    a += v;
+                    b += v * v;
+                }
+            }
+            r1[(size_t)lane * rows + row] = a;
+            r2[(size_t)lane * rows + row] = b;
         }
     }
 }
 
 // For every x-shift and plane of U: prefix along y of the rows' sums over the
-// shift's x-range.  Q[(sxi (UZ) + z - u0.z) (UY + 1) + j].
-__global__ void k_reg_q(const unsigned long long *__restrict__ p1, const unsigned long long *__restrict__ p2,
-                        int X, int3 u0, int3 u1, int d0x, int rx, int side, unsigned long long *__restrict__ q1,
-                        unsigned long long *__restrict__ q2) {
-    const int UY = u1.y - u0.y, UZ = u1.z - u0.z, W = u1.x - u0.x + 1, SX = 2 * rx + 1;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < SX * UZ; i += gridDim.x * blockDim.x) {
-        const int sxi = i / UZ, zz = i % UZ;
-        const Range xr = shared_range(d0x + sxi - rx, X, side);
-        unsigned long long *o1 = q1 + (size_t)i * (UY + 1), *o2 = q2 + (size_t)i * (UY + 1);
+// shift's x-range.  Q[(sxi (UZ) + z - u0.z) (UY + 1) + j].  One block per
+// (x-shift, plane): each thread sums a run of consecutive rows, a block scan
+// of the run totals gives each run's start, then the runs are written.
+constexpr int RQ_THREADS = 256;
+__global__ void __launch_bounds__(RQ_THREADS) k_reg_q(const unsigned long long *__restrict__ r1,
+                                                      const unsigned long long *__restrict__ r2, int3 u0, int3 u1,
+                                                      unsigned long long *__restrict__ q1,
+                                                      unsigned long long *__restrict__ q2) {
+    __shared__ unsigned long long t1[RQ_THREADS], t2[RQ_THREADS];
+    const int UY = u1.y - u0.y, UZ = u1.z - u0.z, rows = UY * UZ;
+    const int i = (int)blockIdx.x, sxi = i / UZ, zz = i % UZ;
+    const unsigned long long *s1 = r1 + (size_t)sxi * rows + (size_t)zz * UY;
+    const unsigned long long *s2 = r2 + (size_t)sxi * rows + (size_t)zz * UY;
+    const int per = (UY + RQ_THREADS - 1) / RQ_THREADS, j0 = threadIdx.x * per, j1 = min(j0 + per, UY);
+    unsigned long long a = 0, b = 0;
+    for (int j = j0; j < j1; ++j) {
+        a += s1[j];
+        b += s2[j];
+    }
+    t1[threadIdx.x] = a;
+    t2[threadIdx.x] = b;
+    __syncthreads();
+    // inclusive scan of the run totals (Hillis-Steele)
+    for (int o = 1; o < RQ_THREADS; o <<= 1) {
+        const unsigned long long x = threadIdx.x >= o ? t1[threadIdx.x - o] : 0ull;
+        const unsigned long long y = threadIdx.x >= o ? t2[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        t1[threadIdx.x] += x;
+        t2[threadIdx.x] += y;
+        __syncthreads();
+    }
+    unsigned long long *o1 = q1 + (size_t)i * (UY + 1), *o2 = q2 + (size_t)i * (UY + 1);
+    a = t1[threadIdx.x] - a;  // exclusive start of this run
+    b = t2[threadIdx.x] - b;
+    if (threadIdx.x == 0) {
         o1[0] = 0;
         o2[0] = 0;
-        unsigned long long a = 0, b = 0;
-        const bool any = xr.lo < xr.hi;
-        const int l = any ? xr.lo - u0.x : 0, h = any ? xr.hi - u0.x : 0;
-        for (int j = 0; j < UY; ++j) {
-            const size_t row = (size_t)(zz * UY + j) * W;
-            if (any) {
-                a += p1[row + h] - p1[row + l];
-                b += p2[row + h] - p2[row + l];
-            }
-            o1[j + 1] = a;
-            o2[j + 1] = b;
-        }
+    }
+    for (int j = j0; j < j1; ++j) {
+        a += s1[j];
+        b += s2[j];
+        o1[j + 1] = a;
+        o2[j + 1] = b;
     }
 }
 
@@ -207,11 +261,12 @@ void side_sizes(const int *D, const int *d0, const int *r, int side, size_t &np,
     int3 u0, u1;
     side_region(d0, r, D, side, u0, u1);
     const size_t UX = (size_t)(u1.x - u0.x), UY = (size_t)(u1.y - u0.y), UZ = (size_t)(u1.z - u0.z);
-    np = UY * UZ * (UX + 1);
+    np = (size_t)(2 * r[0] + 1) * UY * UZ * (UX > 0 ? 1 : 0);
     nq = (size_t)(2 * r[0] + 1) * UZ * (UY + 1);
 }
 
-// Prefix buffers (p1, p2 along x; q1, q2 along y), sized for the largest side.
+// Buffers (p1, p2: x-range sums per row; q1, q2: prefixes along y), sized
+// for the largest side.
 struct Prefix {
     unsigned long long *p1, *p2, *q1, *q2;
 };
@@ -230,8 +285,8 @@ int side_sums(Scratch &sc, const Prefix &pf, const uint16_t *T, const int *D, co
     }
     unsigned long long *p1 = pf.p1, *p2 = pf.p2, *q1 = pf.q1, *q2 = pf.q2;
     const int rows = UY * UZ;
-    k_reg_rowpre<<<(rows + 255) / 256, 256, 0, sc.s>>>(T, D[0], D[1], u0, u1, p1, p2);
-    k_reg_q<<<(SX * UZ + 127) / 128, 128, 0, sc.s>>>(p1, p2, D[0], u0, u1, d0[0], r[0], side, q1, q2);
+    k_reg_rows<<<(rows + 7) / 8, 256, 0, sc.s>>>(T, D[0], D[1], u0, u1, d0[0], r[0], side, p1, p2);
+    k_reg_q<<<SX * UZ, RQ_THREADS, 0, sc.s>>>(p1, p2, u0, u1, q1, q2);
     k_reg_box<<<(S + 127) / 128, 128, 0, sc.s>>>(q1, q2, D[0], D[1], D[2], u0, u1, make_int3(d0[0], d0[1], d0[2]),
                                                  make_int3(r[0], r[1], r[2]), side, s1, s2);
     RK(cudaGetLastError());
