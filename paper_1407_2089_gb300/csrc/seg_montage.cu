@@ -25,13 +25,14 @@
 #include <cstdint>
 #include <cstring>
 #include <numeric>
+#include <utility>
 #include <vector>
 
 #include "seg.h"
 
 namespace {
 
-constexpr int RC_TX = 32, RC_TY = 8, RC_TZ = 4;  // tile-a sub-box of a k_reg_corr block
+constexpr int RC_TX = 32, RC_TY = 8, RC_TZ = 8;  // tile-a sub-box of a k_reg_corr block
 constexpr int RC_THREADS = 256;
 
 // Half-open range [lo, hi) of one axis.
@@ -46,44 +47,90 @@ __host__ __device__ inline Range shared_range(int d, int D, int side) {
     return Range{-d > 0 ? -d : 0, D - d < D ? D - d : D};
 }
 
-// Sab for every shift: block = sub-box of tile a's search region U (in a's
-// coordinates).  Shift index si = ((sz + rz) SY + (sy + ry)) SX + (sx + rx).
+// Sab for every shift: block = sub-box (RC_TX x RC_TY x RC_TZ) of tile a's
+// search region U (in a's coordinates).  Shift index
+// si = ((sz + rz) SY + (sy + ry)) SX + (sx + rx).  Thread (g, c) takes the
+// (y, z)-shift g = (sy, sz) for every x-shift (KX = 2 RX + 1 of them) over
+// the sub-box rows c, c + C, ...: along a row the x-shifts need b values
+// x + 2 RX - k, so a register window of KX b values slides with x and every
+// product costs one multiply-add.  The threads' sums meet in shared memory
+// and go out with one atomic per (block, shift).
+template <int RX>
 __global__ void __launch_bounds__(RC_THREADS) k_reg_corr(const uint16_t *__restrict__ A, const uint16_t *__restrict__ B,
-                                                         int X, int Y, int Z, int3 u0, int3 u1, int3 d0, int3 r,
-                                                         unsigned long long *__restrict__ sab) {
-    extern __shared__ uint16_t rsm[];
-    const int BX = RC_TX + 2 * r.x, BY = RC_TY + 2 * r.y, BZ = RC_TZ + 2 * r.z;
-    uint16_t *As = rsm;                          // [RC_TZ][RC_TY][RC_TX]
-    uint16_t *Bs = rsm + RC_TX * RC_TY * RC_TZ;  // [BZ][BY][BX]
+                                                         int X, int Y, int Z, int3 u0, int3 u1, int3 d0, int ry,
+                                                         int rz, unsigned long long *__restrict__ sab) {
+    constexpr int KX = 2 * RX + 1;
+    constexpr int BX = RC_TX + 2 * RX;
+    extern __shared__ __align__(16) unsigned long long rsm64[];
+    const int BY = RC_TY + 2 * ry, BZ = RC_TZ + 2 * rz, SY = 2 * ry + 1, G = SY * (2 * rz + 1);
+    unsigned long long *red = rsm64;                                      // [G][KX]
+    uint16_t *As = reinterpret_cast<uint16_t *>(rsm64 + (size_t)G * KX);  // [RC_TZ][RC_TY][RC_TX]
+    uint16_t *Bs = As + RC_TX * RC_TY * RC_TZ;                            // [BZ][BY][BX]
     const int nbx = (u1.x - u0.x + RC_TX - 1) / RC_TX, nby = (u1.y - u0.y + RC_TY - 1) / RC_TY;
     const int bi = (int)blockIdx.x;
     const int ax0 = u0.x + (bi % nbx) * RC_TX, ay0 = u0.y + ((bi / nbx) % nby) * RC_TY;
     const int az0 = u0.z + (bi / (nbx * nby)) * RC_TZ;
+    for (int i = threadIdx.x; i < G * KX; i += RC_THREADS) red[i] = 0ull;
     for (int i = threadIdx.x; i < RC_TX * RC_TY * RC_TZ; i += RC_THREADS) {
         const int x = ax0 + i % RC_TX, y = ay0 + (i / RC_TX) % RC_TY, z = az0 + i / (RC_TX * RC_TY);
         As[i] = (x < u1.x && y < u1.y && z < u1.z) ? A[((size_t)z * Y + y) * X + x] : (uint16_t)0;
     }
     // b coordinates of a's sub-box under every shift: a - d0 - s
-    const int bx0 = ax0 - d0.x - r.x, by0 = ay0 - d0.y - r.y, bz0 = az0 - d0.z - r.z;
+    const int bx0 = ax0 - d0.x - RX, by0 = ay0 - d0.y - ry, bz0 = az0 - d0.z - rz;
     for (int i = threadIdx.x; i < BX * BY * BZ; i += RC_THREADS) {
         const int x = bx0 + i % BX, y = by0 + (i / BX) % BY, z = bz0 + i / (BX * BY);
         Bs[i] = (x >= 0 && x < X && y >= 0 && y < Y && z >= 0 && z < Z) ? B[((size_t)z * Y + y) * X + x]
                                                                        : (uint16_t)0;
     }
     __syncthreads();
-    const int SX = 2 * r.x + 1, SY = 2 * r.y + 1, S = SX * SY * (2 * r.z + 1);
-    for (int si = threadIdx.x; si < S; si += RC_THREADS) {
-        const int sx = si % SX - r.x, sy = (si / SX) % SY - r.y, sz = si / (SX * SY) - r.z;
-        unsigned long long acc = 0;
-        for (int z = 0; z < RC_TZ; ++z)
-            for (int y = 0; y < RC_TY; ++y) {
-                const uint16_t *ar = As + (z * RC_TY + y) * RC_TX;
-                const uint16_t *br = Bs + ((z - sz + r.z) * BY + (y - sy + r.y)) * BX + (r.x - sx);
+    constexpr int ROWS = RC_TY * RC_TZ;
+    const int C = G >= RC_THREADS ? 1 : min(ROWS, RC_THREADS / G);  // row chunks per shift group
+    for (int w = threadIdx.x; w < G * C; w += RC_THREADS) {
+        const int g = w % G, c = w / G;
+        const int sy = g % SY - ry, sz = g / SY - rz;
+        unsigned long long acc[KX];
 #pragma unroll
-                for (int x = 0; x < RC_TX; ++x) acc += (unsigned long long)((uint32_t)ar[x] * (uint32_t)br[x]);
+        for (int k = 0; k < KX; ++k) acc[k] = 0ull;
+        for (int row = c; row < ROWS; row += C) {
+            const int y = row % RC_TY, z = row / RC_TY;
+            const uint16_t *ar = As + row * RC_TX;
+            const uint16_t *br = Bs + ((z - sz + rz) * BY + (y - sy + ry)) * BX;
+            uint32_t win[KX];  // b at x .. x + 2 RX
+#pragma unroll
+            for (int j = 0; j < KX - 1; ++j) win[j + 1] = br[j];
+#pragma unroll
+            for (int x = 0; x < RC_TX; ++x) {
+#pragma unroll
+                for (int j = 0; j < KX - 1; ++j) win[j] = win[j + 1];
+                win[KX - 1] = br[x + 2 * RX];
+                const uint32_t a = ar[x];
+#pragma unroll
+                for (int k = 0; k < KX; ++k) acc[k] += (unsigned long long)(a * win[2 * RX - k]);
             }
-        if (acc) atomicAdd(sab + si, acc);
+        }
+#pragma unroll
+        for (int k = 0; k < KX; ++k)
+            if (acc[k]) atomicAdd(red + g * KX + k, acc[k]);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < G * KX; i += RC_THREADS)
+        if (red[i]) atomicAdd(sab + i, red[i]);
+}
+
+// Shared memory of k_reg_corr<RX>.
+size_t reg_corr_smem(int rx, int ry, int rz) {
+    const size_t G = (size_t)(2 * ry + 1) * (2 * rz + 1), KX = 2 * rx + 1;
+    return 8 * G * KX + 2 * ((size_t)RC_TX * RC_TY * RC_TZ +
+                             (size_t)(RC_TX + 2 * rx) * (RC_TY + 2 * ry) * (RC_TZ + 2 * rz));
+}
+
+using RegCorrFn = void (*)(const uint16_t *, const uint16_t *, int, int, int, int3, int3, int3, int, int,
+                           unsigned long long *);
+template <int... R>
+RegCorrFn reg_corr_fn(int rx, std::integer_sequence<int, R...>) {
+    RegCorrFn f = nullptr;
+    ((rx == R ? (f = k_reg_corr<R>, 0) : 0), ...);
+    return f;
 }
 
 // Per row (y, z) of the region U of one tile and x-shift sxi: the sums of v
@@ -189,26 +236,35 @@ __global__ void __launch_bounds__(RQ_THREADS) k_reg_q(const unsigned long long *
     }
 }
 
-// Per shift: the sums of v and v^2 over the tile's shared box.
+// Per shift: the sums of v and v^2 over the tile's shared box; one warp per
+// shift, lanes over the planes of the box.
 __global__ void k_reg_box(const unsigned long long *__restrict__ q1, const unsigned long long *__restrict__ q2,
                           int X, int Y, int Z, int3 u0, int3 u1, int3 d0, int3 r, int side,
                           unsigned long long *__restrict__ s1, unsigned long long *__restrict__ s2) {
-    const int UY = u1.y - u0.y, UZ = u1.z - u0.z;
+    const int UY = u1.y - u0.y, UZ = u1.z - u0.z, lane = threadIdx.x & 31;
     const int SX = 2 * r.x + 1, SY = 2 * r.y + 1, S = SX * SY * (2 * r.z + 1);
-    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < S; si += gridDim.x * blockDim.x) {
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int si = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; si < S; si += nw) {
         const int sxi = si % SX, sy = (si / SX) % SY - r.y, sz = si / (SX * SY) - r.z;
         const Range xr = shared_range(d0.x + sxi - r.x, X, side);
         const Range yr = shared_range(d0.y + sy, Y, side), zr = shared_range(d0.z + sz, Z, side);
         unsigned long long a = 0, b = 0;
         if (xr.lo < xr.hi && yr.lo < yr.hi && zr.lo < zr.hi) {
-            for (int z = zr.lo; z < zr.hi; ++z) {
+            for (int z = zr.lo + lane; z < zr.hi; z += 32) {
                 const size_t q = (size_t)(sxi * UZ + (z - u0.z)) * (UY + 1);
                 a += q1[q + (yr.hi - u0.y)] - q1[q + (yr.lo - u0.y)];
                 b += q2[q + (yr.hi - u0.y)] - q2[q + (yr.lo - u0.y)];
             }
         }
-        s1[si] = a;
-        s2[si] = b;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+            b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        }
+        if (lane == 0) {
+            s1[si] = a;
+            s2[si] = b;
+        }
     }
 }
 
@@ -287,8 +343,8 @@ int side_sums(Scratch &sc, const Prefix &pf, const uint16_t *T, const int *D, co
     const int rows = UY * UZ;
     k_reg_rows<<<(rows + 7) / 8, 256, 0, sc.s>>>(T, D[0], D[1], u0, u1, d0[0], r[0], side, p1, p2);
     k_reg_q<<<SX * UZ, RQ_THREADS, 0, sc.s>>>(p1, p2, u0, u1, q1, q2);
-    k_reg_box<<<(S + 127) / 128, 128, 0, sc.s>>>(q1, q2, D[0], D[1], D[2], u0, u1, make_int3(d0[0], d0[1], d0[2]),
-                                                 make_int3(r[0], r[1], r[2]), side, s1, s2);
+    k_reg_box<<<(S + 7) / 8, 256, 0, sc.s>>>(q1, q2, D[0], D[1], D[2], u0, u1, make_int3(d0[0], d0[1], d0[2]),
+                                             make_int3(r[0], r[1], r[2]), side, s1, s2);
     RK(cudaGetLastError());
     return SEG_OK;
 }
@@ -373,9 +429,10 @@ extern "C" int seg_register_montage(int device, const uint16_t *const *tiles, in
     RK(sc.alloc(&pf.p2, np));
     RK(sc.alloc(&pf.q1, nq));
     RK(sc.alloc(&pf.q2, nq));
-    const size_t smem = sizeof(uint16_t) * ((size_t)RC_TX * RC_TY * RC_TZ +
-                                            (size_t)(RC_TX + 2 * r[0]) * (RC_TY + 2 * r[1]) * (RC_TZ + 2 * r[2]));
-    RK(cudaFuncSetAttribute(k_reg_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = reg_corr_smem(r[0], r[1], r[2]);
+    const RegCorrFn corr = reg_corr_fn(r[0], std::make_integer_sequence<int, SEG_REG_MAX_RXY + 1>{});
+    if (!corr) return SEG_EINVAL;
+    RK(cudaFuncSetAttribute(corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (seg_montage_edge &e : E) {
         const int d0[3] = {stage[e.b].x - stage[e.a].x, stage[e.b].y - stage[e.a].y, stage[e.b].z - stage[e.a].z};
         RK(cudaMemsetAsync(dsum, 0, S * sizeof(unsigned long long), sc.s));
@@ -384,9 +441,8 @@ extern "C" int seg_register_montage(int device, const uint16_t *const *tiles, in
         if (u1.x > u0.x && u1.y > u0.y && u1.z > u0.z) {
             const int nb = ((u1.x - u0.x + RC_TX - 1) / RC_TX) * ((u1.y - u0.y + RC_TY - 1) / RC_TY) *
                            ((u1.z - u0.z + RC_TZ - 1) / RC_TZ);
-            k_reg_corr<<<nb, RC_THREADS, smem, sc.s>>>(dt[e.a], dt[e.b], D[0], D[1], D[2], u0, u1,
-                                                       make_int3(d0[0], d0[1], d0[2]), make_int3(r[0], r[1], r[2]),
-                                                       dsum);
+            corr<<<nb, RC_THREADS, smem, sc.s>>>(dt[e.a], dt[e.b], D[0], D[1], D[2], u0, u1,
+                                                 make_int3(d0[0], d0[1], d0[2]), r[1], r[2], dsum);
             RK(cudaGetLastError());
         }
         int rc = side_sums(sc, pf, dt[e.a], D, d0, r, 0, dsum + S, dsum + 2 * (size_t)S);
