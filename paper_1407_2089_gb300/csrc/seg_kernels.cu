@@ -2011,7 +2011,10 @@ __global__ void __launch_bounds__(MRF_TILE) k_mrf_stats(const BatchHdr *__restri
         const bool vec = n == 8u && V.mrf_vec;  // (mrf_buf is always aligned)
         int32_t c[8];
         mrf_load8(r0, vec, n, c);
-        for (uint32_t j = 0; j < n; ++j) atomicOr(sbits + (c[j] >> 5), 1u << (c[j] & 31));
+        for (uint32_t j = 0; j < n; ++j) {  // most levels are already marked: test before setting
+            const uint32_t bit = 1u << (c[j] & 31);
+            if (!(sbits[c[j] >> 5] & bit)) atomicOr(sbits + (c[j] >> 5), bit);
+        }
         if (y >= 1 && y + 1 < Y) {
             int32_t a[8], b[8];
             mrf_load8(r0 - X, vec, n, a);
