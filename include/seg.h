@@ -193,6 +193,18 @@ int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
 int seg_read_distance(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
                       uint64_t dst_elems, int dst_on_device);
 
+/* The distance of every cell of channel cells_channel to the nearest
+ * foreground voxel of channel map_channel (Fig. 4: each stem cell's distance
+ * to its nearest vessel): dst[k - 1] = the smallest value of map_channel's
+ * distance map over the voxels of cell k (weighted squared distance, see
+ * seg_channel_params.distance_weights), K = the cells of cells_channel
+ * (*n_cells, optional).  dst is host memory of cap entries; dst = NULL with
+ * cap = 0 only reports K.  Blocks until done.  Errors: SEG_EINVAL also when
+ * map_channel has no distance map; SEG_ESMALL (cap < K); otherwise as
+ * seg_read_labels. */
+int seg_read_cell_distance(seg_ctx *ctx, seg_req req, uint32_t cells_channel, uint32_t map_channel, uint32_t *dst,
+                           uint64_t cap, uint64_t *n_cells);
+
 /* Copies the image channel `channel` was segmented from after its denoise
  * (front end or MRF; X*Y*Z uint16, layout of the input) to dst (host, or
  * device when dst_on_device = 1); *mrf_steps (optional) gets the number of

@@ -86,6 +86,8 @@ def _load():
         lib.oracle_mrf.argtypes = [u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u16p,
                                    u32p]
         lib.oracle_mrf.restype = ctypes.c_int
+        lib.oracle_cell_distance.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_uint64, u32p]
+        lib.oracle_cell_distance.restype = ctypes.c_int
         i32p = ctypes.POINTER(ctypes.c_int32)
         lib.oracle_reg_sums.argtypes = [u16p, u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, i32p, u64p]
         lib.oracle_reg_sums.restype = None
@@ -295,6 +297,22 @@ def mrf(vol: np.ndarray, max_iter: int):
     if rc:
         raise RuntimeError("oracle_mrf failed: %d" % rc)
     return out, int(it[0])
+
+
+def cell_distance(labels: np.ndarray, dmap: np.ndarray, k: int) -> np.ndarray:
+    """Per cell 1..k of `labels`, the smallest value of `dmap` over its voxels
+    (the cell's distance to the nearest vessel when dmap is the vessel
+    channel's distance map)."""
+    lab = np.ascontiguousarray(labels, dtype=np.uint32)
+    m = np.ascontiguousarray(dmap, dtype=np.uint32)
+    if lab.shape != m.shape:
+        raise ValueError("labels and map differ in shape")
+    out = np.empty(max(int(k), 1), dtype=np.uint32)
+    rc = _load().oracle_cell_distance(_ptr(lab, ctypes.c_uint32), _ptr(m, ctypes.c_uint32), lab.size, int(k),
+                                      _ptr(out, ctypes.c_uint32))
+    if rc:
+        raise RuntimeError("oracle_cell_distance failed: %d" % rc)
+    return out[: int(k)]
 
 
 EDGE_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("shift", "<i4", (3,)), ("pad0", "<u4"),

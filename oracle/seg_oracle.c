@@ -573,6 +573,22 @@ int oracle_mrf(const uint16_t *v, uint32_t X, uint32_t Y, uint32_t Z, uint32_t m
     return ORACLE_OK;
 }
 
+/* Cell-to-vessel distance (Segmentation section and Fig. 4: each stem cell's
+ * distance to its nearest vessel): for cell k = 1..K of a label image, the
+ * smallest value of a distance map over the cell's voxels (out[k - 1];
+ * 0xFFFFFFFF for a label with no voxel). */
+int oracle_cell_distance(const uint32_t *labels, const uint32_t *map, uint64_t n, uint64_t k, uint32_t *out) {
+    if (!labels || !map || !out) return ORACLE_EINVAL;
+    for (uint64_t c = 0; c < k; ++c) out[c] = 0xFFFFFFFFu;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint32_t l = labels[i];
+        if (l == 0) continue;
+        if (l > k) return ORACLE_EINVAL;
+        if (map[i] < out[l - 1]) out[l - 1] = map[i];
+    }
+    return ORACLE_OK;
+}
+
 /* ---- Montage registration (Registration section, Eq. 4) -------------------
  *
  * Overlapping tiles of a montage are placed at their stage positions; each

@@ -91,7 +91,7 @@ class seg_stats(ctypes.Structure):
 
 
 EXPORTS = ["seg_create", "seg_destroy", "seg_submit_volume", "seg_flush", "seg_poll",
-           "seg_enqueue_wait", "seg_read_labels", "seg_read_distance", "seg_read_denoised",
+           "seg_enqueue_wait", "seg_read_labels", "seg_read_distance", "seg_read_cell_distance", "seg_read_denoised",
            "seg_read_features", "seg_release",
            "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror",
            "seg_otsu_threshold_noalloc", "seg_register_montage"]
@@ -109,6 +109,7 @@ def _bind(lib):
         "seg_enqueue_wait": [vp, u64, vp],
         "seg_read_labels": [vp, u64, u32, vp, u64, i32],
         "seg_read_distance": [vp, u64, u32, vp, u64, i32],
+        "seg_read_cell_distance": [vp, u64, u32, u32, vp, u64, P(u64)],
         "seg_read_denoised": [vp, u64, u32, vp, u64, i32, P(u32)],
         "seg_read_features": [vp, u64, u32, vp, u64, P(u64), P(ctypes.c_uint16)],
         "seg_release": [vp, u64],
@@ -270,6 +271,19 @@ def seg_read_distance(ctx, req, channel, out):
     else:
         ptr, n, dev = out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
     _check(_lib.seg_read_distance(ctx, req, channel, ctypes.c_void_p(ptr), n, dev), "seg_read_distance")
+    return out
+
+
+def seg_read_cell_distance(ctx, req, cells_channel, map_channel):
+    """Per cell of cells_channel, its distance to the nearest foreground voxel
+    of map_channel (a uint32 array of K weighted squared distances)."""
+    k = ctypes.c_uint64()
+    _check(_lib.seg_read_cell_distance(ctx, req, cells_channel, map_channel, None, 0, ctypes.byref(k)),
+           "seg_read_cell_distance")
+    out = np.zeros(k.value, dtype=np.uint32)
+    if k.value:
+        _check(_lib.seg_read_cell_distance(ctx, req, cells_channel, map_channel, ctypes.c_void_p(out.ctypes.data),
+                                           k.value, ctypes.byref(k)), "seg_read_cell_distance")
     return out
 
 

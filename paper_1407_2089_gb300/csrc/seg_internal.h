@@ -204,6 +204,10 @@ constexpr int DN_MAX_R = 16;
 constexpr int CL_MAX_R = 8;      // closing ball radius limit
 cudaError_t launch_denoise(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);
 
+// Cell-to-vessel distance: out[k - 1] = min of map over the voxels labelled k.
+cudaError_t launch_cell_distance(const uint32_t *labels, const uint32_t *map, uint64_t n, uint32_t *out, uint64_t k,
+                                 int sms, cudaStream_t s);
+
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);
 // Sets kernel attributes on `device` and fills the persistent grid sizes of

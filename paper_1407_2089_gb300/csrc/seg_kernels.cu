@@ -2923,6 +2923,29 @@ __global__ void __launch_bounds__(128) k_dist_z(const BatchHdr *__restrict__ h) 
     }
 }
 
+// Cell-to-vessel distance (Fig. 4): out[k - 1] = min over the voxels of cell k
+// of a distance map (out preset to DT_INF).  Each thread takes 8 consecutive
+// voxels and flushes one atomic per run of equal labels.
+__global__ void __launch_bounds__(256) k_cell_distance(const uint32_t *__restrict__ labels,
+                                                       const uint32_t *__restrict__ map, uint64_t n, uint64_t k,
+                                                       uint32_t *__restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
+    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; i0 < n; i0 += stride) {
+        const uint64_t e = i0 + 8 < n ? i0 + 8 : n;
+        uint32_t cur = 0, best = 0xFFFFFFFFu;
+        for (uint64_t i = i0; i < e; ++i) {
+            const uint32_t l = labels[i];
+            if (l != cur) {
+                if (cur && cur <= k) atomicMin(out + (cur - 1), best);
+                cur = l;
+                best = 0xFFFFFFFFu;
+            }
+            if (l) best = min(best, map[i]);
+        }
+        if (cur && cur <= k) atomicMin(out + (cur - 1), best);
+    }
+}
+
 template <int TY>
 cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s,
                                 cudaEvent_t *ev, int &k) {
@@ -3028,6 +3051,16 @@ static void launch_box_passes(const BatchHdr *d, const LaunchPlan &p, cudaStream
     k_box3<0><<<p.grid_box, 256, BOX_SMEM, s>>>(d);
     k_box3<1><<<p.grid_box, 256, BOX_SMEM, s>>>(d);
     k_box3<2><<<p.grid_box, 256, BOX_SMEM, s>>>(d);
+}
+
+cudaError_t launch_cell_distance(const uint32_t *labels, const uint32_t *map, uint64_t n, uint32_t *out, uint64_t k,
+                                 int sms, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0xFF, 4 * (k ? k : 1), s);
+    if (e != cudaSuccess || k == 0 || n == 0) return e;
+    const uint64_t want = (n + 8 * 256 - 1) / (8 * 256);
+    const int grid = (int)std::min<uint64_t>(want, (uint64_t)sms * 8);
+    k_cell_distance<<<grid, 256, 0, s>>>(labels, map, n, k, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_denoise(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {

@@ -1039,6 +1039,35 @@ int seg_read_denoised(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst
     return cuda_fail(e, "seg_read_denoised");
 }
 
+int seg_read_cell_distance(seg_ctx *ctx, seg_req req, uint32_t cells_channel, uint32_t map_channel, uint32_t *dst,
+                           uint64_t cap, uint64_t *n_cells) {
+    if (!ctx) return SEG_EINVAL;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (r->state == SEG_PENDING) return SEG_ENOTREADY;
+        if (r->state == SEG_FAILED) return SEG_EFAILED;
+    }
+    if (cells_channel >= r->C || map_channel >= r->C || !r->dist(map_channel)) return SEG_EINVAL;
+    const uint64_t k = r->ncells[cells_channel];
+    if (n_cells) *n_cells = k;
+    if (!dst) return cap == 0 ? SEG_OK : SEG_EINVAL;
+    if (cap < k) return SEG_ESMALL;
+    if (k == 0) return SEG_OK;
+    cudaSetDevice(ctx->device);
+    uint32_t *d = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d), 4 * k, ctx->read_stream);
+    if (e == cudaSuccess)
+        e = launch_cell_distance(r->labels(cells_channel), r->dist(map_channel), r->g[cells_channel].n, d, k,
+                                 ctx->sms, ctx->read_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, d, 4 * k, cudaMemcpyDeviceToHost, ctx->read_stream);
+    if (d) cudaFreeAsync(d, ctx->read_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
+    return cuda_fail(e, "seg_read_cell_distance");
+}
+
 int seg_read_distance(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst, uint64_t dst_elems,
                       int dst_on_device) {
     if (!ctx || !dst) return SEG_EINVAL;

@@ -180,3 +180,53 @@ def test_vessel_frame_full_size(seg, ctx):
     exp = oracle.distance_at(fg, pts, w)
     got = np.array([dist[p] for p in pts], dtype=np.uint32)
     assert np.array_equal(got, exp)
+
+
+def test_cell_to_vessel_distance(seg, ctx):
+    # cells of a nuclei channel against the distance map of a vessel channel
+    # of the same request (Fig. 4), against the oracle's full map
+    X, Y, Z = 96, 80, 24
+    rng = np.random.default_rng(41)
+    nuc = boxes((X, Y, Z), 42, n=12)
+    ves = rng.normal(200, 20, size=(Z, Y, X))
+    ves[8:12, :, 30:34] += 2500
+    ves[:, 50:53, 10:90] += 2500
+    ves = np.rint(ves).clip(0, 65535).astype(np.uint16)
+    vol = np.stack([nuc, ves])
+    w = (16, 16, 25)
+    req = seg.seg_submit_volume(ctx, vol, min_volume=5, distance_weights=[None, w])
+    seg.seg_flush(ctx)
+    try:
+        assert seg.seg_wait(ctx, req) == seg.SEG_DONE
+        cd = seg.seg_read_cell_distance(ctx, req, 0, 1)
+        with pytest.raises(seg.SegError) as e:
+            seg.seg_read_cell_distance(ctx, req, 1, 0)  # channel 0 has no map
+        assert e.value.code == seg.SEG_EINVAL
+    finally:
+        seg.seg_release(ctx, req)
+    r0 = oracle.segment(nuc, min_volume=5)
+    r1 = oracle.segment(ves, min_volume=5, distance_weights=w)
+    want = oracle.cell_distance(r0.labels, r1.distance, r0.n_cells)
+    assert len(cd) == r0.n_cells > 0 and np.array_equal(cd, want)
+
+
+def test_cell_to_vessel_distance_full_size(seg, ctx):
+    # the time-lapse frame (nuclei and vessel channels): exact for the ten
+    # smallest cells (brute force over the oracle's vessel foreground)
+    tl = synth.TimeLapse(frames=1)
+    vol = np.stack([tl.frame(0, 0), tl.frame(0, 1)])
+    w = (16, 16, 25)
+    req = seg.seg_submit_volume(ctx, vol, min_volume=30, distance_weights=[None, w])
+    seg.seg_flush(ctx)
+    try:
+        assert seg.seg_wait(ctx, req) == seg.SEG_DONE
+        cd = seg.seg_read_cell_distance(ctx, req, 0, 1)
+    finally:
+        seg.seg_release(ctx, req)
+    r0 = oracle.segment(vol[0], min_volume=30)
+    r1 = oracle.segment(vol[1], min_volume=30, keep_smoothed=True)
+    fg = r1.smoothed > r1.threshold
+    assert len(cd) == r0.n_cells
+    for k in np.argsort(r0.cells["count"])[:10] + 1:
+        pts = [tuple(p) for p in np.argwhere(r0.labels == k)]
+        assert cd[k - 1] == oracle.distance_at(fg, pts, w).min(), k

@@ -831,3 +831,26 @@ def test_register_tree_is_maximum():
             best = w if best is None else max(best, w)
     chosen = edges[edges["in_tree"] == 1]["score"].sum()
     assert len(edges[edges["in_tree"] == 1]) == n - 1 and chosen == pytest.approx(best, abs=1e-12)
+
+
+def test_cell_distance_is_the_smallest_map_value_per_cell():
+    rng = np.random.default_rng(95)
+    lab = rng.integers(0, 6, size=(5, 7, 9)).astype(np.uint32)
+    lab[0, 0, 0] = 5
+    m = rng.integers(0, 1 << 31, size=lab.shape).astype(np.uint32)
+    got = oracle.cell_distance(lab, m, 7)  # labels 6 and 7 have no voxel
+    for k in range(1, 8):
+        sel = m[lab == k]
+        assert got[k - 1] == (sel.min() if sel.size else 0xFFFFFFFF), k
+    # a cell touching the vessel foreground is at distance 0; the whole
+    # stage's cells against the oracle's vessel map
+    vol = synth.single_frame()
+    r = oracle.segment(vol, min_volume=30)
+    vessel = np.zeros(vol.shape, bool)
+    vessel[10:12, 40:90, 60:64] = True
+    dmap = oracle.distance(vessel, (16, 16, 25))
+    cd = oracle.cell_distance(r.labels, dmap, r.n_cells)
+    for k in range(1, r.n_cells + 1):
+        inside = (r.labels == k)
+        assert cd[k - 1] == dmap[inside].min()
+        assert (cd[k - 1] == 0) == bool((inside & vessel).any())
