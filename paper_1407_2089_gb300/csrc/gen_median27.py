@@ -110,14 +110,14 @@ def median3x9():
     return kept, out
 
 
-def _cmp(lines, v, a, b, na=True, nb=True):
+def _cmp(lines, v, a, b, na=True, nb=True, mn="min", mx="max"):
     if na and nb:
-        lines.append("    { const uint32_t t = min(%s[%d], %s[%d]); %s[%d] = max(%s[%d], %s[%d]); %s[%d] = t; }"
-                     % (v, a, v, b, v, b, v, a, v, b, v, a))
+        lines.append("    { const uint32_t t = %s(%s[%d], %s[%d]); %s[%d] = %s(%s[%d], %s[%d]); %s[%d] = t; }"
+                     % (mn, v, a, v, b, v, b, mx, v, a, v, b, v, a))
     elif na:
-        lines.append("    %s[%d] = min(%s[%d], %s[%d]);" % (v, a, v, a, v, b))
+        lines.append("    %s[%d] = %s(%s[%d], %s[%d]);" % (v, a, mn, v, a, v, b))
     else:
-        lines.append("    %s[%d] = max(%s[%d], %s[%d]);" % (v, b, v, a, v, b))
+        lines.append("    %s[%d] = %s(%s[%d], %s[%d]);" % (v, b, mx, v, a, v, b))
 
 
 def emit(path):
@@ -125,7 +125,8 @@ def emit(path):
     m_ops, m_out = median3x9()
     lines = [
         "// Generated by gen_median27.py: sort9 (%d comparators) and the median of" % len(s_ops),
-        "// three sorted lists of 9 (%d comparators, pruned Batcher networks)." % len(m_ops),
+        "// three sorted lists of 9 (%d comparators, pruned Batcher networks), on" % len(m_ops),
+        "// one voxel per 32-bit word and on two voxels per word (16-bit halves).",
         "#pragma once",
         "",
         "// Sorts v[0..8] in place (s[k] receives the k-th smallest).",
@@ -145,6 +146,38 @@ def emit(path):
     lines += ["    w[%d] = c[%d];" % (32 + i, i) for i in range(9)]
     for a, b, na, nb in m_ops:
         _cmp(lines, "w", a, b, na, nb)
+    lines += ["    return w[%d];" % m_out, "}"]
+    # the same networks on two voxels at once: each 32-bit word holds two
+    # 16-bit values and every comparator is one packed min and one packed max
+    lines += ["",
+              "// Packed unsigned 16-bit min and max of both halves (sm_90 and later).",
+              "__device__ __forceinline__ uint32_t vmin16x2(uint32_t a, uint32_t b) {",
+              "    uint32_t d;",
+              '    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));',
+              "    return d;",
+              "}",
+              "__device__ __forceinline__ uint32_t vmax16x2(uint32_t a, uint32_t b) {",
+              "    uint32_t d;",
+              '    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));',
+              "    return d;",
+              "}",
+              "",
+              "// sort9 on two voxels: every word of v holds one value of each.",
+              "__device__ __forceinline__ void sort9x2(const uint32_t *v, uint32_t *s) {",
+              "    uint32_t w[16];"]
+    lines += ["    w[%d] = v[%d];" % (i, i) for i in range(9)]
+    for a, b in s_ops:
+        _cmp(lines, "w", a, b, mn="vmin16x2", mx="vmax16x2")
+    lines += ["    s[%d] = w[%d];" % (k, s_out[k]) for k in range(9)]
+    lines += ["}", "",
+              "// median3x9 on two voxels (packed as in sort9x2).",
+              "__device__ __forceinline__ uint32_t median3x9x2(const uint32_t *a, const uint32_t *b, const uint32_t *c) {",
+              "    uint32_t w[64];"]
+    lines += ["    w[%d] = a[%d];" % (i, i) for i in range(9)]
+    lines += ["    w[%d] = b[%d];" % (16 + i, i) for i in range(9)]
+    lines += ["    w[%d] = c[%d];" % (32 + i, i) for i in range(9)]
+    for a, b, na, nb in m_ops:
+        _cmp(lines, "w", a, b, na, nb, mn="vmin16x2", mx="vmax16x2")
     lines += ["    return w[%d];" % m_out, "}"]
     with open(path, "w") as f:
         f.write("\n".join(lines) + "\n")

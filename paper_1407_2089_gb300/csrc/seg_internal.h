@@ -200,6 +200,7 @@ cudaError_t launch_tile_probe(const BatchHdr *d_hdr, const LaunchPlan &plan, cud
 
 // Denoise front end of the volumes with dn_r > 0 (none: the kernels exit).
 constexpr int DN_CHUNK = 128;    // box-pass positions per tile along a line
+constexpr int MED_TILE_X = 64, MED_TILE_Y = 8, MED_TILE_Z = 8;  // k_median27 tile (voxels)
 constexpr int DN_MAX_R = 16;
 constexpr int CL_MAX_R = 8;      // closing ball radius limit
 cudaError_t launch_denoise(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaStream_t stream);

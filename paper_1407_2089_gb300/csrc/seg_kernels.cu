@@ -1703,27 +1703,32 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
     }
 }
 
-// D = max(L - B, 0) staged per tile of 32 x 8 x 8 voxels (plus a one-voxel
+// D = max(L - B, 0) staged per tile of 64 x 8 x 8 voxels (plus a one-voxel
 // halo, clamped), then the median of each voxel's 27 neighbours from the
 // sorted 3x3 neighbourhoods of its three planes; the result is the volume
-// the smoothing reads.
-constexpr int MED_TX = 32, MED_TY = 8, MED_TZ = 8;
+// the smoothing reads.  Each thread takes two neighbouring voxels along x:
+// the comparator networks run on 16-bit halves of 32-bit words (packed min
+// and max), and the pairs of a 3x3 row are two aligned shared-memory words
+// and one byte permutation of them.
+constexpr int MED_TX = 32, MED_TY = 8, MED_TZ = 8;  // threads along x and y; planes per tile
+static_assert(2 * MED_TX == MED_TILE_X && MED_TY == MED_TILE_Y && MED_TZ == MED_TILE_Z, "median tile");
 
 __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr *__restrict__ h) {
     __shared__ VolIndex<&VolDev::dn_tbase> VI;
-    __shared__ uint16_t d[MED_TZ + 2][MED_TY + 2][MED_TX + 2];
+    __shared__ __align__(16) uint16_t d[MED_TZ + 2][MED_TY + 2][MED_TILE_X + 2];  // rows of 132 bytes
     VI.load(h);
     const int tx = threadIdx.x % MED_TX, ty = threadIdx.x / MED_TX;
     for (uint32_t t = blockIdx.x; t < h->dn_tiles; t += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, t)];
         const uint32_t lt = t - V.dn_tbase;
         const int X = (int)V.X, Y = (int)V.Y, Z = (int)V.Z;
-        const int ntx = (X + MED_TX - 1) / MED_TX, nty = (Y + MED_TY - 1) / MED_TY;
-        const int x0 = (int)(lt % ntx) * MED_TX, y0 = (int)((lt / ntx) % nty) * MED_TY;
+        const int ntx = (X + MED_TILE_X - 1) / MED_TILE_X, nty = (Y + MED_TY - 1) / MED_TY;
+        const int x0 = (int)(lt % ntx) * MED_TILE_X, y0 = (int)((lt / ntx) % nty) * MED_TY;
         const int z0 = (int)(lt / ((uint32_t)ntx * nty)) * MED_TZ;
         __syncthreads();  // the previous tile is done with d
-        constexpr int NS = (MED_TZ + 2) * (MED_TY + 2) * (MED_TX + 2);
-        // 14 elements per thread, loaded in two rounds of 7 pairs in flight
+        constexpr int SXW = MED_TILE_X + 2;
+        constexpr int NS = (MED_TZ + 2) * (MED_TY + 2) * SXW;
+        // 26 elements per thread, loaded in rounds of 7 pairs in flight
         constexpr int NT = MED_TX * MED_TY, NB = 7;
         for (int i0 = threadIdx.x; i0 < NS; i0 += NT * NB) {
             uint16_t lv[NB], bv[NB];
@@ -1731,8 +1736,7 @@ __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr 
             for (int j = 0; j < NB; ++j) {
                 const int i = i0 + j * NT;
                 if (i < NS) {
-                    const int sx = i % (MED_TX + 2), sy = (i / (MED_TX + 2)) % (MED_TY + 2);
-                    const int sz = i / ((MED_TX + 2) * (MED_TY + 2));
+                    const int sx = i % SXW, sy = (i / SXW) % (MED_TY + 2), sz = i / (SXW * (MED_TY + 2));
                     const int x = min(max(x0 - 1 + sx, 0), X - 1), y = min(max(y0 - 1 + sy, 0), Y - 1);
                     const int z = min(max(z0 - 1 + sz, 0), Z - 1);
                     const size_t g = (size_t)x + (size_t)X * ((size_t)y + (size_t)Y * z);
@@ -1747,24 +1751,37 @@ __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr 
             }
         }
         __syncthreads();
-        const int x = x0 + tx, y = y0 + ty;
+        const int x = x0 + 2 * tx, y = y0 + ty;
         if (x >= X || y >= Y) continue;
-        // each plane's 3x3 neighbourhood is sorted once and serves the three
-        // voxels above, at and below it
+        // the pair's 3x3 neighbourhood in plane c: shared x indices 2 tx + a
+        // and 2 tx + 1 + a for a = 0, 1, 2, i.e. word tx, the middle of words
+        // tx and tx + 1, and word tx + 1 of each row
         auto plane = [&](int c, uint32_t *srt) {
             uint32_t v[9];
 #pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) v[3 * b + a] = d[c][ty + b][tx + a];
-            sort9(v, srt);
+            for (int b = 0; b < 3; ++b) {
+                const uint32_t *row = reinterpret_cast<const uint32_t *>(&d[c][ty + b][0]);
+                const uint32_t w0 = row[tx], w1 = row[tx + 1];
+                v[3 * b] = w0;
+                v[3 * b + 1] = __byte_perm(w0, w1, 0x5432);
+                v[3 * b + 2] = w1;
+            }
+            sort9x2(v, srt);
         };
+        const bool two = x + 1 < X, wide = two && (X & 1) == 0;  // 32-bit stores at even x of even rows
         uint32_t s0[9], s1[9], s2[9];
         plane(0, s0);
         plane(1, s1);
         for (int k = 0; k < MED_TZ && z0 + k < Z; ++k) {
             plane(k + 2, s2);
-            V.dn_out[(size_t)x + (size_t)X * ((size_t)y + (size_t)Y * (z0 + k))] = (uint16_t)median3x9(s0, s1, s2);
+            const uint32_t m = median3x9x2(s0, s1, s2);
+            uint16_t *o = V.dn_out + (size_t)x + (size_t)X * ((size_t)y + (size_t)Y * (z0 + k));
+            if (wide) {
+                *reinterpret_cast<uint32_t *>(o) = m;
+            } else {
+                o[0] = (uint16_t)(m & 0xFFFFu);
+                if (two) o[1] = (uint16_t)(m >> 16);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 s0[i] = s1[i];

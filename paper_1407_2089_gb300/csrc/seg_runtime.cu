@@ -329,7 +329,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
                 V.dn_n[0] = (uint32_t)(cdiv((uint64_t)g.Y * g.Z, 64) * cdiv(g.X, DN_CHUNK));
                 V.dn_n[1] = (uint32_t)(cdiv(g.X, 64) * g.Z * cdiv(g.Y, DN_CHUNK));
                 V.dn_n[2] = (uint32_t)(cdiv(g.X, 64) * g.Y * cdiv(g.Z, DN_CHUNK));
-                V.dn_tiles = (uint32_t)(cdiv(g.X, 32) * cdiv(g.Y, 8) * cdiv(g.Z, 8));
+                V.dn_tiles = (uint32_t)(cdiv(g.X, MED_TILE_X) * cdiv(g.Y, MED_TILE_Y) * cdiv(g.Z, MED_TILE_Z));
             }
             V.dn_base0 = dn[0];
             V.dn_base1 = dn[1];
