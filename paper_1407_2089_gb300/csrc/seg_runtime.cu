@@ -540,7 +540,14 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
     for (int k = 0; k < DT_NK; ++k) ctx->plan.distance |= s.h_hdr->dt_items[k] > 0;
     ctx->plan.mrf_iters = b.mrf_iters;
     if (ctx->graphs) {
-        cudaGraphExec_t &ge = s.graph[graph_key(ctx->plan)];
+        const uint64_t key = graph_key(ctx->plan);
+        if (s.graph.size() >= 64 && !s.graph.count(key)) {
+            // many distinct plans (e.g. varying MRF step limits): start over
+            for (auto &g : s.graph)
+                if (g.second) cudaGraphExecDestroy(g.second);
+            s.graph.clear();
+        }
+        cudaGraphExec_t &ge = s.graph[key];
         if (!ge) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
