@@ -10,7 +10,8 @@ value:  Gvoxels/s with the inputs already resident in HBM (device-timed with
         CUDA events on the ordering stream around all steps).
 e2e:    the same metric through the C ABI from pinned host buffers: every step
         copies the inputs host->device inside seg_submit_volume and reads the
-        label images and cell tables back to host memory.
+        label images and cell tables back to host memory; one thread submits
+        while another reads, so both directions of the host link overlap.
 roofline: the kernel with the largest share of device time in the timed
         region, its algorithmic bytes per launch over its mean CUDA-event
         duration, against the measured copy bandwidth.
@@ -360,19 +361,52 @@ def run_gpu(args):
         ctx2 = seg.seg_create(device=local, max_inflight=3)
         cells_bytes = 0
 
+        group = max(1, args.e2e_group)
+
         def e2e_step():
+            # One thread submits (each submit copies its frame host->device)
+            # and flushes every `group` frames; this thread waits for the
+            # frames in order, reads labels and cells back and releases them,
+            # so the two directions of the host link and the kernels overlap.
             nonlocal cells_bytes
-            reqs = [seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C) for t in range(T)]
-            seg.seg_flush(ctx2)
+            q, err = [], []
+            cv = threading.Condition()
+
+            def submitter():
+                try:
+                    for t in range(T):
+                        r = seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C)
+                        if (t + 1) % group == 0 or t + 1 == T:
+                            seg.seg_flush(ctx2)
+                        with cv:
+                            q.append(r)
+                            cv.notify()
+                except BaseException as e:  # surfaced by the reader below
+                    err.append(e)
+                    with cv:
+                        cv.notify()
+
+            th = threading.Thread(target=submitter)
+            th.start()
             cb = 0
-            for t, r in enumerate(reqs):
-                if seg.seg_wait(ctx2, r) != seg.SEG_DONE:
-                    raise RuntimeError("request failed")
-                for c in range(C):
-                    seg.seg_read_labels(ctx2, r, c, h_lab[t, c])
-                    cells, _ = seg.seg_read_features(ctx2, r, c)
-                    cb += cells.nbytes
-                seg.seg_release(ctx2, r)
+            try:
+                for t in range(T):
+                    with cv:
+                        cv.wait_for(lambda: len(q) > t or err)
+                        if len(q) <= t:
+                            break
+                        r = q[t]
+                    if seg.seg_wait(ctx2, r) != seg.SEG_DONE:
+                        raise RuntimeError("request failed")
+                    for c in range(C):
+                        seg.seg_read_labels(ctx2, r, c, h_lab[t, c])
+                        cells, _ = seg.seg_read_features(ctx2, r, c)
+                        cb += cells.nbytes
+                    seg.seg_release(ctx2, r)
+            finally:
+                th.join()
+            if err:
+                raise err[0]
             cells_bytes = cb
 
         for _ in range(max(1, min(args.warmup, 2))):
@@ -395,7 +429,7 @@ def run_gpu(args):
         e2e = {"value": job_gvox_per_s(vox_step * n2, ems, ws), "unit": "Gvoxels/s",
                "h2d_bytes_per_step": int(host.nbytes),
                "d2h_bytes_per_step": int(h_lab.numel() * 4 + cells_bytes),
-               "steps": n2}
+               "steps": n2, "pipeline": "submit thread + read thread, flush every %d frames" % group}
 
     if rank == 0:
         line = {
@@ -729,6 +763,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-group", type=int, default=6, help="frames per flush in the e2e pipeline")
     ap.add_argument("--inflight", type=int, default=1,
                     help="batches in flight; 1 keeps per-kernel CUDA-event times free of overlap")
     ap.add_argument("--frames", type=int, default=FRAMES,
