@@ -7,7 +7,8 @@ its Python binding) never imports it, and the two share no code.
 The arithmetic lives in ``seg_oracle.c`` (plain single-threaded C, built by
 ``oracle/build.py``); this module only marshals numpy arrays through ctypes.
 Every function follows the paper's Segmentation section (Otsu thresholding,
-connected components, minimum volume, closing, distance map) and Background
+connected components, minimum volume, closing, distance map, each cell's
+voxels as label runs) and Background
 Noise Removal section (Eq. 1, Gaussian low-pass read as binomial smoothing;
 the stem-cell denoise front end; the MRF vessel denoise of Eqs. 2-3); see
 the C file for the exact readings.
@@ -88,6 +89,8 @@ def _load():
         lib.oracle_mrf.restype = ctypes.c_int
         lib.oracle_cell_distance.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_uint64, u32p]
         lib.oracle_cell_distance.restype = ctypes.c_int
+        lib.oracle_label_runs.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, vp, ctypes.c_uint64, u64p]
+        lib.oracle_label_runs.restype = ctypes.c_int
         i32p = ctypes.POINTER(ctypes.c_int32)
         lib.oracle_reg_sums.argtypes = [u16p, u16p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, i32p, u64p]
         lib.oracle_reg_sums.restype = None
@@ -313,6 +316,30 @@ def cell_distance(labels: np.ndarray, dmap: np.ndarray, k: int) -> np.ndarray:
     if rc:
         raise RuntimeError("oracle_cell_distance failed: %d" % rc)
     return out[: int(k)]
+
+
+RUN_DTYPE = np.dtype([("label", "<u4"), ("row", "<u4"), ("x_begin", "<u2"), ("x_end", "<u2")])
+assert RUN_DTYPE.itemsize == 12
+
+
+def label_runs(labels: np.ndarray) -> np.ndarray:
+    """Each cell's voxels (the set the Segmentation section hands to the
+    convex hull step) as runs: the maximal stretches of equal non-zero label
+    along x in one row (row = y + Y z), in order of row and x; a structured
+    array of RUN_DTYPE (label, row, first x, last x inclusive)."""
+    lab = np.ascontiguousarray(labels, dtype=np.uint32)
+    X = lab.shape[-1] if lab.ndim else 1
+    rows = lab.size // X if X else 0
+    n = np.zeros(1, dtype=np.uint64)
+    lib = _load()
+    rc = lib.oracle_label_runs(_ptr(lab, ctypes.c_uint32), X, rows, None, 0, _ptr(n, ctypes.c_uint64))
+    out = np.zeros(int(n[0]), dtype=RUN_DTYPE)
+    if len(out):
+        rc = lib.oracle_label_runs(_ptr(lab, ctypes.c_uint32), X, rows, ctypes.c_void_p(out.ctypes.data),
+                                   len(out), _ptr(n, ctypes.c_uint64))
+        if rc:
+            raise RuntimeError("oracle_label_runs failed: %d" % rc)
+    return out
 
 
 EDGE_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("shift", "<i4", (3,)), ("pad0", "<u4"),

@@ -589,6 +589,49 @@ int oracle_cell_distance(const uint32_t *labels, const uint32_t *map, uint64_t n
     return ORACLE_OK;
 }
 
+/* ---- Label runs (Segmentation section: each cell's voxels) ---------------
+ *
+ * The voxels of each cell, the set the Segmentation section passes on to the
+ * convex hull step, written as runs: the maximal stretches of equal non-zero
+ * label along x within one row (row = y + Y z), in order of row and then x.
+ * One record per run: label, row, first x, last x (inclusive).  On return *n
+ * is the number of runs; with cap < *n nothing past cap is written and the
+ * call fails with ORACLE_ESMALL. */
+typedef struct {
+    uint32_t label;
+    uint32_t row;
+    uint16_t x_begin;
+    uint16_t x_end;
+} oracle_run;
+
+int oracle_label_runs(const uint32_t *labels, uint32_t X, uint64_t rows, oracle_run *out, uint64_t cap,
+                      uint64_t *n) {
+    if (!labels || !n || X == 0 || X > 65536u) return ORACLE_EINVAL;
+    uint64_t k = 0;
+    for (uint64_t row = 0; row < rows; ++row) {
+        const uint32_t *L = labels + row * X;
+        uint32_t x = 0;
+        while (x < X) {
+            if (L[x] == 0) {
+                ++x;
+                continue;
+            }
+            uint32_t e = x;
+            while (e + 1 < X && L[e + 1] == L[x]) ++e;
+            if (k < cap && out) {
+                out[k].label = L[x];
+                out[k].row = (uint32_t)row;
+                out[k].x_begin = (uint16_t)x;
+                out[k].x_end = (uint16_t)e;
+            }
+            ++k;
+            x = e + 1;
+        }
+    }
+    *n = k;
+    return k > cap ? ORACLE_ESMALL : ORACLE_OK;
+}
+
 /* ---- Montage registration (Registration section, Eq. 4) -------------------
  *
  * Overlapping tiles of a montage are placed at their stage positions; each

@@ -854,3 +854,64 @@ def test_cell_distance_is_the_smallest_map_value_per_cell():
         inside = (r.labels == k)
         assert cd[k - 1] == dmap[inside].min()
         assert (cd[k - 1] == 0) == bool((inside & vessel).any())
+
+
+# ----------------------------------------------------------------------------
+# label runs (Segmentation section: each cell's voxels, passed to the hulls)
+# ----------------------------------------------------------------------------
+
+def runs_bruteforce(lab):
+    """Voxel by voxel: a run opens at a non-zero voxel whose left neighbour in
+    the row differs, and every further voxel of equal label extends it."""
+    X = lab.shape[-1]
+    flat = lab.reshape(-1, X)
+    out = []
+    for row in range(flat.shape[0]):
+        for x in range(X):
+            v = int(flat[row, x])
+            if v == 0:
+                continue
+            if x > 0 and int(flat[row, x - 1]) == v:
+                out[-1][3] = x
+            else:
+                out.append([v, row, x, x])
+    return out
+
+
+def test_label_runs_brute_force_and_repaint():
+    rng = np.random.default_rng(96)
+    for shape in [(1, 1, 1), (1, 1, 9), (3, 4, 1), (2, 5, 17), (4, 3, 33)]:
+        # few labels, zeros and equal neighbours, so runs of every length and
+        # adjacent runs of different labels occur
+        lab = rng.choice([0, 0, 0, 1, 2, 2, 3], size=shape).astype(np.uint32)
+        got = oracle.label_runs(lab)
+        want = runs_bruteforce(lab)
+        assert [list(map(int, r)) for r in got] == want, shape
+        # painting the runs back gives the label image
+        X = shape[-1]
+        paint = np.zeros(lab.size, np.uint32)
+        for r in got:
+            paint[int(r["row"]) * X + int(r["x_begin"]): int(r["row"]) * X + int(r["x_end"]) + 1] = r["label"]
+        assert np.array_equal(paint.reshape(shape), lab)
+    assert len(oracle.label_runs(np.zeros((3, 4, 5), np.uint32))) == 0
+    full = np.full((2, 2, 6), 9, np.uint32)
+    assert [tuple(map(int, r)) for r in oracle.label_runs(full)] == [(9, k, 0, 5) for k in range(4)]
+
+
+def test_label_runs_carry_the_cell_features():
+    # per cell, the run lengths add up to the cell's voxel count and the run
+    # ends span its bounding box
+    vol = synth.single_frame()
+    r = oracle.segment(vol, min_volume=30)
+    runs = oracle.label_runs(r.labels)
+    Z, Y, X = vol.shape
+    ln = runs["x_end"].astype(np.int64) - runs["x_begin"] + 1
+    cnt = np.bincount(runs["label"], weights=ln, minlength=r.n_cells + 1)
+    assert np.array_equal(cnt[1:].astype(np.uint64), r.cells["count"])
+    for k in range(1, r.n_cells + 1):
+        sel = runs[runs["label"] == k]
+        y, z = sel["row"] % Y, sel["row"] // Y
+        assert sel["x_begin"].min() == r.cells["bbox_min"][k - 1][0]
+        assert sel["x_end"].max() == r.cells["bbox_max"][k - 1][0]
+        assert (y.min(), z.min()) == tuple(r.cells["bbox_min"][k - 1][1:])
+        assert (y.max(), z.max()) == tuple(r.cells["bbox_max"][k - 1][1:])
