@@ -10,8 +10,10 @@ value:  Gvoxels/s with the inputs already resident in HBM (device-timed with
         CUDA events on the ordering stream around all steps).
 e2e:    the same metric through the C ABI from pinned host buffers: every step
         copies the inputs host->device inside seg_submit_volume and reads the
-        label images and cell tables back to host memory; one thread submits
-        while another reads, so both directions of the host link overlap.
+        segmentation back to host memory (each cell's voxels as label runs,
+        and the cell table); one thread submits while another reads, so both
+        directions of the host link overlap.  e2e_dense_labels: the same with
+        the dense uint32 label images read instead of the runs.
 roofline: the kernel with the largest share of device time in the timed
         region, its algorithmic bytes per launch over its mean CUDA-event
         duration, against the measured copy bandwidth.
@@ -354,82 +356,15 @@ def run_gpu(args):
                  "plain": serving(seg, torch, local, args.serving_requests, 200.0, seg.SEG_PLAIN, 1)}
 
     # end to end through the C ABI with pinned host buffers
-    e2e = None
+    e2e = e2e_dense = None
     if not args.no_e2e:
         h_in = torch.from_numpy(host.view(np.int16)).pin_memory()
-        h_lab = torch.empty((T, C, Z, Y, X), dtype=torch.int32).pin_memory()
-        ctx2 = seg.seg_create(device=local, max_inflight=3)
-        cells_bytes = 0
-
         group = max(1, args.e2e_group)
-
-        def e2e_step():
-            # One thread submits (each submit copies its frame host->device)
-            # and flushes every `group` frames; this thread waits for the
-            # frames in order, reads labels and cells back and releases them,
-            # so the two directions of the host link and the kernels overlap.
-            nonlocal cells_bytes
-            q, err = [], []
-            cv = threading.Condition()
-
-            def submitter():
-                try:
-                    for t in range(T):
-                        r = seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C)
-                        if (t + 1) % group == 0 or t + 1 == T:
-                            seg.seg_flush(ctx2)
-                        with cv:
-                            q.append(r)
-                            cv.notify()
-                except BaseException as e:  # surfaced by the reader below
-                    err.append(e)
-                    with cv:
-                        cv.notify()
-
-            th = threading.Thread(target=submitter)
-            th.start()
-            cb = 0
-            try:
-                for t in range(T):
-                    with cv:
-                        cv.wait_for(lambda: len(q) > t or err)
-                        if len(q) <= t:
-                            break
-                        r = q[t]
-                    if seg.seg_wait(ctx2, r) != seg.SEG_DONE:
-                        raise RuntimeError("request failed")
-                    for c in range(C):
-                        seg.seg_read_labels(ctx2, r, c, h_lab[t, c])
-                        cells, _ = seg.seg_read_features(ctx2, r, c)
-                        cb += cells.nbytes
-                    seg.seg_release(ctx2, r)
-            finally:
-                th.join()
-            if err:
-                raise err[0]
-            cells_bytes = cb
-
-        for _ in range(max(1, min(args.warmup, 2))):
-            e2e_step()
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        n2 = max(1, min(args.steps, args.e2e_steps))
-        t0 = time.perf_counter()
-        e0.record(stream)
-        for _ in range(n2):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        ems = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), dev, ws)
-        seg.seg_destroy(ctx2)
-        e2e = {"value": job_gvox_per_s(vox_step * n2, ems, ws), "unit": "Gvoxels/s",
-               "h2d_bytes_per_step": int(host.nbytes),
-               "d2h_bytes_per_step": int(h_lab.numel() * 4 + cells_bytes),
-               "steps": n2, "pipeline": "submit thread + read thread, flush every %d frames" % group}
+        e2e = e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, (X, Y, Z), T, C, group, "runs")
+        e2e_dense = e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, (X, Y, Z), T, C, group,
+                            "labels")
+        e2e["value"] = job_gvox_per_s(vox_step * e2e.pop("steps_timed"), e2e.pop("ms"), ws)
+        e2e_dense["value"] = job_gvox_per_s(vox_step * e2e_dense.pop("steps_timed"), e2e_dense.pop("ms"), ws)
 
     if rank == 0:
         line = {
@@ -452,6 +387,7 @@ def run_gpu(args):
             "kernel_share": shares,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_dense_labels": e2e_dense,
             "forms_gvox_s_per_gpu": forms,
             "denoise_front_end": denoise,
             "closing": closing,
@@ -754,6 +690,100 @@ def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "phases": parts,
             "achieved_gvox_s": vox / span / 1e9,
             "offered_gvox_s": vox / reqs[-1][0] / 1e9}
+
+
+def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, group, read):
+    """Steps through the C ABI from pinned host buffers.  One thread submits
+    (each submit copies its frame host->device) and flushes every `group`
+    frames; this thread waits for the frames in order, reads each channel's
+    result back and releases the frame, so the two directions of the host
+    link and the kernels overlap.  read = "runs": the label runs and cells
+    (the complete segmentation: each cell's voxels as x-runs, and its
+    features); read = "labels": the dense uint32 label images and cells."""
+    X, Y, Z = dims
+    ctx2 = seg.seg_create(device=local, max_inflight=3)
+    dense = torch.empty((T, C, Z, Y, X), dtype=torch.int32).pin_memory() if read == "labels" else None
+    run_buf = None
+    d2h = [0]
+
+    def step():
+        q, err = [], []
+        cv = threading.Condition()
+
+        def submitter():
+            try:
+                for t in range(T):
+                    r = seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C)
+                    if (t + 1) % group == 0 or t + 1 == T:
+                        seg.seg_flush(ctx2)
+                    with cv:
+                        q.append(r)
+                        cv.notify()
+            except BaseException as e:  # surfaced by the reader below
+                err.append(e)
+                with cv:
+                    cv.notify()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        nb = 0
+        try:
+            for t in range(T):
+                with cv:
+                    cv.wait_for(lambda: len(q) > t or err)
+                    if len(q) <= t:
+                        break
+                    r = q[t]
+                if seg.seg_wait(ctx2, r) != seg.SEG_DONE:
+                    raise RuntimeError("request failed")
+                for c in range(C):
+                    if dense is not None:
+                        seg.seg_read_labels(ctx2, r, c, dense[t, c])
+                        nb += dense[t, c].numel() * 4
+                    else:
+                        nb += seg.seg_read_label_runs(ctx2, r, c, run_buf[t][c]).numel()
+                    cells, _ = seg.seg_read_features(ctx2, r, c)
+                    nb += cells.nbytes
+                seg.seg_release(ctx2, r)
+        finally:
+            th.join()
+        if err:
+            raise err[0]
+        d2h[0] = nb
+
+    if read == "runs":
+        # size one pinned buffer per volume-channel from a first pass
+        counts = []
+        for t in range(T):
+            r = seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C)
+            seg.seg_flush(ctx2)
+            if seg.seg_wait(ctx2, r) != seg.SEG_DONE:
+                raise RuntimeError("request failed")
+            counts.append([len(seg.seg_read_label_runs(ctx2, r, c)) for c in range(C)])
+            seg.seg_release(ctx2, r)
+        run_buf = [[torch.empty(12 * (n + n // 4 + 1024), dtype=torch.uint8).pin_memory() for n in row]
+                   for row in counts]
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n2 = max(1, min(args.steps, args.e2e_steps))
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(n2):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ems = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), dev, ws)
+    seg.seg_destroy(ctx2)
+    return {"value": None, "unit": "Gvoxels/s", "h2d_bytes_per_step": int(h_in.numel() * 2),
+            "d2h_bytes_per_step": int(d2h[0]), "steps": n2, "read": read,
+            "pipeline": "submit thread + read thread, flush every %d frames" % group,
+            "steps_timed": n2, "ms": ems}
 
 
 def main():

@@ -87,6 +87,15 @@ typedef struct {
     uint32_t pad[2];
 } seg_cell_features;
 
+/* One run of a label image, 12 bytes: voxels x_begin..x_end (inclusive) of
+ * row `row` (= y + Y*z) carry label `label` (>= 1). */
+typedef struct {
+    uint32_t label;
+    uint32_t row;
+    uint16_t x_begin;
+    uint16_t x_end;
+} seg_label_run;
+
 typedef struct {
     int device;                /* CUDA ordinal                                   */
     uint32_t max_inflight;     /* batches in flight (streams); 0 -> 2            */
@@ -185,6 +194,20 @@ int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream);
  * SEG_EINVAL, SEG_ENOENT, SEG_ECUDA. */
 int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
                     uint64_t dst_elems, int dst_on_device);
+
+/* Channel `channel`'s label image as runs (Segmentation section: each
+ * cell's voxels, the set the paper passes on to the convex hull step): the
+ * maximal stretches of equal non-zero label along x within one row, in order
+ * of row (y + Y*z) and then x, one seg_label_run each.  Painting the runs
+ * into a zeroed X*Y*Z image gives exactly seg_read_labels' image; a row of
+ * X voxels holds at most ceil(X/2) runs.  *n_runs gets the number of runs.
+ * dst holds cap runs in host memory, or device memory when dst_on_device = 1;
+ * dst = NULL with cap = 0 only reports the number.  Derived on the device
+ * from the label image (two passes over it) and copied; blocks until done.
+ * Errors: SEG_ESMALL (cap < *n_runs, nothing written); otherwise as
+ * seg_read_labels. */
+int seg_read_label_runs(seg_ctx *ctx, seg_req req, uint32_t channel, seg_label_run *dst, uint64_t cap,
+                        uint64_t *n_runs, int dst_on_device);
 
 /* Copies channel `channel`'s distance map (X*Y*Z uint32, layout of the
  * labels) to dst (host, or device when dst_on_device = 1).  Blocks until the

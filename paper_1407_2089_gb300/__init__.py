@@ -80,6 +80,10 @@ MONTAGE_EDGE_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("shift", "<i4", (3,)
                                ("score", "<f8"), ("in_tree", "<u4"), ("pad1", "<u4")])
 
 
+LABEL_RUN_DTYPE = np.dtype([("label", "<u4"), ("row", "<u4"), ("x_begin", "<u2"), ("x_end", "<u2")])
+assert LABEL_RUN_DTYPE.itemsize == 12
+
+
 class seg_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_uint64), ("volumes", ctypes.c_uint64),
                 ("voxels", ctypes.c_uint64), ("tile_y", ctypes.c_uint32),
@@ -91,7 +95,7 @@ class seg_stats(ctypes.Structure):
 
 
 EXPORTS = ["seg_create", "seg_destroy", "seg_submit_volume", "seg_flush", "seg_poll",
-           "seg_enqueue_wait", "seg_read_labels", "seg_read_distance", "seg_read_cell_distance", "seg_read_denoised",
+           "seg_enqueue_wait", "seg_read_labels", "seg_read_label_runs", "seg_read_distance", "seg_read_cell_distance", "seg_read_denoised",
            "seg_read_features", "seg_release",
            "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror",
            "seg_otsu_threshold_noalloc", "seg_register_montage"]
@@ -108,6 +112,7 @@ def _bind(lib):
         "seg_poll": [vp, u64, u32, P(i32)],
         "seg_enqueue_wait": [vp, u64, vp],
         "seg_read_labels": [vp, u64, u32, vp, u64, i32],
+        "seg_read_label_runs": [vp, u64, u32, vp, u64, P(u64), i32],
         "seg_read_distance": [vp, u64, u32, vp, u64, i32],
         "seg_read_cell_distance": [vp, u64, u32, u32, vp, u64, P(u64)],
         "seg_read_denoised": [vp, u64, u32, vp, u64, i32, P(u32)],
@@ -260,6 +265,34 @@ def seg_read_labels(ctx, req, channel, out):
         ptr, n, dev = out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
     _check(_lib.seg_read_labels(ctx, req, channel, ctypes.c_void_p(ptr), n, dev), "seg_read_labels")
     return out
+
+
+def seg_read_label_runs(ctx, req, channel, out=None):
+    """The channel's label image as runs (LABEL_RUN_DTYPE: label, row =
+    y + Y*z, first and last x), in order of row and x.
+
+    out=None: a new numpy array (the runs are counted first, then read).
+    out: a C-contiguous numpy array of LABEL_RUN_DTYPE, or a uint8 torch
+    tensor (host or CUDA) of 12 bytes per run; returns out[:n] (numpy) or the
+    first 12*n bytes (torch).  Raises SegError(SEG_ESMALL) when out is too
+    small."""
+    n = ctypes.c_uint64()
+    if out is None:
+        _check(_lib.seg_read_label_runs(ctx, req, channel, None, 0, ctypes.byref(n), 0), "seg_read_label_runs")
+        out = np.zeros(n.value, dtype=LABEL_RUN_DTYPE)
+        if not n.value:
+            return out
+    if isinstance(out, np.ndarray):
+        if out.dtype != LABEL_RUN_DTYPE or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous array of LABEL_RUN_DTYPE")
+        ptr, cap, dev = out.ctypes.data, out.size, 0
+    else:
+        if out.element_size() != 1 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous uint8 tensor")
+        ptr, cap, dev = out.data_ptr(), out.numel() // LABEL_RUN_DTYPE.itemsize, 1 if out.is_cuda else 0
+    _check(_lib.seg_read_label_runs(ctx, req, channel, ctypes.c_void_p(ptr) if cap else None, cap,
+                                    ctypes.byref(n), dev), "seg_read_label_runs")
+    return out[: n.value] if isinstance(out, np.ndarray) else out[: n.value * LABEL_RUN_DTYPE.itemsize]
 
 
 def seg_read_distance(ctx, req, channel, out):

@@ -208,6 +208,14 @@ cudaError_t launch_denoise(const BatchHdr *d_hdr, const LaunchPlan &plan, cudaSt
 // Cell-to-vessel distance: out[k - 1] = min of map over the voxels labelled k.
 cudaError_t launch_cell_distance(const uint32_t *labels, const uint32_t *map, uint64_t n, uint32_t *out, uint64_t k,
                                  int sms, cudaStream_t s);
+// Label runs of one label image (rows = Y*Z rows of X voxels): the count
+// pass (per-row counts into rowcnt, per-block offsets into tiles, the total
+// into *total) and the write pass (records into out).
+uint32_t label_runs_tiles(uint32_t rows);
+cudaError_t launch_label_runs_count(const uint32_t *labels, uint32_t X, uint32_t rows, uint32_t *rowcnt,
+                                    uint32_t *tiles, uint32_t *total, int sms, cudaStream_t s);
+cudaError_t launch_label_runs_write(const uint32_t *labels, uint32_t X, uint32_t rows, const uint32_t *rowcnt,
+                                    const uint32_t *tiles, seg_label_run *out, int sms, cudaStream_t s);
 
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);

@@ -2963,6 +2963,110 @@ __global__ void __launch_bounds__(256) k_cell_distance(const uint32_t *__restric
     }
 }
 
+// Label runs (read path; Segmentation section: each cell's voxels, the set
+// handed to the convex hull step): the maximal runs of equal non-zero label
+// along x, in order of (row, x).  With L = 0 outside the row, a run starts at
+// x when L(x) != 0 and L(x) != L(x - 1), and ends at x - 1 when L(x - 1) != 0
+// and L(x - 1) != L(x).  RUNS_ROWS rows per block, one warp per row, lanes on
+// consecutive voxels, eight 32-voxel loads in flight before the boundaries
+// are tested; ballots rank the starts and ends of a row.  The count pass
+// stores each row's runs and each block's total; after the scan over blocks
+// the write pass turns them into row offsets (a block scan) and writes the
+// records, the start fields from the run's first voxel and x_end from the
+// boundary after its last.
+constexpr int RUNS_ROWS = 64;
+constexpr int RUNS_THREADS = 256;
+
+template <bool WRITE>
+__global__ void __launch_bounds__(RUNS_THREADS) k_label_runs(const uint32_t *__restrict__ labels, uint32_t X,
+                                                             uint32_t rows, uint32_t ntiles,
+                                                             uint32_t *__restrict__ rowcnt,
+                                                             uint32_t *__restrict__ tiles,
+                                                             seg_label_run *__restrict__ out) {
+    __shared__ uint32_t sbuf[33];
+    __shared__ uint32_t soff[RUNS_ROWS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t r0 = t * RUNS_ROWS;
+        if (WRITE) {
+            const uint32_t row = r0 + threadIdx.x;
+            const uint32_t c = threadIdx.x < RUNS_ROWS && row < rows ? rowcnt[row] : 0u;
+            uint32_t tot;
+            const uint32_t ex = block_exscan<RUNS_THREADS>(c, &tot, sbuf);
+            if (threadIdx.x < RUNS_ROWS) soff[threadIdx.x] = tiles[t] + ex;
+            __syncthreads();
+        }
+        uint32_t cnt = 0;
+        for (uint32_t rr = warp; rr < RUNS_ROWS; rr += RUNS_THREADS / 32) {
+            const uint32_t row = r0 + rr;
+            if (row >= rows) break;
+            const uint32_t *L = labels + (uint64_t)row * X;
+            const uint32_t base = WRITE ? soff[rr] : 0u;
+            uint32_t carry = 0, ns = 0, ne = 0;
+            for (uint32_t xb = 0; xb < X; xb += 256) {
+                uint32_t v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t x = xb + 32u * j + lane;
+                    v[j] = x < X ? L[x] : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t x = xb + 32u * j + lane;
+                    if (xb + 32u * j >= X) break;
+                    uint32_t prev = __shfl_up_sync(FULL, v[j], 1);
+                    if (lane == 0) prev = carry;
+                    const bool st = v[j] != 0u && v[j] != prev;
+                    const bool en = prev != 0u && prev != v[j];
+                    const uint32_t bs = __ballot_sync(FULL, st), be = __ballot_sync(FULL, en);
+                    if (WRITE) {
+                        if (st) {
+                            seg_label_run *o = out + base + ns + __popc(bs & below);
+                            o->label = v[j];
+                            o->row = row;
+                            o->x_begin = (uint16_t)x;
+                        }
+                        if (en) out[base + ne + __popc(be & below)].x_end = (uint16_t)(x - 1u);
+                    }
+                    ns += __popc(bs);
+                    ne += __popc(be);
+                    carry = __shfl_sync(FULL, v[j], 31);
+                }
+            }
+            // a run reaching the row end (X a multiple of 32: the boundary
+            // after the last voxel is in no step)
+            if (carry) {
+                if (WRITE && lane == 0) out[base + ne].x_end = (uint16_t)(X - 1u);
+                ++ne;
+            }
+            if (!WRITE && lane == 0) rowcnt[row] = ns;
+            cnt += ns;
+        }
+        if (!WRITE) {
+            const uint32_t tot = block_sum<RUNS_THREADS>(lane == 0 ? cnt : 0u, sbuf);
+            if (threadIdx.x == 0) tiles[t] = tot;
+        }
+        __syncthreads();  // soff and sbuf are reused by the next tile
+    }
+}
+
+// Exclusive scan over the blocks' run counts (one block); *total = the sum.
+__global__ void __launch_bounds__(1024) k_label_runs_scan(uint32_t *__restrict__ tiles, uint32_t ntiles,
+                                                          uint32_t *__restrict__ total) {
+    __shared__ uint32_t sbuf[33];
+    uint32_t carry = 0;
+    for (uint32_t b = 0; b < ntiles; b += 1024) {
+        const uint32_t i = b + threadIdx.x;
+        const uint32_t c = i < ntiles ? tiles[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exscan<1024>(c, &tot, sbuf);
+        if (i < ntiles) tiles[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
 template <int TY>
 cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s,
                                 cudaEvent_t *ev, int &k) {
@@ -3077,6 +3181,26 @@ cudaError_t launch_cell_distance(const uint32_t *labels, const uint32_t *map, ui
     const uint64_t want = (n + 8 * 256 - 1) / (8 * 256);
     const int grid = (int)std::min<uint64_t>(want, (uint64_t)sms * 8);
     k_cell_distance<<<grid, 256, 0, s>>>(labels, map, n, k, out);
+    return cudaGetLastError();
+}
+
+uint32_t label_runs_tiles(uint32_t rows) { return (rows + RUNS_ROWS - 1) / RUNS_ROWS; }
+
+cudaError_t launch_label_runs_count(const uint32_t *labels, uint32_t X, uint32_t rows, uint32_t *rowcnt,
+                                    uint32_t *tiles, uint32_t *total, int sms, cudaStream_t s) {
+    const uint32_t nt = label_runs_tiles(rows);
+    const int grid = (int)std::min<uint64_t>(nt, (uint64_t)sms * 8);
+    k_label_runs<false><<<grid, RUNS_THREADS, 0, s>>>(labels, X, rows, nt, rowcnt, tiles, nullptr);
+    k_label_runs_scan<<<1, 1024, 0, s>>>(tiles, nt, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_label_runs_write(const uint32_t *labels, uint32_t X, uint32_t rows, const uint32_t *rowcnt,
+                                    const uint32_t *tiles, seg_label_run *out, int sms, cudaStream_t s) {
+    const uint32_t nt = label_runs_tiles(rows);
+    const int grid = (int)std::min<uint64_t>(nt, (uint64_t)sms * 8);
+    k_label_runs<true><<<grid, RUNS_THREADS, 0, s>>>(labels, X, rows, nt, const_cast<uint32_t *>(rowcnt),
+                                                     const_cast<uint32_t *>(tiles), out);
     return cudaGetLastError();
 }
 

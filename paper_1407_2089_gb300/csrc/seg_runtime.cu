@@ -1075,6 +1075,54 @@ int seg_read_cell_distance(seg_ctx *ctx, seg_req req, uint32_t cells_channel, ui
     return cuda_fail(e, "seg_read_cell_distance");
 }
 
+int seg_read_label_runs(seg_ctx *ctx, seg_req req, uint32_t channel, seg_label_run *dst, uint64_t cap,
+                        uint64_t *n_runs, int dst_on_device) {
+    if (!ctx) return SEG_EINVAL;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (r->state == SEG_PENDING) return SEG_ENOTREADY;
+        if (r->state == SEG_FAILED) return SEG_EFAILED;
+    }
+    if (channel >= r->C || (!dst && cap)) return SEG_EINVAL;
+    const VolGeom &g = r->g[channel];
+    const uint32_t nt = label_runs_tiles(g.rows);
+    const size_t a_rows = al(4ull * g.rows), a_tiles = al(4ull * nt);
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->read_stream;
+    char *tmp = nullptr;
+    seg_label_run *dev_out = nullptr;
+    uint32_t total = 0;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), a_rows + a_tiles + 256, s);
+    uint32_t *rowcnt = reinterpret_cast<uint32_t *>(tmp);
+    uint32_t *tiles = reinterpret_cast<uint32_t *>(tmp + a_rows);
+    uint32_t *d_total = reinterpret_cast<uint32_t *>(tmp + a_rows + a_tiles);
+    if (e == cudaSuccess) e = launch_label_runs_count(r->labels(channel), g.X, g.rows, rowcnt, tiles, d_total,
+                                                      ctx->sms, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int rc = SEG_OK;
+    if (e == cudaSuccess) {
+        if (n_runs) *n_runs = total;
+        if (cap < total) rc = dst ? SEG_ESMALL : SEG_OK;
+        else if (total) {
+            dev_out = dst_on_device ? dst : nullptr;
+            if (!dst_on_device) e = cudaMallocAsync(reinterpret_cast<void **>(&dev_out), sizeof(seg_label_run) * total, s);
+            if (e == cudaSuccess)
+                e = launch_label_runs_write(r->labels(channel), g.X, g.rows, rowcnt, tiles, dev_out, ctx->sms, s);
+            if (e == cudaSuccess && !dst_on_device)
+                e = cudaMemcpyAsync(dst, dev_out, sizeof(seg_label_run) * total, cudaMemcpyDeviceToHost, s);
+            if (!dst_on_device && dev_out) cudaFreeAsync(dev_out, s);
+        }
+    }
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "seg_read_label_runs");
+    return rc;
+}
+
 int seg_read_distance(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst, uint64_t dst_elems,
                       int dst_on_device) {
     if (!ctx || !dst) return SEG_EINVAL;

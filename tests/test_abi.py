@@ -53,6 +53,7 @@ def test_strerror_and_null_arguments(lib):
     assert lib.seg_create(None, None) == -1
     assert lib.seg_destroy(None) == -1
     assert lib.seg_flush(None) == -1
+    assert lib.seg_read_label_runs(None, ctypes.c_uint64(1), 0, None, ctypes.c_uint64(0), None, 0) == -1
 
 
 def test_struct_layouts():
@@ -63,6 +64,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(seg.seg_channel_params) == 28
     assert ctypes.sizeof(seg.seg_offset) == 12
     assert seg.MONTAGE_EDGE_DTYPE.itemsize == 40
+    assert seg.LABEL_RUN_DTYPE.itemsize == 12
 
 
 def test_binding_constants_match_header():
