@@ -360,9 +360,11 @@ def run_gpu(args):
     if not args.no_e2e:
         h_in = torch.from_numpy(host.view(np.int16)).pin_memory()
         group = max(1, args.e2e_group)
-        e2e = e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, (X, Y, Z), T, C, group, "runs")
+        queued = args.e2e_copies == "queued"
+        e2e = e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, (X, Y, Z), T, C, group, "runs", queued,
+                      args.e2e_ahead)
         e2e_dense = e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, (X, Y, Z), T, C, group,
-                            "labels")
+                            "labels", queued, args.e2e_ahead)
         e2e["value"] = job_gvox_per_s(vox_step * e2e.pop("steps_timed"), e2e.pop("ms"), ws)
         e2e_dense["value"] = job_gvox_per_s(vox_step * e2e_dense.pop("steps_timed"), e2e_dense.pop("ms"), ws)
 
@@ -692,33 +694,47 @@ def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
             "offered_gvox_s": vox / reqs[-1][0] / 1e9}
 
 
-def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, group, read):
+def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, group, read, queued=True, ahead=12):
     """Steps through the C ABI from pinned host buffers.  One thread submits
     (each submit copies its frame host->device) and flushes every `group`
     frames; this thread waits for the frames in order, reads each channel's
     result back and releases the frame, so the two directions of the host
     link and the kernels overlap.  read = "runs": the label runs and cells
     (the complete segmentation: each cell's voxels as x-runs, and its
-    features); read = "labels": the dense uint32 label images and cells."""
+    features); read = "labels": the dense uint32 label images and cells.
+    queued: the submits only queue their copies (the pinned inputs stay
+    unchanged until each frame is done), at most `ahead` frames beyond the
+    last frame read back, so the copies run back to back while reads that
+    share the host link never wait behind a long queue of them."""
     X, Y, Z = dims
-    ctx2 = seg.seg_create(device=local, max_inflight=3)
+    # with queued copies every submit returns at once, so a batch is capped
+    # at one flush group (else the first batch would wait for every copy)
+    ctx2 = seg.seg_create(device=local, max_inflight=3, max_batch_volumes=group * C if queued else 0)
     dense = torch.empty((T, C, Z, Y, X), dtype=torch.int32).pin_memory() if read == "labels" else None
     run_buf = None
     d2h = [0]
+    phases = {"inputs_sent_ms": [], "step_ms": []}
 
     def step():
         q, err = [], []
+        done = [0]
         cv = threading.Condition()
+        t_start = time.perf_counter()
 
         def submitter():
             try:
                 for t in range(T):
-                    r = seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C)
+                    if queued:
+                        # at most `ahead` frames queued beyond the last one read back
+                        with cv:
+                            cv.wait_for(lambda: done[0] >= t - ahead or err)
+                    r = seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C, keep_host_input=queued)
                     if (t + 1) % group == 0 or t + 1 == T:
                         seg.seg_flush(ctx2)
                     with cv:
                         q.append(r)
                         cv.notify()
+                phases["inputs_sent_ms"].append((time.perf_counter() - t_start) * 1e3)
             except BaseException as e:  # surfaced by the reader below
                 err.append(e)
                 with cv:
@@ -745,11 +761,15 @@ def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, gr
                     cells, _ = seg.seg_read_features(ctx2, r, c)
                     nb += cells.nbytes
                 seg.seg_release(ctx2, r)
+                with cv:
+                    done[0] = t + 1
+                    cv.notify_all()
         finally:
             th.join()
         if err:
             raise err[0]
         d2h[0] = nb
+        phases["step_ms"].append((time.perf_counter() - t_start) * 1e3)
 
     if read == "runs":
         # size one pinned buffer per volume-channel from a first pass
@@ -765,6 +785,8 @@ def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, gr
                    for row in counts]
     for _ in range(max(1, min(args.warmup, 2))):
         step()
+    for v in phases.values():
+        v.clear()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -782,7 +804,9 @@ def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, gr
     seg.seg_destroy(ctx2)
     return {"value": None, "unit": "Gvoxels/s", "h2d_bytes_per_step": int(h_in.numel() * 2),
             "d2h_bytes_per_step": int(d2h[0]), "steps": n2, "read": read,
-            "pipeline": "submit thread + read thread, flush every %d frames" % group,
+            "pipeline": "submit thread (%s) + read thread, flush every %d frames" % (
+                "copies queued, %d frames ahead" % ahead if queued else "copies awaited", group),
+            "phases_ms": {k: round(statistics.median(v), 2) for k, v in phases.items() if v},
             "steps_timed": n2, "ms": ems}
 
 
@@ -794,6 +818,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-group", type=int, default=6, help="frames per flush in the e2e pipeline")
+    ap.add_argument("--e2e-copies", choices=("queued", "awaited"), default="awaited",
+                    help="e2e submits queue their input copies, or wait for each")
+    ap.add_argument("--e2e-ahead", type=int, default=12, help="queued copies: frames submitted beyond the last read")
     ap.add_argument("--inflight", type=int, default=1,
                     help="batches in flight; 1 keeps per-kernel CUDA-event times free of overlap")
     ap.add_argument("--frames", type=int, default=FRAMES,

@@ -162,10 +162,13 @@ int seg_create(const seg_config *cfg, seg_ctx **out);
 int seg_destroy(seg_ctx *ctx);
 
 /* Submits one volume of `channels` planar channels, each [Z][Y][X] uint16.
- *   voxels     host pointer (on_device = 0) or device pointer (on_device = 1).
- *              A host input is copied before the call returns (the caller may
- *              free or reuse it).  A device input must stay valid and
- *              unchanged until seg_poll reports DONE or FAILED.
+ *   voxels     host pointer (on_device = 0 or 2) or device pointer
+ *              (on_device = 1).  With 0 the input is copied before the call
+ *              returns (the caller may free or reuse it).  With 2 the copy is
+ *              only queued (pinned memory: it runs while the call returns and
+ *              the batch waits for it on the device), so the host input, like
+ *              a device input, must stay valid and unchanged until seg_poll
+ *              reports DONE or FAILED.  Other values: SEG_EINVAL.
  *   per_channel  array of `channels` params, or NULL for the default (30).
  * On success *out is a new handle.  Results stay on the device until
  * seg_release.  Errors: SEG_EINVAL, SEG_ETOOBIG (can never be admitted),

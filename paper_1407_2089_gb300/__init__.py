@@ -191,14 +191,16 @@ def _voxel_ptr(voxels):
 
 
 def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, denoise_radius=0, closing_radius=0,
-                      distance_weights=None, mrf_iterations=0):
+                      distance_weights=None, mrf_iterations=0, keep_host_input=False):
     """Submits [C][Z][Y][X] (or [Z][Y][X]) uint16 voxels; returns the request id.
 
     min_volume, denoise_radius, closing_radius: one int for every channel or
     a sequence of per-channel ints (0 = no denoise front end / no closing).
     distance_weights: None (no distance map), one (wx, wy, wz) for every
     channel, or a per-channel sequence of triples or None.  mrf_iterations:
-    step limit of the MRF vessel denoise (0 = off), one int or per channel."""
+    step limit of the MRF vessel denoise (0 = off), one int or per channel.
+    keep_host_input: for a host input, only queue its copy; the caller then
+    keeps it unchanged until the request is done (best with pinned memory)."""
     shape = tuple(voxels.shape)
     if dims is None:
         if len(shape) == 3:
@@ -211,6 +213,8 @@ def seg_submit_volume(ctx, voxels, dims=None, channels=None, min_volume=30, deno
     if channels is None:
         channels = 1
     ptr, on_dev = _voxel_ptr(voxels)
+    if keep_host_input and not on_dev:
+        on_dev = 2
     mv = [min_volume] * channels if np.isscalar(min_volume) else list(min_volume)
     dr = [denoise_radius] * channels if np.isscalar(denoise_radius) else list(denoise_radius)
     cr = [closing_radius] * channels if np.isscalar(closing_radius) else list(closing_radius)

@@ -210,12 +210,15 @@ cudaError_t launch_cell_distance(const uint32_t *labels, const uint32_t *map, ui
                                  int sms, cudaStream_t s);
 // Label runs of one label image (rows = Y*Z rows of X voxels): the count
 // pass (per-row counts into rowcnt, per-block offsets into tiles, the total
-// into *total) and the write pass (records into out).
+// into *total) and the write pass (records into out, nothing when *total >
+// cap; then, with mapped != null, the records copied on to that
+// device-visible host memory).
 uint32_t label_runs_tiles(uint32_t rows);
 cudaError_t launch_label_runs_count(const uint32_t *labels, uint32_t X, uint32_t rows, uint32_t *rowcnt,
                                     uint32_t *tiles, uint32_t *total, int sms, cudaStream_t s);
 cudaError_t launch_label_runs_write(const uint32_t *labels, uint32_t X, uint32_t rows, const uint32_t *rowcnt,
-                                    const uint32_t *tiles, seg_label_run *out, int sms, cudaStream_t s);
+                                    const uint32_t *tiles, const uint32_t *total, uint64_t cap, seg_label_run *out,
+                                    seg_label_run *mapped, int sms, cudaStream_t s);
 
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);

@@ -2982,9 +2982,11 @@ __global__ void __launch_bounds__(RUNS_THREADS) k_label_runs(const uint32_t *__r
                                                              uint32_t rows, uint32_t ntiles,
                                                              uint32_t *__restrict__ rowcnt,
                                                              uint32_t *__restrict__ tiles,
-                                                             seg_label_run *__restrict__ out) {
+                                                             seg_label_run *__restrict__ out,
+                                                             const uint32_t *__restrict__ total, uint64_t cap) {
     __shared__ uint32_t sbuf[33];
     __shared__ uint32_t soff[RUNS_ROWS];
+    if (WRITE && *total > cap) return;  // the destination is too small: write nothing
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t below = (1u << lane) - 1u;
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -3049,6 +3051,17 @@ __global__ void __launch_bounds__(RUNS_THREADS) k_label_runs(const uint32_t *__r
         }
         __syncthreads();  // soff and sbuf are reused by the next tile
     }
+}
+
+// The records to a destination the device reaches (mapped pinned host
+// memory) as 4-byte words, coalesced; nothing when they do not fit.
+__global__ void __launch_bounds__(256) k_label_runs_copy(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                         const uint32_t *__restrict__ total, uint64_t cap) {
+    const uint64_t n = *total;
+    if (n > cap) return;
+    const uint64_t words = 3 * n;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
 }
 
 // Exclusive scan over the blocks' run counts (one block); *total = the sum.
@@ -3190,17 +3203,24 @@ cudaError_t launch_label_runs_count(const uint32_t *labels, uint32_t X, uint32_t
                                     uint32_t *tiles, uint32_t *total, int sms, cudaStream_t s) {
     const uint32_t nt = label_runs_tiles(rows);
     const int grid = (int)std::min<uint64_t>(nt, (uint64_t)sms * 8);
-    k_label_runs<false><<<grid, RUNS_THREADS, 0, s>>>(labels, X, rows, nt, rowcnt, tiles, nullptr);
+    k_label_runs<false><<<grid, RUNS_THREADS, 0, s>>>(labels, X, rows, nt, rowcnt, tiles, nullptr, nullptr, 0);
     k_label_runs_scan<<<1, 1024, 0, s>>>(tiles, nt, total);
     return cudaGetLastError();
 }
 
 cudaError_t launch_label_runs_write(const uint32_t *labels, uint32_t X, uint32_t rows, const uint32_t *rowcnt,
-                                    const uint32_t *tiles, seg_label_run *out, int sms, cudaStream_t s) {
+                                    const uint32_t *tiles, const uint32_t *total, uint64_t cap, seg_label_run *out,
+                                    seg_label_run *mapped, int sms, cudaStream_t s) {
     const uint32_t nt = label_runs_tiles(rows);
     const int grid = (int)std::min<uint64_t>(nt, (uint64_t)sms * 8);
     k_label_runs<true><<<grid, RUNS_THREADS, 0, s>>>(labels, X, rows, nt, const_cast<uint32_t *>(rowcnt),
-                                                     const_cast<uint32_t *>(tiles), out);
+                                                     const_cast<uint32_t *>(tiles), out, total, cap);
+    if (mapped) {
+        const uint64_t words = 3 * cap;
+        const int cg = (int)std::max<uint64_t>(1, std::min<uint64_t>((words + 255) / 256, (uint64_t)sms * 4));
+        k_label_runs_copy<<<cg, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(out),
+                                             reinterpret_cast<uint32_t *>(mapped), total, cap);
+    }
     return cudaGetLastError();
 }
 

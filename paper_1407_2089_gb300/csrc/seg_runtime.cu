@@ -130,7 +130,7 @@ struct Request {
     int err = SEG_OK;
     size_t persist = 0, scratch = 0;
     std::vector<uint32_t> thresh, ncells, errbits;
-    cudaEvent_t ready_ev = nullptr;  // order-stream point for device inputs
+    cudaEvent_t ready_ev = nullptr;  // order-stream point for device inputs, or the queued host copy
     cudaEvent_t done_ev = nullptr;
     double t_submit = -1, t_admit = -1, t_launch = -1, t_done = -1;
 
@@ -842,8 +842,13 @@ int seg_destroy(seg_ctx *ctx) {
 
 int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_dims dims,
                       uint32_t channels, const seg_channel_params *per_channel, seg_req *out) {
-    if (!ctx || !voxels || !out || channels == 0 || dims.x == 0 || dims.y == 0 || dims.z == 0)
+    if (!ctx || !voxels || !out || channels == 0 || dims.x == 0 || dims.y == 0 || dims.z == 0 || on_device < 0 ||
+        on_device > 2)
         return SEG_EINVAL;
+    // 0: host input copied before the call returns; 1: device input;
+    // 2: host input whose copy is queued (the caller keeps it unchanged until
+    // the request is done)
+    const bool host_in = on_device != 1;
     const uint64_t n = (uint64_t)dims.x * dims.y * dims.z;
     if (n >= (1ull << 32) || dims.x > 65536u) return SEG_ETOOBIG;
     if (channels > ctx->cap_vols) return SEG_ETOOBIG;
@@ -884,8 +889,8 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
     r->mrf_steps.assign(channels, 0);
     r->mrf_sel.assign(channels, 0);
     r->errbits.assign(channels, 0);
-    r->owns_input = !on_device;
-    if (on_device) r->user_dev = voxels;
+    r->owns_input = host_in;
+    if (!host_in) r->user_dev = voxels;
     layout_request(*r);
     if (r->persist + r->scratch > ctx->budget) return SEG_ETOOBIG;
     cudaSetDevice(ctx->device);
@@ -893,7 +898,7 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
         cudaGetLastError();
         return SEG_ECUDA;
     }
-    if (on_device && ctx->cfg.order_stream) {
+    if (!host_in && ctx->cfg.order_stream) {
         if (cudaEventCreateWithFlags(&r->ready_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventRecord(r->ready_ev, static_cast<cudaStream_t>(ctx->cfg.order_stream)) != cudaSuccess) {
             cudaGetLastError();
@@ -911,7 +916,7 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
             if (r->ready_ev) cudaEventDestroy(r->ready_ev);
             return SEG_EAGAIN;
         }
-        if (!on_device && ctx->used + r->persist + r->scratch <= ctx->budget) {
+        if (host_in && ctx->used + r->persist + r->scratch <= ctx->budget) {
             // admit now (its results and its batch scratch reserved) and copy
             // straight from the caller's buffer
             ctx->used += r->persist + r->scratch;
@@ -920,14 +925,20 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
             copy_now = true;
         }
     }
-    if (!on_device) {
+    if (host_in) {
         const size_t bytes = 2ull * n * channels;
         int rc = SEG_OK;
         if (copy_now) {
             cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&r->block), r->block_bytes, ctx->copy_stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(r->block + r->off_input, voxels, bytes, cudaMemcpyHostToDevice, ctx->copy_stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copy_stream);
+            if (on_device == 2) {
+                // the batch waits for the copy on the device
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ready_ev, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(r->ready_ev, ctx->copy_stream);
+            } else if (e == cudaSuccess) {
+                e = cudaStreamSynchronize(ctx->copy_stream);
+            }
             if (e != cudaSuccess) rc = cuda_fail(e, "submit copy");
         } else {
             r->host_copy.assign(voxels, voxels + n * channels);
@@ -937,6 +948,7 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
             if (r->admitted) ctx->used -= r->persist + r->scratch;
             if (r->block) cudaFreeAsync(r->block, ctx->copy_stream);
             cudaEventDestroy(r->done_ev);
+            if (r->ready_ev) cudaEventDestroy(r->ready_ev);
             return rc;
         }
     }
@@ -1090,8 +1102,22 @@ int seg_read_label_runs(seg_ctx *ctx, seg_req req, uint32_t channel, seg_label_r
     const VolGeom &g = r->g[channel];
     const uint32_t nt = label_runs_tiles(g.rows);
     const size_t a_rows = al(4ull * g.rows), a_tiles = al(4ull * nt);
+    const uint64_t most = (uint64_t)g.rows * ((g.X + 1) / 2);  // runs a label image can hold
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->read_stream;
+    // A destination the device reaches (device memory, or pinned host
+    // memory through its mapping) takes the records in the same pass of
+    // launches as the count, with one synchronisation; pageable memory is
+    // filled by a copy once the count is known.
+    seg_label_run *mapped = nullptr;
+    if (dst && cap && !dst_on_device) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, dst) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            mapped = static_cast<seg_label_run *>(pa.devicePointer);
+        cudaGetLastError();
+    }
+    const bool one_pass = dst && cap && (dst_on_device || mapped);
+    const uint64_t stage = mapped ? std::min<uint64_t>(cap, most) : 0;
     char *tmp = nullptr;
     seg_label_run *dev_out = nullptr;
     uint32_t total = 0;
@@ -1101,20 +1127,30 @@ int seg_read_label_runs(seg_ctx *ctx, seg_req req, uint32_t channel, seg_label_r
     uint32_t *d_total = reinterpret_cast<uint32_t *>(tmp + a_rows + a_tiles);
     if (e == cudaSuccess) e = launch_label_runs_count(r->labels(channel), g.X, g.rows, rowcnt, tiles, d_total,
                                                       ctx->sms, s);
+    if (one_pass) {
+        dev_out = dst_on_device ? dst : nullptr;
+        if (e == cudaSuccess && mapped && stage)
+            e = cudaMallocAsync(reinterpret_cast<void **>(&dev_out), sizeof(seg_label_run) * stage, s);
+        if (e == cudaSuccess && dev_out)
+            e = launch_label_runs_write(r->labels(channel), g.X, g.rows, rowcnt, tiles, d_total,
+                                        mapped ? stage : cap, dev_out, mapped, ctx->sms, s);
+        if (mapped && dev_out) cudaFreeAsync(dev_out, s);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int rc = SEG_OK;
     if (e == cudaSuccess) {
         if (n_runs) *n_runs = total;
-        if (cap < total) rc = dst ? SEG_ESMALL : SEG_OK;
-        else if (total) {
-            dev_out = dst_on_device ? dst : nullptr;
-            if (!dst_on_device) e = cudaMallocAsync(reinterpret_cast<void **>(&dev_out), sizeof(seg_label_run) * total, s);
+        if (cap < total) {
+            rc = dst ? SEG_ESMALL : SEG_OK;
+        } else if (total && !one_pass) {
+            e = cudaMallocAsync(reinterpret_cast<void **>(&dev_out), sizeof(seg_label_run) * total, s);
             if (e == cudaSuccess)
-                e = launch_label_runs_write(r->labels(channel), g.X, g.rows, rowcnt, tiles, dev_out, ctx->sms, s);
-            if (e == cudaSuccess && !dst_on_device)
+                e = launch_label_runs_write(r->labels(channel), g.X, g.rows, rowcnt, tiles, d_total, total, dev_out,
+                                            nullptr, ctx->sms, s);
+            if (e == cudaSuccess)
                 e = cudaMemcpyAsync(dst, dev_out, sizeof(seg_label_run) * total, cudaMemcpyDeviceToHost, s);
-            if (!dst_on_device && dev_out) cudaFreeAsync(dev_out, s);
+            if (dev_out) cudaFreeAsync(dev_out, s);
         }
     }
     if (tmp) cudaFreeAsync(tmp, s);

@@ -112,17 +112,30 @@ def test_destinations_and_sizes(seg, ctx):
         # exact-size numpy, oversized numpy (returns the first n), host and device tensors
         assert_runs_equal(seg.seg_read_label_runs(ctx, req, 0, np.zeros(n, seg.LABEL_RUN_DTYPE)), want, "exact")
         assert_runs_equal(seg.seg_read_label_runs(ctx, req, 0, np.zeros(n + 50, seg.LABEL_RUN_DTYPE)), want, "big")
-        for dev in ("cpu", "cuda:0"):
-            t = torch.zeros(12 * (n + 3), dtype=torch.uint8, device=dev)
-            got = seg.seg_read_label_runs(ctx, req, 0, t)
-            assert got.numel() == 12 * n
-            assert_runs_equal(got.cpu().numpy().view(seg.LABEL_RUN_DTYPE), want, dev)
-        # too small: SEG_ESMALL and nothing written
+        # pageable host, pinned host (written through its device mapping) and
+        # device tensors, exact and oversized
+        for kind in ("cpu", "pinned", "cuda:0"):
+            for extra in (0, 3, 10_000):
+                t = torch.zeros(12 * (n + extra), dtype=torch.uint8, device="cuda:0" if kind == "cuda:0" else "cpu")
+                if kind == "pinned":
+                    t = t.pin_memory()
+                got = seg.seg_read_label_runs(ctx, req, 0, t)
+                assert got.numel() == 12 * n
+                assert_runs_equal(got.cpu().numpy().view(seg.LABEL_RUN_DTYPE), want, "%s +%d" % (kind, extra))
+                assert not t[12 * n:].any(), kind  # nothing past the runs
+        # too small: SEG_ESMALL and nothing written, for every kind of destination
         small = np.zeros(n - 1, seg.LABEL_RUN_DTYPE)
         with pytest.raises(seg.SegError) as e:
             seg.seg_read_label_runs(ctx, req, 0, small)
         assert e.value.code == seg.SEG_ESMALL
         assert not small["label"].any()
+        for kind in ("pinned", "cuda:0"):
+            t = torch.zeros(12 * (n - 1), dtype=torch.uint8, device="cuda:0" if kind == "cuda:0" else "cpu")
+            if kind == "pinned":
+                t = t.pin_memory()
+            with pytest.raises(seg.SegError) as e:
+                seg.seg_read_label_runs(ctx, req, 0, t)
+            assert e.value.code == seg.SEG_ESMALL and not t.any(), kind
         with pytest.raises(seg.SegError) as e:
             seg.seg_read_label_runs(ctx, req, 1, None)
         assert e.value.code == seg.SEG_EINVAL

@@ -144,6 +144,35 @@ def test_device_resident_input(seg, ctx):
     seg.seg_release(ctx, req)
 
 
+def test_queued_host_input(seg):
+    # host inputs whose copies are only queued (keep_host_input): pinned and
+    # pageable sources, several requests in one batch, each equal to the oracle
+    import ctypes
+    import torch
+    c = seg.seg_create(device=0, batch_window_us=30_000_000)
+    try:
+        vols = [blobs((70, 40, 9), 40 + k, n=10) for k in range(4)]
+        srcs = [torch.from_numpy(v.view(np.int16).copy()).pin_memory() if k % 2 == 0 else v
+                for k, v in enumerate(vols)]
+        reqs = [seg.seg_submit_volume(c, s_, min_volume=5, keep_host_input=True) for s_ in srcs]
+        seg.seg_flush(c)
+        for k, (v, r) in enumerate(zip(vols, reqs)):
+            assert seg.seg_wait(c, r) == seg.SEG_DONE
+            lab = np.empty(v.shape, np.uint32)
+            seg.seg_read_labels(c, r, 0, lab)
+            cells, thr = seg.seg_read_features(c, r, 0)
+            assert_matches_oracle(v, lab, cells, thr, min_volume=5, what="queued input %d" % k)
+            seg.seg_release(c, r)
+        # input modes other than 0, 1, 2 are rejected
+        out = ctypes.c_uint64()
+        for mode in (-1, 3):
+            rc = seg._lib.seg_submit_volume(c, ctypes.c_void_p(vols[0].ctypes.data), mode,
+                                            seg.seg_dims(70, 40, 9), 1, None, ctypes.byref(out))
+            assert rc == seg.SEG_EINVAL, mode
+    finally:
+        seg.seg_destroy(c)
+
+
 def test_union_find_stress(seg, ctx):
     # dense random masks in many shapes: every missed or wrong union changes
     # the labels (m = 1 keeps every fragment), so races show up here
