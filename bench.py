@@ -807,6 +807,7 @@ def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, gr
             "pipeline": "submit thread (%s) + read thread, flush every %d frames" % (
                 "copies queued, %d frames ahead" % ahead if queued else "copies awaited", group),
             "phases_ms": {k: round(statistics.median(v), 2) for k, v in phases.items() if v},
+            "step_ms_max": round(max(phases["step_ms"]), 2) if phases["step_ms"] else None,
             "steps_timed": n2, "ms": ems}
 
 
@@ -816,7 +817,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-group", type=int, default=6, help="frames per flush in the e2e pipeline")
     ap.add_argument("--e2e-copies", choices=("queued", "awaited"), default="awaited",
                     help="e2e submits queue their input copies, or wait for each")
