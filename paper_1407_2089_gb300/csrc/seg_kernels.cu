@@ -1623,6 +1623,29 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
                         if (q0 + 32 * j < hi) bufA[(q0 + 32 * j - base) * BOX_PITCH + l] = v[j];
                 }
             }
+        } else if ((X & 7) == 0) {
+            // rows of 8-voxel octets (X % 8 == 0, scratch buffers 16-byte
+            // aligned): thread t moves lanes 8 (t % 8) .. + 7 of positions
+            // t / 8 + 32 i as one 16-byte load and four 4-byte shared stores
+            // (pitch 66: the 32 threads of a warp hit 32 different banks)
+            const int oct = t & 7, pr = t >> 3;
+            constexpr int NV = 4;
+            if (8 * oct < nl) {
+                const uint16_t *col = src + gstart + 8 * oct;
+                for (int q0 = lo + pr; q0 < hi; q0 += 32 * NV) {
+                    uint4 v[NV];
+#pragma unroll
+                    for (int j = 0; j < NV; ++j)
+                        if (q0 + 32 * j < hi)
+                            v[j] = *reinterpret_cast<const uint4 *>(col + (size_t)(q0 + 32 * j) * pstride);
+#pragma unroll
+                    for (int j = 0; j < NV; ++j)
+                        if (q0 + 32 * j < hi) {
+                            uint32_t *w = reinterpret_cast<uint32_t *>(bufA + (q0 + 32 * j - base) * BOX_PITCH + 8 * oct);
+                            w[0] = v[j].x; w[1] = v[j].y; w[2] = v[j].z; w[3] = v[j].w;
+                        }
+                }
+            }
         } else {
             const int total = np * BOX_LANES, nt = blockDim.x;
             for (int i0 = t; i0 < total; i0 += nt * NB) {
@@ -1693,6 +1716,15 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
             for (int ll = warp; ll < nl; ll += nw) {
                 uint16_t *row = dst + gstart + (size_t)ll * lstride;
                 for (int q = c0 + lane; q < c1; q += 32) row[q] = bufB[(q - base) * BOX_PITCH + ll];
+            }
+        } else if ((X & 7) == 0) {
+            const int oct = t & 7, pr = t >> 3;
+            if (8 * oct < nl) {
+                uint16_t *col = dst + gstart + 8 * oct;
+                for (int q = c0 + pr; q < c1; q += 32) {
+                    const uint32_t *w = reinterpret_cast<const uint32_t *>(bufB + (q - base) * BOX_PITCH + 8 * oct);
+                    *reinterpret_cast<uint4 *>(col + (size_t)q * pstride) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
             }
         } else {
             for (int i = t; i < nc * BOX_LANES; i += blockDim.x) {

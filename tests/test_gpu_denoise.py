@@ -40,7 +40,9 @@ def test_single_frame_denoised(seg, ctx):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 2), (31, 1, 7), (33, 40, 3), (70, 9, 300), (300, 17, 5),
-                                  (257, 258, 3)])
+                                  (257, 258, 3),
+                                  # X % 8 == 0 (16-byte copies along y and z), lane groups cut short
+                                  (8, 130, 7), (72, 9, 300), (200, 17, 5), (136, 258, 3)])
 @pytest.mark.parametrize("r", [1, 3, 16])
 def test_ragged_shapes(seg, ctx, dims, r):
     # lines shorter than the window, chunks of 256 with ragged tails, X not
