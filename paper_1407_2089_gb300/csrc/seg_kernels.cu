@@ -1675,21 +1675,22 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
                 // every read lies in [q0 - r, q1 - 1 + r] clamped to the line,
                 // inside the positions the previous pass (or the load) covered
                 auto at = [&](int q) { return (uint32_t)in[(min(max(q, 0), n - 1) - base) * BOX_PITCH + l]; };
-                uint32_t sum = 0;
+                // sum holds the window sum plus the rounding term r
+                uint32_t sum = (uint32_t)r;
                 if (q0 - r >= 0 && q0 + r < n) {
                     const uint16_t *pw = in + (q0 - r - base) * BOX_PITCH + l;
                     for (int i = 0; i <= 2 * r; ++i) sum += pw[i * BOX_PITCH];
                 } else {
                     for (int q = q0 - r; q <= q0 + r; ++q) sum += at(q);
                 }
-                out[(q0 - base) * BOX_PITCH + l] = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                out[(q0 - base) * BOX_PITCH + l] = (uint16_t)box_div(sum, mul);
                 // positions q whose window [q - r - 1, q + r] needs no
                 // clamping run through three moving pointers
                 const int qa = min(max(q0 + 1, r + 1), q1), qb = max(min(q1, n - r), qa);
                 int q = q0 + 1;
                 for (; q < qa; ++q) {
                     sum += at(q + r) - at(q - r - 1);
-                    out[(q - base) * BOX_PITCH + l] = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                    out[(q - base) * BOX_PITCH + l] = (uint16_t)box_div(sum, mul);
                 }
                 const uint16_t *pin = in + (q + r - base) * BOX_PITCH + l;
                 const uint16_t *pout = in + (q - r - 1 - base) * BOX_PITCH + l;
@@ -1697,14 +1698,14 @@ __global__ void __launch_bounds__(256) k_box3(const BatchHdr *__restrict__ h) {
 #pragma unroll 4
                 for (; q < qb; ++q) {
                     sum += (uint32_t)*pin - (uint32_t)*pout;
-                    *po = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                    *po = (uint16_t)box_div(sum, mul);
                     pin += BOX_PITCH;
                     pout += BOX_PITCH;
                     po += BOX_PITCH;
                 }
                 for (; q < q1; ++q) {
                     sum += at(q + r) - at(q - r - 1);
-                    out[(q - base) * BOX_PITCH + l] = (uint16_t)box_div(sum + (uint32_t)r, mul);
+                    out[(q - base) * BOX_PITCH + l] = (uint16_t)box_div(sum, mul);
                 }
             }
             __syncthreads();
