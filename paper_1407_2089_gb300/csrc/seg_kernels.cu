@@ -1760,27 +1760,49 @@ __global__ void __launch_bounds__(MED_TX * MED_TY, 4) k_median27(const BatchHdr 
         const int z0 = (int)(lt / ((uint32_t)ntx * nty)) * MED_TZ;
         __syncthreads();  // the previous tile is done with d
         constexpr int SXW = MED_TILE_X + 2;
-        constexpr int NS = (MED_TZ + 2) * (MED_TY + 2) * SXW;
-        // 26 elements per thread, loaded in rounds of 7 pairs in flight
-        constexpr int NT = MED_TX * MED_TY, NB = 7;
-        for (int i0 = threadIdx.x; i0 < NS; i0 += NT * NB) {
-            uint16_t lv[NB], bv[NB];
+        // Staging: one warp per staged row (MED_TZ + 2 planes x MED_TY + 2
+        // rows of SXW voxels, x, y and z clamped to the volume); lane l takes
+        // shared x indices 2l and 2l + 1 (one 32-bit shared word), lanes 0
+        // and 1 also index 64 + l.  A row's clamped y and z and its base are
+        // computed once; four rows' loads are in flight per lane.
+        {
+            static_assert(SXW == 66 && MED_TX * MED_TY == 256, "staging layout");
+            constexpr int NROW = (MED_TZ + 2) * (MED_TY + 2), RB = 4, NW = MED_TX * MED_TY / 32;
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            const int xa = min(max(x0 - 1 + 2 * lane, 0), X - 1), xb = min(max(x0 + 2 * lane, 0), X - 1);
+            const int xc = min(max(x0 + 63 + lane, 0), X - 1);  // index 64 + lane (lanes 0, 1)
+            uint16_t *ds = &d[0][0][0];
+            for (int r0 = warp; r0 < NROW; r0 += NW * RB) {
+                uint32_t la[RB], lb[RB], lc[RB], ba[RB], bb[RB], bc[RB];
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                const int i = i0 + j * NT;
-                if (i < NS) {
-                    const int sx = i % SXW, sy = (i / SXW) % (MED_TY + 2), sz = i / (SXW * (MED_TY + 2));
-                    const int x = min(max(x0 - 1 + sx, 0), X - 1), y = min(max(y0 - 1 + sy, 0), Y - 1);
-                    const int z = min(max(z0 - 1 + sz, 0), Z - 1);
-                    const size_t g = (size_t)x + (size_t)X * ((size_t)y + (size_t)Y * z);
-                    lv[j] = V.dn_src[g];
-                    bv[j] = V.dn_a[g];
+                for (int j = 0; j < RB; ++j) {
+                    const int rr = r0 + NW * j;
+                    la[j] = lb[j] = lc[j] = ba[j] = bb[j] = bc[j] = 0u;
+                    if (rr < NROW) {
+                        const int sz = rr / (MED_TY + 2), sy = rr - sz * (MED_TY + 2);
+                        const int y = min(max(y0 - 1 + sy, 0), Y - 1), z = min(max(z0 - 1 + sz, 0), Z - 1);
+                        const size_t ro = (size_t)X * ((size_t)y + (size_t)Y * z);
+                        const uint16_t *L = V.dn_src + ro, *B = V.dn_a + ro;
+                        la[j] = L[xa];
+                        lb[j] = L[xb];
+                        ba[j] = B[xa];
+                        bb[j] = B[xb];
+                        if (lane < 2) {
+                            lc[j] = L[xc];
+                            bc[j] = B[xc];
+                        }
+                    }
                 }
-            }
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                const int i = i0 + j * NT;
-                if (i < NS) (&d[0][0][0])[i] = (uint16_t)(lv[j] > bv[j] ? lv[j] - bv[j] : 0);
+                for (int j = 0; j < RB; ++j) {
+                    const int rr = r0 + NW * j;
+                    if (rr < NROW) {
+                        const uint32_t da = la[j] > ba[j] ? la[j] - ba[j] : 0u;
+                        const uint32_t db = lb[j] > bb[j] ? lb[j] - bb[j] : 0u;
+                        reinterpret_cast<uint32_t *>(ds + rr * SXW)[lane] = da | (db << 16);
+                        if (lane < 2) ds[rr * SXW + 64 + lane] = (uint16_t)(lc[j] > bc[j] ? lc[j] - bc[j] : 0u);
+                    }
+                }
             }
         }
         __syncthreads();
