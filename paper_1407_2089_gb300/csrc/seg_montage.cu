@@ -281,19 +281,54 @@ int fail(cudaError_t e) {
     } while (0)
 
 // Device buffers of one registration call, freed on every return path.
+// Device scratch of one call, from the stream-ordered pool on stream s, and
+// REG_STREAMS worker streams that take the pairs in turn.
+constexpr int REG_STREAMS = 4;
+
 struct Scratch {
     std::vector<void *> ptrs;
     cudaStream_t s = nullptr;
+    cudaStream_t w[REG_STREAMS] = {};
+    cudaEvent_t ev[REG_STREAMS + 1] = {};
     ~Scratch() {
-        for (void *p : ptrs) cudaFree(p);
+        if (s && w[REG_STREAMS - 1] && ev[REG_STREAMS - 1]) join();  // frees wait for the worker streams too
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+        if (s) cudaStreamSynchronize(s);
+        for (int k = 0; k < REG_STREAMS; ++k)
+            if (w[k]) cudaStreamDestroy(w[k]);
+        for (int k = 0; k <= REG_STREAMS; ++k)
+            if (ev[k]) cudaEventDestroy(ev[k]);
         if (s) cudaStreamDestroy(s);
+    }
+    cudaError_t init() {
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        for (int k = 0; k < REG_STREAMS && e == cudaSuccess; ++k)
+            e = cudaStreamCreateWithFlags(&w[k], cudaStreamNonBlocking);
+        for (int k = 0; k <= REG_STREAMS && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        return e;
     }
     template <class T>
     cudaError_t alloc(T **p, size_t n) {
         void *q = nullptr;
-        const cudaError_t e = cudaMalloc(&q, n ? n * sizeof(T) : 1);
+        const cudaError_t e = cudaMallocAsync(&q, n ? n * sizeof(T) : 1, s);
         if (e == cudaSuccess) ptrs.push_back(q);
         *p = static_cast<T *>(q);
+        return e;
+    }
+    // the worker streams wait for everything queued on s so far
+    cudaError_t fork() {
+        cudaError_t e = cudaEventRecord(ev[REG_STREAMS], s);
+        for (int k = 0; k < REG_STREAMS && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(w[k], ev[REG_STREAMS], 0);
+        return e;
+    }
+    // s waits for everything queued on the worker streams so far
+    cudaError_t join() {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < REG_STREAMS && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(ev[k], w[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[k], 0);
+        }
         return e;
     }
 };
@@ -328,22 +363,22 @@ struct Prefix {
 };
 
 // Sa, Saa (side 0) or Sb, Sbb (side 1) of every shift.
-int side_sums(Scratch &sc, const Prefix &pf, const uint16_t *T, const int *D, const int *d0, const int *r, int side,
-              unsigned long long *s1, unsigned long long *s2) {
+int side_sums(cudaStream_t st, const Prefix &pf, const uint16_t *T, const int *D, const int *d0, const int *r,
+              int side, unsigned long long *s1, unsigned long long *s2) {
     int3 u0, u1;
     side_region(d0, r, D, side, u0, u1);
     const int UX = u1.x - u0.x, UY = u1.y - u0.y, UZ = u1.z - u0.z;
     const int SX = 2 * r[0] + 1, S = SX * (2 * r[1] + 1) * (2 * r[2] + 1);
     if (UX <= 0 || UY <= 0 || UZ <= 0) {
-        RK(cudaMemsetAsync(s1, 0, S * sizeof(unsigned long long), sc.s));
-        RK(cudaMemsetAsync(s2, 0, S * sizeof(unsigned long long), sc.s));
+        RK(cudaMemsetAsync(s1, 0, S * sizeof(unsigned long long), st));
+        RK(cudaMemsetAsync(s2, 0, S * sizeof(unsigned long long), st));
         return SEG_OK;
     }
     unsigned long long *p1 = pf.p1, *p2 = pf.p2, *q1 = pf.q1, *q2 = pf.q2;
     const int rows = UY * UZ;
-    k_reg_rows<<<(rows + 7) / 8, 256, 0, sc.s>>>(T, D[0], D[1], u0, u1, d0[0], r[0], side, p1, p2);
-    k_reg_q<<<SX * UZ, RQ_THREADS, 0, sc.s>>>(p1, p2, u0, u1, q1, q2);
-    k_reg_box<<<(S + 7) / 8, 256, 0, sc.s>>>(q1, q2, D[0], D[1], D[2], u0, u1, make_int3(d0[0], d0[1], d0[2]),
+    k_reg_rows<<<(rows + 7) / 8, 256, 0, st>>>(T, D[0], D[1], u0, u1, d0[0], r[0], side, p1, p2);
+    k_reg_q<<<SX * UZ, RQ_THREADS, 0, st>>>(p1, p2, u0, u1, q1, q2);
+    k_reg_box<<<(S + 7) / 8, 256, 0, st>>>(q1, q2, D[0], D[1], D[2], u0, u1, make_int3(d0[0], d0[1], d0[2]),
                                              make_int3(r[0], r[1], r[2]), side, s1, s2);
     RK(cudaGetLastError());
     return SEG_OK;
@@ -395,9 +430,18 @@ extern "C" int seg_register_montage(int device, const uint16_t *const *tiles, in
     *n_edges = (uint32_t)E.size();
     if (E.size() > edges_cap || (!edges && !E.empty())) return SEG_ESMALL;
 
-    Scratch sc;
     RK(cudaSetDevice(device));
-    RK(cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking));
+    {
+        // keep freed scratch in the pool between calls
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    }
+    Scratch sc;
+    RK(sc.init());
     // the tiles on the device
     std::vector<const uint16_t *> dt(n_tiles);
     if (on_device) {
@@ -411,9 +455,16 @@ extern "C" int seg_register_montage(int device, const uint16_t *const *tiles, in
         }
     }
     const int SX = 2 * r[0] + 1, SY = 2 * r[1] + 1, S = SX * SY * (2 * r[2] + 1);
-    unsigned long long *dsum;  // Sab, Sa, Saa, Sb, Sbb of every shift
-    RK(sc.alloc(&dsum, 5 * (size_t)S));
-    std::vector<unsigned long long> hs(5 * (size_t)S);
+    // Pairs go in groups of up to REG_GROUP: every pair of a group gets its
+    // own slice of sums (Sab, Sa, Saa, Sb, Sbb of every shift), the group's
+    // kernels are queued back to back, and one copy and one synchronisation
+    // bring its sums to the host.
+    constexpr size_t REG_GROUP = 64;
+    const size_t per = 5 * (size_t)S;
+    const size_t gmax = std::max<size_t>(1, std::min(E.size(), REG_GROUP));
+    unsigned long long *dsum;
+    RK(sc.alloc(&dsum, per * gmax));
+    std::vector<unsigned long long> hs(per * gmax);
     size_t np = 1, nq = 1;
     for (const seg_montage_edge &e : E) {
         const int d0[3] = {stage[e.b].x - stage[e.a].x, stage[e.b].y - stage[e.a].y, stage[e.b].z - stage[e.a].z};
@@ -424,55 +475,74 @@ extern "C" int seg_register_montage(int device, const uint16_t *const *tiles, in
             nq = std::max(nq, b);
         }
     }
-    Prefix pf;
-    RK(sc.alloc(&pf.p1, np));
-    RK(sc.alloc(&pf.p2, np));
-    RK(sc.alloc(&pf.q1, nq));
-    RK(sc.alloc(&pf.q2, nq));
+    Prefix pf[REG_STREAMS];
+    for (int k = 0; k < REG_STREAMS; ++k) {
+        RK(sc.alloc(&pf[k].p1, np));
+        RK(sc.alloc(&pf[k].p2, np));
+        RK(sc.alloc(&pf[k].q1, nq));
+        RK(sc.alloc(&pf[k].q2, nq));
+    }
     const size_t smem = reg_corr_smem(r[0], r[1], r[2]);
     const RegCorrFn corr = reg_corr_fn(r[0], std::make_integer_sequence<int, SEG_REG_MAX_RXY + 1>{});
     if (!corr) return SEG_EINVAL;
     RK(cudaFuncSetAttribute(corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    for (seg_montage_edge &e : E) {
-        const int d0[3] = {stage[e.b].x - stage[e.a].x, stage[e.b].y - stage[e.a].y, stage[e.b].z - stage[e.a].z};
-        RK(cudaMemsetAsync(dsum, 0, S * sizeof(unsigned long long), sc.s));
-        int3 u0, u1;
-        side_region(d0, r, D, 0, u0, u1);
-        if (u1.x > u0.x && u1.y > u0.y && u1.z > u0.z) {
-            const int nb = ((u1.x - u0.x + RC_TX - 1) / RC_TX) * ((u1.y - u0.y + RC_TY - 1) / RC_TY) *
-                           ((u1.z - u0.z + RC_TZ - 1) / RC_TZ);
-            corr<<<nb, RC_THREADS, smem, sc.s>>>(dt[e.a], dt[e.b], D[0], D[1], D[2], u0, u1,
-                                                 make_int3(d0[0], d0[1], d0[2]), r[1], r[2], dsum);
-            RK(cudaGetLastError());
-        }
-        int rc = side_sums(sc, pf, dt[e.a], D, d0, r, 0, dsum + S, dsum + 2 * (size_t)S);
-        if (rc != SEG_OK) return rc;
-        rc = side_sums(sc, pf, dt[e.b], D, d0, r, 1, dsum + 3 * (size_t)S, dsum + 4 * (size_t)S);
-        if (rc != SEG_OK) return rc;
-        RK(cudaMemcpyAsync(hs.data(), dsum, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, sc.s));
-        RK(cudaStreamSynchronize(sc.s));
-        // the first best shift in z, y, x order
-        for (int si = 0; si < S; ++si) {
-            const int s[3] = {si % SX - r[0], (si / SX) % SY - r[1], si / (SX * SY) - r[2]};
-            uint64_t cnt = 1;
-            for (int k = 0; k < 3; ++k) {
-                const Range q = shared_range(d0[k] + s[k], D[k], 0);
-                cnt *= (uint64_t)(q.hi > q.lo ? q.hi - q.lo : 0);
+    for (size_t g0 = 0; g0 < E.size(); g0 += REG_GROUP) {
+        const size_t g1 = std::min(E.size(), g0 + REG_GROUP);
+        RK(sc.fork());
+        for (size_t ei = g0; ei < g1; ++ei) {
+            const seg_montage_edge &e = E[ei];
+            unsigned long long *ds = dsum + per * (ei - g0);
+            const int k = (int)(ei % REG_STREAMS);
+            const cudaStream_t st = sc.w[k];
+            const int d0[3] = {stage[e.b].x - stage[e.a].x, stage[e.b].y - stage[e.a].y,
+                               stage[e.b].z - stage[e.a].z};
+            RK(cudaMemsetAsync(ds, 0, S * sizeof(unsigned long long), st));
+            int3 u0, u1;
+            side_region(d0, r, D, 0, u0, u1);
+            if (u1.x > u0.x && u1.y > u0.y && u1.z > u0.z) {
+                const int nb = ((u1.x - u0.x + RC_TX - 1) / RC_TX) * ((u1.y - u0.y + RC_TY - 1) / RC_TY) *
+                               ((u1.z - u0.z + RC_TZ - 1) / RC_TZ);
+                corr<<<nb, RC_THREADS, smem, st>>>(dt[e.a], dt[e.b], D[0], D[1], D[2], u0, u1,
+                                                   make_int3(d0[0], d0[1], d0[2]), r[1], r[2], ds);
+                RK(cudaGetLastError());
             }
-            if (cnt == 0) continue;
-            const unsigned long long sab = hs[si], sa = hs[S + si], saa = hs[2 * (size_t)S + si];
-            const unsigned long long sb = hs[3 * (size_t)S + si], sbb = hs[4 * (size_t)S + si];
-            const __int128 N = (__int128)cnt;
-            const __int128 num = N * (__int128)sab - (__int128)sa * (__int128)sb;
-            const __int128 va = N * (__int128)saa - (__int128)sa * (__int128)sa;
-            const __int128 vb = N * (__int128)sbb - (__int128)sb * (__int128)sb;
-            if (va == 0 || vb == 0) continue;
-            const double rho = (double)num / std::sqrt((double)va * (double)vb);
-            if (rho > e.score) {
-                e.score = rho;
-                e.shift.x = s[0];
-                e.shift.y = s[1];
-                e.shift.z = s[2];
+            int rc = side_sums(st, pf[k], dt[e.a], D, d0, r, 0, ds + S, ds + 2 * (size_t)S);
+            if (rc != SEG_OK) return rc;
+            rc = side_sums(st, pf[k], dt[e.b], D, d0, r, 1, ds + 3 * (size_t)S, ds + 4 * (size_t)S);
+            if (rc != SEG_OK) return rc;
+        }
+        RK(sc.join());
+        RK(cudaMemcpyAsync(hs.data(), dsum, per * (g1 - g0) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           sc.s));
+        RK(cudaStreamSynchronize(sc.s));
+        for (size_t ei = g0; ei < g1; ++ei) {
+            seg_montage_edge &e = E[ei];
+            const unsigned long long *h = hs.data() + per * (ei - g0);
+            const int d0[3] = {stage[e.b].x - stage[e.a].x, stage[e.b].y - stage[e.a].y,
+                               stage[e.b].z - stage[e.a].z};
+            // the first best shift in z, y, x order
+            for (int si = 0; si < S; ++si) {
+                const int s[3] = {si % SX - r[0], (si / SX) % SY - r[1], si / (SX * SY) - r[2]};
+                uint64_t cnt = 1;
+                for (int k = 0; k < 3; ++k) {
+                    const Range q = shared_range(d0[k] + s[k], D[k], 0);
+                    cnt *= (uint64_t)(q.hi > q.lo ? q.hi - q.lo : 0);
+                }
+                if (cnt == 0) continue;
+                const unsigned long long sab = h[si], sa = h[S + si], saa = h[2 * (size_t)S + si];
+                const unsigned long long sb = h[3 * (size_t)S + si], sbb = h[4 * (size_t)S + si];
+                const __int128 N = (__int128)cnt;
+                const __int128 num = N * (__int128)sab - (__int128)sa * (__int128)sb;
+                const __int128 va = N * (__int128)saa - (__int128)sa * (__int128)sa;
+                const __int128 vb = N * (__int128)sbb - (__int128)sb * (__int128)sb;
+                if (va == 0 || vb == 0) continue;
+                const double rho = (double)num / std::sqrt((double)va * (double)vb);
+                if (rho > e.score) {
+                    e.score = rho;
+                    e.shift.x = s[0];
+                    e.shift.y = s[1];
+                    e.shift.z = s[2];
+                }
             }
         }
     }
