@@ -198,6 +198,7 @@ struct seg_ctx {
     bool tuned = false;  // tile shape fixed (forced, or tuned on the first batch)
     cudaStream_t copy_stream = nullptr;
     cudaStream_t read_stream = nullptr;
+    uint32_t *read_pin = nullptr;  // pinned words for small results of the read calls (one reader at a time)
     std::vector<Slot> slots;
     std::mutex mu;
     std::condition_variable cv;
@@ -793,6 +794,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     cudaGetLastError();
     CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&ctx->read_stream, cudaStreamNonBlocking));
+    CK(cudaMallocHost(reinterpret_cast<void **>(&ctx->read_pin), 64));
     ctx->slots.resize(nslots);
     for (Slot &s : ctx->slots) {
         CK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
@@ -836,6 +838,7 @@ int seg_destroy(seg_ctx *ctx) {
     }
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->read_stream) cudaStreamDestroy(ctx->read_stream);
+    if (ctx->read_pin) cudaFreeHost(ctx->read_pin);
     delete ctx;
     return SEG_OK;
 }
@@ -1136,10 +1139,11 @@ int seg_read_label_runs(seg_ctx *ctx, seg_req req, uint32_t channel, seg_label_r
                                         mapped ? stage : cap, dev_out, mapped, ctx->sms, s);
         if (mapped && dev_out) cudaFreeAsync(dev_out, s);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->read_pin, d_total, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int rc = SEG_OK;
     if (e == cudaSuccess) {
+        total = ctx->read_pin[0];
         if (n_runs) *n_runs = total;
         if (cap < total) {
             rc = dst ? SEG_ESMALL : SEG_OK;
