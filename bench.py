@@ -717,7 +717,7 @@ def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, gr
 
     def step():
         q, err = [], []
-        done = [0]
+        done, stop = [0], [False]
         cv = threading.Condition()
         t_start = time.perf_counter()
 
@@ -727,7 +727,9 @@ def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, gr
                     if queued:
                         # at most `ahead` frames queued beyond the last one read back
                         with cv:
-                            cv.wait_for(lambda: done[0] >= t - ahead or err)
+                            cv.wait_for(lambda: done[0] >= t - ahead or stop[0])
+                    if stop[0]:
+                        return
                     r = seg.seg_submit_volume(ctx2, h_in[t], dims=(X, Y, Z), channels=C, keep_host_input=queued)
                     if (t + 1) % group == 0 or t + 1 == T:
                         seg.seg_flush(ctx2)
@@ -765,6 +767,9 @@ def e2e_run(seg, torch, dist, args, local, dev, ws, stream, h_in, dims, T, C, gr
                     done[0] = t + 1
                     cv.notify_all()
         finally:
+            with cv:  # a reader that stops early releases a waiting submitter
+                stop[0] = True
+                cv.notify_all()
             th.join()
         if err:
             raise err[0]
