@@ -350,6 +350,10 @@ def run_gpu(args):
                                                             max(1, min(args.steps, 3)))}
     del d_in
     torch.cuda.empty_cache()
+    uneven = None
+    if not args.no_uneven and rank == 0:
+        uneven = uneven_forms(seg, torch, local, max(1, min(args.steps, 5)))
+        torch.cuda.empty_cache()
     serve = None
     if args.serving_requests and rank == 0:
         serve = {"batched": serving(seg, torch, local, args.serving_requests, 200.0, 0, 2),
@@ -391,6 +395,7 @@ def run_gpu(args):
             "e2e": e2e,
             "e2e_dense_labels": e2e_dense,
             "forms_gvox_s_per_gpu": forms,
+            "uneven_batch": uneven,
             "denoise_front_end": denoise,
             "closing": closing,
             "distance_map": distmap,
@@ -619,6 +624,74 @@ def plain_form(seg, torch, d_in, dims, local, steps):
     return vox / (ms / 1e3) / 1e9
 
 
+def uneven_forms(seg, torch, local, steps):
+    """The batched-uneven workload (48 uint16 volumes, 64^3 ... 1024x1024x96,
+    nuclei 1 per 40^3 voxels), resident on the device: all of them in one
+    graph-captured launch sequence (batched) against one plain launch
+    sequence per volume, timed on an ordering stream like the main line.
+    Also the single 128x128x32 frame through the plain form: median latency
+    of sequential requests, submit to done."""
+    import synth
+    vols = synth.batched_uneven()
+    dvols = [torch.from_numpy(v.view(np.int16)).to("cuda:%d" % local) for v in vols]
+    vox = int(sum(v.size for v in vols))
+    out = {"volumes": len(vols), "voxels": vox}
+    for name, flags in (("batched", 0), ("plain", seg.SEG_PLAIN)):
+        stream = torch.cuda.Stream()
+        # a long batch window: the flush after the last submit starts one batch
+        ctx = seg.seg_create(device=local, flags=flags, order_stream=stream.cuda_stream,
+                             batch_window_us=0 if flags else 10_000_000)
+
+        def one_pass():
+            reqs = [seg.seg_submit_volume(ctx, dv, dims=(v.shape[2], v.shape[1], v.shape[0]), channels=1)
+                    for dv, v in zip(dvols, vols)]
+            seg.seg_flush(ctx)
+            for r in reqs:
+                seg.seg_enqueue_wait(ctx, r, stream.cuda_stream)
+            return reqs
+
+        def finish(reqs):
+            for r in reqs:
+                if seg.seg_wait(ctx, r) != seg.SEG_DONE:
+                    raise RuntimeError("request failed")
+                seg.seg_release(ctx, r)
+
+        for _ in range(2):
+            finish(one_pass())
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            finish(one_pass())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if name == "batched":
+            out["batches_per_pass"] = seg.seg_get_stats(ctx)["batches"] / (steps + 2)
+        seg.seg_destroy(ctx)
+        out[name] = {"ms_per_pass": ms, "gvox_s": vox / (ms / 1e3) / 1e9}
+    del dvols
+    # the single frame, plain form
+    v1 = synth.single_frame()
+    d1 = torch.from_numpy(v1.view(np.int16)).to("cuda:%d" % local)
+    ctx = seg.seg_create(device=local, flags=seg.SEG_PLAIN)
+    lat = []
+    for i in range(23):
+        t0 = time.perf_counter()
+        r = seg.seg_submit_volume(ctx, d1, dims=(v1.shape[2], v1.shape[1], v1.shape[0]), channels=1)
+        if seg.seg_wait(ctx, r) != seg.SEG_DONE:
+            raise RuntimeError("request failed")
+        if i >= 3:
+            lat.append((time.perf_counter() - t0) * 1e3)
+        seg.seg_release(ctx, r)
+    seg.seg_destroy(ctx)
+    out["single_frame_plain"] = {"dims": [int(v1.shape[2]), int(v1.shape[1]), int(v1.shape[0])],
+                                 "latency_ms_median": statistics.median(lat),
+                                 "gvox_s": v1.size / (statistics.median(lat) / 1e3) / 1e9}
+    return out
+
+
 def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
     """Open-loop Poisson request stream (2-channel volumes, sizes log-uniform
     from 128^3 to 2048x2048x64) through the C ABI from pinned host memory.
@@ -845,6 +918,7 @@ def main():
                          "dz^2 (0.8 x 0.8 x 1.0 um in 0.2 um units; 0 skips)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the 48 uneven volumes and the single frame")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain per-frame comparison")
     ap.add_argument("--serving-requests", type=int, default=400,
                     help="Poisson requests (200/s) for the served latency; 0 skips serving")
