@@ -207,8 +207,8 @@ int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
  * dst holds cap runs in host memory, or device memory when dst_on_device = 1;
  * dst = NULL with cap = 0 only reports the number.  Derived on the device
  * from the label image (two passes over it) and copied; blocks until done.
- * Errors: SEG_ESMALL (cap < *n_runs, nothing written); otherwise as
- * seg_read_labels. */
+ * Errors: SEG_ESMALL (cap < *n_runs, nothing written); SEG_ETOOBIG for an
+ * image of more than 2^32 - 65 rows; otherwise as seg_read_labels. */
 int seg_read_label_runs(seg_ctx *ctx, seg_req req, uint32_t channel, seg_label_run *dst, uint64_t cap,
                         uint64_t *n_runs, int dst_on_device);
 

@@ -1103,6 +1103,7 @@ int seg_read_label_runs(seg_ctx *ctx, seg_req req, uint32_t channel, seg_label_r
     }
     if (channel >= r->C || (!dst && cap)) return SEG_EINVAL;
     const VolGeom &g = r->g[channel];
+    if (g.rows > 0xFFFFFFFFu - 64u) return SEG_ETOOBIG;  // row indices of the blocks stay in 32 bits
     const uint32_t nt = label_runs_tiles(g.rows);
     const size_t a_rows = al(4ull * g.rows), a_tiles = al(4ull * nt);
     const uint64_t most = (uint64_t)g.rows * ((g.X + 1) / 2);  // runs a label image can hold
