@@ -45,7 +45,8 @@ ALGO_BYTES_PER_VOXEL = 8.0  # 2 B raw read + 2 B re-read after Otsu + 4 B label 
 # Algorithmic bytes per voxel of each kernel (the units one launch processes
 # are all voxels of the batch).
 KERNEL_BYTES_PER_VOXEL = {
-    "smooth_hist_otsu": 2.0,       # raw uint16 read once
+    "smooth_rows_otsu": 2.0,       # raw uint16 read once (row-aligned volumes)
+    "smooth_hist_otsu": 2.0,       # raw uint16 read once (other volumes)
     "threshold_runs": 1 / 8.0,     # 1-bit mask write (the smoothed re-read is the 2 B
                                    # counted in the 8 B/voxel path total)
     "label_features": 4.0,         # uint32 label write (run tables are O(runs))
@@ -293,9 +294,16 @@ def run_gpu(args):
                 raise RuntimeError("request failed")
             seg.seg_release(ctx, r)
 
-    # warm-up
+    # warm-up, in the same pipelined pattern as the timed steps (one step in
+    # flight while the previous one is read), so that the memory pool and the
+    # captured graphs of every slot are in their steady state before timing
+    pend = []
     for _ in range(args.warmup):
-        finish(step(ctx, submit_dev))
+        pend.append(step(ctx, submit_dev))
+        if len(pend) > 1:
+            finish(pend.pop(0))
+    for p in pend:
+        finish(p)
     torch.cuda.synchronize()
     seg.seg_reset_stats(ctx)
     if ws > 1:
@@ -901,7 +909,8 @@ def main():
                     help="e2e submits queue their input copies, or wait for each")
     ap.add_argument("--e2e-ahead", type=int, default=12, help="queued copies: frames submitted beyond the last read")
     ap.add_argument("--inflight", type=int, default=1,
-                    help="batches in flight; 1 keeps per-kernel CUDA-event times free of overlap")
+                    help="batch slots; batches run one after another on the device either way, so with 2 "
+                         "the host prepares the next batch while one runs")
     ap.add_argument("--frames", type=int, default=FRAMES,
                     help="time-lapse frames per step (fewer frames: a small case for profiling)")
     ap.add_argument("--tile", default="", help="force the tile height and z-chunk, e.g. 32,64")

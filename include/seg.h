@@ -70,6 +70,8 @@ extern "C" {
                                      once and raises its error bit, so requests
                                      with adjacent runs end FAILED (error path
                                      without any device fault)                  */
+#define SEG_KEEP_SMOOTHED 0x20u /* keep each channel's smoothed image (2 bytes per
+                                   voxel more per request) for seg_read_smoothed */
 
 typedef struct seg_ctx seg_ctx; /* opaque; owns streams, graphs, device state   */
 typedef uint64_t seg_req;       /* request handle, never 0                       */
@@ -98,9 +100,9 @@ typedef struct {
 
 typedef struct {
     int device;                /* CUDA ordinal                                   */
-    uint32_t max_inflight;     /* batches in flight (streams); 0 -> 2            */
     uint64_t hbm_budget_bytes; /* admission limit for all device state; 0 -> 80 %
                                   of the device's free memory at seg_create      */
+    uint32_t max_inflight;     /* batches in flight (streams); 0 -> 2            */
     uint32_t flags;            /* SEG_FORCE_TILE | SEG_PLAIN | ...               */
     uint32_t tile_y;           /* smoothing tile rows: 16, 32 or 64 (FORCE_TILE) */
     uint32_t tile_z;           /* smoothing z-chunk, >= 1 (FORCE_TILE)           */
@@ -239,6 +241,17 @@ int seg_read_cell_distance(seg_ctx *ctx, seg_req req, uint32_t cells_channel, ui
  * seg_read_labels. */
 int seg_read_denoised(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst, uint64_t dst_elems,
                       int dst_on_device, uint32_t *mrf_steps);
+
+/* Copies the smoothed image of channel `channel` (X*Y*Z uint16, layout of the
+ * input) to dst (host, or device when dst_on_device = 1): the low-pass of
+ * Background Noise Removal, Eq. 1, as computed here -- the binomial
+ * [1 4 6 4 1] along x, y and z, the uint32 sum S rounded once to
+ * (S + 2048) >> 12, edges replicated -- which is the image the Otsu
+ * histogram counts and the threshold compares.  Only for contexts created
+ * with SEG_KEEP_SMOOTHED (otherwise SEG_EINVAL); blocks until the copy is
+ * complete.  Other errors as seg_read_labels. */
+int seg_read_smoothed(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst, uint64_t dst_elems,
+                      int dst_on_device);
 
 /* Copies channel `channel`'s cells (label order) to host memory dst (cap
  * entries) and reports n_cells and the Otsu level t* (foreground = s > t*).

@@ -36,6 +36,7 @@ SEG_PLAIN = 0x2
 SEG_NO_GRAPH = 0x4
 SEG_PROFILE = 0x8
 SEG_TEST_UNION_FAIL = 0x10
+SEG_KEEP_SMOOTHED = 0x20
 
 SEG_MAX_KERNELS = 32
 SEG_REG_MAX_RXY = 12
@@ -59,8 +60,8 @@ assert FEATURE_DTYPE.itemsize == ctypes.sizeof(seg_cell_features) == 64
 
 
 class seg_config(ctypes.Structure):
-    _fields_ = [("device", ctypes.c_int), ("max_inflight", ctypes.c_uint32),
-                ("hbm_budget_bytes", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("tile_y", ctypes.c_uint32), ("tile_z", ctypes.c_uint32),
                 ("max_batch_volumes", ctypes.c_uint32), ("batch_window_us", ctypes.c_uint32),
                 ("host_queue", ctypes.c_uint32), ("order_stream", ctypes.c_void_p)]
@@ -96,7 +97,7 @@ class seg_stats(ctypes.Structure):
 
 EXPORTS = ["seg_create", "seg_destroy", "seg_submit_volume", "seg_flush", "seg_poll",
            "seg_enqueue_wait", "seg_read_labels", "seg_read_label_runs", "seg_read_distance", "seg_read_cell_distance", "seg_read_denoised",
-           "seg_read_features", "seg_release",
+           "seg_read_smoothed", "seg_read_features", "seg_release",
            "seg_request_times", "seg_get_stats", "seg_reset_stats", "seg_strerror",
            "seg_otsu_threshold_noalloc", "seg_register_montage"]
 
@@ -116,6 +117,7 @@ def _bind(lib):
         "seg_read_distance": [vp, u64, u32, vp, u64, i32],
         "seg_read_cell_distance": [vp, u64, u32, u32, vp, u64, P(u64)],
         "seg_read_denoised": [vp, u64, u32, vp, u64, i32, P(u32)],
+        "seg_read_smoothed": [vp, u64, u32, vp, u64, i32],
         "seg_read_features": [vp, u64, u32, vp, u64, P(u64), P(ctypes.c_uint16)],
         "seg_release": [vp, u64],
         "seg_request_times": [vp, u64, P(ctypes.c_double), P(ctypes.c_double),
@@ -164,7 +166,7 @@ def seg_strerror(code: int) -> str:
 def seg_create(device=0, max_inflight=0, hbm_budget_bytes=0, flags=0, tile_y=0, tile_z=0,
                max_batch_volumes=0, batch_window_us=0, host_queue=0, order_stream=None):
     """Returns an opaque context handle (int)."""
-    cfg = seg_config(device, max_inflight, hbm_budget_bytes, flags, tile_y, tile_z,
+    cfg = seg_config(device, hbm_budget_bytes, max_inflight, flags, tile_y, tile_z,
                      max_batch_volumes, batch_window_us, host_queue,
                      ctypes.c_void_p(order_stream) if order_stream else None)
     out = ctypes.c_void_p()
@@ -337,6 +339,19 @@ def seg_read_denoised(ctx, req, channel, out):
     _check(_lib.seg_read_denoised(ctx, req, channel, ctypes.c_void_p(ptr), n, dev, ctypes.byref(steps)),
            "seg_read_denoised")
     return steps.value
+
+
+def seg_read_smoothed(ctx, req, channel, out):
+    """Copies the channel's smoothed image into `out` (a numpy uint16 array or
+    a torch int16/uint16 tensor); the context needs SEG_KEEP_SMOOTHED."""
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.uint16 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be C-contiguous uint16")
+        ptr, n, dev = out.ctypes.data, out.size, 0
+    else:
+        ptr, n, dev = out.data_ptr(), out.numel(), 1 if out.is_cuda else 0
+    _check(_lib.seg_read_smoothed(ctx, req, channel, ctypes.c_void_p(ptr), n, dev), "seg_read_smoothed")
+    return out
 
 
 def seg_read_features(ctx, req, channel):

@@ -69,9 +69,17 @@ struct VolDev {
     uint32_t rows;            // Y * Z
     uint32_t min_volume;
     uint32_t union_limit;     // retries before a union gives up (ERR_UNION)
-    uint32_t ntx, nty, ntz;   // smoothing tiles per axis
+    uint32_t ntx, nty, ntz;   // smoothing tiles per axis (k_smooth_hist; 0 for row-aligned volumes)
     uint32_t nrt;             // row tiles
     uint32_t tile_base;       // first flat smoothing-tile index
+    // k_smooth_rows (rows 16-byte aligned: X % 8 == 0 and an aligned input);
+    // fs_ntx = 0 for the other volumes
+    uint32_t fs_rt;           // octets per tile row (min(X / 8, 64))
+    uint32_t fs_ty;           // rows per tile (FS_NT / fs_rt)
+    uint32_t fs_hx;           // 1: x-tiled (X > 512), staged rows carry a halo chunk on each side
+    uint32_t fs_tz;           // planes per tile
+    uint32_t fs_ntx, fs_nty, fs_ntz;  // tiles per axis
+    uint32_t fs_base;         // first flat k_smooth_rows tile index
     uint32_t rt_base;         // first flat row-tile index
     uint32_t nby;             // union-find bricks along y
     uint32_t nbk;             // union-find bricks
@@ -142,6 +150,7 @@ struct BatchHdr {
     uint32_t nrowtiles;  // row tiles over the batch
     uint32_t tile_z;     // z-chunk of a smoothing tile
     uint32_t tile_y;     // rows of a smoothing tile
+    uint32_t fs_tiles;   // k_smooth_rows tiles over the batch
     uint32_t nbricks;    // union-find bricks over the batch
     uint32_t nbtasks;    // k_union tasks over the batch
     uint32_t dn_items[3];// denoise box-pass items per axis over the batch
@@ -158,7 +167,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 25;
+constexpr int NUM_KERNELS = 26;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {
@@ -222,6 +231,11 @@ cudaError_t launch_label_runs_write(const uint32_t *labels, uint32_t X, uint32_t
 
 // Histogram-kernel shared memory per block for a tile height.
 size_t hist_smem_bytes(int tile_y);
+// k_smooth_rows: threads per block, octets per tile row at most, and the
+// tile shape of a row-aligned volume of width X.
+constexpr int FS_NT = 512;
+constexpr int FS_RT = 64;
+inline uint32_t fs_rows_rt(uint32_t X) { return X >= 8u * FS_RT ? (uint32_t)FS_RT : X / 8u; }
 // Sets kernel attributes on `device` and fills the persistent grid sizes of
 // `plan` (plan.sms must be set).
 cudaError_t configure_kernels(int device, LaunchPlan &plan);

@@ -34,6 +34,7 @@
 #include <mutex>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "median27_net.h"
 #include "seg_internal.h"
@@ -42,7 +43,7 @@ namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
     "denoise_box", "denoise_median", "init",       "mrf_stats",        "mrf_iterate",
-    "smooth_hist_otsu", "threshold_runs",
+    "smooth_rows_otsu", "smooth_hist_otsu", "threshold_runs",
     "dilate",      "erode",          "dist_xy",    "dist_xy_1024",     "dist_x",
     "dist_y",      "dist_z",         "dist_z_long", "scan_runs",       "row_runs",
     "union_local", "union",          "flatten",    "keep_count",       "scan_keep",
@@ -654,7 +655,8 @@ __device__ void otsu_block(const uint32_t *__restrict__ gh, uint32_t *stat, uint
 // Merge the block's shared histogram into the volume's bins, then count the
 // block's finished tiles; the block that completes the volume runs Otsu.
 template <int NT>
-__device__ void flush_hist(const BatchHdr *__restrict__ h, uint32_t v, uint32_t ndone, uint32_t *sh) {
+__device__ void flush_hist(const BatchHdr *__restrict__ h, uint32_t v, uint32_t ndone, uint32_t *sh,
+                           uint32_t ntiles) {
     __shared__ uint32_t s_last;
     const VolDev &V = h->vol[v];
     __syncthreads();
@@ -689,9 +691,8 @@ __device__ void flush_hist(const BatchHdr *__restrict__ h, uint32_t v, uint32_t 
     if (threadIdx.x == 0) {
         s_last = 0;
         if (ndone) {
-            const uint32_t nt = V.ntx * V.nty * V.ntz;
             const uint32_t prev = atomicAdd(V.stat + ST_TILES_DONE, ndone);
-            s_last = (prev + ndone == nt);
+            s_last = (prev + ndone == ntiles);
         }
     }
     __syncthreads();
@@ -740,7 +741,7 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist(const BatchHdr *__res
     const int tz = (int)h->tile_z;
     for (uint32_t t = tb; t < te; ++t) {
         while (v + 1 < h->nvol && t >= h->vol[v + 1].tile_base) {
-            flush_hist<T::NT>(h, v, ndone, sh);
+            flush_hist<T::NT>(h, v, ndone, sh, h->vol[v].ntx * h->vol[v].nty * h->vol[v].ntz);
             ndone = 0;
             ++v;
         }
@@ -754,7 +755,331 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist(const BatchHdr *__res
         smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
         ++ndone;
     }
-    flush_hist<T::NT>(h, v, ndone, sh);
+    flush_hist<T::NT>(h, v, ndone, sh, h->vol[v].ntx * h->vol[v].nty * h->vol[v].ntz);
+}
+
+// ----------------------------------------------------------------------------
+// Smoothing + histogram of volumes whose rows are 16-byte aligned
+// (X % 8 == 0, 16-byte aligned input): k_smooth_rows
+// ----------------------------------------------------------------------------
+//
+// The same arithmetic as smooth_tile (binomial [1 4 6 4 1] per axis, exact
+// uint32 sums, one rounding (S + 2048) >> 12, replicate edges), ordered so
+// that the block moves fewer bytes through shared memory:
+//   y pass first, on the raw voxels as staged: a thread reads its octet of
+//     the five rows around its own (five 16-byte loads) and sums the packed
+//     16-bit pairs of each word at once; when every raw value is below 4096
+//     no lane of a word can exceed 16 * 4095 = 65520, so the packed sum is
+//     exact.  Each staged row is checked by the thread whose centre row it
+//     is (and the edge rows by the tile's first and last row of threads); if
+//     any value of a plane is 4096 or more, the whole block recomputes that
+//     plane's y pass in 32-bit lanes.
+//   x pass in registers: the two y-sums left and right of a thread's octet
+//     come from its neighbours through a small exchange buffer (one word each
+//     way), from the edge voxel at the volume's x-edges, or from a halo chunk
+//     that the tile's first / last thread of a row y-sums itself.
+//   z pass in registers (scatter form, four running sums per output), with
+//     the rounding constant carried in the newest running sum.
+// A tile is FS_RT octets (512 voxels) wide, or the whole row when X <= 512,
+// and FS_NT / octets-per-row rows high; it marches down z through a ring of
+// staged planes (16-byte cp.async copies, FS_S planes in flight).  The last
+// tile's threads beyond the row or the volume compute but do not emit.
+// Consecutive tiles of a block are y-neighbours, so the four rows that two
+// of them share are fetched again while still in L2.
+
+constexpr int FS_S = 4;                  // ring stages
+constexpr int FS_STAGE = 12 * 66 * 16;   // bytes per stage: 12 rows x 66 chunks (x-tiled) bound all shapes
+constexpr size_t FS_SMEM = 4ull * HIST_WORDS + (size_t)FS_S * FS_STAGE + 4ull * 4 * FS_NT + 8ull * 2 * FS_NT;
+static_assert((8 * FS_RT / FS_RT + 4) * (FS_RT + 2) * 16 <= FS_STAGE, "x-tiled stage");
+static_assert((FS_NT / FS_RT + 4) * FS_RT * 16 <= FS_STAGE && (FS_NT + 4) * 16 <= FS_STAGE, "stage bound");
+
+__device__ __forceinline__ uint32_t find_vol_fs(const BatchHdr *__restrict__ h, uint32_t t) {
+    uint32_t lo = 0, hi = h->nvol;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (h->vol[mid].fs_base <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t fs_ysum(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4) {
+    return r0 + r4 + 4u * (r1 + r3) + 6u * r2;
+}
+
+// y-sums (32-bit) of the low and high voxel of five staged words
+__device__ __forceinline__ void fs_ysum32(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
+                                          uint32_t &lo, uint32_t &hi) {
+    lo = fs_ysum(r0 & 0xFFFFu, r1 & 0xFFFFu, r2 & 0xFFFFu, r3 & 0xFFFFu, r4 & 0xFFFFu);
+    hi = fs_ysum(r0 >> 16, r1 >> 16, r2 >> 16, r3 >> 16, r4 >> 16);
+}
+
+// One tile: octets [x0, x0 + 8 rte) of rows [y0, y0 + TYF) of planes [z0, z1).
+// RTC = FS_RT: rows of 64 octets (8 rows per tile), HXC: halo chunks
+// (x-tiled rows), both known at compile time; RTC = 0: the shape of V.
+// Planes run through the ring from stage 0 in every tile, four per loop
+// turn, so the stage of each plane and its exchange buffer are fixed.
+template <int RTC, int HXC>
+__device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, uint32_t iy, int z0, int z1,
+                                                 unsigned char *ring, uint32_t *exw, uint2 *exs, uint32_t *sh) {
+    static_assert(FS_S == 4, "the plane loop is unrolled by the ring depth");
+    const int tid = threadIdx.x;
+    const int X = (int)V.X, Y = (int)V.Y, Z = (int)V.Z;
+    const int RT = RTC ? RTC : (int)V.fs_rt;
+    const int TYF = RTC ? FS_NT / RTC : (int)V.fs_ty;
+    const int hx = RTC ? HXC : (int)V.fs_hx;
+    const int RC = RT + 2 * hx;   // 16-byte chunks per staged row
+    const int RB = 16 * RC;       // bytes per staged row
+    const int x0 = (int)ix * 8 * RT, y0 = (int)iy * TYF;
+    const int rte = min(RT, (X - x0) >> 3);  // octets of this tile
+    const int q = RTC ? (tid & (RTC - 1)) : tid % RT;
+    const int ty = RTC ? tid / RTC : tid / RT;
+    const bool act = ty < TYF && q < rte;
+    const int tyc = ty < TYF ? ty : 0;       // threads past the tile read a valid row
+    const bool emit_ok = act && y0 + ty < Y;
+    const bool haloL = x0 > 0, haloR = x0 + 8 * rte < X;
+    const bool fixL = act && q == 0 && haloL, fixR = act && q == rte - 1 && haloR;
+    const bool edgeL = q == 0, edgeR = q == rte - 1;
+    const bool chk_top = ty == 0, chk_bot = ty == TYF - 1;
+    // this thread's copy chunks (at most two per plane): staged row r, chunk
+    // cc, as 32-bit voxel offsets from the volume's start at plane 0
+    const int nchunk = (TYF + 4) * RC;
+    uint32_t cdst[2], csrc[2];
+    bool cok[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int c = tid + u * FS_NT;
+        cok[u] = false;
+        cdst[u] = 0;
+        csrc[u] = 0;
+        if (c < nchunk) {
+            const int r = c / RC, cc = c - r * RC;
+            const int x = x0 - 8 * hx + 8 * cc;
+            cok[u] = x >= 0 && x < X;
+            const int yy = min(max(y0 - 2 + r, 0), Y - 1);
+            cdst[u] = (uint32_t)(r * RB + cc * 16);
+            csrc[u] = (uint32_t)yy * (uint32_t)X + (uint32_t)x;
+        }
+    }
+    const uint32_t plane = (uint32_t)X * (uint32_t)Y;  // < 2^32 (X Y Z < 2^32)
+    const int n = z1 - z0 + 4;
+    const uint32_t ring0 = smem_addr(ring);
+    const uint16_t *raw = V.raw;
+    auto issue = [&](int k, uint32_t st) {
+        if (k < n) {
+            const uint32_t zoff = plane * (uint32_t)min(max(z0 - 2 + k, 0), Z - 1);
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (cok[u]) cp_async16(ring0 + st * FS_STAGE + cdst[u], reinterpret_cast<uintptr_t>(raw + (csrc[u] + zoff)));
+        }
+        cp_async_commit();
+    };
+    uint32_t a0[8], a1[8], a2[8], a3[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a0[j] = a1[j] = a2[j] = a3[j] = 0u;
+    uint16_t *osm = V.smooth;
+    const uint32_t orow = (uint32_t)(y0 + tyc) * (uint32_t)X + (uint32_t)(x0 + 8 * q);
+    uint32_t *hc = sh + ((threadIdx.x & 16u) ? (uint32_t)HIST_COPY1 : 0u);
+    const int colo = tyc * RB + (hx + q) * 16;                  // this thread's octet in a staged plane
+    const int fixo = tyc * RB + (fixL ? 12 : (hx + rte) * 16);  // the halo word it y-sums, if any
+    __syncthreads();  // the previous tile's reads of the ring and the exchange buffers are over
+#pragma unroll
+    for (int j = 0; j < FS_S; ++j) issue(j, (uint32_t)j);
+    // y pass of plane k from stage ST on packed pairs: its four words, and
+    // the first and last word to the neighbours through exchange buffer k & 1
+    auto ypass = [&](uint32_t ST, uint32_t *yw, uint32_t &hw) -> bool {
+        const unsigned char *stg = ring + ST * FS_STAGE;
+        uint32_t *exL = exw + (ST & 1u) * 2 * FS_NT, *exR = exL + FS_NT;
+        const unsigned char *cp = stg + colo;
+        const uint4 r0 = *reinterpret_cast<const uint4 *>(cp);
+        const uint4 r1 = *reinterpret_cast<const uint4 *>(cp + RB);
+        const uint4 r2 = *reinterpret_cast<const uint4 *>(cp + 2 * RB);
+        const uint4 r3 = *reinterpret_cast<const uint4 *>(cp + 3 * RB);
+        const uint4 r4 = *reinterpret_cast<const uint4 *>(cp + 4 * RB);
+        yw[0] = fs_ysum(r0.x, r1.x, r2.x, r3.x, r4.x);
+        yw[1] = fs_ysum(r0.y, r1.y, r2.y, r3.y, r4.y);
+        yw[2] = fs_ysum(r0.z, r1.z, r2.z, r3.z, r4.z);
+        yw[3] = fs_ysum(r0.w, r1.w, r2.w, r3.w, r4.w);
+        uint32_t chk = r2.x | r2.y | r2.z | r2.w;
+        if (chk_top) chk |= r0.x | r0.y | r0.z | r0.w | r1.x | r1.y | r1.z | r1.w;
+        if (chk_bot) chk |= r3.x | r3.y | r3.z | r3.w | r4.x | r4.y | r4.z | r4.w;
+        hw = 0u;  // packed y-sum of the halo word (fixL / fixR)
+        if (fixL || fixR) {
+            const unsigned char *hp = stg + fixo;
+            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(hp);
+            const uint32_t w1 = *reinterpret_cast<const uint32_t *>(hp + RB);
+            const uint32_t w2 = *reinterpret_cast<const uint32_t *>(hp + 2 * RB);
+            const uint32_t w3 = *reinterpret_cast<const uint32_t *>(hp + 3 * RB);
+            const uint32_t w4 = *reinterpret_cast<const uint32_t *>(hp + 4 * RB);
+            hw = fs_ysum(w0, w1, w2, w3, w4);
+            chk |= w0 | w1 | w2 | w3 | w4;
+        }
+        exL[tid] = yw[0];
+        exR[tid] = yw[3];
+        return act && (chk & 0xF000F000u) != 0u;
+    };
+    cp_async_wait<FS_S - 1>();
+    __syncthreads();  // plane 0 staged
+    uint32_t yw[4], hw;
+    bool big = ypass(0u, yw, hw);
+    cp_async_wait<FS_S - 2>();
+    bool slow = __syncthreads_or(big);  // plane 1 staged, plane 0's exchange visible
+    // Plane k: its x and z passes (and output plane z0 + k - 4 from k = 4 on)
+    // with the y pass of plane k + 1 between the same two barriers, so that
+    // every warp has shared-memory and arithmetic work at once.
+    auto plane_step = [&](int k, auto stc) {
+        constexpr uint32_t ST = decltype(stc)::value;     // stage of plane k
+        constexpr uint32_t ST1 = (ST + 1u) % FS_S;        // stage of plane k + 1
+        const unsigned char *stg = ring + ST * FS_STAGE;
+        const uint32_t *exL = exw + (ST & 1u) * 2 * FS_NT, *exR = exL + FS_NT;
+        uint32_t v[12];
+        if (!slow) {
+            const uint32_t wl = edgeL ? (haloL ? hw : __byte_perm(yw[0], 0u, 0x1010u)) : exR[tid - 1];
+            const uint32_t wr = edgeR ? (haloR ? hw : __byte_perm(yw[3], 0u, 0x3232u)) : exL[tid + 1];
+            v[0] = wl & 0xFFFFu;
+            v[1] = wl >> 16;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[2 + 2 * i] = yw[i] & 0xFFFFu;
+                v[3 + 2 * i] = yw[i] >> 16;
+            }
+            v[10] = wr & 0xFFFFu;
+            v[11] = wr >> 16;
+        } else {
+            // some raw value of plane k is >= 4096: its y pass again, in
+            // 32-bit lanes (stage ST is refilled only after this)
+            const unsigned char *cp = stg + colo;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const unsigned char *wp = cp + 4 * i;
+                fs_ysum32(*reinterpret_cast<const uint32_t *>(wp), *reinterpret_cast<const uint32_t *>(wp + RB),
+                          *reinterpret_cast<const uint32_t *>(wp + 2 * RB),
+                          *reinterpret_cast<const uint32_t *>(wp + 3 * RB),
+                          *reinterpret_cast<const uint32_t *>(wp + 4 * RB), v[2 + 2 * i], v[3 + 2 * i]);
+            }
+            uint32_t hlo = 0u, hhi = 0u;
+            if (fixL || fixR) {
+                const unsigned char *hp = stg + fixo;
+                fs_ysum32(*reinterpret_cast<const uint32_t *>(hp), *reinterpret_cast<const uint32_t *>(hp + RB),
+                          *reinterpret_cast<const uint32_t *>(hp + 2 * RB),
+                          *reinterpret_cast<const uint32_t *>(hp + 3 * RB),
+                          *reinterpret_cast<const uint32_t *>(hp + 4 * RB), hlo, hhi);
+            }
+            exs[tid] = make_uint2(v[2], v[3]);
+            exs[FS_NT + tid] = make_uint2(v[8], v[9]);
+            __syncthreads();
+            if (edgeL) {
+                v[0] = haloL ? hlo : v[2];
+                v[1] = haloL ? hhi : v[2];
+            } else {
+                const uint2 e = exs[FS_NT + tid - 1];
+                v[0] = e.x;
+                v[1] = e.y;
+            }
+            if (edgeR) {
+                v[10] = haloR ? hlo : v[9];
+                v[11] = haloR ? hhi : v[9];
+            } else {
+                const uint2 e = exs[tid + 1];
+                v[10] = e.x;
+                v[11] = e.y;
+            }
+        }
+        // every thread is past its reads of stage ST: refill it
+        issue(k + FS_S, ST);
+        // the next plane's y pass (its data landed before the last barrier)
+        bool bign = false;
+        if (k + 1 < n) bign = ypass(ST1, yw, hw);
+        // x pass, then the z pass in scatter form; a3 starts each output's
+        // sum at 2048 so that s = sum >> 12 rounds half up
+        uint32_t s[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t p = v[j] + v[j + 4] + 4u * (v[j + 1] + v[j + 3]) + 6u * v[j + 2];
+            const uint32_t o = a0[j] + p;
+            a0[j] = a1[j] + 4u * p;
+            a1[j] = a2[j] + 6u * p;
+            a2[j] = a3[j] + 4u * p;
+            a3[j] = p + 2048u;
+            s[j] = o >> 12;
+        }
+        if (k >= 4) {
+            const uint32_t vmax = max(max(max(s[0], s[1]), max(s[2], s[3])), max(max(s[4], s[5]), max(s[6], s[7])));
+            const bool fast = __all_sync(FULL, !emit_ok || vmax < (uint32_t)HIST_LOW);
+            if (emit_ok) {
+                *reinterpret_cast<uint4 *>(osm + (orow + plane * (uint32_t)(z0 + k - 4))) =
+                    make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
+                if (fast) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) atomicAdd(hc + s[j], 1u);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t u = min(s[j], 65535u);  // (always true for exact sums)
+                        if (u < (uint32_t)HIST_LOW) {
+                            atomicAdd(hc + u, 1u);
+                        } else {
+                            const uint32_t w = HIST_PAIRS + ((u - HIST_LOW) >> 1);
+                            const uint32_t sft = (u & 1u) << 4;
+                            const uint32_t old = atomicAdd(sh + w, 1u << sft);
+                            if (((old >> sft) & 0xFFFFu) == 0x7FFFu) {
+                                atomicSub(sh + w, 0x8000u << sft);
+                                atomicAdd(V.hist + u, 0x8000u);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        cp_async_wait<FS_S - 2>();  // own copies of plane k + 2 have landed
+        slow = __syncthreads_or(bign);
+    };
+    for (int k = 0; k < n; k += FS_S) {
+        plane_step(k, std::integral_constant<uint32_t, 0>());
+        if (k + 1 < n) plane_step(k + 1, std::integral_constant<uint32_t, 1>());
+        if (k + 2 < n) plane_step(k + 2, std::integral_constant<uint32_t, 2>());
+        if (k + 3 < n) plane_step(k + 3, std::integral_constant<uint32_t, 3>());
+    }
+    cp_async_wait<0>();
+}
+
+__global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__restrict__ h) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    uint32_t *sh = reinterpret_cast<uint32_t *>(dsm);
+    unsigned char *ring = dsm + 4 * HIST_WORDS;
+    uint32_t *exw = reinterpret_cast<uint32_t *>(ring + FS_S * FS_STAGE);  // [2 planes][L, R][FS_NT]
+    uint2 *exs = reinterpret_cast<uint2 *>(exw + 4 * FS_NT);              // [L, R][FS_NT]
+    const uint32_t nt = h->fs_tiles, G = gridDim.x;
+    const uint32_t tb = (uint32_t)(((uint64_t)nt * blockIdx.x) / G);
+    const uint32_t te = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / G);
+    if (tb >= te) return;
+    for (int i = threadIdx.x; i < HIST_WORDS / 4; i += FS_NT)
+        reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    uint32_t v = find_vol_fs(h, tb);
+    uint32_t ndone = 0;
+    for (uint32_t t = tb; t < te; ++t) {
+        while (v + 1 < h->nvol && t >= h->vol[v + 1].fs_base) {
+            const VolDev &P = h->vol[v];
+            flush_hist<FS_NT>(h, v, ndone, sh, P.fs_ntx * P.fs_nty * P.fs_ntz);
+            ndone = 0;
+            ++v;
+        }
+        const VolDev &V = h->vol[v];
+        const uint32_t tl = t - V.fs_base;
+        const uint32_t iy = tl % V.fs_nty, rest = tl / V.fs_nty;
+        const uint32_t ix = rest % V.fs_ntx, iz = rest / V.fs_ntx;
+        const int z0 = (int)(iz * V.fs_tz);
+        const int z1 = min(z0 + (int)V.fs_tz, (int)V.Z);
+        if (V.fs_rt == (uint32_t)FS_RT) {
+            if (V.fs_hx) smooth_rows_tile<FS_RT, 1>(V, ix, iy, z0, z1, ring, exw, exs, sh);
+            else smooth_rows_tile<FS_RT, 0>(V, ix, iy, z0, z1, ring, exw, exs, sh);
+        } else {
+            smooth_rows_tile<0, 0>(V, ix, iy, z0, z1, ring, exw, exs, sh);
+        }
+        ++ndone;
+    }
+    const VolDev &P = h->vol[v];
+    flush_hist<FS_NT>(h, v, ndone, sh, P.fs_ntx * P.fs_nty * P.fs_ntz);
 }
 
 // Foreground bits of 8 consecutive smoothed voxels (a 16-byte load, two per
@@ -3143,6 +3468,8 @@ cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStre
         ++k;
     };
     rec();
+    k_smooth_rows<<<p.grid_hist, FS_NT, FS_SMEM, s>>>(d);
+    rec();
     k_smooth_hist<TY><<<p.grid_hist, Tile<TY>::NT, hist_smem_bytes(TY), s>>>(d);
     return cudaGetLastError();
 }
@@ -3170,6 +3497,8 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     SEG_CFG(32)
     SEG_CFG(64)
 #undef SEG_CFG
+    e = cudaFuncSetAttribute(k_smooth_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS_SMEM);
+    if (e != cudaSuccess) return e;
     auto resident = [&](const void *fn, int threads, int *grid) -> cudaError_t {
         int per_sm = 0;
         const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
@@ -3228,6 +3557,7 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
 
 cudaError_t launch_tile_probe(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
     k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
+    k_smooth_rows<<<p.grid_hist, FS_NT, FS_SMEM, s>>>(d);
     switch (p.tile_y) {
         case 16: k_smooth_hist<16><<<p.grid_hist, Tile<16>::NT, hist_smem_bytes(16), s>>>(d); break;
         case 32: k_smooth_hist<32><<<p.grid_hist, Tile<32>::NT, hist_smem_bytes(32), s>>>(d); break;
@@ -3422,7 +3752,7 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist_noalloc(const __grid_
         smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
         ++ndone;
     }
-    flush_hist<T::NT>(h, 0, ndone, sh);
+    flush_hist<T::NT>(h, 0, ndone, sh, V.ntx * V.nty * V.ntz);
 }
 
 // Once per device, with that device current: resolve the scratch address and

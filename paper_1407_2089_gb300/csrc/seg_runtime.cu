@@ -120,6 +120,7 @@ struct Request {
     size_t off_labels = 0, off_feat = 0, off_stat = 0, off_input = 0;
     std::vector<size_t> off_dist;         // per channel; SIZE_MAX = no distance map
     std::vector<size_t> off_den;          // per channel; SIZE_MAX = no denoise (front end: 1 image, MRF: 2)
+    size_t off_smooth = SIZE_MAX;         // smoothed images of all channels (SEG_KEEP_SMOOTHED)
     std::vector<uint32_t> mrf_steps, mrf_sel;
     size_t per_labels = 0, per_feat = 0;  // bytes per channel
     bool owns_input = false;
@@ -145,6 +146,10 @@ struct Request {
         return off_den[c] == SIZE_MAX ? nullptr
                                       : reinterpret_cast<uint16_t *>(block + off_den[c]) + (size_t)k * g[c].n;
     }
+    uint16_t *smoothed(uint32_t c) const {
+        return off_smooth == SIZE_MAX ? nullptr
+                                      : reinterpret_cast<uint16_t *>(block + off_smooth) + (size_t)c * g[0].n;
+    }
     uint32_t *dist(uint32_t c) const {
         return off_dist[c] == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(block + off_dist[c]);
     }
@@ -164,6 +169,7 @@ struct Slot {
     uint32_t *d_stat = nullptr;
     std::map<uint64_t, cudaGraphExec_t> graph;  // by graph_key of the launch plan
     cudaEvent_t ev[NUM_KERNELS + 1] = {};
+    cudaEvent_t end_ev = nullptr;  // recorded after the slot's last batch
     Batch *busy = nullptr;
 };
 
@@ -196,6 +202,10 @@ struct seg_ctx {
     uint32_t cap_vols = 512;
     bool plain = false, graphs = true, profile = false;
     bool tuned = false;  // tile shape fixed (forced, or tuned on the first batch)
+    // end of the most recently launched batch: the next batch, on whichever
+    // slot, starts on the device after it, so batches never share the GPU
+    // while the host prepares the next one during the current one
+    cudaEvent_t prev_end = nullptr;
     cudaStream_t copy_stream = nullptr;
     cudaStream_t read_stream = nullptr;
     uint32_t *read_pin = nullptr;  // pinned words for small results of the read calls (one reader at a time)
@@ -245,8 +255,9 @@ void CUDART_CB on_batch_done(void *p) {
     ctx->cv.notify_all();
 }
 
-// Lays out a request's device block: labels, features, status, [input].
-void layout_request(Request &r) {
+// Lays out a request's device block: labels, features, status, [distance
+// maps], [denoised images], [smoothed images], [input].
+void layout_request(Request &r, bool keep_smoothed) {
     const VolGeom &g = r.g[0];
     r.per_labels = al(4ull * g.n);
     r.per_feat = al(sizeof(seg_cell_features) * g.k_cap);
@@ -270,6 +281,11 @@ void layout_request(Request &r) {
             r.off_den[c] = off;
             off += al(2ull * g.n * (r.g[c].mrf_max ? 2 : 1));
         }
+    r.off_smooth = SIZE_MAX;
+    if (keep_smoothed) {
+        r.off_smooth = off;
+        off += al(2ull * g.n * r.C);
+    }
     r.off_input = off;
     if (r.owns_input) off += al(2ull * g.n * r.C);
     r.block_bytes = off;
@@ -282,6 +298,16 @@ void layout_request(Request &r) {
 // z-chunk for a batch: the tuned one, halved (down to 8 planes) while the
 // batch would have fewer than two smoothing tiles per multiprocessor, so that
 // small batches still spread over the whole GPU.  A forced shape is kept.
+// Row-aligned volumes (X % 8 == 0, 16-byte aligned first input of the
+// smoothing) take k_smooth_rows; the others k_smooth_hist.
+bool rows_aligned(const VolGeom &g, const void *smooth_in) {
+    return g.X % 8u == 0u && (reinterpret_cast<uintptr_t>(smooth_in) & 15u) == 0u;
+}
+
+const void *smooth_input(const Request *r, uint32_t c) {
+    return r->g[c].dn_r ? static_cast<const void *>(r->den(c)) : static_cast<const void *>(r->input(c));
+}
+
 uint32_t batch_tile_z(const seg_ctx *ctx, const Batch &b) {
     const uint32_t ty = (uint32_t)ctx->plan.tile_y;
     uint32_t tz = ctx->tile_z;
@@ -291,6 +317,7 @@ uint32_t batch_tile_z(const seg_ctx *ctx, const Batch &b) {
         for (const Request *r : b.reqs)
             for (uint32_t c = 0; c < r->C; ++c) {
                 const VolGeom &g = r->g[c];
+                if (rows_aligned(g, smooth_input(r, c))) continue;
                 tiles += cdiv(g.X, TILE_X) * cdiv(g.Y, ty) * cdiv(g.Z, tz);
             }
         if (tz <= 8 || tiles >= 2ull * (uint64_t)ctx->sms) return tz;
@@ -298,9 +325,28 @@ uint32_t batch_tile_z(const seg_ctx *ctx, const Batch &b) {
     }
 }
 
+// Planes per k_smooth_rows tile for a batch: as deep as 256 planes, halved
+// (down to 8) while the batch has fewer than three tiles per multiprocessor.
+uint32_t batch_rows_tile_z(const seg_ctx *ctx, const Batch &b) {
+    uint32_t tz = 256;
+    for (;;) {
+        uint64_t tiles = 0;
+        for (const Request *r : b.reqs)
+            for (uint32_t c = 0; c < r->C; ++c) {
+                const VolGeom &g = r->g[c];
+                if (!rows_aligned(g, smooth_input(r, c))) continue;
+                const uint32_t rt = fs_rows_rt(g.X);
+                tiles += cdiv(g.X, 8ull * rt) * cdiv(g.Y, FS_NT / rt) * cdiv(g.Z, tz);
+            }
+        if (tz <= 8 || tiles >= 3ull * (uint64_t)ctx->sms) return tz;
+        tz /= 2;
+    }
+}
+
 void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
-    const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b);
+    const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b), fz = batch_rows_tile_z(ctx, b);
+    uint32_t fst = 0;
     uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0, cl = 0;
     uint32_t dtb[DT_NK] = {0, 0, 0, 0, 0, 0};
     uint32_t mrft = 0, mrfc = 0, mrf_iters = 0;
@@ -398,6 +444,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
             }
             V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
             V.smooth = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
+            if (r->smoothed(c)) V.smooth = r->smoothed(c);
             V.mask = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows * g.W);
             V.rowoff = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * (g.rows + 1));
             V.rowk = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows);
@@ -412,9 +459,24 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.rows = g.rows;
             V.min_volume = r->minvol[c];
             V.union_limit = (ctx->cfg.flags & SEG_TEST_UNION_FAIL) ? 0u : UNION_LIMIT;
-            V.ntx = (uint32_t)cdiv(g.X, TILE_X);
-            V.nty = (uint32_t)cdiv(g.Y, ty);
-            V.ntz = (uint32_t)cdiv(g.Z, tz);
+            if (rows_aligned(g, V.raw)) {
+                V.ntx = V.nty = V.ntz = 0;
+                V.fs_rt = fs_rows_rt(g.X);
+                V.fs_ty = (uint32_t)FS_NT / V.fs_rt;
+                V.fs_hx = g.X > 8u * FS_RT ? 1u : 0u;
+                V.fs_tz = fz;
+                V.fs_ntx = (uint32_t)cdiv(g.X, 8ull * V.fs_rt);
+                V.fs_nty = (uint32_t)cdiv(g.Y, V.fs_ty);
+                V.fs_ntz = (uint32_t)cdiv(g.Z, fz);
+            } else {
+                V.ntx = (uint32_t)cdiv(g.X, TILE_X);
+                V.nty = (uint32_t)cdiv(g.Y, ty);
+                V.ntz = (uint32_t)cdiv(g.Z, tz);
+                V.fs_rt = V.fs_ty = V.fs_hx = V.fs_tz = 0;
+                V.fs_ntx = V.fs_nty = V.fs_ntz = 0;
+            }
+            V.fs_base = fst;
+            fst += V.fs_ntx * V.fs_nty * V.fs_ntz;
             V.nrt = g.nrt;
             V.tile_base = tiles;
             V.rt_base = rts;
@@ -439,6 +501,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     }
     h->nvol = v;
     h->ntiles = tiles;
+    h->fs_tiles = fst;
     h->nrowtiles = rts;
     h->nbricks = bks;
     h->nbtasks = bts;
@@ -516,6 +579,7 @@ int tune_tiles(seg_ctx *ctx, Batch &b) {
 
 int launch_batch(seg_ctx *ctx, Batch &b) {
     Slot &s = *b.slot;
+    if (ctx->prev_end) CK(cudaStreamWaitEvent(s.stream, ctx->prev_end, 0));
     // Inputs that waited on the host are copied now (pageable source: the
     // call returns once the data is staged).
     for (Request *r : b.reqs) {
@@ -566,6 +630,8 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
         if (rc != SEG_OK) return rc;
     }
     for (Request *r : b.reqs) CK(cudaEventRecord(r->done_ev, s.stream));
+    CK(cudaEventRecord(s.end_ev, s.stream));
+    ctx->prev_end = s.end_ev;
     CK(cudaFreeAsync(b.scratch, s.stream));
     b.scratch = nullptr;
     CK(cudaLaunchHostFunc(s.stream, on_batch_done, &b));
@@ -804,6 +870,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
         CK(cudaMalloc(reinterpret_cast<void **>(&s.d_stat), 4ull * ST_WORDS * ctx->cap_vols));
         std::memset(s.h_hdr, 0, batch_bytes(ctx->cap_vols));
         for (auto &e : s.ev) CK(cudaEventCreate(&e));
+        CK(cudaEventCreateWithFlags(&s.end_ev, cudaEventDisableTiming));
     }
     ctx->worker = std::thread(worker_main, ctx.get());
     *out = ctx.release();
@@ -830,6 +897,7 @@ int seg_destroy(seg_ctx *ctx) {
             if (g.second) cudaGraphExecDestroy(g.second);
         for (auto &e : s.ev)
             if (e) cudaEventDestroy(e);
+        if (s.end_ev) cudaEventDestroy(s.end_ev);
         if (s.h_hdr) cudaFreeHost(s.h_hdr);
         if (s.d_hdr) cudaFree(s.d_hdr);
         if (s.h_stat) cudaFreeHost(s.h_stat);
@@ -894,7 +962,7 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
     r->errbits.assign(channels, 0);
     r->owns_input = host_in;
     if (!host_in) r->user_dev = voxels;
-    layout_request(*r);
+    layout_request(*r, (ctx->cfg.flags & SEG_KEEP_SMOOTHED) != 0);
     if (r->persist + r->scratch > ctx->budget) return SEG_ETOOBIG;
     cudaSetDevice(ctx->device);
     if (cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -1059,6 +1127,28 @@ int seg_read_denoised(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst
                                     ctx->read_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
     return cuda_fail(e, "seg_read_denoised");
+}
+
+int seg_read_smoothed(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst, uint64_t dst_elems,
+                      int dst_on_device) {
+    if (!ctx || !dst) return SEG_EINVAL;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        r = find_req(ctx, req);
+        if (!r) return SEG_ENOENT;
+        if (r->state == SEG_PENDING) return SEG_ENOTREADY;
+        if (r->state == SEG_FAILED) return SEG_EFAILED;
+    }
+    if (channel >= r->C || !r->smoothed(channel)) return SEG_EINVAL;
+    const uint64_t n = r->g[channel].n;
+    if (dst_elems < n) return SEG_ESMALL;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpyAsync(dst, r->smoothed(channel), 2ull * n,
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    ctx->read_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->read_stream);
+    return cuda_fail(e, "seg_read_smoothed");
 }
 
 int seg_read_cell_distance(seg_ctx *ctx, seg_req req, uint32_t cells_channel, uint32_t map_channel, uint32_t *dst,

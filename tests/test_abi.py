@@ -60,7 +60,7 @@ def test_struct_layouts():
     import paper_1407_2089_gb300 as seg
     assert ctypes.sizeof(seg.seg_cell_features) == 64
     assert ctypes.sizeof(seg.seg_dims) == 12
-    assert ctypes.sizeof(seg.seg_config) == 48
+    assert ctypes.sizeof(seg.seg_config) == 56
     assert ctypes.sizeof(seg.seg_channel_params) == 28
     assert ctypes.sizeof(seg.seg_offset) == 12
     assert seg.MONTAGE_EDGE_DTYPE.itemsize == 40
@@ -73,6 +73,6 @@ def test_binding_constants_match_header():
     defs = dict(re.findall(r"#define\s+(SEG_[A-Z_]+)\s+\(?(-?0x[0-9a-fA-F]+|-?[0-9]+)u?\)?", hdr))
     import paper_1407_2089_gb300 as seg
     for name in ("SEG_MAX_KERNELS", "SEG_FORCE_TILE", "SEG_PLAIN", "SEG_NO_GRAPH", "SEG_PROFILE", "SEG_REG_MAX_RXY",
-                 "SEG_REG_MAX_RZ"):
+                 "SEG_REG_MAX_RZ", "SEG_TEST_UNION_FAIL", "SEG_KEEP_SMOOTHED"):
         assert name in defs, name
         assert getattr(seg, name) == int(defs[name], 0), name
