@@ -189,6 +189,66 @@ def cpu_baseline(host, budget_s=12.0):
 _CACHE = {}
 
 
+def _oracle_config_job(args):
+    """Segments one volume-channel of another workload with the oracle:
+    ("uneven", i) is volume i of the batched-uneven workload, ("serving", i, c)
+    channel c of request i of the serving stream.  Volumes are generated in
+    the worker before the clock starts; returns (voxels, seconds, pid)."""
+    import oracle
+    import synth
+    key = args
+    if key not in _CACHE:
+        if args[0] == "uneven":
+            d = synth.batched_uneven_dims()[args[1]]
+            _CACHE[key] = synth.density_volume(d, synth.mix_seed(3, 3, args[1]))
+        else:
+            d = synth.serving_requests(seed=5, n=args[1] + 1)[args[1]][1]
+            _CACHE[key] = synth.serving_volume(d, 5, args[1], args[2])
+    vol = _CACHE.pop(key)
+    t0 = time.perf_counter()
+    oracle.segment(vol, min_volume=30)
+    return vol.size, time.perf_counter() - t0, os.getpid()
+
+
+def cpu_other_configs(n_serving=32):
+    """The CPU oracle on the other workloads, in the same run: the single
+    128x128x32 frame on one core (repeated for about 2 s), and with one
+    process per host core all 48 batched-uneven volumes and the first
+    n_serving requests (both channels) of the serving stream.  A multi-core
+    figure divides the voxels by the makespan (the largest per-process sum
+    of oracle time; generation is excluded)."""
+    import multiprocessing as mp
+    import oracle
+    import synth
+    cores = os.cpu_count() or 1
+    out = {}
+    v1 = synth.single_frame()
+    oracle.segment(v1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 2.0:
+        oracle.segment(v1, min_volume=30)
+        n += 1
+    dt = time.perf_counter() - t0
+    out["single_frame"] = {"value": n * v1.size / dt / 1e9, "unit": "Gvoxels/s", "cores": 1, "kind": "oracle",
+                           "latency_ms": dt / n * 1e3,
+                           "sample": "the 128x128x32 frame segmented %d times, single-threaded" % n}
+    jobs = {"uneven": [("uneven", i) for i in range(48)],
+            "serving": [("serving", i, c) for i in range(n_serving) for c in range(2)]}
+    samples = {"uneven": "all 48 volumes (0.73 G voxels)",
+               "serving": "requests 0-%d of the Poisson stream, both channels" % (n_serving - 1)}
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for name, jl in jobs.items():
+            res = pool.map(_oracle_config_job, jl, chunksize=1)
+            per, vox = {}, 0
+            for v, d, pid in res:
+                per[pid] = per.get(pid, 0.0) + d
+                vox += v
+            span = max(per.values())
+            out[name] = {"value": vox / span / 1e9, "unit": "Gvoxels/s", "cores": cores, "kind": "oracle",
+                         "sample": samples[name] + ", one oracle process per core; makespan %.1f s" % span}
+    return out
+
+
 def _oracle_job(args):
     """Segments one volume-channel with the oracle; returns (voxels, oracle
     seconds, pid).  Volumes are generated once per worker and cached, so the
@@ -261,6 +321,7 @@ def run_gpu(args):
     T, C, Z, Y, X = host.shape
     vox_step = host.size
     cpu = cpu_baseline(host) if (rank == 0 and not args.no_cpu) else None
+    cpu_other = cpu_other_configs() if (rank == 0 and not args.no_cpu) else None
 
     d_in = torch.from_numpy(host.view(np.int16)).to(dev)
     torch.cuda.synchronize()
@@ -362,6 +423,10 @@ def run_gpu(args):
     if not args.no_uneven and rank == 0:
         uneven = uneven_forms(seg, torch, local, max(1, min(args.steps, 5)))
         torch.cuda.empty_cache()
+    mont = None
+    if args.montage and rank == 0:
+        mont = montage_run(seg, torch, local, max(1, min(args.steps, 3)))
+        torch.cuda.empty_cache()
     serve = None
     if args.serving_requests and rank == 0:
         serve = {"batched": serving(seg, torch, local, args.serving_requests, 200.0, 0, 2),
@@ -379,6 +444,10 @@ def run_gpu(args):
                             "labels", queued, args.e2e_ahead)
         e2e["value"] = job_gvox_per_s(vox_step * e2e.pop("steps_timed"), e2e.pop("ms"), ws)
         e2e_dense["value"] = job_gvox_per_s(vox_step * e2e_dense.pop("steps_timed"), e2e_dense.pop("ms"), ws)
+        # the boundary's own result call (seg_read_labels: dense uint32 label
+        # images) beside the run-encoded read of the headline figure
+        e2e["dense_labels"] = {k: e2e_dense[k] for k in ("value", "d2h_bytes_per_step", "step_ms_max")
+                               if k in e2e_dense}
 
     if rank == 0:
         line = {
@@ -400,10 +469,12 @@ def run_gpu(args):
                          "algo_bytes_per_voxel": KERNEL_BYTES_PER_VOXEL[dom]},
             "kernel_share": shares,
             "cpu_baseline": cpu,
+            "cpu_baseline_other_configs": cpu_other,
             "e2e": e2e,
             "e2e_dense_labels": e2e_dense,
             "forms_gvox_s_per_gpu": forms,
             "uneven_batch": uneven,
+            "montage": mont,
             "denoise_front_end": denoise,
             "closing": closing,
             "distance_map": distmap,
@@ -700,6 +771,75 @@ def uneven_forms(seg, torch, local, steps):
     return out
 
 
+def montage_run(seg, torch, local, steps):
+    """The montage workload, 5530 x 5530 x 80 x 2 channels (4.9 G voxels),
+    segmented whole as one request: resident on the device (CUDA events on an
+    ordering stream around submit -> done) and end to end through the C ABI
+    from pinned host memory (input copied inside seg_submit_volume, both
+    label images and cell tables read back to host memory)."""
+    import synth
+    dims = (5530, 5530, 80)
+    t0 = time.perf_counter()
+    host = np.empty((2, dims[2], dims[1], dims[0]), dtype=np.uint16)
+    for c in range(2):
+        host[c] = synth.montage(channel=c)
+    gen_s = time.perf_counter() - t0
+    vox = host.size
+    stream = torch.cuda.Stream()
+    ctx = seg.seg_create(device=local, order_stream=stream.cuda_stream)
+    out = {"dims": list(dims), "channels": 2, "voxels": int(vox), "generation_s": gen_s}
+    try:
+        d_in = torch.from_numpy(host.view(np.int16)).to("cuda:%d" % local)
+
+        def dev_step():
+            r = seg.seg_submit_volume(ctx, d_in, dims=dims, channels=2)
+            seg.seg_flush(ctx)
+            seg.seg_enqueue_wait(ctx, r, stream.cuda_stream)
+            return r
+
+        def finish(r):
+            if seg.seg_wait(ctx, r) != seg.SEG_DONE:
+                raise RuntimeError("request failed")
+            seg.seg_release(ctx, r)
+
+        finish(dev_step())
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            finish(dev_step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        del d_in
+        torch.cuda.empty_cache()
+        peak, _ = peaks()
+        out["device"] = {"ms": ms, "gvox_s": vox / (ms / 1e3) / 1e9,
+                         "hbm_fraction": vox * ALGO_BYTES_PER_VOXEL / (ms / 1e3) / 1e9 / peak}
+        pin = torch.from_numpy(host.view(np.int16)).pin_memory()
+        labs = [torch.empty(host[0].size, dtype=torch.int32).pin_memory() for _ in range(2)]
+        walls = []
+        for i in range(steps + 1):
+            t0 = time.perf_counter()
+            r = seg.seg_submit_volume(ctx, pin, dims=dims, channels=2)
+            seg.seg_flush(ctx)
+            if seg.seg_wait(ctx, r) != seg.SEG_DONE:
+                raise RuntimeError("request failed")
+            for c in range(2):
+                seg.seg_read_labels(ctx, r, c, labs[c])
+                seg.seg_read_features(ctx, r, c)
+            seg.seg_release(ctx, r)
+            if i:
+                walls.append(time.perf_counter() - t0)
+        w = statistics.median(walls)
+        out["e2e"] = {"ms": w * 1e3, "gvox_s": vox / w / 1e9, "h2d_bytes": int(host.nbytes),
+                      "d2h_bytes": int(4 * vox), "read": "dense labels + cells, both channels"}
+    finally:
+        seg.seg_destroy(ctx)
+    return out
+
+
 def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
     """Open-loop Poisson request stream (2-channel volumes, sizes log-uniform
     from 128^3 to 2048x2048x64) through the C ABI from pinned host memory.
@@ -929,7 +1069,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-uneven", action="store_true", help="skip the 48 uneven volumes and the single frame")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain per-frame comparison")
-    ap.add_argument("--serving-requests", type=int, default=400,
+    ap.add_argument("--montage", type=int, default=1, help="1: segment the 5530x5530x80x2 montage as well")
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="Poisson requests (200/s) for the served latency; 0 skips serving")
     args = ap.parse_args()
     if args.warmup < 3:

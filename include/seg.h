@@ -27,7 +27,8 @@
  *
  * Layout: a volume is uint16 [C][Z][Y][X] (channels planar, x fastest);
  * linear index i = x + X*(y + Y*z).  Labels are uint32 [Z][Y][X] per channel,
- * 0 = background, 1..K = cells.  Limits: X*Y*Z < 2^32, X <= 65536.
+ * 0 = background, 1..K = cells.  Limits: X*Y*Z < 2^32, X <= 65536, Y and Z
+ * <= SEG_MAX_YZ.
  *
  * Threading: one thread may submit while another polls and reads; calls on
  * one context are otherwise serialised by the caller.  No call throws; every
@@ -54,6 +55,10 @@ extern "C" {
 #define SEG_ESMALL (-7)    /* destination too small (n_cells is still reported)     */
 #define SEG_ENOENT (-8)    /* unknown or released request handle                    */
 #define SEG_EFAILED (-9)   /* the request FAILED (device error flag or CUDA error)  */
+
+/* Largest Y and Z of a volume (row and plane indices stay int-sized with
+ * their halos); larger extents give SEG_ETOOBIG. */
+#define SEG_MAX_YZ 2147483583u
 
 /* ---- request states (seg_poll) ------------------------------------------ */
 #define SEG_PENDING 0
@@ -165,7 +170,7 @@ int seg_destroy(seg_ctx *ctx);
 
 /* Submits one volume of `channels` planar channels, each [Z][Y][X] uint16.
  *   voxels     host pointer (on_device = 0 or 2) or device pointer
- *              (on_device = 1).  With 0 the input is copied before the call
+ *              (on_device = 1, 2-byte aligned, else SEG_EINVAL).  With 0 the input is copied before the call
  *              returns (the caller may free or reuse it).  With 2 the copy is
  *              only queued (pinned memory: it runs while the call returns and
  *              the batch waits for it on the device), so the host input, like
@@ -294,8 +299,9 @@ int seg_reset_stats(seg_ctx *ctx);
  * loops where cudaMalloc/cudaFree and their implicit synchronisation are not
  * acceptable.  It needs no seg_ctx and calls no allocating routine.
  *
- *   d_voxels  device pointer, uint16 [Z][Y][X] of the current device.
- *   d_result  device pointer to 2 uint32: [0] = Otsu level t* of the
+ *   d_voxels  device pointer, uint16 [Z][Y][X] of the current device,
+ *             2-byte aligned (else SEG_EINVAL).
+ *   d_result  device pointer (4-byte aligned) to 2 uint32: [0] = Otsu level t* of the
  *             smoothed volume (the value seg_read_features reports for the
  *             same input), [1] = error bits (0 = ok).
  *   stream    cudaStream_t on the current device (NULL = legacy default).
@@ -309,8 +315,10 @@ int seg_reset_stats(seg_ctx *ctx);
  * and must be serialised by the caller.  The first call on a device (with
  * that device current) resolves the array's device address and sets kernel
  * attributes; make that first call before any stream capture.
- * Limits: X*Y*Z <= SEG_NOALLOC_MAX_VOXELS (the bins count in uint32) and
- * X <= 65536, else SEG_ETOOBIG.  Other errors: SEG_EINVAL, SEG_ECUDA. */
+ * Limits: X*Y*Z <= SEG_NOALLOC_MAX_VOXELS (the bins count in uint32),
+ * X <= 65536 and Y, Z <= SEG_MAX_YZ, else SEG_ETOOBIG; these and the
+ * argument checks are made before any CUDA call.  Other errors: SEG_EINVAL,
+ * SEG_ECUDA. */
 #define SEG_NOALLOC_MAX_VOXELS 4294967295ull
 int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dims, uint32_t *d_result,
                                void *stream);

@@ -26,6 +26,7 @@ SEG_ECUDA = -6
 SEG_ESMALL = -7
 SEG_ENOENT = -8
 SEG_EFAILED = -9
+SEG_MAX_YZ = 2147483583
 
 SEG_PENDING = 0
 SEG_DONE = 1

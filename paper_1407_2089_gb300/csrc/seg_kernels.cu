@@ -3787,8 +3787,12 @@ extern "C" int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dim
                                           void *stream) {
     using namespace seg;
     if (!d_voxels || !d_result || dims.x == 0 || dims.y == 0 || dims.z == 0) return SEG_EINVAL;
+    // uint16 voxels and uint32 results must be naturally aligned
+    if ((reinterpret_cast<uintptr_t>(d_voxels) & 1u) || (reinterpret_cast<uintptr_t>(d_result) & 3u))
+        return SEG_EINVAL;
     const uint64_t n = (uint64_t)dims.x * dims.y * dims.z;
-    if (n > SEG_NOALLOC_MAX_VOXELS || dims.x > 65536u) return SEG_ETOOBIG;
+    if (n > SEG_NOALLOC_MAX_VOXELS || dims.x > 65536u || dims.y > SEG_MAX_YZ || dims.z > SEG_MAX_YZ)
+        return SEG_ETOOBIG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
     uint32_t *scratch = nullptr;
@@ -3803,9 +3807,9 @@ extern "C" int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dim
     V.hist = scratch;
     V.stat = scratch + HIST_BINS;
     V.X = dims.x; V.Y = dims.y; V.Z = dims.z;
-    V.ntx = (dims.x + TILE_X - 1) / TILE_X;
-    V.nty = (dims.y + NOALLOC_TY - 1) / NOALLOC_TY;
-    V.ntz = (dims.z + NOALLOC_TZ - 1) / NOALLOC_TZ;
+    V.ntx = (uint32_t)(((uint64_t)dims.x + TILE_X - 1) / TILE_X);
+    V.nty = (uint32_t)(((uint64_t)dims.y + NOALLOC_TY - 1) / NOALLOC_TY);
+    V.ntz = (uint32_t)(((uint64_t)dims.z + NOALLOC_TZ - 1) / NOALLOC_TZ);
     hdr.nvol = 1;
     hdr.ntiles = V.ntx * V.nty * V.ntz;
     hdr.tile_z = NOALLOC_TZ;

@@ -921,7 +921,11 @@ int seg_submit_volume(seg_ctx *ctx, const uint16_t *voxels, int on_device, seg_d
     // the request is done)
     const bool host_in = on_device != 1;
     const uint64_t n = (uint64_t)dims.x * dims.y * dims.z;
-    if (n >= (1ull << 32) || dims.x > 65536u) return SEG_ETOOBIG;
+    // the kernels index rows and planes with int arithmetic (tile origins
+    // plus halos): Y and Z stay below INT_MAX - 64
+    if (n >= (1ull << 32) || dims.x > 65536u || dims.y > SEG_MAX_YZ || dims.z > SEG_MAX_YZ) return SEG_ETOOBIG;
+    // uint16 voxels: a device input must be 2-byte aligned
+    if (!host_in && (reinterpret_cast<uintptr_t>(voxels) & 1u)) return SEG_EINVAL;
     if (channels > ctx->cap_vols) return SEG_ETOOBIG;
     std::unique_ptr<Request> r(new Request());
     r->dims = dims;

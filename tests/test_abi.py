@@ -73,6 +73,23 @@ def test_binding_constants_match_header():
     defs = dict(re.findall(r"#define\s+(SEG_[A-Z_]+)\s+\(?(-?0x[0-9a-fA-F]+|-?[0-9]+)u?\)?", hdr))
     import paper_1407_2089_gb300 as seg
     for name in ("SEG_MAX_KERNELS", "SEG_FORCE_TILE", "SEG_PLAIN", "SEG_NO_GRAPH", "SEG_PROFILE", "SEG_REG_MAX_RXY",
-                 "SEG_REG_MAX_RZ", "SEG_TEST_UNION_FAIL", "SEG_KEEP_SMOOTHED"):
+                 "SEG_REG_MAX_RZ", "SEG_TEST_UNION_FAIL", "SEG_KEEP_SMOOTHED", "SEG_MAX_YZ"):
         assert name in defs, name
         assert getattr(seg, name) == int(defs[name], 0), name
+
+
+def test_noalloc_argument_checks_without_cuda(lib):
+    # the allocation-free entry point validates its arguments before any CUDA
+    # call, so these return at once on a machine without a GPU
+    import paper_1407_2089_gb300 as seg
+    f = lib.seg_otsu_threshold_noalloc
+    f.argtypes = [ctypes.c_void_p, seg.seg_dims, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    aligned, res = 1 << 20, 1 << 21
+    assert f(None, seg.seg_dims(4, 4, 4), res, None) == seg.SEG_EINVAL
+    assert f(aligned, seg.seg_dims(4, 0, 4), res, None) == seg.SEG_EINVAL
+    assert f(aligned + 1, seg.seg_dims(4, 4, 4), res, None) == seg.SEG_EINVAL   # odd uint16 address
+    assert f(aligned, seg.seg_dims(4, 4, 4), res + 2, None) == seg.SEG_EINVAL   # unaligned uint32 result
+    for dims in [(1, 2 ** 31 + 5, 1), (1, 2 ** 32 - 1, 1), (1, 1, 2 ** 31 + 5), (1, seg.SEG_MAX_YZ + 1, 1),
+                 (65537, 1, 1), (65536, 65536, 1)]:
+        assert f(aligned, seg.seg_dims(*dims), res, None) == seg.SEG_ETOOBIG, dims

@@ -34,6 +34,16 @@ def test_argument_checks(seg):
         assert code_of(seg, seg.seg_submit_volume, ctx, v, dims=(4, 4, 4), channels=0) == seg.SEG_EINVAL
         assert code_of(seg, seg.seg_submit_volume, ctx, v, dims=(65537, 1, 1), channels=1) == seg.SEG_ETOOBIG
         assert code_of(seg, seg.seg_submit_volume, ctx, v, dims=(65536, 65536, 1), channels=1) == seg.SEG_ETOOBIG
+        for big in [(1, 2 ** 31 + 5, 1), (1, 2 ** 32 - 1, 1), (1, 1, 2 ** 31 + 5)]:
+            assert code_of(seg, seg.seg_submit_volume, ctx, v, dims=big, channels=1) == seg.SEG_ETOOBIG, big
+        # a device input at an odd address is rejected before it is read
+        import ctypes
+        import torch
+        t = torch.zeros(64, dtype=torch.int16, device="cuda")
+        out = ctypes.c_uint64()
+        rc = seg._lib.seg_submit_volume(ctx, ctypes.c_void_p(t.data_ptr() + 1), 1, seg.seg_dims(4, 4, 2), 1, None,
+                                        ctypes.byref(out))
+        assert rc == seg.SEG_EINVAL
         assert code_of(seg, seg.seg_release, ctx, 123456) == seg.SEG_ENOENT
         assert code_of(seg, seg.seg_read_features, ctx, 123456, 0) == seg.SEG_ENOENT
         assert code_of(seg, seg.seg_create, device=10 ** 6) == seg.SEG_EINVAL

@@ -23,9 +23,12 @@ def test_noalloc_matches_regular_path_twice():
     import paper_1407_2089_gb300 as seg
 
     assert torch.cuda.is_available()
+    # the third volume has ragged rows (X % 8 != 0) and small odd Y and Z, so
+    # the edge-clamped loads of the smoothing run through this entry point too
     vols = [synth.single_frame(),
             synth.nuclei_volume((200, 150, 45), 77, 60, peak=3000.0, noise_mean=500.0,
-                                noise_sigma=25.0)[0]]
+                                noise_sigma=25.0)[0],
+            synth.nuclei_volume((37, 23, 5), 78, 2, r_lo=2.0, r_hi=3.0, peak=2000.0)[0]]
     ctx = seg.seg_create(device=0)
     try:
         expected = []
@@ -34,7 +37,7 @@ def test_noalloc_matches_regular_path_twice():
             expected.append(thr)
     finally:
         seg.seg_destroy(ctx)
-    assert expected[0] != expected[1]
+    assert len(set(expected)) == len(expected)
 
     stream = torch.cuda.current_stream()
     dev_vols = [torch.from_numpy(v.view(np.int16).copy()).cuda() for v in vols]
@@ -45,8 +48,8 @@ def test_noalloc_matches_regular_path_twice():
         seg.seg_otsu_threshold_noalloc(d.data_ptr(), (X, Y, Z), r.data_ptr(), stream.cuda_stream)
     torch.cuda.synchronize()
     got = [tuple(int(x) for x in r.cpu()) for r in results]
-    assert got[0] == (expected[0], 0)
-    assert got[1] == (expected[1], 0)
+    for g, e in zip(got, expected):
+        assert g == (e, 0)
 
 
 def test_noalloc_rejects_bad_arguments():
@@ -57,3 +60,10 @@ def test_noalloc_rejects_bad_arguments():
     with pytest.raises(seg.SegError) as e:
         seg.seg_otsu_threshold_noalloc(16, (65536, 65536, 1), 16)
     assert e.value.code == seg.SEG_ETOOBIG
+    for dims in [(1, 2 ** 31 + 5, 1), (1, 2 ** 32 - 1, 1)]:
+        with pytest.raises(seg.SegError) as e:
+            seg.seg_otsu_threshold_noalloc(16, dims, 16)
+        assert e.value.code == seg.SEG_ETOOBIG
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_otsu_threshold_noalloc(17, (4, 4, 4), 16)
+    assert e.value.code == seg.SEG_EINVAL
