@@ -1049,8 +1049,7 @@ def main():
                     help="e2e submits queue their input copies, or wait for each")
     ap.add_argument("--e2e-ahead", type=int, default=12, help="queued copies: frames submitted beyond the last read")
     ap.add_argument("--inflight", type=int, default=1,
-                    help="batch slots; batches run one after another on the device either way, so with 2 "
-                         "the host prepares the next batch while one runs")
+                    help="batches in flight; 1 keeps per-kernel CUDA-event times free of overlap")
     ap.add_argument("--frames", type=int, default=FRAMES,
                     help="time-lapse frames per step (fewer frames: a small case for profiling)")
     ap.add_argument("--tile", default="", help="force the tile height and z-chunk, e.g. 32,64")

@@ -764,32 +764,43 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist(const BatchHdr *__res
 // ----------------------------------------------------------------------------
 //
 // The same arithmetic as smooth_tile (binomial [1 4 6 4 1] per axis, exact
-// uint32 sums, one rounding (S + 2048) >> 12, replicate edges), ordered so
-// that the block moves fewer bytes through shared memory:
-//   y pass first, on the raw voxels as staged: a thread reads its octet of
-//     the five rows around its own (five 16-byte loads) and sums the packed
+// uint32 sums, one rounding (S + 2048) >> 12, replicate edges), arranged so
+// that every warp works on its own:
+//   y pass first, on the raw voxels as staged: a lane reads its octet of the
+//     five rows around its own (five 16-byte loads) and sums the packed
 //     16-bit pairs of each word at once; when every raw value is below 4096
 //     no lane of a word can exceed 16 * 4095 = 65520, so the packed sum is
-//     exact.  Each staged row is checked by the thread whose centre row it
-//     is (and the edge rows by the tile's first and last row of threads); if
-//     any value of a plane is 4096 or more, the whole block recomputes that
-//     plane's y pass in 32-bit lanes.
-//   x pass in registers: the two y-sums left and right of a thread's octet
-//     come from its neighbours through a small exchange buffer (one word each
-//     way), from the edge voxel at the volume's x-edges, or from a halo chunk
-//     that the tile's first / last thread of a row y-sums itself.
+//     exact.  Each lane checks the words it reads; a warp in which one of
+//     them is 4096 or more redoes that plane's y pass in 32-bit lanes.
+//   x pass in registers: the y-sums left and right of a lane's octet come
+//     from the neighbouring lanes by shuffles; a lane at the end of a warp
+//     y-sums the neighbouring word itself from the staged plane (also the
+//     halo chunks of x-tiled rows), and at the volume's x-edges the edge
+//     voxel is repeated.
 //   z pass in registers (scatter form, four running sums per output), with
 //     the rounding constant carried in the newest running sum.
 // A tile is FS_RT octets (512 voxels) wide, or the whole row when X <= 512,
 // and FS_NT / octets-per-row rows high; it marches down z through a ring of
-// staged planes (16-byte cp.async copies, FS_S planes in flight).  The last
-// tile's threads beyond the row or the volume compute but do not emit.
-// Consecutive tiles of a block are y-neighbours, so the four rows that two
-// of them share are fetched again while still in L2.
+// FS_S staged planes filled with 16-byte cp.async copies by all threads.
+// The ring is driven by mbarriers instead of block barriers: a stage's
+// "full" barrier completes when every thread's copies of its plane have
+// landed (cp.async.mbarrier.arrive), its "empty" barrier when every warp has
+// read it, and a thread refills a stage only after the plane two behind its
+// own is empty (five stages, three planes staged ahead), so warps drift up
+// to two planes apart.  Every wait is bounded:
+// a wait that runs out raises ERR_TIMEOUT for the volume and puts the block
+// in a mode that skips the remaining work but still reaches every block
+// barrier.  Consecutive tiles of a block are y-neighbours, so the rows two of
+// them share are fetched again while still in L2.
 
-constexpr int FS_S = 4;                  // ring stages
+constexpr int FS_S = 5;                  // ring stages
+constexpr int FS_LEAD = 3;               // planes staged ahead of the one being read
+// a thread refills the stage of plane k - (FS_S - FS_LEAD) while reading
+// plane k: warps may drift FS_S - FS_LEAD planes apart
 constexpr int FS_STAGE = 12 * 66 * 16;   // bytes per stage: 12 rows x 66 chunks (x-tiled) bound all shapes
-constexpr size_t FS_SMEM = 4ull * HIST_WORDS + (size_t)FS_S * FS_STAGE + 4ull * 4 * FS_NT + 8ull * 2 * FS_NT;
+constexpr int FS_WARPS = FS_NT / 32;
+constexpr uint32_t FS_WAIT_LIMIT = 1u << 20;  // mbarrier polls before a wait gives up
+constexpr size_t FS_SMEM = 4ull * HIST_WORDS + (size_t)FS_S * FS_STAGE + 16ull * 2 * FS_S + 16;
 static_assert((8 * FS_RT / FS_RT + 4) * (FS_RT + 2) * 16 <= FS_STAGE, "x-tiled stage");
 static_assert((FS_NT / FS_RT + 4) * FS_RT * 16 <= FS_STAGE && (FS_NT + 4) * 16 <= FS_STAGE, "stage bound");
 
@@ -813,17 +824,67 @@ __device__ __forceinline__ void fs_ysum32(uint32_t r0, uint32_t r1, uint32_t r2,
     hi = fs_ysum(r0 >> 16, r1 >> 16, r2 >> 16, r3 >> 16, r4 >> 16);
 }
 
+// ---- mbarriers ------------------------------------------------------------
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+// arrives on b once all of this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void mbar_arrive_copies(uint64_t *b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Polls b until the given phase completes: false once the block has
+// aborted, or when FS_WAIT_LIMIT polls have passed (then the block is
+// aborted and the volume flagged).
+__device__ __noinline__ bool fs_wait_slow(uint64_t *b, uint32_t parity, volatile uint32_t *abort, uint32_t *stat) {
+    for (uint32_t i = 0; !mbar_test(b, parity); ++i) {
+        if ((i & 63u) == 0u && *abort) return false;
+        if (i >= FS_WAIT_LIMIT) {
+            *abort = 1u;
+            atomicOr(stat + ST_ERROR, ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// The ring's synchronisation state of one block.
+struct FsSync {
+    uint64_t *full;           // FS_S barriers: the stage's plane has landed
+    uint64_t *empty;          // FS_S barriers: every warp has read the stage
+    volatile uint32_t *abort; // set when a wait ran out
+    uint32_t g;               // planes this block has run through the ring
+    __device__ __forceinline__ bool wait(uint64_t *b, uint32_t parity, uint32_t *stat) {
+        return mbar_test(b, parity) || fs_wait_slow(b, parity, abort, stat);
+    }
+};
+
 // One tile: octets [x0, x0 + 8 rte) of rows [y0, y0 + TYF) of planes [z0, z1).
 // RTC = FS_RT: rows of 64 octets (8 rows per tile), HXC: halo chunks
 // (x-tiled rows), both known at compile time; RTC = 0: the shape of V.
-// Planes run through the ring from stage 0 in every tile, four per loop
-// turn, so the stage of each plane and its exchange buffer are fixed.
 template <int RTC, int HXC>
 __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, uint32_t iy, int z0, int z1,
-                                                 unsigned char *ring, uint32_t *exw, uint2 *exs, uint32_t *sh) {
-    static_assert(FS_S == 4, "the plane loop is unrolled by the ring depth");
-    const int tid = threadIdx.x;
+                                                 unsigned char *ring, uint32_t *sh, FsSync &S) {
+    const int tid = threadIdx.x, lane = tid & 31;
     const int X = (int)V.X, Y = (int)V.Y, Z = (int)V.Z;
+    // the descriptor's fields in registers (the barrier operations below are
+    // memory clobbers, which would reload them from global memory)
+    const uint16_t *raw = V.raw;
+    uint16_t *osm = V.smooth;
+    uint32_t *stat = V.stat, *ghist = V.hist;
     const int RT = RTC ? RTC : (int)V.fs_rt;
     const int TYF = RTC ? FS_NT / RTC : (int)V.fs_ty;
     const int hx = RTC ? HXC : (int)V.fs_hx;
@@ -837,9 +898,13 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     const int tyc = ty < TYF ? ty : 0;       // threads past the tile read a valid row
     const bool emit_ok = act && y0 + ty < Y;
     const bool haloL = x0 > 0, haloR = x0 + 8 * rte < X;
-    const bool fixL = act && q == 0 && haloL, fixR = act && q == rte - 1 && haloR;
     const bool edgeL = q == 0, edgeR = q == rte - 1;
-    const bool chk_top = ty == 0, chk_bot = ty == TYF - 1;
+    // neighbour words this lane y-sums itself: at a warp's ends and at the
+    // tile's ends of x-tiled rows (the halo chunks)
+    const bool ownL = edgeL ? haloL : lane == 0;
+    const bool ownR = edgeR ? haloR : lane == 31;
+    const int colo = tyc * RB + (hx + q) * 16;                     // this lane's octet in a staged plane
+    const int fixo = ownL ? colo - 4 : colo + 16;                  // the word it y-sums, if any
     // this thread's copy chunks (at most two per plane): staged row r, chunk
     // cc, as 32-bit voxel offsets from the volume's start at plane 0
     const int nchunk = (TYF + 4) * RC;
@@ -863,47 +928,55 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     const uint32_t plane = (uint32_t)X * (uint32_t)Y;  // < 2^32 (X Y Z < 2^32)
     const int n = z1 - z0 + 4;
     const uint32_t ring0 = smem_addr(ring);
-    const uint16_t *raw = V.raw;
-    auto issue = [&](int k, uint32_t st) {
-        if (k < n) {
-            const uint32_t zoff = plane * (uint32_t)min(max(z0 - 2 + k, 0), Z - 1);
+    const uint32_t g0 = S.g;
+    // stage and phase parity of the next plane to stage (is) and to read (rs)
+    uint32_t is = g0 % FS_S, ip = (g0 / FS_S) & 1u;
+    uint32_t rs = is, rp = ip;
+    // copies of tile plane k into stage `is`, once every warp has read the
+    // plane that stage held before (empty phase ip ^ 1, if there was one)
+    auto issue = [&](int k) {
+        const uint32_t gp = g0 + (uint32_t)k;
+        const bool ok = gp < FS_S || S.wait(S.empty + is, ip ^ 1u, stat);
+        const uint32_t zoff = plane * (uint32_t)min(max(z0 - 2 + k, 0), Z - 1);
+        const uint32_t dst = ring0 + is * FS_STAGE;
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-                if (cok[u]) cp_async16(ring0 + st * FS_STAGE + cdst[u], reinterpret_cast<uintptr_t>(raw + (csrc[u] + zoff)));
-        }
-        cp_async_commit();
+        for (int u = 0; u < 2; ++u)
+            if (ok && cok[u]) cp_async16(dst + cdst[u], reinterpret_cast<uintptr_t>(raw + (csrc[u] + zoff)));
+        mbar_arrive_copies(S.full + is);
+        if (++is == FS_S) { is = 0; ip ^= 1u; }
     };
     uint32_t a0[8], a1[8], a2[8], a3[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) a0[j] = a1[j] = a2[j] = a3[j] = 0u;
-    uint16_t *osm = V.smooth;
     const uint32_t orow = (uint32_t)(y0 + tyc) * (uint32_t)X + (uint32_t)(x0 + 8 * q);
     uint32_t *hc = sh + ((threadIdx.x & 16u) ? (uint32_t)HIST_COPY1 : 0u);
-    const int colo = tyc * RB + (hx + q) * 16;                  // this thread's octet in a staged plane
-    const int fixo = tyc * RB + (fixL ? 12 : (hx + rte) * 16);  // the halo word it y-sums, if any
-    __syncthreads();  // the previous tile's reads of the ring and the exchange buffers are over
-#pragma unroll
-    for (int j = 0; j < FS_S; ++j) issue(j, (uint32_t)j);
-    // y pass of plane k from stage ST on packed pairs: its four words, and
-    // the first and last word to the neighbours through exchange buffer k & 1
-    auto ypass = [&](uint32_t ST, uint32_t *yw, uint32_t &hw) -> bool {
-        const unsigned char *stg = ring + ST * FS_STAGE;
-        uint32_t *exL = exw + (ST & 1u) * 2 * FS_NT, *exR = exL + FS_NT;
+    for (int k = 0; k < FS_LEAD && k < n; ++k) issue(k);
+    for (int k = 0; k < n; ++k) {
+        if (k + FS_LEAD < n) issue(k + FS_LEAD);
+        const uint32_t st = rs;
+        const bool ok = S.wait(S.full + st, rp, stat);
+        if (++rs == FS_S) { rs = 0; rp ^= 1u; }
+        // a warp whose wait gave up skips the work (the block stays in step
+        // for its block barriers); warp-uniform, so that the shuffles below
+        // see every lane
+        if (!__all_sync(FULL, ok)) continue;
+        const unsigned char *stg = ring + st * FS_STAGE;
+        // y pass on packed pairs
         const unsigned char *cp = stg + colo;
         const uint4 r0 = *reinterpret_cast<const uint4 *>(cp);
         const uint4 r1 = *reinterpret_cast<const uint4 *>(cp + RB);
         const uint4 r2 = *reinterpret_cast<const uint4 *>(cp + 2 * RB);
         const uint4 r3 = *reinterpret_cast<const uint4 *>(cp + 3 * RB);
         const uint4 r4 = *reinterpret_cast<const uint4 *>(cp + 4 * RB);
+        uint32_t yw[4];
         yw[0] = fs_ysum(r0.x, r1.x, r2.x, r3.x, r4.x);
         yw[1] = fs_ysum(r0.y, r1.y, r2.y, r3.y, r4.y);
         yw[2] = fs_ysum(r0.z, r1.z, r2.z, r3.z, r4.z);
         yw[3] = fs_ysum(r0.w, r1.w, r2.w, r3.w, r4.w);
-        uint32_t chk = r2.x | r2.y | r2.z | r2.w;
-        if (chk_top) chk |= r0.x | r0.y | r0.z | r0.w | r1.x | r1.y | r1.z | r1.w;
-        if (chk_bot) chk |= r3.x | r3.y | r3.z | r3.w | r4.x | r4.y | r4.z | r4.w;
-        hw = 0u;  // packed y-sum of the halo word (fixL / fixR)
-        if (fixL || fixR) {
+        uint32_t chk = (r0.x | r0.y | r0.z | r0.w | r1.x | r1.y | r1.z | r1.w | r2.x | r2.y) |
+                       (r2.z | r2.w | r3.x | r3.y | r3.z | r3.w | r4.x | r4.y | r4.z | r4.w);
+        uint32_t hw = 0u;  // packed y-sum of the neighbour word this lane reads itself
+        if (ownL || ownR) {
             const unsigned char *hp = stg + fixo;
             const uint32_t w0 = *reinterpret_cast<const uint32_t *>(hp);
             const uint32_t w1 = *reinterpret_cast<const uint32_t *>(hp + RB);
@@ -913,28 +986,12 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
             hw = fs_ysum(w0, w1, w2, w3, w4);
             chk |= w0 | w1 | w2 | w3 | w4;
         }
-        exL[tid] = yw[0];
-        exR[tid] = yw[3];
-        return act && (chk & 0xF000F000u) != 0u;
-    };
-    cp_async_wait<FS_S - 1>();
-    __syncthreads();  // plane 0 staged
-    uint32_t yw[4], hw;
-    bool big = ypass(0u, yw, hw);
-    cp_async_wait<FS_S - 2>();
-    bool slow = __syncthreads_or(big);  // plane 1 staged, plane 0's exchange visible
-    // Plane k: its x and z passes (and output plane z0 + k - 4 from k = 4 on)
-    // with the y pass of plane k + 1 between the same two barriers, so that
-    // every warp has shared-memory and arithmetic work at once.
-    auto plane_step = [&](int k, auto stc) {
-        constexpr uint32_t ST = decltype(stc)::value;     // stage of plane k
-        constexpr uint32_t ST1 = (ST + 1u) % FS_S;        // stage of plane k + 1
-        const unsigned char *stg = ring + ST * FS_STAGE;
-        const uint32_t *exL = exw + (ST & 1u) * 2 * FS_NT, *exR = exL + FS_NT;
+        const uint32_t nl = __shfl_up_sync(FULL, yw[3], 1);
+        const uint32_t nr = __shfl_down_sync(FULL, yw[0], 1);
         uint32_t v[12];
-        if (!slow) {
-            const uint32_t wl = edgeL ? (haloL ? hw : __byte_perm(yw[0], 0u, 0x1010u)) : exR[tid - 1];
-            const uint32_t wr = edgeR ? (haloR ? hw : __byte_perm(yw[3], 0u, 0x3232u)) : exL[tid + 1];
+        if (!__any_sync(FULL, act && (chk & 0xF000F000u) != 0u)) {
+            const uint32_t wl = ownL ? hw : (edgeL ? __byte_perm(yw[0], 0u, 0x1010u) : nl);
+            const uint32_t wr = ownR ? hw : (edgeR ? __byte_perm(yw[3], 0u, 0x3232u) : nr);
             v[0] = wl & 0xFFFFu;
             v[1] = wl >> 16;
 #pragma unroll
@@ -945,9 +1002,8 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
             v[10] = wr & 0xFFFFu;
             v[11] = wr >> 16;
         } else {
-            // some raw value of plane k is >= 4096: its y pass again, in
-            // 32-bit lanes (stage ST is refilled only after this)
-            const unsigned char *cp = stg + colo;
+            // a raw value of 4096 or more in this warp's part of the plane:
+            // its y pass again, in 32-bit lanes
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const unsigned char *wp = cp + 4 * i;
@@ -957,38 +1013,23 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
                           *reinterpret_cast<const uint32_t *>(wp + 4 * RB), v[2 + 2 * i], v[3 + 2 * i]);
             }
             uint32_t hlo = 0u, hhi = 0u;
-            if (fixL || fixR) {
+            if (ownL || ownR) {
                 const unsigned char *hp = stg + fixo;
                 fs_ysum32(*reinterpret_cast<const uint32_t *>(hp), *reinterpret_cast<const uint32_t *>(hp + RB),
                           *reinterpret_cast<const uint32_t *>(hp + 2 * RB),
                           *reinterpret_cast<const uint32_t *>(hp + 3 * RB),
                           *reinterpret_cast<const uint32_t *>(hp + 4 * RB), hlo, hhi);
             }
-            exs[tid] = make_uint2(v[2], v[3]);
-            exs[FS_NT + tid] = make_uint2(v[8], v[9]);
-            __syncthreads();
-            if (edgeL) {
-                v[0] = haloL ? hlo : v[2];
-                v[1] = haloL ? hhi : v[2];
-            } else {
-                const uint2 e = exs[FS_NT + tid - 1];
-                v[0] = e.x;
-                v[1] = e.y;
-            }
-            if (edgeR) {
-                v[10] = haloR ? hlo : v[9];
-                v[11] = haloR ? hhi : v[9];
-            } else {
-                const uint2 e = exs[tid + 1];
-                v[10] = e.x;
-                v[11] = e.y;
-            }
+            const uint32_t l0 = __shfl_up_sync(FULL, v[8], 1), l1 = __shfl_up_sync(FULL, v[9], 1);
+            const uint32_t q0 = __shfl_down_sync(FULL, v[2], 1), q1 = __shfl_down_sync(FULL, v[3], 1);
+            v[0] = ownL ? hlo : (edgeL ? v[2] : l0);
+            v[1] = ownL ? hhi : (edgeL ? v[2] : l1);
+            v[10] = ownR ? hlo : (edgeR ? v[9] : q0);
+            v[11] = ownR ? hhi : (edgeR ? v[9] : q1);
         }
-        // every thread is past its reads of stage ST: refill it
-        issue(k + FS_S, ST);
-        // the next plane's y pass (its data landed before the last barrier)
-        bool bign = false;
-        if (k + 1 < n) bign = ypass(ST1, yw, hw);
+        // this warp is done with the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(S.empty + st);
         // x pass, then the z pass in scatter form; a3 starts each output's
         // sum at 2048 so that s = sum >> 12 rounds half up
         uint32_t s[8];
@@ -1023,35 +1064,35 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
                             const uint32_t old = atomicAdd(sh + w, 1u << sft);
                             if (((old >> sft) & 0xFFFFu) == 0x7FFFu) {
                                 atomicSub(sh + w, 0x8000u << sft);
-                                atomicAdd(V.hist + u, 0x8000u);
+                                atomicAdd(ghist + u, 0x8000u);
                             }
                         }
                     }
                 }
             }
         }
-        cp_async_wait<FS_S - 2>();  // own copies of plane k + 2 have landed
-        slow = __syncthreads_or(bign);
-    };
-    for (int k = 0; k < n; k += FS_S) {
-        plane_step(k, std::integral_constant<uint32_t, 0>());
-        if (k + 1 < n) plane_step(k + 1, std::integral_constant<uint32_t, 1>());
-        if (k + 2 < n) plane_step(k + 2, std::integral_constant<uint32_t, 2>());
-        if (k + 3 < n) plane_step(k + 3, std::integral_constant<uint32_t, 3>());
     }
-    cp_async_wait<0>();
+    S.g = g0 + (uint32_t)n;
 }
 
 __global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__restrict__ h) {
     extern __shared__ __align__(128) unsigned char dsm[];
     uint32_t *sh = reinterpret_cast<uint32_t *>(dsm);
     unsigned char *ring = dsm + 4 * HIST_WORDS;
-    uint32_t *exw = reinterpret_cast<uint32_t *>(ring + FS_S * FS_STAGE);  // [2 planes][L, R][FS_NT]
-    uint2 *exs = reinterpret_cast<uint2 *>(exw + 4 * FS_NT);              // [L, R][FS_NT]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ring + FS_S * FS_STAGE);
     const uint32_t nt = h->fs_tiles, G = gridDim.x;
     const uint32_t tb = (uint32_t)(((uint64_t)nt * blockIdx.x) / G);
     const uint32_t te = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / G);
     if (tb >= te) return;
+    FsSync S{bars, bars + FS_S, reinterpret_cast<volatile uint32_t *>(bars + 2 * FS_S), 0u};
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < FS_S; ++i) {
+            mbar_init(S.full + i, FS_NT);
+            mbar_init(S.empty + i, FS_WARPS);
+        }
+        *S.abort = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int i = threadIdx.x; i < HIST_WORDS / 4; i += FS_NT)
         reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
@@ -1071,13 +1112,14 @@ __global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__rest
         const int z0 = (int)(iz * V.fs_tz);
         const int z1 = min(z0 + (int)V.fs_tz, (int)V.Z);
         if (V.fs_rt == (uint32_t)FS_RT) {
-            if (V.fs_hx) smooth_rows_tile<FS_RT, 1>(V, ix, iy, z0, z1, ring, exw, exs, sh);
-            else smooth_rows_tile<FS_RT, 0>(V, ix, iy, z0, z1, ring, exw, exs, sh);
+            if (V.fs_hx) smooth_rows_tile<FS_RT, 1>(V, ix, iy, z0, z1, ring, sh, S);
+            else smooth_rows_tile<FS_RT, 0>(V, ix, iy, z0, z1, ring, sh, S);
         } else {
-            smooth_rows_tile<0, 0>(V, ix, iy, z0, z1, ring, exw, exs, sh);
+            smooth_rows_tile<0, 0>(V, ix, iy, z0, z1, ring, sh, S);
         }
         ++ndone;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy into this block's shared memory outlives it
     const VolDev &P = h->vol[v];
     flush_hist<FS_NT>(h, v, ndone, sh, P.fs_ntx * P.fs_nty * P.fs_ntz);
 }

@@ -169,7 +169,6 @@ struct Slot {
     uint32_t *d_stat = nullptr;
     std::map<uint64_t, cudaGraphExec_t> graph;  // by graph_key of the launch plan
     cudaEvent_t ev[NUM_KERNELS + 1] = {};
-    cudaEvent_t end_ev = nullptr;  // recorded after the slot's last batch
     Batch *busy = nullptr;
 };
 
@@ -202,10 +201,6 @@ struct seg_ctx {
     uint32_t cap_vols = 512;
     bool plain = false, graphs = true, profile = false;
     bool tuned = false;  // tile shape fixed (forced, or tuned on the first batch)
-    // end of the most recently launched batch: the next batch, on whichever
-    // slot, starts on the device after it, so batches never share the GPU
-    // while the host prepares the next one during the current one
-    cudaEvent_t prev_end = nullptr;
     cudaStream_t copy_stream = nullptr;
     cudaStream_t read_stream = nullptr;
     uint32_t *read_pin = nullptr;  // pinned words for small results of the read calls (one reader at a time)
@@ -579,7 +574,6 @@ int tune_tiles(seg_ctx *ctx, Batch &b) {
 
 int launch_batch(seg_ctx *ctx, Batch &b) {
     Slot &s = *b.slot;
-    if (ctx->prev_end) CK(cudaStreamWaitEvent(s.stream, ctx->prev_end, 0));
     // Inputs that waited on the host are copied now (pageable source: the
     // call returns once the data is staged).
     for (Request *r : b.reqs) {
@@ -630,8 +624,6 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
         if (rc != SEG_OK) return rc;
     }
     for (Request *r : b.reqs) CK(cudaEventRecord(r->done_ev, s.stream));
-    CK(cudaEventRecord(s.end_ev, s.stream));
-    ctx->prev_end = s.end_ev;
     CK(cudaFreeAsync(b.scratch, s.stream));
     b.scratch = nullptr;
     CK(cudaLaunchHostFunc(s.stream, on_batch_done, &b));
@@ -870,7 +862,6 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
         CK(cudaMalloc(reinterpret_cast<void **>(&s.d_stat), 4ull * ST_WORDS * ctx->cap_vols));
         std::memset(s.h_hdr, 0, batch_bytes(ctx->cap_vols));
         for (auto &e : s.ev) CK(cudaEventCreate(&e));
-        CK(cudaEventCreateWithFlags(&s.end_ev, cudaEventDisableTiming));
     }
     ctx->worker = std::thread(worker_main, ctx.get());
     *out = ctx.release();
@@ -897,7 +888,6 @@ int seg_destroy(seg_ctx *ctx) {
             if (g.second) cudaGraphExecDestroy(g.second);
         for (auto &e : s.ev)
             if (e) cudaEventDestroy(e);
-        if (s.end_ev) cudaEventDestroy(s.end_ev);
         if (s.h_hdr) cudaFreeHost(s.h_hdr);
         if (s.d_hdr) cudaFree(s.d_hdr);
         if (s.h_stat) cudaFreeHost(s.h_stat);
