@@ -55,6 +55,8 @@ struct VolDev {
     uint32_t *stat;           // ST_WORDS words
     uint32_t *hist;           // 65536 uint32 bins
     uint16_t *smooth;         // [Z][Y][X] smoothed voxels (pass 1 -> threshold pass)
+    uint16_t *wmax;           // rows x W: largest smoothed value of each mask word (k_smooth_rows
+                              // volumes with X % 32 == 0 or X > 512; else null)
     uint32_t *mask;           // rows x W words, bit b of word w is x = 32w + b
     uint32_t *rowoff;         // rows + 1: run count per row, then run offsets
     uint32_t *rowk;           // rows: kept-root count per row, then label base

@@ -885,6 +885,8 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     const uint16_t *raw = V.raw;
     uint16_t *osm = V.smooth;
     uint32_t *stat = V.stat, *ghist = V.hist;
+    uint16_t *wmax = V.wmax;
+    const uint32_t W = V.W;
     const int RT = RTC ? RTC : (int)V.fs_rt;
     const int TYF = RTC ? FS_NT / RTC : (int)V.fs_ty;
     const int hx = RTC ? HXC : (int)V.fs_hx;
@@ -1046,6 +1048,15 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
         if (k >= 4) {
             const uint32_t vmax = max(max(max(s[0], s[1]), max(s[2], s[3])), max(max(s[4], s[5]), max(s[6], s[7])));
             const bool fast = __all_sync(FULL, !emit_ok || vmax < (uint32_t)HIST_LOW);
+            if (wmax) {
+                // the largest value of each 32-voxel mask word (four lanes),
+                // so that the threshold pass reads only words above t*
+                uint32_t wm = emit_ok ? vmax : 0u;
+                wm = max(wm, __shfl_xor_sync(FULL, wm, 1));
+                wm = max(wm, __shfl_xor_sync(FULL, wm, 2));
+                if (emit_ok && (q & 3) == 0)
+                    wmax[(uint32_t)((z0 + k - 4) * Y + y0 + ty) * W + (uint32_t)((x0 + 8 * q) >> 5)] = (uint16_t)wm;
+            }
             if (emit_ok) {
                 *reinterpret_cast<uint4 *>(osm + (orow + plane * (uint32_t)(z0 + k - 4))) =
                     make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
@@ -1155,7 +1166,67 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
         const uint32_t X = V.X, W = V.W, t = V.stat[ST_THRESH];
         const bool vec = (X & 7u) == 0u;
         uint32_t wtot = 0;
-        if (vec && X <= 512u) {
+        const uint16_t *wmax = V.wmax;
+        if (wmax && (X & 255u) == 0u && W <= 256u && ((W >> 3) & ((W >> 3) - 1u)) == 0u) {
+            // Word maxima (rows of 256, 512, ..., 8192 voxels): a lane owns
+            // 8 consecutive mask words of one row
+            // (one 16-byte load of their maxima), reads the 64 bytes of each
+            // word whose maximum is above t* (about one word in eight on
+            // microscope data; the others are background) and writes its 8
+            // words; a row is W / 8 consecutive lanes, a warp 256 / W rows.
+            const uint32_t seg = W >> 3;             // lanes per row: 1, 2, 4, ..., 32
+            const uint32_t rows_pw = 32u / seg;      // rows per warp step
+            const uint32_t lrow = (uint32_t)lane / seg, lw = ((uint32_t)lane & (seg - 1u)) * 8u;
+            for (uint32_t rb = warp * rows_pw; rb < nrows; rb += WARPS * rows_pw) {
+                const uint32_t rr = rb + lrow;
+                const bool live = rr < nrows;
+                const size_t wbase = (size_t)(row0 + rr) * W + lw;
+                uint4 mx = make_uint4(0, 0, 0, 0);
+                if (live) mx = __ldcs(reinterpret_cast<const uint4 *>(wmax + wbase));
+                const uint32_t mw[4] = {mx.x, mx.y, mx.z, mx.w};
+                uint32_t act = 0;  // bit i: word lw + i has a voxel above t*
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    act |= ((mw[i] & 0xFFFFu) > t ? 1u : 0u) << (2 * i) | ((mw[i] >> 16) > t ? 2u : 0u) << (2 * i);
+                uint32_t word[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) word[i] = 0u;
+                const uint16_t *src = V.smooth + (size_t)(row0 + rr) * X + 32u * lw;
+                for (uint32_t a = act; a; a &= a - 1u) {
+                    const int i = __ffs(a) - 1;
+                    const uint4 *p = reinterpret_cast<const uint4 *>(src + 32 * i);
+                    const uint4 o0 = __ldcs(p), o1 = __ldcs(p + 1), o2 = __ldcs(p + 2), o3 = __ldcs(p + 3);
+                    const uint32_t w = octet_bits(o0, t) | octet_bits(o1, t) << 8 | octet_bits(o2, t) << 16 |
+                                       octet_bits(o3, t) << 24;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j == i) word[j] = w;
+                }
+                // run starts: a set bit whose left neighbour (across words,
+                // and from the previous lane of the same row) is clear
+                uint32_t left = __shfl_up_sync(FULL, word[7], 1) >> 31;
+                if (lw == 0u) left = 0u;
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    cnt += __popc(word[i] & ~((word[i] << 1) | left));
+                    left = word[i] >> 31;
+                }
+                for (uint32_t o = 1; o < seg; o <<= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+                if (live) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(V.mask + wbase);
+                    dst[0] = make_uint4(word[0], word[1], word[2], word[3]);
+                    dst[1] = make_uint4(word[4], word[5], word[6], word[7]);
+                    if (lw == 0u) {
+                        V.rowoff[row0 + rr] = cnt;
+                        wtot += cnt;
+                    }
+                }
+            }
+            // each row was counted by its first lane: the warp's total
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wtot += __shfl_xor_sync(FULL, wtot, o);
+        } else if (vec && X <= 512u) {
             // 4 rows per warp at once, all 16-byte loads issued first
             for (uint32_t rb = warp; rb < nrows; rb += 4 * WARPS) {
                 uint4 q4[4][2];

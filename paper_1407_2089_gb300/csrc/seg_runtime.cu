@@ -86,7 +86,8 @@ VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, cons
     uint64_t kc = cdiv(d.x, 2) * cdiv(d.y, 2) * cdiv(d.z, 2);
     if (min_volume > 1) kc = std::min<uint64_t>(kc, g.n / min_volume + 1);
     g.k_cap = std::max<uint64_t>(kc, 1);
-    g.scratch = al(4ull * HIST_BINS) + al(2ull * g.n) + al(4ull * g.rows * g.W) + al(4ull * (g.rows + 1)) +
+    g.scratch = al(4ull * HIST_BINS) + al(2ull * g.n) + al(2ull * g.rows * g.W) + al(4ull * g.rows * g.W) +
+                al(4ull * (g.rows + 1)) +
                 al(4ull * g.rows) + 2 * al(4ull * g.nrt) + 3 * al(4ull * g.r_cap);
     g.dn_r = dn_r;
     if (dn_r) g.scratch += 2 * al(2ull * g.n);  // two box-pass buffers (the denoised image persists)
@@ -440,6 +441,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
             V.hist = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * HIST_BINS);
             V.smooth = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.n);
             if (r->smoothed(c)) V.smooth = r->smoothed(c);
+            V.wmax = reinterpret_cast<uint16_t *>(sp); sp += al(2ull * g.rows * g.W);
             V.mask = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows * g.W);
             V.rowoff = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * (g.rows + 1));
             V.rowk = reinterpret_cast<uint32_t *>(sp); sp += al(4ull * g.rows);
@@ -463,7 +465,10 @@ void build_header(seg_ctx *ctx, Batch &b) {
                 V.fs_ntx = (uint32_t)cdiv(g.X, 8ull * V.fs_rt);
                 V.fs_nty = (uint32_t)cdiv(g.Y, V.fs_ty);
                 V.fs_ntz = (uint32_t)cdiv(g.Z, fz);
+                // word maxima: groups of four octet lanes hold one mask word
+                if (!(g.X > 8u * FS_RT || g.X % 32u == 0u)) V.wmax = nullptr;
             } else {
+                V.wmax = nullptr;
                 V.ntx = (uint32_t)cdiv(g.X, TILE_X);
                 V.nty = (uint32_t)cdiv(g.Y, ty);
                 V.ntz = (uint32_t)cdiv(g.Z, tz);
@@ -671,6 +676,15 @@ void worker_main(seg_ctx *ctx) {
     for (;;) {
         bool progressed = false;
         for (Slot &s : ctx->slots) {
+            if (s.busy && !s.busy->done.load()) {
+                // a device fault leaves the context unusable and the batch's
+                // host function never runs: fail the batch instead of waiting
+                const cudaError_t e = cudaStreamQuery(s.stream);
+                if (e != cudaSuccess && e != cudaErrorNotReady) {
+                    s.busy->launch_err = SEG_ECUDA;
+                    s.busy->done.store(true);
+                }
+            }
             if (s.busy && s.busy->done.load()) {
                 finalize_batch(ctx, s);
                 progressed = true;

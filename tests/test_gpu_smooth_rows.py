@@ -4,14 +4,18 @@ created with SEG_KEEP_SMOOTHED, read with seg_read_smoothed), then labels,
 cells and t*.
 
 The kernel sums the five rows of the y pass on packed 16-bit pairs, which is
-exact while every raw value is below 4096, and redoes a plane in 32-bit lanes
-when one is not; x-neighbours come through an exchange buffer, from the edge
-voxel, or (x-tiled rows, X > 512) from halo chunks.  The cases cover every
-tile shape class (one octet per row up to 64, rows wider than a tile, a last
-x-tile of one octet), values at and above 4096 placed in a tile's own rows,
-in the halo rows shared with the next tile and in the x-halo columns, planes
-split into z-chunks, and batches that mix these volumes with ones the other
-smoothing kernel takes (ragged X, unaligned device input)."""
+exact while every raw value is below 4096, and a warp redoes a plane in
+32-bit lanes when one of its values is not; x-neighbours come from the
+neighbouring lanes, from the staged plane at a warp's ends, from the edge
+voxel, or (x-tiled rows, X > 512) from halo chunks.  It also stores each mask
+word's largest value, so that the threshold pass reads only the words above
+t*.  The cases cover every tile shape class (one octet per row up to 64, rows
+wider than a tile, a last x-tile of one octet), values at and above 4096
+placed in a tile's own rows, in the halo rows shared with the next tile and
+in the x-halo columns, planes split into z-chunks, rows of 256 .. 2048 voxels
+over several row tiles (the word-maximum threshold pass), and batches that
+mix these volumes with ones the other smoothing kernel takes (ragged X,
+unaligned device input)."""
 import numpy as np
 import pytest
 
@@ -153,6 +157,21 @@ def test_mixed_batch_with_other_kernel(seg):
         cells, thr = seg.seg_read_features(c, r, 0)
         assert_matches_oracle(v, lab, cells, thr, min_volume=5, ref=ref, what="unaligned device input")
         seg.seg_release(c, r)
+    finally:
+        seg.seg_destroy(c)
+
+
+def test_word_maxima_threshold_many_row_tiles(seg):
+    # rows of 256 .. 2048 voxels take the threshold pass that reads only the
+    # mask words whose maximum is above t*; several row tiles of 256 rows
+    # per volume, in one batch and alone
+    c = seg.seg_create(device=0, flags=seg.SEG_KEEP_SMOOTHED, batch_window_us=10_000_000)
+    try:
+        vols = [noisy((256, 300, 3), 21, n_blobs=30), noisy((512, 130, 4), 22, n_blobs=30),
+                noisy((1024, 150, 3), 23, n_blobs=40), noisy((2048, 200, 2), 24, n_blobs=50)]
+        check(seg, c, vols, m=1, what="word maxima, batch")
+        for v in vols:
+            check(seg, c, [v], m=1, what="word maxima, alone")
     finally:
         seg.seg_destroy(c)
 
