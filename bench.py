@@ -751,23 +751,27 @@ def uneven_forms(seg, torch, local, steps):
         seg.seg_destroy(ctx)
         out[name] = {"ms_per_pass": ms, "gvox_s": vox / (ms / 1e3) / 1e9}
     del dvols
-    # the single frame, plain form
+    # the single frame, submit -> done, sequential requests: the plain form,
+    # and the same with every kernel launched on its own (no graph)
     v1 = synth.single_frame()
     d1 = torch.from_numpy(v1.view(np.int16)).to("cuda:%d" % local)
-    ctx = seg.seg_create(device=local, flags=seg.SEG_PLAIN)
-    lat = []
-    for i in range(23):
-        t0 = time.perf_counter()
-        r = seg.seg_submit_volume(ctx, d1, dims=(v1.shape[2], v1.shape[1], v1.shape[0]), channels=1)
-        if seg.seg_wait(ctx, r) != seg.SEG_DONE:
-            raise RuntimeError("request failed")
-        if i >= 3:
-            lat.append((time.perf_counter() - t0) * 1e3)
-        seg.seg_release(ctx, r)
-    seg.seg_destroy(ctx)
-    out["single_frame_plain"] = {"dims": [int(v1.shape[2]), int(v1.shape[1]), int(v1.shape[0])],
-                                 "latency_ms_median": statistics.median(lat),
-                                 "gvox_s": v1.size / (statistics.median(lat) / 1e3) / 1e9}
+    for name, flags in (("single_frame_plain", seg.SEG_PLAIN),
+                        ("single_frame_plain_no_graph", seg.SEG_PLAIN | seg.SEG_NO_GRAPH)):
+        ctx = seg.seg_create(device=local, flags=flags)
+        lat = []
+        for i in range(53):
+            t0 = time.perf_counter()
+            r = seg.seg_submit_volume(ctx, d1, dims=(v1.shape[2], v1.shape[1], v1.shape[0]), channels=1)
+            if seg.seg_wait(ctx, r) != seg.SEG_DONE:
+                raise RuntimeError("request failed")
+            if i >= 3:
+                lat.append((time.perf_counter() - t0) * 1e3)
+            seg.seg_release(ctx, r)
+        seg.seg_destroy(ctx)
+        out[name] = {"dims": [int(v1.shape[2]), int(v1.shape[1]), int(v1.shape[0])],
+                     "latency_ms_median": statistics.median(lat),
+                     "latency_ms_p99": float(np.percentile(lat, 99)),
+                     "gvox_s": v1.size / (statistics.median(lat) / 1e3) / 1e9}
     return out
 
 

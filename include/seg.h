@@ -68,8 +68,9 @@ extern "C" {
 /* ---- seg_config.flags ---------------------------------------------------- */
 #define SEG_FORCE_TILE 0x1u /* use tile_y / tile_z as given, skip the autotuner   */
 #define SEG_PLAIN 0x2u      /* plain per-frame form: one request per launch
-                               sequence, one stream, no batching, no graphs      */
-#define SEG_NO_GRAPH 0x4u   /* batched form without CUDA-graph capture           */
+                               sequence, one stream, no batching                 */
+#define SEG_NO_GRAPH 0x4u   /* kernels launched one by one, without CUDA-graph
+                               capture                                           */
 #define SEG_PROFILE 0x8u    /* record CUDA events around every kernel launch     */
 #define SEG_TEST_UNION_FAIL 0x10u /* test hook: every union-find union gives up at
                                      once and raises its error bit, so requests

@@ -187,6 +187,8 @@ struct LaunchPlan {
     int grid_lab;        // k_label_features
     int grid_box;        // k_box_pass
     int grid_med;        // k_median27
+    bool rows;           // some volume of the batch takes k_smooth_rows
+    bool tiles;          // some volume of the batch takes k_smooth_hist
     bool denoise;        // some volume of the batch runs the denoise front end
     bool closing;        // some volume of the batch closes its foreground
     bool distance;       // some volume of the batch has a distance map

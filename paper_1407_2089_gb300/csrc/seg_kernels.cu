@@ -3581,9 +3581,9 @@ cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStre
         ++k;
     };
     rec();
-    k_smooth_rows<<<p.grid_hist, FS_NT, FS_SMEM, s>>>(d);
+    if (p.rows) k_smooth_rows<<<p.grid_hist, FS_NT, FS_SMEM, s>>>(d);
     rec();
-    k_smooth_hist<TY><<<p.grid_hist, Tile<TY>::NT, hist_smem_bytes(TY), s>>>(d);
+    if (p.tiles) k_smooth_hist<TY><<<p.grid_hist, Tile<TY>::NT, hist_smem_bytes(TY), s>>>(d);
     return cudaGetLastError();
 }
 

@@ -521,7 +521,8 @@ void build_header(seg_ctx *ctx, Batch &b) {
 
 // A captured graph fixes which optional kernels launch and how many MRF steps.
 uint64_t graph_key(const LaunchPlan &p) {
-    return (uint64_t)p.tile_y | (uint64_t)p.denoise << 8 | (uint64_t)p.closing << 9 | (uint64_t)p.distance << 10 |
+    return (uint64_t)p.tile_y | (uint64_t)p.rows << 11 | (uint64_t)p.tiles << 12 |
+           (uint64_t)p.denoise << 8 | (uint64_t)p.closing << 9 | (uint64_t)p.distance << 10 |
            (uint64_t)p.mrf_iters << 16;
 }
 
@@ -598,6 +599,8 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
         if (rc != SEG_OK) return rc;
     }
     build_header(ctx, b);
+    ctx->plan.rows = s.h_hdr->fs_tiles > 0;
+    ctx->plan.tiles = s.h_hdr->ntiles > 0;
     ctx->plan.denoise = s.h_hdr->dn_tiles > 0;
     ctx->plan.closing = s.h_hdr->cl_items > 0;
     ctx->plan.distance = false;
@@ -837,7 +840,9 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, cfg->device));
 
     ctx->plain = (cfg->flags & SEG_PLAIN) != 0;
-    ctx->graphs = !ctx->plain && !(cfg->flags & SEG_NO_GRAPH);
+    // the plain form runs one request per launch sequence, captured like the
+    // batched form's (one graph per slot and launch plan)
+    ctx->graphs = !(cfg->flags & SEG_NO_GRAPH);
     ctx->profile = (cfg->flags & SEG_PROFILE) != 0;
     ctx->cap_vols = cfg->max_batch_volumes ? cfg->max_batch_volumes : 512;
     const uint32_t nslots = ctx->plain ? 1 : (cfg->max_inflight ? cfg->max_inflight : 2);
@@ -853,6 +858,7 @@ int seg_create(const seg_config *cfg, seg_ctx **out) {
     ctx->plan.tile_y = ty;
     ctx->plan.grid_hist = ctx->sms;  // one resident block per SM (176 KiB histogram)
     ctx->plan.grid_vols = ctx->sms;
+    ctx->plan.rows = ctx->plan.tiles = true;
     ctx->plan.denoise = false;
     ctx->plan.closing = false;
     ctx->plan.distance = false;
