@@ -45,8 +45,8 @@ ALGO_BYTES_PER_VOXEL = 8.0  # 2 B raw read + 2 B re-read after Otsu + 4 B label 
 # Algorithmic bytes per voxel of each kernel (the units one launch processes
 # are all voxels of the batch).
 KERNEL_BYTES_PER_VOXEL = {
-    "smooth_rows_otsu": 2.0,       # raw uint16 read once (row-aligned volumes)
-    "smooth_hist_otsu": 2.0,       # raw uint16 read once (other volumes)
+    "smooth_rows": 2.0,            # raw uint16 read once (row-aligned volumes)
+    "smooth_hist": 2.0,            # raw uint16 read once (other volumes)
     "threshold_runs": 1 / 8.0,     # 1-bit mask write (the smoothed re-read is the 2 B
                                    # counted in the 8 B/voxel path total)
     "label_features": 4.0,         # uint32 label write (run tables are O(runs))
@@ -59,7 +59,7 @@ KERNEL_BYTES_PER_VOXEL = {
 # than L2); the per-launch figure scales with the voxels a launch processes
 # since every 512x512x64 volume is tiled the same way.
 KERNEL_TRAFFIC_BYTES_PER_VOXEL = {
-    "smooth_hist_otsu": 7.69,      # 5.88 read (halo lines re-read) + 1.81 smoothed write
+    "smooth_hist": 7.69,           # 5.88 read (halo lines re-read) + 1.81 smoothed write
 }
 
 

@@ -16,7 +16,7 @@ enum StatWord : uint32_t {
     ST_THRESH = 0,     // Otsu level t* (foreground = s > t*)
     ST_RUNS = 1,       // number of foreground runs R
     ST_CELLS = 2,      // number of surviving cells K
-    ST_TILES_DONE = 3, // smoothing tiles whose histogram share is merged
+    // word 3 unused
     ST_ERROR = 4,      // error bits (ERR_*)
     ST_MRF_STEPS = 5,  // MRF denoise: steps kept
     ST_MRF_SEL = 6,    // MRF denoise: result buffer (0 input, 1 mrf_buf[0], 2 mrf_buf[1])
@@ -169,7 +169,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 26;
+constexpr int NUM_KERNELS = 27;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {

@@ -43,7 +43,7 @@ namespace seg {
 
 const char *const kKernelNames[NUM_KERNELS] = {
     "denoise_box", "denoise_median", "init",       "mrf_stats",        "mrf_iterate",
-    "smooth_rows_otsu", "smooth_hist_otsu", "threshold_runs",
+    "smooth_rows", "smooth_hist",  "otsu",       "threshold_runs",
     "dilate",      "erode",          "dist_xy",    "dist_xy_1024",     "dist_x",
     "dist_y",      "dist_z",         "dist_z_long", "scan_runs",       "row_runs",
     "union_local", "union",          "flatten",    "keep_count",       "scan_keep",
@@ -556,109 +556,312 @@ struct HistEmit {
 // h[t] > 0 are evaluated: for an empty level (n0, s0) repeat those of t - 1,
 // so the value repeats and t can never be the lowest maximiser.  Ties go to
 // the lowest t.  With no admissible t (one distinct level) t* is that level.
+//
+// Binary64 arithmetic is slow on this GPU (a division takes about 650
+// cycles of latency, an add or compare 70 to 175), so the binary64 formula is
+// evaluated only where it can decide the maximum.  A first pass bounds every
+// occupied level's variance in binary32: each operand is converted within
+// 2 ulp (2^-23 relative) and each quotient is correctly rounded, so a class
+// mean is within 5 * 2^-24 relative, i.e. 0.02 voxel-value units for values
+// below 65536; the difference d of the means is off by less than 0.05, and
+// n0*n1 by less than 10^-6 relative; hence
+//     lo = n0 n1 (1 - 1e-5) max(|d~| - 0.05, 0)^2 <= var <= hi = n0 n1 (1 + 1e-5) (|d~| + 0.05)^2,
+// where var is the exact (rational) variance, and the binary64 value is
+// within 10^-13 relative of it.  Every level whose hi is below the largest
+// lo is below the maximum and cannot win or tie (two distinct binary32
+// values differ by at least 2^-24 relative, far more than the binary64
+// values can move); the binary64 formula is evaluated, in the stated order,
+// at the remaining levels only.
 
 template <int NT>
-__device__ void otsu_block(const uint32_t *__restrict__ gh, uint32_t *stat, uint64_t nvox) {
-    constexpr int PER = HIST_BINS / NT;
-    __shared__ unsigned long long s_n[32], s_s[32];
-    __shared__ double s_bv[32];
-    __shared__ uint32_t s_bt[32], s_mn[32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const uint32_t base = (uint32_t)tid * PER;
-    unsigned long long n = 0, s = 0;
-    for (int i = 0; i < PER; i += 4) {
-        const uint4 c = __ldcg(reinterpret_cast<const uint4 *>(gh + base + i));
-        const unsigned long long u = base + i;
-        n += (unsigned long long)c.x + c.y + c.z + c.w;
-        s += u * c.x + (u + 1) * c.y + (u + 2) * c.z + (u + 3) * c.w;
-    }
-    unsigned long long ni = n, si = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long a = __shfl_up_sync(FULL, ni, o), b = __shfl_up_sync(FULL, si, o);
-        if (lane >= o) { ni += a; si += b; }
-    }
-    if (lane == 31) { s_n[wid] = ni; s_s[wid] = si; }
-    __syncthreads();
-    if (wid == 0) {
-        unsigned long long wn = lane < NT / 32 ? s_n[lane] : 0ull;
-        unsigned long long ws = lane < NT / 32 ? s_s[lane] : 0ull;
-        unsigned long long in = wn, is = ws;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long a = __shfl_up_sync(FULL, in, o), b = __shfl_up_sync(FULL, is, o);
-            if (lane >= o) { in += a; is += b; }
-        }
-        if (lane < NT / 32) { s_n[lane] = in - wn; s_s[lane] = is - ws; }
-    }
-    __syncthreads();
+__device__ void otsu_block(const uint32_t *__restrict__ gh, uint32_t *stat, uint64_t nvox,
+                           unsigned char *scr, uint32_t scr_bytes) {
+    constexpr int NW = NT / 32;
+    constexpr int GL = 128;               // levels per group (one 16-byte load per lane)
+    constexpr int NG = HIST_BINS / GL;    // groups
+    constexpr int GPW = NG / NW;          // groups per warp
+    constexpr int LF = NT >= 1024 ? 4 : 8;   // group loads in flight per lane
+    static_assert(GPW % LF == 0 && NG <= NT, "group layout");
+    __shared__ unsigned long long g_n[NG], g_s[NG];  // group totals, then exclusive prefixes
+    __shared__ uint32_t g_k[NG];                      // occupied levels per group, then prefix
+    __shared__ uint16_t g_id[NG];                     // the occupied groups, in level order
+    __shared__ unsigned long long w_n[32], w_s[32];
+    __shared__ uint32_t w_k[32], w_g[32];
     __shared__ unsigned long long s_tot[2];
-    if (tid == NT - 1) { s_tot[0] = s_n[wid] + ni; s_tot[1] = s_s[wid] + si; }
+    __shared__ uint32_t s_ktot, s_gtot, s_cnt;
+    __shared__ unsigned long long s_best;  // largest binary64 variance (bits)
+    __shared__ uint32_t s_lvl, s_only, s_lb;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(gh);
+    if (tid == 0) { s_cnt = 0; s_best = 0ull; s_lvl = 0xFFFFFFFFu; s_only = 0u; s_lb = 0u; }
+    // 1. totals of every group of 128 levels: warp wid reads groups wid,
+    // wid + NW, wid + 2 NW, ... (the occupied levels, low in the range,
+    // spread over all warps), one coalesced 512-byte load per group
+#pragma unroll 1
+    for (int r = 0; r < GPW; r += LF) {
+        uint4 c[LF];
+#pragma unroll
+        for (int k = 0; k < LF; ++k) c[k] = __ldcg(h4 + (size_t)((r + k) * NW + wid) * 32 + lane);
+#pragma unroll
+        for (int k = 0; k < LF; ++k) {
+            const int g = (r + k) * NW + wid;
+            const uint32_t u0 = (uint32_t)g * GL + 4u * (uint32_t)lane;
+            unsigned long long n = (unsigned long long)c[k].x + c[k].y + c[k].z + c[k].w;
+            if (!__any_sync(FULL, n != 0)) {
+                if (lane == 0) { g_n[g] = 0; g_s[g] = 0; g_k[g] = 0; }
+                continue;
+            }
+            unsigned long long s = (unsigned long long)u0 * n + c[k].y + 2ull * c[k].z + 3ull * c[k].w;
+            uint32_t o = (c[k].x != 0) + (c[k].y != 0) + (c[k].z != 0) + (c[k].w != 0);
+#pragma unroll 1
+            for (int off = 16; off > 0; off >>= 1) {
+                n += __shfl_xor_sync(FULL, n, off);
+                s += __shfl_xor_sync(FULL, s, off);
+                o += __shfl_xor_sync(FULL, o, off);
+            }
+            if (lane == 0) { g_n[g] = n; g_s[g] = s; g_k[g] = o; }
+        }
+    }
     __syncthreads();
+    // 2. exclusive prefixes over the groups (thread g holds group g), the
+    // totals, and the list of occupied groups
+    {
+        unsigned long long gn = 0, gs = 0;
+        uint32_t gk = 0;
+        if (tid < NG) { gn = g_n[tid]; gs = g_s[tid]; gk = g_k[tid]; }
+        const uint32_t ne = gk != 0u;
+        unsigned long long in = gn, is = gs;
+        uint32_t ik = gk, ie = ne;
+#pragma unroll 1
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long a = __shfl_up_sync(FULL, in, o), b = __shfl_up_sync(FULL, is, o);
+            const uint32_t c = __shfl_up_sync(FULL, ik, o), d = __shfl_up_sync(FULL, ie, o);
+            if (lane >= o) { in += a; is += b; ik += c; ie += d; }
+        }
+        if (lane == 31) { w_n[wid] = in; w_s[wid] = is; w_k[wid] = ik; w_g[wid] = ie; }
+        __syncthreads();
+        // every warp scans the warp totals itself (no further barrier): its
+        // own exclusive prefix sits in lane wid, the grand totals in lane 31
+        {
+            const unsigned long long wn = lane < NW ? w_n[lane] : 0ull, ws = lane < NW ? w_s[lane] : 0ull;
+            const uint32_t wk = lane < NW ? w_k[lane] : 0u, wg = lane < NW ? w_g[lane] : 0u;
+            unsigned long long an = wn, as = ws;
+            uint32_t ak = wk, ag = wg;
+#pragma unroll 1
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long a = __shfl_up_sync(FULL, an, o), b = __shfl_up_sync(FULL, as, o);
+                const uint32_t c = __shfl_up_sync(FULL, ak, o), d = __shfl_up_sync(FULL, ag, o);
+                if (lane >= o) { an += a; as += b; ak += c; ag += d; }
+            }
+            const unsigned long long bn = __shfl_sync(FULL, an - wn, wid), bs = __shfl_sync(FULL, as - ws, wid);
+            const uint32_t bk = __shfl_sync(FULL, ak - wk, wid), bg = __shfl_sync(FULL, ag - wg, wid);
+            if (tid == 31) { s_tot[0] = an; s_tot[1] = as; s_ktot = ak; s_gtot = ag; }
+            if (tid < NG) {
+                g_n[tid] = bn + in - gn;
+                g_s[tid] = bs + is - gs;
+                g_k[tid] = bk + ik - gk;
+                if (ne) g_id[bg + ie - 1u] = (uint16_t)tid;
+            }
+        }
+        __syncthreads();
+    }
     const unsigned long long Nt = s_tot[0], St = s_tot[1];
-    unsigned long long n0 = s_n[wid] + ni - n;
-    unsigned long long s0 = s_s[wid] + si - s;
-    double best = -1.0;
-    uint32_t bt = 0xFFFFFFFFu, mn = 0xFFFFFFFFu;
-    for (int i = 0; i < PER; i += 4) {
-        const uint4 c4 = __ldcg(reinterpret_cast<const uint4 *>(gh + base + i));
-        const uint32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+    const uint32_t K = s_ktot;  // occupied levels
+    // binary32 bounds of the variance at level u (classes n0, s0 / n1, s1);
+    // each operand converted from its two 32-bit halves (one rounding of
+    // the high half, one of the fused sum: within 2 ulp)
+    auto f32 = [](unsigned long long x) {
+        const uint32_t hi32 = (uint32_t)(x >> 32), lo32 = (uint32_t)x;
+        return hi32 ? __fmaf_rn(__uint2float_rn(hi32), 4294967296.0f, __uint2float_rn(lo32)) : __uint2float_rn(lo32);
+    };
+    auto bounds = [&](unsigned long long n0, unsigned long long s0, unsigned long long n1, float &lo, float &hi) {
+        const float d = __fsub_rn(__fdiv_rn(f32(St - s0), f32(n1)), __fdiv_rn(f32(s0), f32(n0)));
+        const float nn = __fmul_rn(f32(n0), f32(n1));
+        const float e = fmaxf(fabsf(d) - 0.05f, 0.0f), f = fabsf(d) + 0.05f;
+        lo = __fmul_rn(__fmul_rn(nn, 0.99999f), __fmul_rn(e, e));
+        hi = __fmul_rn(__fmul_rn(nn, 1.00001f), __fmul_rn(f, f));
+    };
+    // The variance is never negative (n0 n1 d d with n0, n1 > 0, and d d is
+    // +0 at worst), so the order of the binary64 values is the order of
+    // their bit patterns read as unsigned integers; the running maximum is
+    // kept as those bits, with level 0xFFFFFFFF for "none yet".
+    unsigned long long best = 0ull;
+    uint32_t bt = 0xFFFFFFFFu;
+    auto eval = [&](uint32_t u, unsigned long long n0, unsigned long long s0) {
+        const unsigned long long n1 = Nt - n0, s1 = St - s0;
+        const double m0 = __ddiv_rn(__ull2double_rn(s0), __ull2double_rn(n0));
+        const double m1 = __ddiv_rn(__ull2double_rn(s1), __ull2double_rn(n1));
+        const double d = __dsub_rn(m1, m0);
+        const double var = __dmul_rn(__dmul_rn(__dmul_rn(__ull2double_rn(n0), __ull2double_rn(n1)), d), d);
+        const unsigned long long vb = (unsigned long long)__double_as_longlong(var);
+        if (vb > best || (vb == best && u < bt)) { best = vb; bt = u; }
+    };
+    // largest of the threads' non-negative binary32 values (their bit
+    // patterns order as unsigned integers)
+    auto block_max = [&](float x) {
+        const uint32_t m = __reduce_max_sync(FULL, __float_as_uint(x));
+        if (lane == 0 && m) atomicMax(&s_lb, m);
+        __syncthreads();
+        return __uint_as_float(s_lb);
+    };
+    // The occupied levels (a frame's values span a few thousand of the 65536)
+    // are listed in the scratch with their class prefixes (n0, s0), each
+    // occupied group by one warp; every later step runs over the list, NT
+    // entries at a time.
+    const uint32_t lcap = (scr_bytes / 22u) & ~7u;
+    if (K <= lcap) {
+        unsigned long long *ln = reinterpret_cast<unsigned long long *>(scr), *ls = ln + lcap;
+        float *lh = reinterpret_cast<float *>(ls + lcap);
+        uint16_t *lu = reinterpret_cast<uint16_t *>(lh + lcap);
+        const uint32_t ng = s_gtot;
+#pragma unroll 1
+        for (uint32_t q = (uint32_t)wid; q < ng; q += NW) {
+            const uint32_t g = g_id[q];
+            const uint4 c = __ldcg(h4 + (size_t)g * 32 + lane);
+            const uint32_t u0 = g * GL + 4u * (uint32_t)lane;
+            const unsigned long long n = (unsigned long long)c.x + c.y + c.z + c.w;
+            const unsigned long long s = (unsigned long long)u0 * n + c.y + 2ull * c.z + 3ull * c.w;
+            const uint32_t o = (c.x != 0) + (c.y != 0) + (c.z != 0) + (c.w != 0);
+            unsigned long long in = n, is = s;
+            uint32_t io = o;
+#pragma unroll 1
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long a = __shfl_up_sync(FULL, in, off), b = __shfl_up_sync(FULL, is, off);
+                const uint32_t d = __shfl_up_sync(FULL, io, off);
+                if (lane >= off) { in += a; is += b; io += d; }
+            }
+            unsigned long long n0 = g_n[g] + in - n, s0 = g_s[g] + is - s;
+            uint32_t k = g_k[g] + io - o;
+            const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t c = cs[j];
-            if (!c) continue;
-            const uint32_t u = base + i + j;
-            if (mn == 0xFFFFFFFFu) mn = u;
-            n0 += c;
-            s0 += (unsigned long long)u * c;
-            const unsigned long long n1 = Nt - n0;
-            if (n1 == 0) continue;
-            const unsigned long long s1 = St - s0;
-            const double m0 = __ddiv_rn(__ull2double_rn(s0), __ull2double_rn(n0));
-            const double m1 = __ddiv_rn(__ull2double_rn(s1), __ull2double_rn(n1));
-            const double d = __dsub_rn(m1, m0);
-            const double var =
-                __dmul_rn(__dmul_rn(__dmul_rn(__ull2double_rn(n0), __ull2double_rn(n1)), d), d);
-            if (var > best) { best = var; bt = u; }
+            for (int j = 0; j < 4; ++j) {
+                if (!cs[j]) continue;
+                n0 += cs[j];
+                s0 += (unsigned long long)(u0 + j) * cs[j];
+                ln[k] = n0;
+                ls[k] = s0;
+                lu[k] = (uint16_t)(u0 + j);
+                ++k;
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && K == 1) s_only = lu[0];
+        // bounds of every listed level, the largest lower bound
+        float lo_max = 0.0f;
+#pragma unroll 1
+        for (uint32_t k = (uint32_t)tid; k < K; k += NT) {
+            const unsigned long long n0 = ln[k];
+            float lo = 0.0f, hi = -1.0f;  // the top level (empty upper class) is no candidate
+            if (Nt - n0 != 0) bounds(n0, ls[k], Nt - n0, lo, hi);
+            lh[k] = hi;
+            lo_max = fmaxf(lo_max, lo);
+        }
+        const float LB = block_max(lo_max);
+        // binary64 at the levels whose upper bound reaches LB
+#pragma unroll 1
+        for (uint32_t k = (uint32_t)tid; k < K; k += NT)
+            if (lh[k] >= LB) eval(lu[k], ln[k], ls[k]);
+    } else {
+        // More occupied levels than the list holds: each thread takes PER
+        // consecutive levels; its class prefixes start from its group's
+        // prefix plus the sums of the group's levels below its own.
+        constexpr int PER = HIST_BINS / NT;
+        static_assert(GL % PER == 0, "whole threads per group");
+        const uint32_t base = (uint32_t)tid * PER, g = base / GL;
+        unsigned long long n0b = g_n[g], s0b = g_s[g];
+        if (base % GL) {
+#pragma unroll 4
+            for (uint32_t q = g * (GL / 4); q < base / 4; ++q) {
+                const uint4 c = __ldcg(h4 + q);
+                const unsigned long long n = (unsigned long long)c.x + c.y + c.z + c.w;
+                n0b += n;
+                s0b += (unsigned long long)(4u * q) * n + c.y + 2ull * c.z + 3ull * c.w;
+            }
+        }
+        // the thread's levels, four per load, the next load in flight
+        auto sweep = [&](auto &&level) {
+            uint4 nx = __ldcg(h4 + base / 4);
+#pragma unroll 1
+            for (uint32_t q = 0; q < PER / 4; ++q) {
+                const uint4 c = nx;
+                if (q + 1 < PER / 4) nx = __ldcg(h4 + base / 4 + q + 1);
+                const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (cs[j]) level(base + 4u * q + (uint32_t)j, cs[j]);
+            }
+        };
+        float lo_max = 0.0f;
+        {
+            unsigned long long n0 = n0b, s0 = s0b;
+            sweep([&](uint32_t u, uint32_t c) {
+                n0 += c;
+                s0 += (unsigned long long)u * c;
+                if (Nt - n0 == 0) return;
+                float lo, hi;
+                bounds(n0, s0, Nt - n0, lo, hi);
+                lo_max = fmaxf(lo_max, lo);
+            });
+        }
+        const float LB = block_max(lo_max);
+        // the levels whose upper bound reaches LB go to a list in the
+        // scratch, so that all threads share their binary64 evaluations
+        const uint32_t cap = scr_bytes / 20u;
+        unsigned long long *cn = reinterpret_cast<unsigned long long *>(scr), *cs = cn + cap;
+        uint32_t *cu = reinterpret_cast<uint32_t *>(cs + cap);
+        {
+            unsigned long long n0 = n0b, s0 = s0b;
+            sweep([&](uint32_t u, uint32_t c) {
+                n0 += c;
+                s0 += (unsigned long long)u * c;
+                if (Nt - n0 == 0) return;
+                float lo, hi;
+                bounds(n0, s0, Nt - n0, lo, hi);
+                if (hi < LB) return;  // below the maximum
+                const uint32_t k = atomicAdd(&s_cnt, 1u);
+                if (k < cap) {
+                    cu[k] = u;
+                    cn[k] = n0;
+                    cs[k] = s0;
+                }
+            });
+        }
+        __syncthreads();
+        const uint32_t nc = s_cnt;
+        if (nc <= cap) {
+#pragma unroll 1
+            for (uint32_t k = (uint32_t)tid; k < nc; k += NT) eval(cu[k], cn[k], cs[k]);
+        } else {
+            // more candidates than the scratch holds: each thread its own
+            unsigned long long n0 = n0b, s0 = s0b;
+            sweep([&](uint32_t u, uint32_t c) {
+                n0 += c;
+                s0 += (unsigned long long)u * c;
+                if (Nt - n0 == 0) return;
+                float lo, hi;
+                bounds(n0, s0, Nt - n0, lo, hi);
+                if (hi >= LB) eval(u, n0, s0);
+            });
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(FULL, best, o);
-        const uint32_t ot = __shfl_xor_sync(FULL, bt, o);
-        const uint32_t om = __shfl_xor_sync(FULL, mn, o);
-        if (ov > best || (ov == best && ot < bt)) { best = ov; bt = ot; }
-        mn = min(mn, om);
-    }
-    if (lane == 0) { s_bv[wid] = best; s_bt[wid] = bt; s_mn[wid] = mn; }
+    // the largest variance, then the lowest level that reaches it.  With two
+    // or more occupied levels some level survives the pruning (the one whose
+    // lower bound is LB); with one, t* is that level, with none 0.
+    if (bt != 0xFFFFFFFFu) atomicMax(&s_best, best);
     __syncthreads();
-    if (wid == 0) {
-        best = lane < NT / 32 ? s_bv[lane] : -1.0;
-        bt = lane < NT / 32 ? s_bt[lane] : 0xFFFFFFFFu;
-        mn = lane < NT / 32 ? s_mn[lane] : 0xFFFFFFFFu;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(FULL, best, o);
-            const uint32_t ot = __shfl_xor_sync(FULL, bt, o);
-            const uint32_t om = __shfl_xor_sync(FULL, mn, o);
-            if (ov > best || (ov == best && ot < bt)) { best = ov; bt = ot; }
-            mn = min(mn, om);
-        }
-        if (lane == 0) {
-            stat[ST_THRESH] = bt != 0xFFFFFFFFu ? bt : (mn != 0xFFFFFFFFu ? mn : 0u);
-            if (Nt != nvox) atomicOr(stat + ST_ERROR, ERR_OTSU);
-        }
+    if (bt != 0xFFFFFFFFu && best == s_best) atomicMin(&s_lvl, bt);
+    __syncthreads();
+    if (tid == 0) {
+        stat[ST_THRESH] = s_lvl != 0xFFFFFFFFu ? s_lvl : s_only;
+        if (Nt != nvox) atomicOr(stat + ST_ERROR, ERR_OTSU);
     }
     __syncthreads();
 }
 
-// Merge the block's shared histogram into the volume's bins, then count the
-// block's finished tiles; the block that completes the volume runs Otsu.
+// Merge the block's shared histogram into the volume's bins (and leave it
+// zero for the block's next volume).
 template <int NT>
-__device__ void flush_hist(const BatchHdr *__restrict__ h, uint32_t v, uint32_t ndone, uint32_t *sh,
-                           uint32_t ntiles) {
-    __shared__ uint32_t s_last;
-    const VolDev &V = h->vol[v];
+__device__ void flush_hist(const VolDev &V, uint32_t *sh) {
     __syncthreads();
     for (int i = threadIdx.x; i < HIST_LOW / 4; i += NT) {
         uint4 a = reinterpret_cast<uint4 *>(sh)[i];
@@ -686,21 +889,32 @@ __device__ void flush_hist(const BatchHdr *__restrict__ h, uint32_t v, uint32_t 
             }
         }
     }
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        s_last = 0;
-        if (ndone) {
-            const uint32_t prev = atomicAdd(V.stat + ST_TILES_DONE, ndone);
-            s_last = (prev + ndone == ntiles);
-        }
+}
+
+// Otsu level of every volume of a batch (Segmentation section, ref. [11]:
+// the level that maximises the between-class variance of the smoothed
+// volume's histogram), one block per volume, after all smoothing tiles have
+// merged their bins.  The dynamic shared memory holds the list of occupied
+// levels.
+constexpr int OTSU_NT = 512;
+constexpr uint32_t OTSU_SMEM = 192u * 1024u;
+
+__global__ void __launch_bounds__(OTSU_NT, 1) k_otsu(const BatchHdr *__restrict__ h) {
+    extern __shared__ __align__(16) unsigned char oscr[];
+    const uint32_t nv = h->nvol;
+#pragma unroll 1
+    for (uint32_t v = blockIdx.x; v < nv; v += gridDim.x) {
+        const VolDev &V = h->vol[v];
+        otsu_block<OTSU_NT>(V.hist, V.stat, (uint64_t)V.X * V.Y * V.Z, oscr, OTSU_SMEM);
     }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        otsu_block<NT>(V.hist, V.stat, (uint64_t)V.X * V.Y * V.Z);
-    }
-    __syncthreads();
+}
+
+// The same for one volume given by its bins and status words.
+__global__ void __launch_bounds__(OTSU_NT, 1) k_otsu_one(const uint32_t *__restrict__ hist, uint32_t *stat,
+                                                         uint64_t nvox) {
+    extern __shared__ __align__(16) unsigned char oscr[];
+    otsu_block<OTSU_NT>(hist, stat, nvox, oscr, OTSU_SMEM);
 }
 
 // ----------------------------------------------------------------------------
@@ -737,12 +951,10 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist(const BatchHdr *__res
     const uint32_t te = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / G);
     if (tb >= te) return;
     uint32_t v = find_vol_tile(h, tb);
-    uint32_t ndone = 0;
     const int tz = (int)h->tile_z;
     for (uint32_t t = tb; t < te; ++t) {
         while (v + 1 < h->nvol && t >= h->vol[v + 1].tile_base) {
-            flush_hist<T::NT>(h, v, ndone, sh, h->vol[v].ntx * h->vol[v].nty * h->vol[v].ntz);
-            ndone = 0;
+            flush_hist<T::NT>(h->vol[v], sh);
             ++v;
         }
         const VolDev &V = h->vol[v];
@@ -753,9 +965,8 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist(const BatchHdr *__res
         const int z1 = min(z0 + tz, (int)V.Z);
         HistEmit<true> e{sh, V.hist, V.smooth, V.X, V.Y, 0u, 0u, nullptr, 0, false};
         smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
-        ++ndone;
     }
-    flush_hist<T::NT>(h, v, ndone, sh, h->vol[v].ntx * h->vol[v].nty * h->vol[v].ntz);
+    flush_hist<T::NT>(h->vol[v], sh);
 }
 
 // ----------------------------------------------------------------------------
@@ -799,7 +1010,7 @@ constexpr int FS_LEAD = 3;               // planes staged ahead of the one being
 // plane k: warps may drift FS_S - FS_LEAD planes apart
 constexpr int FS_STAGE = 12 * 66 * 16;   // bytes per stage: 12 rows x 66 chunks (x-tiled) bound all shapes
 constexpr int FS_WARPS = FS_NT / 32;
-constexpr uint32_t FS_WAIT_LIMIT = 1u << 20;  // mbarrier polls before a wait gives up
+constexpr uint32_t FS_WAIT_LIMIT = 1u << 23;  // mbarrier polls (each suspends <= ~256 ns) before a wait gives up
 constexpr size_t FS_SMEM = 4ull * HIST_WORDS + (size_t)FS_S * FS_STAGE + 16ull * 2 * FS_S + 16;
 static_assert((8 * FS_RT / FS_RT + 4) * (FS_RT + 2) * 16 <= FS_STAGE, "x-tiled stage");
 static_assert((FS_NT / FS_RT + 4) * FS_RT * 16 <= FS_STAGE && (FS_NT + 4) * 16 <= FS_STAGE, "stage bound");
@@ -836,12 +1047,23 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
 __device__ __forceinline__ void mbar_arrive_copies(uint64_t *b) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
 }
+// non-blocking test of the given phase
 __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// waits for the phase, suspending the thread for at most about 256 ns
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity), "r"(256u)
         : "memory");
     return ok != 0;
 }
@@ -850,7 +1072,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
 // aborted, or when FS_WAIT_LIMIT polls have passed (then the block is
 // aborted and the volume flagged).
 __device__ __noinline__ bool fs_wait_slow(uint64_t *b, uint32_t parity, volatile uint32_t *abort, uint32_t *stat) {
-    for (uint32_t i = 0; !mbar_test(b, parity); ++i) {
+    for (uint32_t i = 0; !mbar_try(b, parity); ++i) {
         if ((i & 63u) == 0u && *abort) return false;
         if (i >= FS_WAIT_LIMIT) {
             *abort = 1u;
@@ -930,170 +1152,207 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     const uint32_t plane = (uint32_t)X * (uint32_t)Y;  // < 2^32 (X Y Z < 2^32)
     const int n = z1 - z0 + 4;
     const uint32_t ring0 = smem_addr(ring);
-    const uint32_t g0 = S.g;
-    // stage and phase parity of the next plane to stage (is) and to read (rs)
-    uint32_t is = g0 % FS_S, ip = (g0 / FS_S) & 1u;
-    uint32_t rs = is, rp = ip;
-    // copies of tile plane k into stage `is`, once every warp has read the
-    // plane that stage held before (empty phase ip ^ 1, if there was one)
-    auto issue = [&](int k) {
-        const uint32_t gp = g0 + (uint32_t)k;
-        const bool ok = gp < FS_S || S.wait(S.empty + is, ip ^ 1u, stat);
-        const uint32_t zoff = plane * (uint32_t)min(max(z0 - 2 + k, 0), Z - 1);
-        const uint32_t dst = ring0 + is * FS_STAGE;
+    // Tiles run through the ring in whole rounds of FS_S planes (a tile's
+    // planes padded with planes that only keep the barriers' phases in step),
+    // so that the stage of every plane is a compile-time constant; `par` is
+    // the phase parity of the current round.
+    const uint32_t g0 = S.g;                   // a multiple of FS_S
+    const int npad = (n + FS_S - 1) / FS_S * FS_S;
+    // tile plane k into stage ST (full phase fp), once every warp has read
+    // the plane that stage held before (empty phase fp ^ 1, if there was one)
+    auto issue = [&](int k, auto stc, uint32_t fp) {
+        constexpr uint32_t ST = decltype(stc)::value;
+        const bool ok = g0 + (uint32_t)k < (uint32_t)FS_S || S.wait(S.empty + ST, fp ^ 1u, stat);
+        if (ok && k < n) {
+            const uint32_t zoff = plane * (uint32_t)min(max(z0 - 2 + k, 0), Z - 1);
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-            if (ok && cok[u]) cp_async16(dst + cdst[u], reinterpret_cast<uintptr_t>(raw + (csrc[u] + zoff)));
-        mbar_arrive_copies(S.full + is);
-        if (++is == FS_S) { is = 0; ip ^= 1u; }
+            for (int u = 0; u < 2; ++u)
+                if (cok[u]) cp_async16(ring0 + ST * FS_STAGE + cdst[u], reinterpret_cast<uintptr_t>(raw + (csrc[u] + zoff)));
+        }
+        mbar_arrive_copies(S.full + ST);
     };
     uint32_t a0[8], a1[8], a2[8], a3[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) a0[j] = a1[j] = a2[j] = a3[j] = 0u;
     const uint32_t orow = (uint32_t)(y0 + tyc) * (uint32_t)X + (uint32_t)(x0 + 8 * q);
     uint32_t *hc = sh + ((threadIdx.x & 16u) ? (uint32_t)HIST_COPY1 : 0u);
-    for (int k = 0; k < FS_LEAD && k < n; ++k) issue(k);
-    for (int k = 0; k < n; ++k) {
-        if (k + FS_LEAD < n) issue(k + FS_LEAD);
-        const uint32_t st = rs;
-        const bool ok = S.wait(S.full + st, rp, stat);
-        if (++rs == FS_S) { rs = 0; rp ^= 1u; }
+    // plane k from stage ST (full phase fp): nothing but the barriers for
+    // the padding planes k >= n
+    auto step = [&](int k, auto stc, uint32_t fp) {
+        constexpr uint32_t ST = decltype(stc)::value;
+        const bool ok = S.wait(S.full + ST, fp, stat);
         // a warp whose wait gave up skips the work (the block stays in step
         // for its block barriers); warp-uniform, so that the shuffles below
         // see every lane
-        if (!__all_sync(FULL, ok)) continue;
-        const unsigned char *stg = ring + st * FS_STAGE;
-        // y pass on packed pairs
-        const unsigned char *cp = stg + colo;
-        const uint4 r0 = *reinterpret_cast<const uint4 *>(cp);
-        const uint4 r1 = *reinterpret_cast<const uint4 *>(cp + RB);
-        const uint4 r2 = *reinterpret_cast<const uint4 *>(cp + 2 * RB);
-        const uint4 r3 = *reinterpret_cast<const uint4 *>(cp + 3 * RB);
-        const uint4 r4 = *reinterpret_cast<const uint4 *>(cp + 4 * RB);
-        uint32_t yw[4];
-        yw[0] = fs_ysum(r0.x, r1.x, r2.x, r3.x, r4.x);
-        yw[1] = fs_ysum(r0.y, r1.y, r2.y, r3.y, r4.y);
-        yw[2] = fs_ysum(r0.z, r1.z, r2.z, r3.z, r4.z);
-        yw[3] = fs_ysum(r0.w, r1.w, r2.w, r3.w, r4.w);
-        uint32_t chk = (r0.x | r0.y | r0.z | r0.w | r1.x | r1.y | r1.z | r1.w | r2.x | r2.y) |
-                       (r2.z | r2.w | r3.x | r3.y | r3.z | r3.w | r4.x | r4.y | r4.z | r4.w);
-        uint32_t hw = 0u;  // packed y-sum of the neighbour word this lane reads itself
-        if (ownL || ownR) {
-            const unsigned char *hp = stg + fixo;
-            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(hp);
-            const uint32_t w1 = *reinterpret_cast<const uint32_t *>(hp + RB);
-            const uint32_t w2 = *reinterpret_cast<const uint32_t *>(hp + 2 * RB);
-            const uint32_t w3 = *reinterpret_cast<const uint32_t *>(hp + 3 * RB);
-            const uint32_t w4 = *reinterpret_cast<const uint32_t *>(hp + 4 * RB);
-            hw = fs_ysum(w0, w1, w2, w3, w4);
-            chk |= w0 | w1 | w2 | w3 | w4;
+        if (!__all_sync(FULL, ok)) return;
+        if (k >= n) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(S.empty + ST);
+            return;
         }
-        const uint32_t nl = __shfl_up_sync(FULL, yw[3], 1);
-        const uint32_t nr = __shfl_down_sync(FULL, yw[0], 1);
-        uint32_t v[12];
-        if (!__any_sync(FULL, act && (chk & 0xF000F000u) != 0u)) {
-            const uint32_t wl = ownL ? hw : (edgeL ? __byte_perm(yw[0], 0u, 0x1010u) : nl);
-            const uint32_t wr = ownR ? hw : (edgeR ? __byte_perm(yw[3], 0u, 0x3232u) : nr);
-            v[0] = wl & 0xFFFFu;
-            v[1] = wl >> 16;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                v[2 + 2 * i] = yw[i] & 0xFFFFu;
-                v[3 + 2 * i] = yw[i] >> 16;
-            }
-            v[10] = wr & 0xFFFFu;
-            v[11] = wr >> 16;
-        } else {
-            // a raw value of 4096 or more in this warp's part of the plane:
-            // its y pass again, in 32-bit lanes
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const unsigned char *wp = cp + 4 * i;
-                fs_ysum32(*reinterpret_cast<const uint32_t *>(wp), *reinterpret_cast<const uint32_t *>(wp + RB),
-                          *reinterpret_cast<const uint32_t *>(wp + 2 * RB),
-                          *reinterpret_cast<const uint32_t *>(wp + 3 * RB),
-                          *reinterpret_cast<const uint32_t *>(wp + 4 * RB), v[2 + 2 * i], v[3 + 2 * i]);
-            }
-            uint32_t hlo = 0u, hhi = 0u;
+            const unsigned char *stg = ring + ST * FS_STAGE;
+            // y pass on packed pairs
+            const unsigned char *cp = stg + colo;
+            const uint4 r0 = *reinterpret_cast<const uint4 *>(cp);
+            const uint4 r1 = *reinterpret_cast<const uint4 *>(cp + RB);
+            const uint4 r2 = *reinterpret_cast<const uint4 *>(cp + 2 * RB);
+            const uint4 r3 = *reinterpret_cast<const uint4 *>(cp + 3 * RB);
+            const uint4 r4 = *reinterpret_cast<const uint4 *>(cp + 4 * RB);
+            uint32_t yw[4];
+            yw[0] = fs_ysum(r0.x, r1.x, r2.x, r3.x, r4.x);
+            yw[1] = fs_ysum(r0.y, r1.y, r2.y, r3.y, r4.y);
+            yw[2] = fs_ysum(r0.z, r1.z, r2.z, r3.z, r4.z);
+            yw[3] = fs_ysum(r0.w, r1.w, r2.w, r3.w, r4.w);
+            uint32_t chk = (r0.x | r0.y | r0.z | r0.w | r1.x | r1.y | r1.z | r1.w | r2.x | r2.y) |
+                           (r2.z | r2.w | r3.x | r3.y | r3.z | r3.w | r4.x | r4.y | r4.z | r4.w);
+            uint32_t hw = 0u;  // packed y-sum of the neighbour word this lane reads itself
             if (ownL || ownR) {
                 const unsigned char *hp = stg + fixo;
-                fs_ysum32(*reinterpret_cast<const uint32_t *>(hp), *reinterpret_cast<const uint32_t *>(hp + RB),
-                          *reinterpret_cast<const uint32_t *>(hp + 2 * RB),
-                          *reinterpret_cast<const uint32_t *>(hp + 3 * RB),
-                          *reinterpret_cast<const uint32_t *>(hp + 4 * RB), hlo, hhi);
+                const uint32_t w0 = *reinterpret_cast<const uint32_t *>(hp);
+                const uint32_t w1 = *reinterpret_cast<const uint32_t *>(hp + RB);
+                const uint32_t w2 = *reinterpret_cast<const uint32_t *>(hp + 2 * RB);
+                const uint32_t w3 = *reinterpret_cast<const uint32_t *>(hp + 3 * RB);
+                const uint32_t w4 = *reinterpret_cast<const uint32_t *>(hp + 4 * RB);
+                hw = fs_ysum(w0, w1, w2, w3, w4);
+                chk |= w0 | w1 | w2 | w3 | w4;
             }
-            const uint32_t l0 = __shfl_up_sync(FULL, v[8], 1), l1 = __shfl_up_sync(FULL, v[9], 1);
-            const uint32_t q0 = __shfl_down_sync(FULL, v[2], 1), q1 = __shfl_down_sync(FULL, v[3], 1);
-            v[0] = ownL ? hlo : (edgeL ? v[2] : l0);
-            v[1] = ownL ? hhi : (edgeL ? v[2] : l1);
-            v[10] = ownR ? hlo : (edgeR ? v[9] : q0);
-            v[11] = ownR ? hhi : (edgeR ? v[9] : q1);
-        }
-        // this warp is done with the stage
-        __syncwarp();
-        if (lane == 0) mbar_arrive(S.empty + st);
-        // x pass, then the z pass in scatter form; a3 starts each output's
-        // sum at 2048 so that s = sum >> 12 rounds half up
-        uint32_t s[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t p = v[j] + v[j + 4] + 4u * (v[j + 1] + v[j + 3]) + 6u * v[j + 2];
-            const uint32_t o = a0[j] + p;
-            a0[j] = a1[j] + 4u * p;
-            a1[j] = a2[j] + 6u * p;
-            a2[j] = a3[j] + 4u * p;
-            a3[j] = p + 2048u;
-            s[j] = o >> 12;
-        }
-        if (k >= 4) {
-            const uint32_t vmax = max(max(max(s[0], s[1]), max(s[2], s[3])), max(max(s[4], s[5]), max(s[6], s[7])));
-            const bool fast = __all_sync(FULL, !emit_ok || vmax < (uint32_t)HIST_LOW);
-            if (wmax) {
-                // the largest value of each 32-voxel mask word (four lanes),
-                // so that the threshold pass reads only words above t*
-                uint32_t wm = emit_ok ? vmax : 0u;
-                wm = max(wm, __shfl_xor_sync(FULL, wm, 1));
-                wm = max(wm, __shfl_xor_sync(FULL, wm, 2));
-                if (emit_ok && (q & 3) == 0)
-                    wmax[(uint32_t)((z0 + k - 4) * Y + y0 + ty) * W + (uint32_t)((x0 + 8 * q) >> 5)] = (uint16_t)wm;
+            const uint32_t nl = __shfl_up_sync(FULL, yw[3], 1);
+            const uint32_t nr = __shfl_down_sync(FULL, yw[0], 1);
+            uint32_t v[12];
+            if (!__any_sync(FULL, act && (chk & 0xF000F000u) != 0u)) {
+                const uint32_t wl = ownL ? hw : (edgeL ? __byte_perm(yw[0], 0u, 0x1010u) : nl);
+                const uint32_t wr = ownR ? hw : (edgeR ? __byte_perm(yw[3], 0u, 0x3232u) : nr);
+                v[0] = wl & 0xFFFFu;
+                v[1] = wl >> 16;
+    #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    v[2 + 2 * i] = yw[i] & 0xFFFFu;
+                    v[3 + 2 * i] = yw[i] >> 16;
+                }
+                v[10] = wr & 0xFFFFu;
+                v[11] = wr >> 16;
+            } else {
+                // a raw value of 4096 or more in this warp's part of the plane:
+                // its y pass again, in 32-bit lanes
+    #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const unsigned char *wp = cp + 4 * i;
+                    fs_ysum32(*reinterpret_cast<const uint32_t *>(wp), *reinterpret_cast<const uint32_t *>(wp + RB),
+                              *reinterpret_cast<const uint32_t *>(wp + 2 * RB),
+                              *reinterpret_cast<const uint32_t *>(wp + 3 * RB),
+                              *reinterpret_cast<const uint32_t *>(wp + 4 * RB), v[2 + 2 * i], v[3 + 2 * i]);
+                }
+                uint32_t hlo = 0u, hhi = 0u;
+                if (ownL || ownR) {
+                    const unsigned char *hp = stg + fixo;
+                    fs_ysum32(*reinterpret_cast<const uint32_t *>(hp), *reinterpret_cast<const uint32_t *>(hp + RB),
+                              *reinterpret_cast<const uint32_t *>(hp + 2 * RB),
+                              *reinterpret_cast<const uint32_t *>(hp + 3 * RB),
+                              *reinterpret_cast<const uint32_t *>(hp + 4 * RB), hlo, hhi);
+                }
+                const uint32_t l0 = __shfl_up_sync(FULL, v[8], 1), l1 = __shfl_up_sync(FULL, v[9], 1);
+                const uint32_t q0 = __shfl_down_sync(FULL, v[2], 1), q1 = __shfl_down_sync(FULL, v[3], 1);
+                v[0] = ownL ? hlo : (edgeL ? v[2] : l0);
+                v[1] = ownL ? hhi : (edgeL ? v[2] : l1);
+                v[10] = ownR ? hlo : (edgeR ? v[9] : q0);
+                v[11] = ownR ? hhi : (edgeR ? v[9] : q1);
             }
-            if (emit_ok) {
-                *reinterpret_cast<uint4 *>(osm + (orow + plane * (uint32_t)(z0 + k - 4))) =
-                    make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
-                if (fast) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) atomicAdd(hc + s[j], 1u);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const uint32_t u = min(s[j], 65535u);  // (always true for exact sums)
-                        if (u < (uint32_t)HIST_LOW) {
-                            atomicAdd(hc + u, 1u);
-                        } else {
-                            const uint32_t w = HIST_PAIRS + ((u - HIST_LOW) >> 1);
-                            const uint32_t sft = (u & 1u) << 4;
-                            const uint32_t old = atomicAdd(sh + w, 1u << sft);
-                            if (((old >> sft) & 0xFFFFu) == 0x7FFFu) {
-                                atomicSub(sh + w, 0x8000u << sft);
-                                atomicAdd(ghist + u, 0x8000u);
+            // this warp is done with the stage
+            __syncwarp();
+            if (lane == 0) mbar_arrive(S.empty + ST);
+            // x pass, then the z pass in scatter form; a3 starts each output's
+            // sum at 2048 so that s = sum >> 12 rounds half up
+            uint32_t s[8];
+    #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t p = v[j] + v[j + 4] + 4u * (v[j + 1] + v[j + 3]) + 6u * v[j + 2];
+                const uint32_t o = a0[j] + p;
+                a0[j] = a1[j] + 4u * p;
+                a1[j] = a2[j] + 6u * p;
+                a2[j] = a3[j] + 4u * p;
+                a3[j] = p + 2048u;
+                s[j] = o >> 12;
+            }
+            if (k >= 4) {
+                const uint32_t vmax = max(max(max(s[0], s[1]), max(s[2], s[3])), max(max(s[4], s[5]), max(s[6], s[7])));
+                const bool fast = __all_sync(FULL, !emit_ok || vmax < (uint32_t)HIST_LOW);
+                if (wmax) {
+                    // the largest value of each 32-voxel mask word (four lanes),
+                    // so that the threshold pass reads only words above t*
+                    uint32_t wm = emit_ok ? vmax : 0u;
+                    wm = max(wm, __shfl_xor_sync(FULL, wm, 1));
+                    wm = max(wm, __shfl_xor_sync(FULL, wm, 2));
+                    if (emit_ok && (q & 3) == 0)
+                        wmax[(uint32_t)((z0 + k - 4) * Y + y0 + ty) * W + (uint32_t)((x0 + 8 * q) >> 5)] = (uint16_t)wm;
+                }
+                if (emit_ok) {
+                    *reinterpret_cast<uint4 *>(osm + (orow + plane * (uint32_t)(z0 + k - 4))) =
+                        make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
+                    if (fast) {
+    #pragma unroll
+                        for (int j = 0; j < 8; ++j) atomicAdd(hc + s[j], 1u);
+                    } else {
+    #pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const uint32_t u = min(s[j], 65535u);  // (always true for exact sums)
+                            if (u < (uint32_t)HIST_LOW) {
+                                atomicAdd(hc + u, 1u);
+                            } else {
+                                const uint32_t w = HIST_PAIRS + ((u - HIST_LOW) >> 1);
+                                const uint32_t sft = (u & 1u) << 4;
+                                const uint32_t old = atomicAdd(sh + w, 1u << sft);
+                                if (((old >> sft) & 0xFFFFu) == 0x7FFFu) {
+                                    atomicSub(sh + w, 0x8000u << sft);
+                                    atomicAdd(ghist + u, 0x8000u);
+                                }
                             }
                         }
                     }
                 }
             }
-        }
+    };
+    using C0 = std::integral_constant<uint32_t, 0>;
+    using C1 = std::integral_constant<uint32_t, 1>;
+    using C2 = std::integral_constant<uint32_t, 2>;
+    using C3 = std::integral_constant<uint32_t, 3>;
+    using C4 = std::integral_constant<uint32_t, 4>;
+    static_assert(FS_S == 5 && FS_LEAD == 3, "the round below stages three planes ahead in a ring of five");
+    uint32_t par = (g0 / FS_S) & 1u;
+    issue(0, C0(), par);
+    issue(1, C1(), par);
+    issue(2, C2(), par);
+    for (int k0 = 0; k0 < npad; k0 += FS_S) {
+        if (k0 + 3 < npad) issue(k0 + 3, C3(), par);
+        step(k0, C0(), par);
+        if (k0 + 4 < npad) issue(k0 + 4, C4(), par);
+        step(k0 + 1, C1(), par);
+        if (k0 + 5 < npad) issue(k0 + 5, C0(), par ^ 1u);
+        step(k0 + 2, C2(), par);
+        if (k0 + 6 < npad) issue(k0 + 6, C1(), par ^ 1u);
+        step(k0 + 3, C3(), par);
+        if (k0 + 7 < npad) issue(k0 + 7, C2(), par ^ 1u);
+        step(k0 + 4, C4(), par);
+        par ^= 1u;
     }
-    S.g = g0 + (uint32_t)n;
+    S.g = g0 + (uint32_t)npad;
 }
+
+constexpr uint32_t FS_GROUP = 1;
 
 __global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__restrict__ h) {
     extern __shared__ __align__(128) unsigned char dsm[];
     uint32_t *sh = reinterpret_cast<uint32_t *>(dsm);
     unsigned char *ring = dsm + 4 * HIST_WORDS;
     uint64_t *bars = reinterpret_cast<uint64_t *>(ring + FS_S * FS_STAGE);
+    // Groups of FS_GROUP consecutive blocks share a contiguous range of
+    // tiles and take its tiles in turn, so that y-adjacent tiles of a volume
+    // are smoothed at the same time and the rows one stages as halo are
+    // still in L2 when its neighbour stages them as its own.
     const uint32_t nt = h->fs_tiles, G = gridDim.x;
-    const uint32_t tb = (uint32_t)(((uint64_t)nt * blockIdx.x) / G);
-    const uint32_t te = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / G);
+    const uint32_t gs = G % FS_GROUP == 0 ? FS_GROUP : 1u;
+    const uint32_t nq = G / gs, q = blockIdx.x / gs, m = blockIdx.x % gs;
+    const uint32_t tb = (uint32_t)(((uint64_t)nt * q) / nq) + m;
+    const uint32_t te = (uint32_t)(((uint64_t)nt * (q + 1)) / nq);
     if (tb >= te) return;
     FsSync S{bars, bars + FS_S, reinterpret_cast<volatile uint32_t *>(bars + 2 * FS_S), 0u};
     if (threadIdx.x == 0) {
@@ -1108,12 +1367,9 @@ __global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__rest
         reinterpret_cast<uint4 *>(sh)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     uint32_t v = find_vol_fs(h, tb);
-    uint32_t ndone = 0;
-    for (uint32_t t = tb; t < te; ++t) {
+    for (uint32_t t = tb; t < te; t += gs) {
         while (v + 1 < h->nvol && t >= h->vol[v + 1].fs_base) {
-            const VolDev &P = h->vol[v];
-            flush_hist<FS_NT>(h, v, ndone, sh, P.fs_ntx * P.fs_nty * P.fs_ntz);
-            ndone = 0;
+            flush_hist<FS_NT>(h->vol[v], sh);
             ++v;
         }
         const VolDev &V = h->vol[v];
@@ -1128,11 +1384,9 @@ __global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__rest
         } else {
             smooth_rows_tile<0, 0>(V, ix, iy, z0, z1, ring, sh, S);
         }
-        ++ndone;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy into this block's shared memory outlives it
-    const VolDev &P = h->vol[v];
-    flush_hist<FS_NT>(h, v, ndone, sh, P.fs_ntx * P.fs_nty * P.fs_ntz);
+    flush_hist<FS_NT>(h->vol[v], sh);
 }
 
 // Foreground bits of 8 consecutive smoothed voxels (a 16-byte load, two per
@@ -3584,6 +3838,8 @@ cudaError_t launch_tile_kernels(const BatchHdr *d, const LaunchPlan &p, cudaStre
     if (p.rows) k_smooth_rows<<<p.grid_hist, FS_NT, FS_SMEM, s>>>(d);
     rec();
     if (p.tiles) k_smooth_hist<TY><<<p.grid_hist, Tile<TY>::NT, hist_smem_bytes(TY), s>>>(d);
+    rec();
+    k_otsu<<<p.grid_vols, OTSU_NT, OTSU_SMEM, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -3611,6 +3867,8 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
     SEG_CFG(64)
 #undef SEG_CFG
     e = cudaFuncSetAttribute(k_smooth_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_otsu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OTSU_SMEM);
     if (e != cudaSuccess) return e;
     auto resident = [&](const void *fn, int threads, int *grid) -> cudaError_t {
         int per_sm = 0;
@@ -3676,6 +3934,7 @@ cudaError_t launch_tile_probe(const BatchHdr *d, const LaunchPlan &p, cudaStream
         case 32: k_smooth_hist<32><<<p.grid_hist, Tile<32>::NT, hist_smem_bytes(32), s>>>(d); break;
         default: k_smooth_hist<64><<<p.grid_hist, Tile<64>::NT, hist_smem_bytes(64), s>>>(d); break;
     }
+    k_otsu<<<p.grid_vols, OTSU_NT, OTSU_SMEM, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -3825,7 +4084,7 @@ constexpr int NOALLOC_WORDS = HIST_BINS + ST_WORDS;  // 262,208 bytes per device
 // Every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
 
-constexpr int NOALLOC_TY = 64;
+constexpr int NOALLOC_TY = 32;
 constexpr int NOALLOC_TZ = 64;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
@@ -3855,7 +4114,6 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist_noalloc(const __grid_
     const uint32_t te = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / G);
     if (tb >= te) return;
     const int tz = (int)h->tile_z;
-    uint32_t ndone = 0;
     for (uint32_t t = tb; t < te; ++t) {
         const uint32_t ix = t % V.ntx, rest = t / V.ntx;
         const uint32_t iy = rest % V.nty, iz = rest / V.nty;
@@ -3863,9 +4121,8 @@ __global__ void __launch_bounds__(8 * TY, 1) k_smooth_hist_noalloc(const __grid_
         const int z1 = min(z0 + tz, (int)V.Z);
         HistEmit<false> e{sh, V.hist, nullptr, V.X, V.Y, 0u, 0u, nullptr, 0, false};
         smooth_tile<TY>(V.raw, V.X, V.Y, V.Z, (int)ix * TILE_X, (int)iy * TY, z0, z1, spx, R, e);
-        ++ndone;
     }
-    flush_hist<T::NT>(h, 0, ndone, sh, V.ntx * V.nty * V.ntz);
+    flush_hist<T::NT>(V, sh);
 }
 
 // Once per device, with that device current: resolve the scratch address and
@@ -3880,6 +4137,8 @@ int noalloc_setup(int dev, uint32_t **ptr, int *sms) {
         e = cudaFuncSetAttribute(k_smooth_hist_noalloc<NOALLOC_TY>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)hist_smem_bytes(NOALLOC_TY));
+        if (e != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
+        e = cudaFuncSetAttribute(k_otsu_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OTSU_SMEM);
         if (e != cudaSuccess) { cudaGetLastError(); return SEG_ECUDA; }
         int n = 0;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
@@ -3931,6 +4190,7 @@ extern "C" int seg_otsu_threshold_noalloc(const uint16_t *d_voxels, seg_dims dim
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * NOALLOC_WORDS, s);
     if (e == cudaSuccess) {
         k_smooth_hist_noalloc<NOALLOC_TY><<<sms, Tile<NOALLOC_TY>::NT, hist_smem_bytes(NOALLOC_TY), s>>>(hdr);
+        k_otsu_one<<<1, OTSU_NT, OTSU_SMEM, s>>>(V.hist, V.stat, n);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)

@@ -176,6 +176,37 @@ def test_word_maxima_threshold_many_row_tiles(seg):
         seg.seg_destroy(c)
 
 
+def test_otsu_flat_maxima(seg, ctx):
+    # Histograms whose between-class variance is nearly flat around its
+    # maximum (unimodal noise of many widths, two modes of nearly equal
+    # weight, a few isolated levels): many levels come close to the maximum,
+    # so the binary64 Otsu sweep must still pick the oracle's level among
+    # them.  Row-aligned and ragged shapes (both smoothing kernels).  The
+    # uniform 16-bit noise and the ramp occupy 10000 to 65000 levels, more
+    # than the Otsu kernel lists in shared memory (its per-thread path); the
+    # others occupy 4 to 1400 (its listed path).
+    rng = np.random.default_rng(123)
+    vols = []
+    for dims in [(64, 40, 9), (67, 40, 9), (256, 33, 5)]:
+        X, Y, Z = dims
+        for lo, hi in [(0, 65536), (1000, 1100), (30000, 30008), (0, 4096)]:
+            vols.append(rng.integers(lo, hi, size=(Z, Y, X), dtype=np.uint16))
+        a = np.full((Z, Y, X), 500, np.uint16)
+        a[:, :, X // 2:] = 3000
+        a[:, Y // 2:, :] += rng.integers(0, 3, size=(Z, Y - Y // 2, X), dtype=np.uint16)
+        vols.append(a)
+        b = rng.normal(800, 30, size=(Z, Y, X)).clip(0, 65535).astype(np.uint16)
+        b[: Z // 2] = rng.normal(2000, 30, size=(Z // 2, Y, X)).clip(0, 65535).astype(np.uint16)
+        vols.append(b)
+    # a ramp through all 65536 values: the smoothing keeps its interior, so
+    # almost every level is occupied about equally (the variance peaks in the
+    # middle, where neighbouring levels come within rounding of each other)
+    X, Y, Z = 256, 256, 3
+    r = (np.arange(Y)[:, None] * X + np.arange(X)[None, :]).astype(np.uint16)
+    vols.append(np.broadcast_to(r, (Z, Y, X)).copy())
+    check(seg, ctx, vols, m=1, what="flat Otsu maxima")
+
+
 def test_time_lapse_frame_smoothed(seg, ctx):
     import synth
     tl = synth.TimeLapse()
