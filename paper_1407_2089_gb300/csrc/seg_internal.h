@@ -39,7 +39,8 @@ enum ErrBits : uint32_t {
 
 constexpr int TILE_X = 64;        // smoothing tile width (outputs along x)
 constexpr uint32_t UNION_LIMIT = 1u << 24;  // union-find retries before ERR_UNION
-constexpr int ROW_TILE = 256;     // rows per row tile (run kernels)
+constexpr int ROW_TILE = 256;     // rows per row tile (run kernels; their block size)
+constexpr int ROW_TILE_MIN = 32;  // smallest row tile (batches with few rows)
 constexpr int HIST_BINS = 65536;
 // Union-find bricks: BRICK_Y x BRICK_Z rows (one thread each) whose runs are
 // united in shared memory when there are at most BRICK_CAP of them.
@@ -72,7 +73,7 @@ struct VolDev {
     uint32_t min_volume;
     uint32_t union_limit;     // retries before a union gives up (ERR_UNION)
     uint32_t ntx, nty, ntz;   // smoothing tiles per axis (k_smooth_hist; 0 for row-aligned volumes)
-    uint32_t nrt;             // row tiles
+    uint32_t nrt;             // row tiles (of BatchHdr::row_tile rows)
     uint32_t tile_base;       // first flat smoothing-tile index
     // k_smooth_rows (rows 16-byte aligned: X % 8 == 0 and an aligned input);
     // fs_ntx = 0 for the other volumes
@@ -161,6 +162,8 @@ struct BatchHdr {
     uint32_t dt_items[DT_NK]; // distance-map items per DtKernel over the batch
     uint32_t mrf_tiles;       // k_mrf_stats tiles over the batch
     uint32_t mrf_ctiles;      // k_mrf_step tiles over the batch
+    uint32_t row_tile;        // rows per row tile: ROW_TILE, or down to ROW_TILE_MIN
+                              // so that a batch with few rows still fills the GPU
     VolDev vol[1];       // nvol entries
 };
 

@@ -1337,7 +1337,7 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     S.g = g0 + (uint32_t)npad;
 }
 
-constexpr uint32_t FS_GROUP = 1;
+constexpr uint32_t FS_GROUP = 4;
 
 __global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__restrict__ h) {
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -1415,8 +1415,8 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
-        const uint32_t row0 = lt * ROW_TILE;
-        const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
+        const uint32_t row0 = lt * h->row_tile;
+        const uint32_t nrows = min(h->row_tile, V.rows - row0);
         const uint32_t X = V.X, W = V.W, t = V.stat[ST_THRESH];
         const bool vec = (X & 7u) == 0u;
         uint32_t wtot = 0;
@@ -1626,11 +1626,12 @@ __global__ void __launch_bounds__(ROW_TILE) k_row_runs(const BatchHdr *__restric
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
-        const uint32_t row = lt * ROW_TILE + threadIdx.x;
-        const uint32_t cnt = row < V.rows ? V.rowoff[row] : 0u;
+        const uint32_t row = lt * h->row_tile + threadIdx.x;
+        const bool own = threadIdx.x < h->row_tile && row < V.rows;
+        const uint32_t cnt = own ? V.rowoff[row] : 0u;
         uint32_t tot;
         const uint32_t ex = block_exscan<ROW_TILE>(cnt, &tot, sbuf);
-        if (row < V.rows) {
+        if (own) {
             const uint32_t off = V.tsum[lt] + ex;
             V.rowoff[row] = off;
             if (row == V.rows - 1) V.rowoff[V.rows] = off + cnt;
@@ -1937,9 +1938,9 @@ __global__ void __launch_bounds__(ROW_TILE) k_keep_count(const BatchHdr *__restr
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
-        const uint32_t row = lt * ROW_TILE + threadIdx.x;
+        const uint32_t row = lt * h->row_tile + threadIdx.x;
         uint32_t cnt = 0;
-        if (row < V.rows) {
+        if (threadIdx.x < h->row_tile && row < V.rows) {
             const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
             for (uint32_t r = ib; r < ie; ++r)
                 cnt += (V.run_par[r] == r && V.run_aux[r] >= V.min_volume) ? 1u : 0u;
@@ -1957,11 +1958,12 @@ __global__ void __launch_bounds__(ROW_TILE) k_rank(const BatchHdr *__restrict__ 
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
-        const uint32_t row = lt * ROW_TILE + threadIdx.x;
-        const uint32_t cnt = row < V.rows ? V.rowk[row] : 0u;
+        const uint32_t row = lt * h->row_tile + threadIdx.x;
+        const bool own = threadIdx.x < h->row_tile && row < V.rows;
+        const uint32_t cnt = own ? V.rowk[row] : 0u;
         uint32_t tot;
         const uint32_t ex = block_exscan<ROW_TILE>(cnt, &tot, sbuf);
-        if (row < V.rows) {
+        if (own) {
             uint32_t lab = V.tkeep[lt] + ex;
             const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
             for (uint32_t r = ib; r < ie; ++r) {
@@ -2050,8 +2052,8 @@ __global__ void __launch_bounds__(ROW_TILE, 6) k_label_features(const BatchHdr *
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, rt)];
         const uint32_t lt = rt - V.rt_base;
-        const uint32_t row0 = lt * ROW_TILE;
-        const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
+        const uint32_t row0 = lt * h->row_tile;
+        const uint32_t nrows = min(h->row_tile, V.rows - row0);
         __syncthreads();  // previous tile done with soff, srx, slab and T
         for (uint32_t i = tid; i <= nrows; i += ROW_TILE) soff[i] = V.rowoff[row0 + i];
         T.key[tid] = 0u;
@@ -2631,8 +2633,8 @@ __global__ void __launch_bounds__(ROW_TILE) k_erode(const BatchHdr *__restrict__
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
         const VolDev &V = h->vol[VI.find(h, rt)];
         if (V.cl_r == 0) continue;  // the same for the whole block
-        const uint32_t lt = rt - V.rt_base, row0 = lt * ROW_TILE;
-        const uint32_t nrows = min((uint32_t)ROW_TILE, V.rows - row0);
+        const uint32_t lt = rt - V.rt_base, row0 = lt * h->row_tile;
+        const uint32_t nrows = min(h->row_tile, V.rows - row0);
         const int rho = (int)V.cl_r, W = (int)V.W, WE = W + 2, Y = (int)V.Y;
         const int YE = Y + 2 * rho;
         // rows of at most 16 words share a warp: segments of seg lanes

@@ -78,7 +78,7 @@ VolGeom geom(seg_dims d, uint32_t min_volume, uint32_t dn_r, uint32_t cl_r, cons
     g.X = d.x; g.Y = d.y; g.Z = d.z;
     g.W = (uint32_t)cdiv(d.x, 32);
     g.rows = d.y * d.z;
-    g.nrt = (uint32_t)cdiv(g.rows, ROW_TILE);
+    g.nrt = (uint32_t)cdiv(g.rows, ROW_TILE_MIN);  // room for the smallest row tile
     g.n = (uint64_t)d.x * d.y * d.z;
     g.r_cap = (uint64_t)g.rows * cdiv(d.x, 2);
     // 26-separated components: at most one per 2x2x2 block; each surviving
@@ -339,9 +339,22 @@ uint32_t batch_rows_tile_z(const seg_ctx *ctx, const Batch &b) {
     }
 }
 
+// Rows per row tile for a batch: ROW_TILE, halved while the batch has fewer
+// than two row tiles per multiprocessor (a lone small volume), down to
+// ROW_TILE_MIN.
+uint32_t batch_row_tile(const seg_ctx *ctx, const Batch &b) {
+    uint64_t rows = 0;
+    for (const Request *r : b.reqs)
+        for (uint32_t c = 0; c < r->C; ++c) rows += r->g[c].rows;
+    uint32_t rt = ROW_TILE;
+    while (rt > (uint32_t)ROW_TILE_MIN && cdiv(rows, rt) < 2ull * (uint64_t)ctx->sms) rt /= 2;
+    return rt;
+}
+
 void build_header(seg_ctx *ctx, Batch &b) {
     BatchHdr *h = b.slot->h_hdr;
     const uint32_t ty = (uint32_t)ctx->plan.tile_y, tz = batch_tile_z(ctx, b), fz = batch_rows_tile_z(ctx, b);
+    const uint32_t rtile = batch_row_tile(ctx, b);
     uint32_t fst = 0;
     uint32_t v = 0, tiles = 0, rts = 0, bks = 0, bts = 0, dn[3] = {0, 0, 0}, dnt = 0, cl = 0;
     uint32_t dtb[DT_NK] = {0, 0, 0, 0, 0, 0};
@@ -477,7 +490,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
             }
             V.fs_base = fst;
             fst += V.fs_ntx * V.fs_nty * V.fs_ntz;
-            V.nrt = g.nrt;
+            V.nrt = (uint32_t)cdiv(g.rows, rtile);
             V.tile_base = tiles;
             V.rt_base = rts;
             V.nby = (uint32_t)cdiv(g.Y, BRICK_Y);
@@ -494,7 +507,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
             }
             V.bt_base = bts;
             tiles += V.ntx * V.nty * V.ntz;
-            rts += g.nrt;
+            rts += V.nrt;
             bks += V.nbk;
             bts += V.nbt;
         }
@@ -503,6 +516,7 @@ void build_header(seg_ctx *ctx, Batch &b) {
     h->ntiles = tiles;
     h->fs_tiles = fst;
     h->nrowtiles = rts;
+    h->row_tile = rtile;
     h->nbricks = bks;
     h->nbtasks = bts;
     h->dn_items[0] = dn[0];

@@ -50,6 +50,25 @@ def test_single_frame_workload(seg, ctx):
     assert ref.n_cells >= 30
 
 
+# Row counts Y*Z that take each row-tile size on a 152-multiprocessor GPU: a
+# batch with fewer than two row tiles per multiprocessor halves its tile
+# (256 rows) down to 32, so the run kernels still fill the GPU.  Tall, narrow
+# volumes with many runs per tile and cells that cross tile boundaries.
+@pytest.mark.parametrize("dims", [(8, 100, 900), (16, 300, 200), (32, 200, 150), (40, 64, 100), (7, 33, 20)])
+def test_row_tile_sizes(seg, ctx, dims):
+    X, Y, Z = dims
+    rng = np.random.default_rng(X * Y + Z)
+    vol = rng.normal(300, 30, size=(Z, Y, X)).clip(0, 65535).astype(np.uint16)
+    for _ in range(Y * Z // 400):
+        c = rng.integers(0, [Z, Y, X])
+        r = rng.integers(1, 4, size=3)
+        sl = tuple(slice(max(0, c[i] - r[i]), c[i] + r[i] + 1) for i in range(3))
+        vol[sl] = rng.integers(1500, 3000)
+    for m in (1, 10):
+        lab, cells, thr = run(seg, ctx, vol, m)
+        assert_matches_oracle(vol, lab, cells, thr, min_volume=m, what="%s m=%d" % (dims, m))
+
+
 @pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 2), (31, 1, 7), (33, 40, 3), (64, 16, 5),
                                   (65, 17, 9), (130, 70, 21), (200, 3, 66), (97, 131, 40)])
 def test_ragged_shapes(seg, ctx, dims):
