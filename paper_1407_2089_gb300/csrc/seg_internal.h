@@ -172,7 +172,7 @@ inline size_t batch_bytes(uint32_t nvol) {
 }
 
 // Host-side description of the kernels launched for one batch.
-constexpr int NUM_KERNELS = 27;
+constexpr int NUM_KERNELS = 25;
 extern const char *const kKernelNames[NUM_KERNELS];
 
 struct LaunchPlan {

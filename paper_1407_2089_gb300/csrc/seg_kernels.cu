@@ -8,22 +8,23 @@
 // Pipeline for one batch of volume-channels (all kernels walk the batch
 // descriptor, so one launch sequence serves any mix of volume sizes):
 //   init            zero histograms and status words
-//   smooth_hist     the one pass over the raw voxels: binomial smoothing in
-//                   shared memory and registers, the smoothed volume written
-//                   as uint16, a 65536-bin shared histogram (two 16-bit
-//                   counters per word) merged into the volume's histogram;
-//                   the last block of a volume runs Otsu
-//   threshold_runs  streaming pass over the smoothed volume: foreground =
-//                   s > t*, written as a bit mask (32 voxels per word along
-//                   x), foreground runs counted per x-row
-//   scan_runs       per-volume scan of run counts over row tiles
-//   row_runs        run table (x0, x1) per row; union-find parent = self
-//   union           26-adjacency between runs of neighbouring rows, union by
-//                   minimum run index (atomicMin), so a component's root is
-//                   its first run in raster order
+//   smooth_rows /   the one pass over the raw voxels: binomial smoothing in
+//   smooth_hist     shared memory and registers, the smoothed volume written
+//                   as uint16 (with each 32-voxel word's maximum for
+//                   row-aligned volumes), a 65536-bin shared histogram merged
+//                   into the volume's bins
+//   otsu            one block per volume: bins -> t*
+//   threshold_runs  pass over the smoothed volume: foreground = s > t*,
+//                   written as a bit mask (32 voxels per word along x),
+//                   foreground runs counted per x-row
+//   row_runs        run table (x0, x1) per row (offsets from the row tiles
+//                   below and the row counts); union-find parent = self
+//   union_local,    26-adjacency between runs of neighbouring rows, union by
+//   union           minimum run index, so a component's root is its first
+//                   run in raster order (in shared memory within bricks of
+//                   rows, then across brick faces)
 //   flatten         parent = root; voxel count accumulated at the root
 //   keep_count      roots with count >= min_volume, per row
-//   scan_keep       per-volume scan of kept roots -> K
 //   rank            label of each kept root = 1 + its rank in raster order
 //   label_features  per-voxel labels (coalesced uint32 rows) and per-cell
 //                   count / bbox / coordinate sums
@@ -45,8 +46,8 @@ const char *const kKernelNames[NUM_KERNELS] = {
     "denoise_box", "denoise_median", "init",       "mrf_stats",        "mrf_iterate",
     "smooth_rows", "smooth_hist",  "otsu",       "threshold_runs",
     "dilate",      "erode",          "dist_xy",    "dist_xy_1024",     "dist_x",
-    "dist_y",      "dist_z",         "dist_z_long", "scan_runs",       "row_runs",
-    "union_local", "union",          "flatten",    "keep_count",       "scan_keep",
+    "dist_y",      "dist_z",         "dist_z_long", "row_runs",
+    "union_local", "union",          "flatten",    "keep_count",
     "rank",        "label_features", "gather_stat"};
 
 namespace {
@@ -145,6 +146,15 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t x, uint32_t *sbuf) {
     uint32_t t;
     block_exscan<NT>(x, &t, sbuf);
     return t;
+}
+
+// Sum of a volume's row-tile totals below row tile lt, by the whole block
+// (each block scans the tiles before its own instead of a separate scan
+// kernel: a volume has at most a few thousand row tiles).
+__device__ __forceinline__ uint32_t tiles_below(const uint32_t *__restrict__ tot, uint32_t lt, uint32_t *sbuf) {
+    uint32_t s = 0;
+    for (uint32_t i = threadIdx.x; i < lt; i += ROW_TILE) s += tot[i];
+    return block_sum<ROW_TILE>(s, sbuf);
 }
 
 // First x >= p in the row whose mask bit equals `want`; X if none.  Bits at
@@ -1590,35 +1600,6 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
     }
 }
 
-// Per-volume exclusive scan over row-tile totals; the grand total is R or K.
-template <int WHICH>
-__global__ void __launch_bounds__(1024) k_tile_scan(const BatchHdr *__restrict__ h) {
-    __shared__ uint32_t sbuf[33];
-    for (uint32_t v = blockIdx.x; v < h->nvol; v += gridDim.x) {
-        const VolDev &V = h->vol[v];
-        uint32_t *a = WHICH ? V.tkeep : V.tsum;
-        uint32_t carry = 0;
-        for (uint32_t b = 0; b < V.nrt; b += 1024) {
-            const uint32_t i = b + threadIdx.x;
-            const uint32_t x = i < V.nrt ? a[i] : 0u;
-            uint32_t tot;
-            const uint32_t ex = block_exscan<1024>(x, &tot, sbuf);
-            if (i < V.nrt) a[i] = carry + ex;
-            carry += tot;
-        }
-        if (threadIdx.x == 0) {
-            if (WHICH == 0) {
-                V.stat[ST_RUNS] = carry;
-                if (carry > V.r_cap) atomicOr(V.stat + ST_ERROR, ERR_RCAP);
-            } else {
-                V.stat[ST_CELLS] = carry;
-                if (carry > V.k_cap) atomicOr(V.stat + ST_ERROR, ERR_KCAP);
-            }
-        }
-        __syncthreads();
-    }
-}
-
 __global__ void __launch_bounds__(ROW_TILE) k_row_runs(const BatchHdr *__restrict__ h) {
     __shared__ VolIndex<&VolDev::rt_base> VI;
     VI.load(h);
@@ -1629,10 +1610,15 @@ __global__ void __launch_bounds__(ROW_TILE) k_row_runs(const BatchHdr *__restric
         const uint32_t row = lt * h->row_tile + threadIdx.x;
         const bool own = threadIdx.x < h->row_tile && row < V.rows;
         const uint32_t cnt = own ? V.rowoff[row] : 0u;
+        const uint32_t base = tiles_below(V.tsum, lt, sbuf);
         uint32_t tot;
         const uint32_t ex = block_exscan<ROW_TILE>(cnt, &tot, sbuf);
+        if (lt + 1 == V.nrt && threadIdx.x == 0) {  // the volume's run count R
+            V.stat[ST_RUNS] = base + tot;
+            if (base + tot > V.r_cap) atomicOr(V.stat + ST_ERROR, ERR_RCAP);
+        }
         if (own) {
-            const uint32_t off = V.tsum[lt] + ex;
+            const uint32_t off = base + ex;
             V.rowoff[row] = off;
             if (row == V.rows - 1) V.rowoff[V.rows] = off + cnt;
             if (cnt && off + cnt <= V.r_cap) {
@@ -1961,10 +1947,15 @@ __global__ void __launch_bounds__(ROW_TILE) k_rank(const BatchHdr *__restrict__ 
         const uint32_t row = lt * h->row_tile + threadIdx.x;
         const bool own = threadIdx.x < h->row_tile && row < V.rows;
         const uint32_t cnt = own ? V.rowk[row] : 0u;
+        const uint32_t base = tiles_below(V.tkeep, lt, sbuf);
         uint32_t tot;
         const uint32_t ex = block_exscan<ROW_TILE>(cnt, &tot, sbuf);
+        if (lt + 1 == V.nrt && threadIdx.x == 0) {  // the volume's cell count K
+            V.stat[ST_CELLS] = base + tot;
+            if (base + tot > V.k_cap) atomicOr(V.stat + ST_ERROR, ERR_KCAP);
+        }
         if (own) {
-            uint32_t lab = V.tkeep[lt] + ex;
+            uint32_t lab = base + ex;
             const uint32_t ib = V.rowoff[row], ie = V.rowoff[row + 1];
             for (uint32_t r = ib; r < ie; ++r) {
                 if (V.run_par[r] != r) continue;
@@ -3930,13 +3921,11 @@ cudaError_t configure_kernels(int device, LaunchPlan &plan) {
 
 cudaError_t launch_tile_probe(const BatchHdr *d, const LaunchPlan &p, cudaStream_t s) {
     k_init<<<p.grid_vols * 4, 256, 0, s>>>(d);
-    k_smooth_rows<<<p.grid_hist, FS_NT, FS_SMEM, s>>>(d);
     switch (p.tile_y) {
         case 16: k_smooth_hist<16><<<p.grid_hist, Tile<16>::NT, hist_smem_bytes(16), s>>>(d); break;
         case 32: k_smooth_hist<32><<<p.grid_hist, Tile<32>::NT, hist_smem_bytes(32), s>>>(d); break;
         default: k_smooth_hist<64><<<p.grid_hist, Tile<64>::NT, hist_smem_bytes(64), s>>>(d); break;
     }
-    k_otsu<<<p.grid_vols, OTSU_NT, OTSU_SMEM, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -4040,8 +4029,6 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     rec();
     if (p.distance) k_dist_line<2><<<p.grid_dist, 256, 0, s>>>(d);
     rec();
-    k_tile_scan<0><<<p.grid_vols, 1024, 0, s>>>(d);
-    rec();
     k_row_runs<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();
     k_union_local<<<p.grid_ul, BRICK_Y * BRICK_Z, 0, s>>>(d);
@@ -4051,8 +4038,6 @@ cudaError_t launch_pipeline(const BatchHdr *d, const LaunchPlan &p, cudaStream_t
     k_flatten<<<p.grid_task, ROW_TILE, 0, s>>>(d);
     rec();
     k_keep_count<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
-    rec();
-    k_tile_scan<1><<<p.grid_vols, 1024, 0, s>>>(d);
     rec();
     k_rank<<<p.grid_rows, ROW_TILE, 0, s>>>(d);
     rec();

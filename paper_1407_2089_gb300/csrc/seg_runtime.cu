@@ -608,11 +608,14 @@ int launch_batch(seg_ctx *ctx, Batch &b) {
     }
     for (Request *r : b.reqs) std::vector<uint16_t>().swap(r->host_copy);
     CK(cudaMallocAsync(reinterpret_cast<void **>(&b.scratch), b.scratch_bytes, s.stream));
-    if (!ctx->tuned) {
+    build_header(ctx, b);
+    if (!ctx->tuned && s.h_hdr->ntiles > 0) {
+        // the tile shape only concerns k_smooth_hist: tune on the first
+        // batch that has volumes for it
         const int rc = tune_tiles(ctx, b);
         if (rc != SEG_OK) return rc;
+        build_header(ctx, b);
     }
-    build_header(ctx, b);
     ctx->plan.rows = s.h_hdr->fs_tiles > 0;
     ctx->plan.tiles = s.h_hdr->ntiles > 0;
     ctx->plan.denoise = s.h_hdr->dn_tiles > 0;
