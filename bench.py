@@ -792,7 +792,7 @@ def montage_run(seg, torch, local, steps):
     gen_s = time.perf_counter() - t0
     vox = host.size
     stream = torch.cuda.Stream()
-    ctx = seg.seg_create(device=local, order_stream=stream.cuda_stream)
+    ctx = seg.seg_create(device=local, flags=seg.SEG_PROFILE, order_stream=stream.cuda_stream)
     out = {"dims": list(dims), "channels": 2, "voxels": int(vox), "generation_s": gen_s}
     try:
         d_in = torch.from_numpy(host.view(np.int16)).to("cuda:%d" % local)
@@ -810,6 +810,7 @@ def montage_run(seg, torch, local, steps):
 
         finish(dev_step())
         torch.cuda.synchronize()
+        seg.seg_reset_stats(ctx)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -818,11 +819,14 @@ def montage_run(seg, torch, local, steps):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        st = seg.seg_get_stats(ctx)
+        kernel_ms = {n: round(v["ms"] / steps, 3) for n, v in st["kernels"].items() if v["ms"] / steps > 0.05}
         del d_in
         torch.cuda.empty_cache()
         peak, _ = peaks()
         out["device"] = {"ms": ms, "gvox_s": vox / (ms / 1e3) / 1e9,
-                         "hbm_fraction": vox * ALGO_BYTES_PER_VOXEL / (ms / 1e3) / 1e9 / peak}
+                         "hbm_fraction": vox * ALGO_BYTES_PER_VOXEL / (ms / 1e3) / 1e9 / peak,
+                         "kernel_ms": kernel_ms}
         pin = torch.from_numpy(host.view(np.int16)).pin_memory()
         labs = [torch.empty(host[0].size, dtype=torch.int32).pin_memory() for _ in range(2)]
         walls = []

@@ -46,7 +46,7 @@ constexpr int HIST_BINS = 65536;
 // united in shared memory when there are at most BRICK_CAP of them.
 constexpr int BRICK_Y = 32;
 constexpr int BRICK_Z = 8;
-constexpr int BRICK_CAP = 4096;
+constexpr int BRICK_CAP = 2048;
 
 // One volume-channel inside a batch.  All pointers are device addresses.
 struct VolDev {
