@@ -75,11 +75,12 @@ struct VolDev {
     uint32_t ntx, nty, ntz;   // smoothing tiles per axis (k_smooth_hist; 0 for row-aligned volumes)
     uint32_t nrt;             // row tiles (of BatchHdr::row_tile rows)
     uint32_t tile_base;       // first flat smoothing-tile index
-    // k_smooth_rows (rows 16-byte aligned: X % 8 == 0 and an aligned input);
-    // fs_ntx = 0 for the other volumes
-    uint32_t fs_rt;           // octets per tile row (min(X / 8, 64))
+    // k_smooth_rows (X % 8 == 0 with a 16-byte aligned input, or X even and
+    // at least 10 with a 4-byte aligned input); fs_ntx = 0 for the other volumes
+    uint32_t fs_rt;           // octets per tile row (min(ceil(X / 8), 64))
     uint32_t fs_ty;           // rows per tile (FS_NT / fs_rt)
     uint32_t fs_hx;           // 1: x-tiled (X > 512), staged rows carry a halo chunk on each side
+    uint32_t fs_rag;          // 1: X % 8 != 0 (X even): 4-byte copies and stores, a partial last octet
     uint32_t fs_tz;           // planes per tile
     uint32_t fs_ntx, fs_nty, fs_ntz;  // tiles per axis
     uint32_t fs_base;         // first flat k_smooth_rows tile index
@@ -242,7 +243,7 @@ size_t hist_smem_bytes(int tile_y);
 // tile shape of a row-aligned volume of width X.
 constexpr int FS_NT = 512;
 constexpr int FS_RT = 64;
-inline uint32_t fs_rows_rt(uint32_t X) { return X >= 8u * FS_RT ? (uint32_t)FS_RT : X / 8u; }
+inline uint32_t fs_rows_rt(uint32_t X) { return X >= 8u * FS_RT ? (uint32_t)FS_RT : (X + 7u) / 8u; }
 // Sets kernel attributes on `device` and fills the persistent grid sizes of
 // `plan` (plan.sms must be set).
 cudaError_t configure_kernels(int device, LaunchPlan &plan);

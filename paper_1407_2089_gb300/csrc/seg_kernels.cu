@@ -244,6 +244,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, uintptr_t src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
+// 4-byte copy; n = 4 copies, n = 0 writes zeros (the source is not read).
+__device__ __forceinline__ void cp_async4(uint32_t dst, uintptr_t src, uint32_t n) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 // Waits until at most N of this thread's committed groups are outstanding.
@@ -1107,7 +1112,7 @@ struct FsSync {
 // One tile: octets [x0, x0 + 8 rte) of rows [y0, y0 + TYF) of planes [z0, z1).
 // RTC = FS_RT: rows of 64 octets (8 rows per tile), HXC: halo chunks
 // (x-tiled rows), both known at compile time; RTC = 0: the shape of V.
-template <int RTC, int HXC>
+template <int RTC, int HXC, int RAG>
 __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, uint32_t iy, int z0, int z1,
                                                  unsigned char *ring, uint32_t *sh, FsSync &S) {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -1125,7 +1130,10 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     const int RC = RT + 2 * hx;   // 16-byte chunks per staged row
     const int RB = 16 * RC;       // bytes per staged row
     const int x0 = (int)ix * 8 * RT, y0 = (int)iy * TYF;
-    const int rte = min(RT, (X - x0) >> 3);  // octets of this tile
+    // octets of this tile; rows of X % 8 != 0 voxels (RAG) end in a partial
+    // octet of nvl voxels (X even: 2, 4 or 6), whose missing voxels repeat
+    // the last one in the x pass and are neither stored nor counted
+    const int rte = RAG ? min(RT, (X - x0 + 7) >> 3) : min(RT, (X - x0) >> 3);
     const int q = RTC ? (tid & (RTC - 1)) : tid % RT;
     const int ty = RTC ? tid / RTC : tid / RT;
     const bool act = ty < TYF && q < rte;
@@ -1133,6 +1141,7 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     const bool emit_ok = act && y0 + ty < Y;
     const bool haloL = x0 > 0, haloR = x0 + 8 * rte < X;
     const bool edgeL = q == 0, edgeR = q == rte - 1;
+    const int nvl = RAG && edgeR ? min(8, X - (x0 + 8 * q)) : 8;  // valid voxels of this lane's octet
     // neighbour words this lane y-sums itself: at a warp's ends and at the
     // tile's ends of x-tiled rows (the halo chunks)
     const bool ownL = edgeL ? haloL : lane == 0;
@@ -1143,6 +1152,7 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
     // cc, as 32-bit voxel offsets from the volume's start at plane 0
     const int nchunk = (TYF + 4) * RC;
     uint32_t cdst[2], csrc[2];
+    int cend[2];  // voxels of the chunk before the row's end (RAG)
     bool cok[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -1150,10 +1160,12 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
         cok[u] = false;
         cdst[u] = 0;
         csrc[u] = 0;
+        cend[u] = 0;
         if (c < nchunk) {
             const int r = c / RC, cc = c - r * RC;
             const int x = x0 - 8 * hx + 8 * cc;
             cok[u] = x >= 0 && x < X;
+            cend[u] = X - x;
             const int yy = min(max(y0 - 2 + r, 0), Y - 1);
             cdst[u] = (uint32_t)(r * RB + cc * 16);
             csrc[u] = (uint32_t)yy * (uint32_t)X + (uint32_t)x;
@@ -1176,8 +1188,21 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
         if (ok && k < n) {
             const uint32_t zoff = plane * (uint32_t)min(max(z0 - 2 + k, 0), Z - 1);
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-                if (cok[u]) cp_async16(ring0 + ST * FS_STAGE + cdst[u], reinterpret_cast<uintptr_t>(raw + (csrc[u] + zoff)));
+            for (int u = 0; u < 2; ++u) {
+                if (!cok[u]) continue;
+                if (!RAG) {
+                    cp_async16(ring0 + ST * FS_STAGE + cdst[u], reinterpret_cast<uintptr_t>(raw + (csrc[u] + zoff)));
+                } else {
+                    // rows start 4-byte aligned only: four pairs, those at
+                    // or past the row's end zero-filled
+#pragma unroll
+                    for (int pq = 0; pq < 4; ++pq) {
+                        const bool in = 2 * pq < cend[u];
+                        cp_async4(ring0 + ST * FS_STAGE + cdst[u] + 4 * pq,
+                                  reinterpret_cast<uintptr_t>(in ? raw + (csrc[u] + zoff + 2 * pq) : raw), in ? 4u : 0u);
+                    }
+                }
+            }
         }
         mbar_arrive_copies(S.full + ST);
     };
@@ -1267,6 +1292,14 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
                 v[10] = ownR ? hlo : (edgeR ? v[9] : q0);
                 v[11] = ownR ? hhi : (edgeR ? v[9] : q1);
             }
+            if (RAG && nvl < 8) {
+                // the row's last octet is partial (nvl = 2, 4 or 6 for even
+                // X): the voxels past the end repeat the last one
+                const uint32_t e = nvl <= 2 ? v[3] : (nvl <= 4 ? v[5] : v[7]);
+#pragma unroll
+                for (int k = 4; k < 12; ++k)
+                    if (k >= 2 + nvl) v[k] = e;
+            }
             // this warp is done with the stage
             __syncwarp();
             if (lane == 0) mbar_arrive(S.empty + ST);
@@ -1284,6 +1317,11 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
                 s[j] = o >> 12;
             }
             if (k >= 4) {
+                if (RAG) {
+#pragma unroll
+                    for (int j = 2; j < 8; ++j)
+                        if (j >= nvl) s[j] = 0u;  // not emitted (and below any t*)
+                }
                 const uint32_t vmax = max(max(max(s[0], s[1]), max(s[2], s[3])), max(max(s[4], s[5]), max(s[6], s[7])));
                 const bool fast = __all_sync(FULL, !emit_ok || vmax < (uint32_t)HIST_LOW);
                 if (wmax) {
@@ -1296,14 +1334,24 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
                         wmax[(uint32_t)((z0 + k - 4) * Y + y0 + ty) * W + (uint32_t)((x0 + 8 * q) >> 5)] = (uint16_t)wm;
                 }
                 if (emit_ok) {
-                    *reinterpret_cast<uint4 *>(osm + (orow + plane * (uint32_t)(z0 + k - 4))) =
-                        make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
+                    uint16_t *op = osm + (orow + plane * (uint32_t)(z0 + k - 4));
+                    if (!RAG) {
+                        *reinterpret_cast<uint4 *>(op) =
+                            make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
+                    } else {
+                        // rows start 4-byte aligned only; the pairs past the end stay unwritten
+#pragma unroll
+                        for (int j = 0; j < 8; j += 2)
+                            if (j < nvl) *reinterpret_cast<uint32_t *>(op + j) = s[j] | (s[j + 1] << 16);
+                    }
                     if (fast) {
     #pragma unroll
-                        for (int j = 0; j < 8; ++j) atomicAdd(hc + s[j], 1u);
+                        for (int j = 0; j < 8; ++j)
+                            if (!RAG || j < nvl) atomicAdd(hc + s[j], 1u);
                     } else {
     #pragma unroll
                         for (int j = 0; j < 8; ++j) {
+                            if (RAG && j >= nvl) continue;
                             const uint32_t u = min(s[j], 65535u);  // (always true for exact sums)
                             if (u < (uint32_t)HIST_LOW) {
                                 atomicAdd(hc + u, 1u);
@@ -1388,11 +1436,14 @@ __global__ void __launch_bounds__(FS_NT, 1) k_smooth_rows(const BatchHdr *__rest
         const uint32_t ix = rest % V.fs_ntx, iz = rest / V.fs_ntx;
         const int z0 = (int)(iz * V.fs_tz);
         const int z1 = min(z0 + (int)V.fs_tz, (int)V.Z);
-        if (V.fs_rt == (uint32_t)FS_RT) {
-            if (V.fs_hx) smooth_rows_tile<FS_RT, 1>(V, ix, iy, z0, z1, ring, sh, S);
-            else smooth_rows_tile<FS_RT, 0>(V, ix, iy, z0, z1, ring, sh, S);
+        if (V.fs_rag) {
+            if (V.fs_hx) smooth_rows_tile<FS_RT, 1, 1>(V, ix, iy, z0, z1, ring, sh, S);
+            else smooth_rows_tile<0, 0, 1>(V, ix, iy, z0, z1, ring, sh, S);
+        } else if (V.fs_rt == (uint32_t)FS_RT) {
+            if (V.fs_hx) smooth_rows_tile<FS_RT, 1, 0>(V, ix, iy, z0, z1, ring, sh, S);
+            else smooth_rows_tile<FS_RT, 0, 0>(V, ix, iy, z0, z1, ring, sh, S);
         } else {
-            smooth_rows_tile<0, 0>(V, ix, iy, z0, z1, ring, sh, S);
+            smooth_rows_tile<0, 0, 0>(V, ix, iy, z0, z1, ring, sh, S);
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy into this block's shared memory outlives it
@@ -1488,6 +1539,63 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
                 }
             }
             // each row was counted by its first lane: the warp's total
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wtot += __shfl_xor_sync(FULL, wtot, o);
+        } else if (wmax && W <= 256u && (X & 1u) == 0u) {
+            // Word maxima, any other row width up to 8192 voxels: a lane owns
+            // 8 consecutive mask words (lanes past the row's words hold none),
+            // a row is seg lanes (the power of two >= W / 8).  Each word
+            // above t* is read as octets (16-byte aligned rows, X % 8 == 0)
+            // or as voxel pairs (rows of an even X start 4-byte aligned);
+            // the last word of a row stops at X.
+            uint32_t seg = 1u;
+            while (seg * 8u < W) seg <<= 1;
+            const uint32_t rows_pw = 32u / seg;
+            const uint32_t lrow = (uint32_t)lane / seg, lw = ((uint32_t)lane & (seg - 1u)) * 8u;
+            for (uint32_t rb = warp * rows_pw; rb < nrows; rb += WARPS * rows_pw) {
+                const uint32_t rr = rb + lrow;
+                const bool live = rr < nrows;
+                const uint16_t *mp = wmax + (size_t)(row0 + rr) * W;
+                const uint16_t *src = V.smooth + (size_t)(row0 + rr) * X;
+                uint32_t word[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    word[i] = 0u;
+                    const uint32_t w = lw + (uint32_t)i;
+                    if (!live || w >= W || mp[w] <= t) continue;
+                    const uint32_t xb = 32u * w, nv = min(32u, X - xb);  // voxels of word w
+                    uint32_t bits = 0u;
+                    if (vec) {
+                        for (uint32_t o = 0; o < nv; o += 8u)
+                            bits |= octet_bits(__ldcs(reinterpret_cast<const uint4 *>(src + xb + o)), t) << o;
+                    } else {
+                        for (uint32_t o = 0; o < nv; o += 2u) {
+                            const uint32_t pr = __ldcs(reinterpret_cast<const unsigned int *>(src + xb + o));
+                            bits |= (((pr & 0xFFFFu) > t ? 1u : 0u) | ((pr >> 16) > t ? 2u : 0u)) << o;
+                        }
+                    }
+                    word[i] = bits;
+                }
+                uint32_t left = __shfl_up_sync(FULL, word[7], 1) >> 31;
+                if (lw == 0u) left = 0u;
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    cnt += __popc(word[i] & ~((word[i] << 1) | left));
+                    left = word[i] >> 31;
+                }
+                for (uint32_t o = 1; o < seg; o <<= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+                if (live) {
+                    uint32_t *dst = V.mask + (size_t)(row0 + rr) * W;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (lw + (uint32_t)i < W) dst[lw + i] = word[i];
+                    if (lw == 0u) {
+                        V.rowoff[row0 + rr] = cnt;
+                        wtot += cnt;
+                    }
+                }
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) wtot += __shfl_xor_sync(FULL, wtot, o);
         } else if (vec && X <= 512u) {

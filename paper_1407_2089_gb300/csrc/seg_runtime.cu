@@ -296,8 +296,13 @@ void layout_request(Request &r, bool keep_smoothed) {
 // small batches still spread over the whole GPU.  A forced shape is kept.
 // Row-aligned volumes (X % 8 == 0, 16-byte aligned first input of the
 // smoothing) take k_smooth_rows; the others k_smooth_hist.
+// Volumes for k_smooth_rows: rows of X % 8 == 0 voxels from a 16-byte
+// aligned input (16-byte copies), or of an even X >= 10 from a 4-byte aligned
+// input (4-byte copies: every row start is then 4-byte aligned).
 bool rows_aligned(const VolGeom &g, const void *smooth_in) {
-    return g.X % 8u == 0u && (reinterpret_cast<uintptr_t>(smooth_in) & 15u) == 0u;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(smooth_in);
+    if (g.X % 8u == 0u) return (a & 15u) == 0u;
+    return g.X % 2u == 0u && g.X >= 10u && (a & 3u) == 0u;
 }
 
 const void *smooth_input(const Request *r, uint32_t c) {
@@ -474,18 +479,20 @@ void build_header(seg_ctx *ctx, Batch &b) {
                 V.fs_rt = fs_rows_rt(g.X);
                 V.fs_ty = (uint32_t)FS_NT / V.fs_rt;
                 V.fs_hx = g.X > 8u * FS_RT ? 1u : 0u;
+                V.fs_rag = g.X % 8u != 0u ? 1u : 0u;
                 V.fs_tz = fz;
                 V.fs_ntx = (uint32_t)cdiv(g.X, 8ull * V.fs_rt);
                 V.fs_nty = (uint32_t)cdiv(g.Y, V.fs_ty);
                 V.fs_ntz = (uint32_t)cdiv(g.Z, fz);
-                // word maxima: groups of four octet lanes hold one mask word
-                if (!(g.X > 8u * FS_RT || g.X % 32u == 0u)) V.wmax = nullptr;
+                // word maxima: groups of four octet lanes of one tile row hold
+                // one mask word, so the tile's rows span whole groups
+                if (V.fs_rt % 4u != 0u) V.wmax = nullptr;
             } else {
                 V.wmax = nullptr;
                 V.ntx = (uint32_t)cdiv(g.X, TILE_X);
                 V.nty = (uint32_t)cdiv(g.Y, ty);
                 V.ntz = (uint32_t)cdiv(g.Z, tz);
-                V.fs_rt = V.fs_ty = V.fs_hx = V.fs_tz = 0;
+                V.fs_rt = V.fs_ty = V.fs_hx = V.fs_tz = V.fs_rag = 0;
                 V.fs_ntx = V.fs_nty = V.fs_ntz = 0;
             }
             V.fs_base = fst;

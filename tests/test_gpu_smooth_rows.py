@@ -1,5 +1,6 @@
-"""The smoothing kernel for row-aligned volumes (X % 8 == 0, 16-byte aligned
-input) against the oracle: the smoothed image element by element (contexts
+"""The smoothing kernel for row-aligned volumes (X % 8 == 0 with a 16-byte
+aligned input, or an even X >= 10 with a 4-byte aligned input) against the
+oracle: the smoothed image element by element (contexts
 created with SEG_KEEP_SMOOTHED, read with seg_read_smoothed), then labels,
 cells and t*.
 
@@ -211,6 +212,62 @@ def test_time_lapse_frame_smoothed(seg, ctx):
     import synth
     tl = synth.TimeLapse()
     check(seg, ctx, [tl.frame(5, 0), tl.frame(5, 1)], m=30, what="time-lapse")
+
+
+# Even X that is not a multiple of 8: 4-byte copies and stores, a partial
+# last octet of 2, 4 or 6 voxels whose missing neighbours repeat the last
+# voxel; rows narrower than a tile (one tile row, several rows per tile, tile
+# rows of 2 .. 64 octets), just below and above 512 (x-tiled rows with a
+# partial last tile), and the montage's row width.  The threshold pass reads
+# the word maxima with voxel pairs for these widths.
+RAGGED_EVEN = [(10, 7, 3), (14, 40, 5), (18, 3, 9), (26, 33, 4), (34, 20, 6), (100, 17, 5), (250, 12, 7),
+               (254, 9, 4), (506, 8, 5), (510, 11, 3), (514, 9, 4), (522, 6, 5), (1030, 7, 3), (2046, 4, 3),
+               (5530, 5, 3)]
+
+
+@pytest.mark.parametrize("dims", RAGGED_EVEN)
+def test_ragged_even_rows(seg, ctx, dims):
+    X, Y, Z = dims
+    v = noisy(dims, X + 7 * Y + Z, n_blobs=max(3, X * Y * Z // 2000))
+    # bright voxels at the row's last columns (the partial octet and its
+    # left neighbour) and one value above 4096 there
+    v[Z // 2, Y // 2, X - 1] = 3000
+    v[Z // 2, Y // 2, X - 2] = 2800
+    v[Z - 1, Y - 1, X - 3] = 50000
+    check(seg, ctx, [v], m=1, what="ragged even")
+
+
+def test_ragged_even_batch_and_alignment(seg):
+    import torch
+    c = seg.seg_create(device=0, flags=seg.SEG_KEEP_SMOOTHED, batch_window_us=10_000_000)
+    try:
+        # ragged and aligned widths and the other smoothing kernel (odd X)
+        # in one batch; many row tiles per volume
+        vols = [noisy((130, 200, 6), 31, n_blobs=30), noisy((512, 40, 5), 32), noisy((5530, 12, 3), 33, n_blobs=20),
+                noisy((33, 50, 7), 34), noisy((1030, 60, 4), 35, n_blobs=25)]
+        check(seg, c, vols, m=1, what="ragged batch")
+        # device input 4 bytes off a 16-byte boundary (the 4-byte copies) and
+        # 2 bytes off (the other smoothing kernel)
+        for off in (2, 1):
+            v = noisy((130, 30, 6), 40 + off)
+            buf = torch.zeros(v.size + 16, dtype=torch.int16, device="cuda")
+            buf[off:off + v.size] = torch.from_numpy(v.view(np.int16).ravel().copy()).cuda()
+            t = buf[off:off + v.size]
+            assert t.data_ptr() % 16 == 2 * off
+            r = seg.seg_submit_volume(c, t, dims=(130, 30, 6), channels=1, min_volume=1)
+            seg.seg_flush(c)
+            assert seg.seg_wait(c, r) == seg.SEG_DONE
+            ref = oracle.segment(v, min_volume=1, keep_smoothed=True)
+            sm = np.empty(v.shape, np.uint16)
+            seg.seg_read_smoothed(c, r, 0, sm)
+            assert np.array_equal(sm, ref.smoothed)
+            lab = np.empty(v.shape, np.uint32)
+            seg.seg_read_labels(c, r, 0, lab)
+            cells, thr = seg.seg_read_features(c, r, 0)
+            assert_matches_oracle(v, lab, cells, thr, min_volume=1, ref=ref, what="device input offset %d" % (2 * off))
+            seg.seg_release(c, r)
+    finally:
+        seg.seg_destroy(c)
 
 
 def test_read_smoothed_needs_the_flag(seg):
