@@ -1541,8 +1541,9 @@ __global__ void __launch_bounds__(ROW_TILE) k_threshold_runs(const BatchHdr *__r
             // each row was counted by its first lane: the warp's total
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) wtot += __shfl_xor_sync(FULL, wtot, o);
-        } else if (wmax && W <= 256u && (X & 1u) == 0u) {
-            // Word maxima, any other row width up to 8192 voxels: a lane owns
+        } else if (wmax && W <= 256u && (X & 1u) == 0u && ((X & 7u) != 0u || X > 512u)) {
+            // Word maxima, the other row widths up to 8192 voxels that the
+            // 16-byte loop below does not take (X % 8 != 0, or X > 512): a lane owns
             // 8 consecutive mask words (lanes past the row's words hold none),
             // a row is seg lanes (the power of two >= W / 8).  Each word
             // above t* is read as octets (16-byte aligned rows, X % 8 == 0)

@@ -327,7 +327,8 @@ uint32_t batch_tile_z(const seg_ctx *ctx, const Batch &b) {
 }
 
 // Planes per k_smooth_rows tile for a batch: as deep as 256 planes, halved
-// (down to 8) while the batch has fewer than three tiles per multiprocessor.
+// (down to 1) while the batch has fewer than three tiles per multiprocessor
+// (a lone small volume: more tiles, each with its four halo planes).
 uint32_t batch_rows_tile_z(const seg_ctx *ctx, const Batch &b) {
     uint32_t tz = 256;
     for (;;) {
@@ -339,7 +340,7 @@ uint32_t batch_rows_tile_z(const seg_ctx *ctx, const Batch &b) {
                 const uint32_t rt = fs_rows_rt(g.X);
                 tiles += cdiv(g.X, 8ull * rt) * cdiv(g.Y, FS_NT / rt) * cdiv(g.Z, tz);
             }
-        if (tz <= 8 || tiles >= 3ull * (uint64_t)ctx->sms) return tz;
+        if (tz <= 1 || tiles >= 3ull * (uint64_t)ctx->sms) return tz;
         tz /= 2;
     }
 }
