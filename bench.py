@@ -431,8 +431,10 @@ def run_gpu(args):
         torch.cuda.empty_cache()
     serve = None
     if args.serving_requests and rank == 0:
-        serve = {"batched": serving(seg, torch, local, args.serving_requests, 200.0, 0, 2),
-                 "plain": serving(seg, torch, local, args.serving_requests, 200.0, seg.SEG_PLAIN, 1)}
+        queued = args.serving_copies == "queued"
+        serve = {"batched": serving(seg, torch, local, args.serving_requests, 200.0, 0, 2, queued),
+                 "plain": serving(seg, torch, local, args.serving_requests, 200.0, seg.SEG_PLAIN, 1, queued),
+                 "input_copies": args.serving_copies}
 
     # end to end through the C ABI with pinned host buffers
     e2e = e2e_dense = None
@@ -850,7 +852,7 @@ def montage_run(seg, torch, local, steps):
     return out
 
 
-def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
+def serving(seg, torch, local, n_requests, rate, flags, max_inflight, queued=False):
     """Open-loop Poisson request stream (2-channel volumes, sizes log-uniform
     from 128^3 to 2048x2048x64) through the C ABI from pinned host memory.
     Latency = completion observed by the runtime - arrival time."""
@@ -906,7 +908,9 @@ def serving(seg, torch, local, n_requests, rate, flags, max_inflight):
             if left > 0.001:
                 time.sleep(left - 0.0005)
         a_wall = t0 + arrival
-        rid = seg.seg_submit_volume(ctx, host, dims=(X, Y, Z), channels=2)
+        # queued: the call only queues the copy (the pool never changes, so
+        # it stays valid until the request is done)
+        rid = seg.seg_submit_volume(ctx, host, dims=(X, Y, Z), channels=2, keep_host_input=queued)
         s_wall = time.perf_counter()
         vox += 2 * n
         with lock:
@@ -1081,6 +1085,8 @@ def main():
     ap.add_argument("--montage", type=int, default=1, help="1: segment the 5530x5530x80x2 montage as well")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="Poisson requests (200/s) for the served latency; 0 skips serving")
+    ap.add_argument("--serving-copies", choices=("queued", "awaited"), default="awaited",
+                    help="serving: queue each request's input copy, or await it in the submit call")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
