@@ -1206,9 +1206,13 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
         }
         mbar_arrive_copies(S.full + ST);
     };
-    uint32_t a0[8], a1[8], a2[8], a3[8];
+    // x-sums of the last planes, plane k in slot k % 5 (the ring stage, a
+    // compile-time index in every step)
+    uint32_t pr[FS_S][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a0[j] = a1[j] = a2[j] = a3[j] = 0u;
+    for (int i = 0; i < FS_S; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pr[i][j] = 0u;
     const uint32_t orow = (uint32_t)(y0 + tyc) * (uint32_t)X + (uint32_t)(x0 + 8 * q);
     uint32_t *hc = sh + ((threadIdx.x & 16u) ? (uint32_t)HIST_COPY1 : 0u);
     // plane k from stage ST (full phase fp): nothing but the barriers for
@@ -1303,18 +1307,17 @@ __device__ __forceinline__ void smooth_rows_tile(const VolDev &V, uint32_t ix, u
             // this warp is done with the stage
             __syncwarp();
             if (lane == 0) mbar_arrive(S.empty + ST);
-            // x pass, then the z pass in scatter form; a3 starts each output's
-            // sum at 2048 so that s = sum >> 12 rounds half up
+            // x pass, then the z pass over planes k-4 .. k in gather form; the
+            // 2048 enters with the outer pair so that s = sum >> 12 rounds
+            // half up
             uint32_t s[8];
     #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const uint32_t p = v[j] + v[j + 4] + 4u * (v[j + 1] + v[j + 3]) + 6u * v[j + 2];
-                const uint32_t o = a0[j] + p;
-                a0[j] = a1[j] + 4u * p;
-                a1[j] = a2[j] + 6u * p;
-                a2[j] = a3[j] + 4u * p;
-                a3[j] = p + 2048u;
-                s[j] = o >> 12;
+                const uint32_t A = pr[(ST + 1) % FS_S][j], B = pr[(ST + 2) % FS_S][j];
+                const uint32_t C = pr[(ST + 3) % FS_S][j], D = pr[(ST + 4) % FS_S][j];
+                s[j] = (A + p + 2048u + 4u * (B + D) + 6u * C) >> 12;
+                pr[ST][j] = p;
             }
             if (k >= 4) {
                 if (RAG) {
