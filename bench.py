@@ -59,7 +59,7 @@ KERNEL_BYTES_PER_VOXEL = {
 # than L2); the per-launch figure scales with the voxels a launch processes
 # since every 512x512x64 volume is tiled the same way.
 KERNEL_TRAFFIC_BYTES_PER_VOXEL = {
-    "smooth_rows": 4.03,           # 2.27 read (halo rows partly from L2) + 1.76 smoothed
+    "smooth_rows": 4.04,           # 2.28 read (halo rows partly from L2) + 1.76 smoothed
                                    # and word-maximum writes
     "smooth_hist": 7.69,           # 5.88 read (halo lines re-read) + 1.81 smoothed write
 }
