@@ -2149,7 +2149,7 @@ __global__ void __launch_bounds__(ROW_TILE, 6) k_label_features(const BatchHdr *
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int WARPS = ROW_TILE / 32;
     __shared__ uint32_t soff[ROW_TILE + 1];
-    __shared__ uint32_t srx[LABEL_RUNS], slab[LABEL_RUNS];
+    __shared__ uint2 srl[LABEL_RUNS];  // staged runs: x0 | x1 << 16, final label
     __shared__ uint8_t srow[LABEL_RUNS];  // row of each staged run in the tile
     __shared__ FeatTable T;
     for (uint32_t rt = blockIdx.x; rt < h->nrowtiles; rt += gridDim.x) {
@@ -2157,7 +2157,7 @@ __global__ void __launch_bounds__(ROW_TILE, 6) k_label_features(const BatchHdr *
         const uint32_t lt = rt - V.rt_base;
         const uint32_t row0 = lt * h->row_tile;
         const uint32_t nrows = min(h->row_tile, V.rows - row0);
-        __syncthreads();  // previous tile done with soff, srx, slab and T
+        __syncthreads();  // previous tile done with soff, srl and T
         for (uint32_t i = tid; i <= nrows; i += ROW_TILE) soff[i] = V.rowoff[row0 + i];
         T.key[tid] = 0u;
         T.cx[tid] = T.sy[tid] = T.sz[tid] = 0ull;
@@ -2173,15 +2173,14 @@ __global__ void __launch_bounds__(ROW_TILE, 6) k_label_features(const BatchHdr *
         const bool staged = re - rb <= (uint32_t)LABEL_RUNS;  // the same in every thread
         if (staged) {
             for (uint32_t j = rb + tid; j < re; j += ROW_TILE) {
-                srx[j - rb] = RX[j];
-                slab[j - rb] = RA[RP[j]];
+                srl[j - rb] = make_uint2(RX[j], RA[RP[j]]);
             }
             if ((uint32_t)tid < nrows)
                 for (uint32_t j = soff[tid]; j < soff[tid + 1]; ++j) srow[j - rb] = (uint8_t)tid;
             __syncthreads();
         }
-        auto run_x = [&](uint32_t j) { return staged ? srx[j - rb] : RX[j]; };
-        auto run_label = [&](uint32_t j) { return staged ? slab[j - rb] : RA[RP[j]]; };
+        auto run_x = [&](uint32_t j) { return staged ? srl[j - rb].x : RX[j]; };
+        auto run_label = [&](uint32_t j) { return staged ? srl[j - rb].y : RA[RP[j]]; };
         // labels
         const uint32_t X = V.X;
         const bool vec = (X & 3u) == 0u;
@@ -2202,13 +2201,14 @@ __global__ void __launch_bounds__(ROW_TILE, 6) k_label_features(const BatchHdr *
                     for (uint32_t sb = 0; sb < X; sb += 128) {
                         const uint32_t xb = sb + 4u * lane;
                         uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-                        while (j < ie && (srx[j - rb] >> 16) < sb) ++j;
+                        while (j < ie && (srl[j - rb].x >> 16) < sb) ++j;
                         for (uint32_t k = j; k < ie; ++k) {
-                            const uint32_t rx = srx[k - rb];
+                            const uint2 rl = srl[k - rb];  // one 8-byte load: extent and label
+                            const uint32_t rx = rl.x;
                             const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16;
                             if (x0 >= sb + 128u) break;
                             if (x1 < xb || x0 > xb + 3u) continue;
-                            const uint32_t L = slab[k - rb], w = x1 - x0;
+                            const uint32_t L = rl.y, w = x1 - x0;
                             if (xb - x0 <= w) v0 = L;
                             if (xb + 1u - x0 <= w) v1 = L;
                             if (xb + 2u - x0 <= w) v2 = L;
