@@ -169,9 +169,16 @@ int seg_create(const seg_config *cfg, seg_ctx **out);
 /* Waits for all in-flight work, frees every request and the context. */
 int seg_destroy(seg_ctx *ctx);
 
-/* Submits one volume of `channels` planar channels, each [Z][Y][X] uint16.
+/* Submits one volume of `channels` planar channels, each [Z][Y][X] uint16,
+ * for the segmentation stage of each channel (Background Noise Removal,
+ * Eq. 1: the binomial low-pass; Segmentation section: Otsu threshold (ref.
+ * [11]), 26-connected components, components below the minimum volume
+ * discarded, cells numbered by lowest linear index).
  *   voxels     host pointer (on_device = 0 or 2) or device pointer
- *              (on_device = 1, 2-byte aligned, else SEG_EINVAL).  With 0 the input is copied before the call
+ *              (on_device = 1, 2-byte aligned, else SEG_EINVAL; rows of
+ *              X % 8 == 0 voxels from a 16-byte aligned pointer, or of an
+ *              even X >= 10 from a 4-byte aligned one, take the faster
+ *              smoothing kernel, the same results either way).  With 0 the input is copied before the call
  *              returns (the caller may free or reuse it).  With 2 the copy is
  *              only queued (pinned memory: it runs while the call returns and
  *              the batch waits for it on the device), so the host input, like
@@ -199,8 +206,10 @@ int seg_poll(seg_ctx *ctx, seg_req req, uint32_t timeout_ms, int *state);
  * blocks the host. */
 int seg_enqueue_wait(seg_ctx *ctx, seg_req req, void *stream);
 
-/* Copies channel `channel`'s label image (X*Y*Z uint32) to dst (host, or
- * device when dst_on_device = 1).  Blocks until the copy is complete.
+/* Copies channel `channel`'s label image (X*Y*Z uint32; Segmentation
+ * section: 0 = background, 1..K = the cells in order of their lowest linear
+ * index) to dst (host, or device when dst_on_device = 1).  Blocks until the
+ * copy is complete.
  * Errors: SEG_ENOTREADY, SEG_EFAILED, SEG_ESMALL (dst_elems < X*Y*Z),
  * SEG_EINVAL, SEG_ENOENT, SEG_ECUDA. */
 int seg_read_labels(seg_ctx *ctx, seg_req req, uint32_t channel, uint32_t *dst,
@@ -259,8 +268,10 @@ int seg_read_denoised(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst
 int seg_read_smoothed(seg_ctx *ctx, seg_req req, uint32_t channel, uint16_t *dst, uint64_t dst_elems,
                       int dst_on_device);
 
-/* Copies channel `channel`'s cells (label order) to host memory dst (cap
- * entries) and reports n_cells and the Otsu level t* (foreground = s > t*).
+/* Copies channel `channel`'s cells (label order; per cell the voxel count,
+ * bounding box and coordinate sums, which stand in for the hull the
+ * Segmentation section builds) to host memory dst (cap entries) and reports
+ * n_cells and the Otsu level t* (foreground = s > t*).
  * dst may be NULL with cap 0 to query n_cells.  SEG_ESMALL if cap < n_cells
  * (n_cells and the threshold are still set). */
 int seg_read_features(seg_ctx *ctx, seg_req req, uint32_t channel, seg_cell_features *dst,
